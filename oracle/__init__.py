@@ -1,0 +1,268 @@
+"""CPU oracle for the dense revised simplex method (Sections 2.1-2.2, 3.1, 3.4).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; the solver package never imports
+it.  It shares no code with the CUDA path.
+
+* ``solve``            -- plain FP64 revised simplex in C (``simplex_oracle.c``),
+                          with the tabu entering rule and optional follow mode.
+* ``gj_inverse``       -- Gauss-Jordan inverse with partial pivoting (C).
+* ``reduced_costs``    -- d = c - A^T y and d_slack = -y (C).
+* ``brute_force``      -- vertex enumeration for tiny LPs (numpy).
+* ``certificate``      -- primal/dual feasibility and duality-gap residuals.
+
+Every floating-point function here is FP64.  Parity status: every function is
+pinned by tests in ``tests/test_oracle.py`` (brute force, closed forms,
+Klee-Minty pivot counts, Beale's cycling example, duality certificates and an
+independent HiGHS solve).
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "simplex_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OPTIMAL, UNBOUNDED, ITER_LIMIT, SINGULAR, MISMATCH = 1, 2, 3, 4, 5
+STATUS_NAMES = {0: "running", 1: "optimal", 2: "unbounded", 3: "iter_limit",
+                4: "singular", 5: "mismatch", 6: "nomem"}
+TF_DEGENERATE, TF_TABU_PUSH, TF_ASPIRATION, TF_BLAND = 1, 2, 4, 8
+TF_ADOPT_Q, TF_ADOPT_R, TF_TIE_SET = 16, 32, 64
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle with gcc (no FP contraction, same bits on x86/Arm)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("reinvert_every", ctypes.c_int32), ("tabu_tenure", ctypes.c_int32),
+                ("max_iters", ctypes.c_int32), ("bland_after", ctypes.c_int32),
+                ("ratio_rule", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("tol_d", ctypes.c_double), ("tol_piv", ctypes.c_double),
+                ("tol_tie", ctypes.c_double), ("tie_cmp", ctypes.c_double)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("reinversions", ctypes.c_int32), ("degenerate", ctypes.c_int32),
+                ("tabu_pushes", ctypes.c_int32), ("bland_fallbacks", ctypes.c_int32),
+                ("aspirations", ctypes.c_int32), ("adopted", ctypes.c_int32),
+                ("mismatch_at", ctypes.c_int32), ("mismatch_kind", ctypes.c_int32),
+                ("objective", ctypes.c_double)]
+
+
+class _Trace(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_void_p), ("r", ctypes.c_void_p), ("theta", ctypes.c_void_p),
+                ("dq", ctypes.c_void_p), ("flags", ctypes.c_void_p),
+                ("margin_q", ctypes.c_void_p), ("margin_r", ctypes.c_void_p),
+                ("cap", ctypes.c_int32)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            vp, i32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+            lib.oracle_solve.restype = i32
+            lib.oracle_solve.argtypes = [i32, i32, vp, vp, vp, ctypes.POINTER(_Opts), vp,
+                                         vp, vp, i32, i32, ctypes.POINTER(_Trace),
+                                         vp, vp, vp, vp, vp, ctypes.POINTER(_Result)]
+            lib.oracle_gj_inverse.restype = i32
+            lib.oracle_gj_inverse.argtypes = [i32, vp, vp]
+            lib.oracle_reduced_costs.restype = None
+            lib.oracle_reduced_costs.argtypes = [i32, i32, vp, vp, vp, vp]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+@dataclass
+class Options:
+    """Solver options; the defaults are the method's settings: reinversion
+    every 64 iterations, tabu tenure 7, Bland fallback after 50 consecutive
+    degenerate pivots, tolerances 1e-9 / 1e-9 / 1e-12."""
+    reinvert_every: int = 64
+    tabu_tenure: int = 7
+    max_iters: int = 1_000_000
+    bland_after: int = 50
+    ratio_rule: int = 0
+    tol_d: float = 1e-9
+    tol_piv: float = 1e-9
+    tol_tie: float = 1e-12
+    tie_cmp: float = 1e-12
+
+
+@dataclass
+class Solution:
+    status: int
+    iterations: int
+    objective: float
+    x: np.ndarray
+    y: np.ndarray
+    basis: np.ndarray
+    bbar: np.ndarray
+    binv: np.ndarray | None
+    reinversions: int = 0
+    degenerate: int = 0
+    tabu_pushes: int = 0
+    bland_fallbacks: int = 0
+    aspirations: int = 0
+    adopted: int = 0
+    mismatch_at: int = -1
+    mismatch_kind: int = 0
+    trace: dict = field(default_factory=dict)
+
+    @property
+    def status_name(self) -> str:
+        return STATUS_NAMES.get(self.status, str(self.status))
+
+
+def solve(A, b, c, opts: Options | None = None, start_basis=None, follow=None,
+          follow_status: int = OPTIMAL, want_binv: bool = False, trace_cap: int = 0) -> Solution:
+    """Runs the oracle on ``max c^T x, A x <= b, x >= 0``.
+
+    ``follow=(q_seq, r_seq)`` checks another solver's pivot sequence pivot by
+    pivot (see the C file); ``q_seq[t] = -1`` marks where it stopped.
+    """
+    lib = _load()
+    o = opts or Options()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    m, n = A.shape
+    assert b.shape == (m,) and c.shape == (n,)
+    copts = _Opts(o.reinvert_every, o.tabu_tenure, o.max_iters, o.bland_after, o.ratio_rule, 0,
+                  o.tol_d, o.tol_piv, o.tol_tie, o.tie_cmp)
+    sb = None if start_basis is None else np.ascontiguousarray(start_basis, dtype=np.int32)
+    fq = fr = None
+    flen = 0
+    if follow is not None:
+        fq = np.ascontiguousarray(follow[0], dtype=np.int32)
+        fr = np.ascontiguousarray(follow[1], dtype=np.int32)
+        flen = len(fq)
+    tr = None
+    arrays = {}
+    if trace_cap > 0:
+        arrays = dict(q=np.full(trace_cap, -1, np.int32), r=np.full(trace_cap, -1, np.int32),
+                      theta=np.zeros(trace_cap), dq=np.zeros(trace_cap),
+                      flags=np.zeros(trace_cap, np.int32), margin_q=np.zeros(trace_cap),
+                      margin_r=np.zeros(trace_cap))
+        tr = _Trace(*(arrays[k].ctypes.data for k in ("q", "r", "theta", "dq", "flags",
+                                                      "margin_q", "margin_r")), trace_cap)
+    x = np.zeros(n)
+    y = np.zeros(m)
+    basis = np.zeros(m, np.int32)
+    bbar = np.zeros(m)
+    binv = np.zeros((m, m)) if want_binv else None
+    res = _Result()
+    lib.oracle_solve(m, n, _p(A), _p(b), _p(c), ctypes.byref(copts), _p(sb), _p(fq), _p(fr),
+                     flen, follow_status, ctypes.byref(tr) if tr is not None else None,
+                     _p(x), _p(y), _p(basis), _p(binv), _p(bbar), ctypes.byref(res))
+    if arrays:
+        k = min(res.iterations, trace_cap)
+        arrays = {key: v[:k].copy() for key, v in arrays.items()}
+    return Solution(res.status, res.iterations, res.objective, x, y, basis, bbar, binv,
+                    res.reinversions, res.degenerate, res.tabu_pushes, res.bland_fallbacks,
+                    res.aspirations, res.adopted, res.mismatch_at, res.mismatch_kind, arrays)
+
+
+def gj_inverse(M) -> np.ndarray:
+    """Gauss-Jordan inverse with partial pivoting (raises on a zero pivot column)."""
+    lib = _load()
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    k = M.shape[0]
+    out = np.zeros_like(M)
+    rc = lib.oracle_gj_inverse(k, _p(M), _p(out))
+    if rc != 0:
+        raise np.linalg.LinAlgError("singular matrix")
+    return out
+
+
+def reduced_costs(A, c, y) -> np.ndarray:
+    """d_j = c_j - y^T a_j for j < n and d_{n+i} = -y_i."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    m, n = A.shape
+    d = np.zeros(n + m)
+    lib.oracle_reduced_costs(m, n, _p(A), _p(c), _p(y), _p(d))
+    return d
+
+
+def basis_matrix(A, basis) -> np.ndarray:
+    """B = [A | I][:, basis]."""
+    m, n = A.shape
+    full = np.hstack([A, np.eye(m)])
+    return full[:, np.asarray(basis)]
+
+
+def brute_force(A, b, c, tol: float = 1e-9):
+    """Optimum of max c^T x, Ax <= b, x >= 0 by enumerating every basis of
+    [A | I] (tiny problems only).  Uses numpy's LAPACK solve per basis, an
+    independent route from the simplex iterations.  Returns (z, x) or
+    (None, None) if no feasible basis exists."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    full = np.hstack([A, np.eye(m)])
+    cf = np.concatenate([c, np.zeros(m)])
+    best, bx = None, None
+    for cols in itertools.combinations(range(n + m), m):
+        B = full[:, cols]
+        if abs(np.linalg.det(B)) < 1e-12:
+            continue
+        xb = np.linalg.solve(B, b)
+        if np.min(xb) < -tol:
+            continue
+        zz = float(cf[list(cols)] @ xb)
+        if best is None or zz > best:
+            best = zz
+            bx = np.zeros(n + m)
+            bx[list(cols)] = xb
+    return (best, None if bx is None else bx[:n])
+
+
+def certificate(A, b, c, x, y) -> dict:
+    """Residuals of an optimality certificate for max c^T x, Ax <= b, x >= 0
+    with dual min b^T y, A^T y >= c, y >= 0 (all relative to max(1, scale))."""
+    A = np.asarray(A, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    s = b - A @ x
+    primal = max(float(np.max(-s, initial=0.0)), float(np.max(-x, initial=0.0)))
+    dual_slack = A.T @ y - c
+    dual = max(float(np.max(-dual_slack, initial=0.0)), float(np.max(-y, initial=0.0)))
+    pz, dz = float(c @ x), float(b @ y)
+    gap = abs(pz - dz) / max(1.0, abs(pz))
+    # complementary slackness: x_j * (A^T y - c)_j and y_i * s_i
+    cs = max(float(np.max(np.abs(x * dual_slack), initial=0.0)),
+             float(np.max(np.abs(y * s), initial=0.0)))
+    scale_b = max(1.0, float(np.max(np.abs(b), initial=0.0)))
+    scale_c = max(1.0, float(np.max(np.abs(c), initial=0.0)))
+    return dict(primal=primal / scale_b, dual=dual / scale_c, gap=gap,
+                cs=cs / max(1.0, abs(pz)), primal_obj=pz, dual_obj=dz)
