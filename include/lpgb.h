@@ -1,0 +1,182 @@
+/*
+ * lpgb.h -- C ABI of the GB300 dense revised simplex solver.
+ *
+ * Solves   max c^T x   s.t.   A x <= b,  x >= 0,  b >= 0
+ * with the revised simplex method of Section 2.1 (Steps 1-8): slack columns
+ * A = (A', I_m) form the starting basis, Dantzig pricing (Step 3/4), the ratio
+ * test (Step 6), and the explicit-inverse tableau pivot (Step 8, Figure 1),
+ * with the tabu anti-cycling rule of Sections 2.2 and 3.4.  Every step runs in
+ * the library's own CUDA kernels (sm_103a); there is no CPU fallback.
+ *
+ * Conventions
+ *  - m = number of constraints (rows of A), n = number of structural
+ *    variables.  Variable j < n is x_j; variable n+i is the slack of row i.
+ *  - A is dense, row-major, m x n, FP64 (the paper's d_A[i*n+j], Section 3.2).
+ *  - Every pointer argument is a HOST pointer unless the argument says
+ *    otherwise.  Host buffers are read or written synchronously; the caller
+ *    keeps ownership of every buffer it passes.
+ *  - Return codes: LP_OK (0) or a negative LP_ERR_*.  A solve that ends
+ *    optimal, unbounded or at the iteration limit returns LP_OK and reports
+ *    the outcome in lp_result.status.
+ *  - A handle owns all of its device memory.  One handle must not be used
+ *    from two host threads at once; different handles are independent.
+ */
+#ifndef LPGB_H
+#define LPGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define LP_OK 0
+#define LP_ERR_INVALID_ARG (-1) /* bad size, NULL pointer, NaN/Inf, b_i < 0 */
+#define LP_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define LP_ERR_OOM (-3)         /* device allocation failed */
+#define LP_ERR_SINGULAR (-4)    /* reinversion met a zero pivot column */
+#define LP_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define LP_ERR_STATE (-6)       /* call not valid in the handle's state */
+#define LP_ERR_DEVICE (-7)      /* a kernel reported an internal error */
+
+/* ---- solve outcome (lp_result.status) ----------------------------------- */
+#define LP_RUNNING 0
+#define LP_OPTIMAL 1            /* Step 4: every reduced cost <= tol_d */
+#define LP_UNBOUNDED 2          /* Step 5: no alpha_i > tol_piv */
+#define LP_ITER_LIMIT 3
+
+/* ---- trace flags (lp_get_trace) ----------------------------------------- */
+#define LP_TF_DEGENERATE 1      /* step length theta <= tol_tie */
+#define LP_TF_TABU_PUSH 2       /* the leaving variable became tabu */
+#define LP_TF_ASPIRATION 4      /* every improving candidate was tabu */
+#define LP_TF_BLAND 8           /* Bland safety net active */
+#define LP_TF_TIE_SET 64        /* the ratio test had more than one tied row */
+
+typedef struct lp_handle lp_handle;
+
+/*
+ * Options.  lp_default_options() fills the method's settings:
+ * reinvert_every 64, tabu_tenure 7, bland_after 50, max_iters 50,000,000,
+ * price_mode 0, topk 16, trace_cap 0, graph_iters 64, kernel_timing 0,
+ * tol_d 1e-9, tol_piv 1e-9, tol_tie 1e-12, cuda_stream NULL.
+ */
+typedef struct lp_options {
+    int32_t reinvert_every; /* rebuild B^-1 from the basis every k pivots (0: never) */
+    int32_t tabu_tenure;    /* iterations a tabu variable may not enter (0: rule off) */
+    int32_t max_iters;      /* iteration limit */
+    int32_t bland_after;    /* consecutive degenerate pivots before Bland's rule (0: off) */
+    int32_t price_mode;     /* 0: FP64 PRICE (the only mode of this version) */
+    int32_t topk;           /* reserved for price_mode 1 */
+    int32_t trace_cap;      /* record (q, r, theta, d_q, flags) of the first trace_cap pivots */
+    int32_t graph_iters;    /* pivots per captured CUDA graph launch */
+    int32_t kernel_timing;  /* 1: time every PRICE and UPDATE launch with CUDA events */
+    int32_t reserved_;      /* must be 0 */
+    double tol_d;           /* optimality tolerance on the reduced costs */
+    double tol_piv;         /* smallest admissible pivot alpha_r */
+    double tol_tie;         /* relative width of the ratio-test tie set */
+    void* cuda_stream;      /* cudaStream_t to run on; NULL: the handle's own stream */
+} lp_options;
+
+/* Outcome and counters of one lp_solve call. */
+typedef struct lp_result {
+    int32_t status;          /* LP_OPTIMAL, LP_UNBOUNDED or LP_ITER_LIMIT */
+    int32_t iterations;      /* pivots performed (cumulative over the handle) */
+    int32_t reinversions;    /* reinversions performed */
+    int32_t degenerate;      /* pivots with theta <= tol_tie */
+    int32_t tabu_pushes;     /* times the tabu rule fired */
+    int32_t bland_fallbacks; /* times the Bland safety net switched on */
+    int32_t aspirations;     /* iterations where every improving candidate was tabu */
+    int32_t reserved;
+    double objective;        /* c^T x at the final basis */
+    double seconds;          /* device time of the solve (CUDA events) */
+    double reinvert_seconds; /* device time spent in reinversion */
+    double bytes_moved;      /* algorithmic HBM bytes of PRICE and UPDATE/FTRAN */
+    double price_seconds;    /* kernel_timing: summed device time of PRICE launches */
+    double update_seconds;   /* kernel_timing: summed device time of UPDATE launches */
+    double price_bytes;      /* algorithmic bytes of the timed PRICE launches */
+    double update_bytes;     /* algorithmic bytes of the timed UPDATE launches */
+    int32_t price_launches;  /* kernel_timing: PRICE launches timed */
+    int32_t update_launches; /* kernel_timing: UPDATE launches timed */
+    int64_t kernel_launches; /* all kernels this call launched (graph nodes included) */
+} lp_result;
+
+/* Fills *opt with the defaults listed above. */
+void lp_default_options(lp_options* opt);
+
+/*
+ * lp_create -- copies the problem to the GPU and prepares the slack basis
+ * (Step 1 with B = I_m, Section 2.1; the whole tableau stays resident in
+ * device memory, Case 1 of Section 3).
+ *  out              receives the new handle (set to NULL on error)
+ *  m, n             constraints and structural variables, both >= 1
+ *  A_rowmajor       m x n FP64, row-major
+ *  b, c             m and n FP64 values; every b_i must be >= 0 (no Phase I)
+ *  inputs_on_device 0: A, b, c are host pointers; 1: device pointers, which
+ *                   must stay valid until lp_create returns
+ *  opt              options, or NULL for the defaults
+ * Errors: LP_ERR_INVALID_ARG (sizes, NULL, NaN/Inf, b_i < 0), LP_ERR_OOM,
+ * LP_ERR_CUDA.  The handle is on the current CUDA device.
+ */
+int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A_rowmajor,
+              const double* b, const double* c, int32_t inputs_on_device,
+              const lp_options* opt);
+
+/*
+ * lp_set_basis -- warm start: the next lp_solve starts from this basis
+ * instead of the slack basis.  basis_m holds m distinct variable indices in
+ * [0, n+m) (host pointer).  B^-1 is rebuilt from the basis columns when the
+ * solve starts; a basis that is not primal feasible (some bbar_i < 0) is
+ * rejected at that point with LP_ERR_INVALID_ARG, a singular one with
+ * LP_ERR_SINGULAR.
+ */
+int lp_set_basis(lp_handle* h, const int32_t* basis_m);
+
+/* lp_reset -- return to the slack basis and clear all counters. */
+int lp_reset(lp_handle* h);
+
+/*
+ * lp_solve -- runs simplex iterations (Steps 3-8) until optimal, unbounded or
+ * the iteration limit, on the handle's stream; returns when the device is done.
+ * After it returns, lp_get_* read the final state.  Errors: LP_ERR_CUDA,
+ * LP_ERR_SINGULAR, LP_ERR_DEVICE, LP_ERR_INVALID_ARG (infeasible warm basis).
+ */
+int lp_solve(lp_handle* h, lp_result* out);
+
+/*
+ * lp_get_solution -- x (n values), duals y = c_B^T B^-1 (m values; y_i >= 0 at
+ * an optimum), objective.  Any output pointer may be NULL.  LP_ERR_STATE
+ * before the first lp_solve.
+ */
+int lp_get_solution(const lp_handle* h, double* x_n, double* y_m, double* objective);
+
+/* lp_get_basis -- the m basic variable indices, in basis-position order. */
+int lp_get_basis(const lp_handle* h, int32_t* basis_m);
+
+/*
+ * lp_get_state -- inspection of the explicit inverse (Figure 1 tableau):
+ * binv (m*m, row-major, row p belongs to basis position p) and bbar (m).
+ * Either pointer may be NULL.
+ */
+int lp_get_state(const lp_handle* h, double* binv, double* bbar);
+
+/*
+ * lp_get_trace -- the recorded pivots (needs trace_cap > 0): entering
+ * variable q, leaving basis position r, step length theta, reduced cost d_q
+ * and LP_TF_* flags of pivot t in element t.  Copies min(cap, recorded)
+ * entries and stores that number in *count.  Any array may be NULL.
+ */
+int lp_get_trace(const lp_handle* h, int32_t* q, int32_t* r, double* theta,
+                 double* dq, int32_t* flags, int32_t cap, int32_t* count);
+
+/* lp_destroy -- frees the handle and its device memory (NULL is ignored). */
+void lp_destroy(lp_handle* h);
+
+/* lp_strerror -- a static description of a return code. */
+const char* lp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPGB_H */

@@ -1,0 +1,157 @@
+// lpgb_internal.cuh -- device data layout and kernel declarations of the
+// dense revised simplex solver (Section 2.1, Steps 1-8; tabu rule of Sections
+// 2.2 and 3.4; tableau of Figure 1 held resident in device memory, Case 1 of
+// Section 3).
+//
+// Device layout (HBM):
+//   A_cm   n columns of ld doubles (column-major, ld = m rounded up to 64,
+//          padding rows zero): PRICE streams whole columns, FTRAN stages one.
+//   binv   m rows of ld doubles (row-major explicit B^-1, padding zero).
+//   bbar, theta: m doubles.   y, rho: ld doubles (padding zero).
+//   alpha  two buffers of ld doubles (current / next pivot column).
+//   basis  m int32 (basis position -> variable); pos n+m int32 (variable ->
+//          position or -1); tabu_until n+m int32.
+//   ctrl   one Ctrl block: every decision of the iteration lives on the
+//          device, so a captured graph of many iterations needs no host
+//          round trip.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lpgb {
+
+constexpr int kLdAlign = 64;          // doubles; one warp-wide double2 sweep
+constexpr int kWarp = 32;
+
+// internal status values (beyond the public LP_* outcomes)
+constexpr int kRunning = 0;
+constexpr int kOptimal = 1;
+constexpr int kUnbounded = 2;
+constexpr int kIterLimit = 3;
+constexpr int kReinvert = 10;          // host must rebuild B^-1 before continuing
+
+// device error codes (Ctrl::err)
+constexpr int kErrNone = 0;
+constexpr int kErrSingular = 1;
+constexpr int kErrBadIndex = 2;
+constexpr int kErrInfeasibleStart = 3;
+
+// trace flags (same values as LP_TF_*)
+constexpr int kTfDegenerate = 1;
+constexpr int kTfTabuPush = 2;
+constexpr int kTfAspiration = 4;
+constexpr int kTfBland = 8;
+constexpr int kTfTieSet = 64;
+
+struct Params {
+    int32_t m, n, ld;
+    int32_t reinvert_every, tabu_tenure, max_iters, bland_after, trace_cap;
+    double tol_d, tol_piv, tol_tie;
+    double b_scale;        // max(1, max_i b_i): scale of the feasibility check
+};
+
+struct Ctrl {
+    int32_t status;        // kRunning / kOptimal / kUnbounded / kIterLimit / kReinvert
+    int32_t it;            // pivots done
+    int32_t q;             // entering variable of the pending pivot
+    int32_t r;             // leaving basis position of the pending pivot
+    int32_t tcount;        // size of the ratio-test tie set
+    int32_t abuf;          // which alpha buffer is current
+    int32_t pending;       // 1: the B^-1 update of the last pivot is still to be applied
+    int32_t flags;         // trace flags gathered during the iteration
+    int32_t degen_run;     // consecutive degenerate pivots
+    int32_t bland;         // Bland safety net active
+    int32_t n_degenerate, n_tabu, n_bland, n_asp;
+    int32_t n_reinv;
+    int32_t err;           // kErr*
+    int32_t ticket_price;  // last-block tickets (reset by the last block)
+    int32_t ticket_update;
+    int32_t k_struct;      // reinversion: number of structural basic columns
+    int32_t ticket_pivot;
+    int32_t nsb;           // structural variables in the basis
+    int32_t pad_;
+    int32_t n_price;       // PRICE launches that did work
+    int32_t n_update;      // UPDATE launches that did work
+    double bytes_price;    // algorithmic HBM bytes moved by PRICE
+    double bytes_update;   // algorithmic HBM bytes moved by UPDATE/FTRAN
+    double dq;             // d_q of the pending pivot
+    double theta;          // step length bbar_r / alpha_r
+    double alpha_r;        // pivot element
+    double z;              // objective c_B^T bbar
+};
+
+// Candidate triple of CHUZC (per block partial).
+struct PriceCand {
+    double d_all; int32_t j_all;   // best nonbasic (optimality test, aspiration)
+    int32_t j_min;                 // smallest improving index (Bland)
+    double d_nt;  int32_t j_nt;    // best nonbasic non-tabu
+    int32_t pad_;
+    double d_min;                  // d of j_min
+};
+
+struct TraceBuf {
+    int32_t* q; int32_t* r; double* theta; double* dq; int32_t* flags;
+};
+
+struct DevState {
+    Params p;
+    const double* A_cm;
+    const double* c;
+    const double* b;
+    double* binv;
+    double* bbar;
+    double* y;
+    double* rho;
+    double* alpha;      // 2 * ld
+    double* theta;      // m
+    int32_t* basis;
+    int32_t* pos;
+    int32_t* tabu_until;
+    Ctrl* ctrl;
+    PriceCand* price_part;
+    double* upd_part;   // per-block theta minima
+    TraceBuf trace;
+    // reinversion scratch
+    int32_t* rv_struct_pos;  // k structural basis positions (increasing)
+    int32_t* rv_rows;        // k rows whose slack is nonbasic (increasing)
+    int32_t* rv_row_index;   // m: row -> index in rv_rows, or -1
+    int32_t* rv_slack_pos;   // m-k basis positions holding a slack (increasing)
+    int32_t* rv_pivrow;      // k: pivot row chosen for column t (GJ)
+    int32_t* rv_rowdone;     // k: row already used as pivot
+    double* rv_M;            // k*k column-major workspace (B11 then its GJ form)
+    double* rv_f;            // 2*k published pivot columns
+};
+
+// ---- launch geometry -----------------------------------------------------
+struct Geometry {
+    int sms;
+    int price_blocks, price_threads;
+    int update_blocks, update_threads;
+    int pivot_blocks, pivot_threads;
+};
+
+// ---- kernels (kernels_iter.cu) ----------------------------------------------
+void launch_init_slack(const DevState& s, cudaStream_t st);
+void launch_pivot(const DevState& s, const Geometry& g, cudaStream_t st);
+void launch_price(const DevState& s, const Geometry& g, cudaStream_t st);
+void launch_update(const DevState& s, const Geometry& g, cudaStream_t st);
+size_t price_smem_bytes(int ld);
+size_t update_smem_bytes(int ld);
+void configure_iter_kernels(int ld);
+
+// ---- reinversion (kernels_reinv.cu) -------------------------------------------
+void launch_reinv_classify(const DevState& s, cudaStream_t st);
+void launch_reinv_gather(const DevState& s, int k, cudaStream_t st);
+void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t st);
+void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st);
+void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible);
+int occupancy_price(int ld);
+int occupancy_update(int ld);
+
+// ---- setup (kernels_setup.cu) ---------------------------------------------------
+void launch_transpose_pad(const double* A_rm, int m, int n, int ld, double* A_cm, cudaStream_t st);
+void launch_validate(const double* A_cm, const double* b, const double* c, int m, int n, int ld,
+                     int32_t* flag, cudaStream_t st);
+void launch_load_basis(const DevState& s, cudaStream_t st);
+
+}  // namespace lpgb

@@ -1,0 +1,536 @@
+// solver.cu -- host driver and C ABI (include/lpgb.h).
+//
+// A handle keeps the whole tableau resident in device memory (Case 1 of
+// Section 3; the out-of-core Case 2 is not needed within GB300 memory).  The
+// iteration loop runs as a captured CUDA graph of `graph_iters` iterations
+// (each = pivot bookkeeping, PRICE+CHUZC, UPDATE+FTRAN+CHUZR); the host only
+// reads the 160-byte control block after each graph launch, and rebuilds B^-1
+// when the device asks for it.
+#include "lpgb_internal.cuh"
+#include "../../include/lpgb.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace lpgb;
+
+struct lp_handle {
+    int device = 0;
+    int m = 0, n = 0, ld = 0;
+    lp_options opt{};
+    Params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevState ds{};
+    Geometry geo{};
+    Ctrl* h_ctrl = nullptr;          // pinned mirror of the control block
+    cudaGraphExec_t graph = nullptr;
+    std::vector<void*> allocs;
+    bool solved = false;
+    bool primed = false;             // q and r of the next pivot are on the device
+    bool warm_pending = false;
+    std::vector<int32_t> warm_basis;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr;
+    std::vector<cudaEvent_t> tev;    // kernel_timing: 3 events per captured iteration
+    double reinvert_seconds = 0.0;
+    // per-solve accumulators
+    double price_s = 0.0, update_s = 0.0, price_b = 0.0, update_b = 0.0;
+    int32_t price_n = 0, update_n = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return LP_ERR_OOM;
+    return LP_ERR_CUDA;
+}
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+template <typename T>
+int dalloc(lp_handle* h, T** ptr, size_t count) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->allocs.push_back(p);
+    *ptr = static_cast<T*>(p);
+    return LP_OK;
+}
+
+#define TRY(x)                  \
+    do {                        \
+        int rc_ = (x);          \
+        if (rc_ != LP_OK) return rc_; \
+    } while (0)
+
+int device_err_code(int err) {
+    switch (err) {
+        case kErrNone: return LP_OK;
+        case kErrSingular: return LP_ERR_SINGULAR;
+        case kErrInfeasibleStart: return LP_ERR_INVALID_ARG;
+        default: return LP_ERR_DEVICE;
+    }
+}
+
+int read_ctrl(lp_handle* h) {
+    CK(cudaMemcpyAsync(h->h_ctrl, h->ds.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+void free_all(lp_handle* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->er0) cudaEventDestroy(h->er0);
+    if (h->er1) cudaEventDestroy(h->er1);
+    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+    h->tev.clear();
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+int setup_geometry(lp_handle* h) {
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, h->device));
+    Geometry& g = h->geo;
+    g.sms = prop.multiProcessorCount;
+    configure_iter_kernels(h->ld);
+    const int occ_p = std::max(1, occupancy_price(h->ld));
+    const int occ_u = std::max(1, occupancy_update(h->ld));
+    g.price_threads = 512;
+    g.update_threads = 512;
+    g.pivot_threads = 256;
+    // PRICE: one warp per nonbasic column; no more warps than columns
+    const int warps_p = g.price_threads / 32;
+    int pb = g.sms * occ_p;
+    pb = std::min(pb, std::max(1, (h->n + warps_p - 1) / warps_p));
+    g.price_blocks = std::max(1, pb);
+    // UPDATE: one warp per row
+    const int warps_u = g.update_threads / 32;
+    int ub = g.sms * occ_u;
+    ub = std::min(ub, std::max(1, (h->m + warps_u - 1) / warps_u));
+    g.update_blocks = std::max(1, ub);
+    g.pivot_blocks = std::max(1, std::min(g.sms, (h->ld + g.pivot_threads - 1) / g.pivot_threads));
+    return LP_OK;
+}
+
+int capture_graph(lp_handle* h) {
+    cudaGraph_t graph = nullptr;
+    const int G = h->opt.graph_iters;
+    const bool timing = h->opt.kernel_timing != 0;
+    if (timing) {
+        h->tev.resize(3 * (size_t)G, nullptr);
+        for (auto& e : h->tev) CK(cudaEventCreate(&e));
+    }
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int t = 0; t < G; ++t) {
+        launch_pivot(h->ds, h->geo, h->stream);
+        if (timing) cudaEventRecordWithFlags(h->tev[3 * t], h->stream, cudaEventRecordExternal);
+        launch_price(h->ds, h->geo, h->stream);
+        if (timing) cudaEventRecordWithFlags(h->tev[3 * t + 1], h->stream, cudaEventRecordExternal);
+        launch_update(h->ds, h->geo, h->stream);
+        if (timing) cudaEventRecordWithFlags(h->tev[3 * t + 2], h->stream, cudaEventRecordExternal);
+    }
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return LP_OK;
+}
+
+// Rebuild B^-1, bbar, y, z from the current basis.
+int reinvert(lp_handle* h, int check_feasible) {
+    CK(cudaEventRecord(h->er0, h->stream));
+    launch_reinv_classify(h->ds, h->stream);
+    TRY(read_ctrl(h));
+    if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
+    const int k = h->h_ctrl->k_struct;
+    h->launches += 1 + (k > 0 ? k + 5 : 0) + 5;
+    launch_reinv_gather(h->ds, k, h->stream);
+    launch_reinv_gj(h->ds, k, h->geo, h->stream);
+    launch_reinv_assemble(h->ds, k, h->geo, h->stream);
+    launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(h->er1, h->stream));
+    TRY(read_ctrl(h));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->er0, h->er1));
+    h->reinvert_seconds += ms * 1e-3;
+    h->primed = false;
+    if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
+    return LP_OK;
+}
+
+int reset_state(lp_handle* h) {
+    launch_init_slack(h->ds, h->stream);
+    CK(cudaGetLastError());
+    h->primed = false;
+    h->solved = false;
+    h->reinvert_seconds = 0.0;
+    return LP_OK;
+}
+
+bool finite_all(const double* x, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lp_default_options(lp_options* o) {
+    if (!o) return;
+    o->reinvert_every = 64;
+    o->tabu_tenure = 7;
+    o->max_iters = 50000000;
+    o->bland_after = 50;
+    o->price_mode = 0;
+    o->topk = 16;
+    o->trace_cap = 0;
+    o->graph_iters = 64;
+    o->kernel_timing = 0;
+    o->reserved_ = 0;
+    o->tol_d = 1e-9;
+    o->tol_piv = 1e-9;
+    o->tol_tie = 1e-12;
+    o->cuda_stream = nullptr;
+}
+
+const char* lp_strerror(int code) {
+    switch (code) {
+        case LP_OK: return "ok";
+        case LP_ERR_INVALID_ARG: return "invalid argument";
+        case LP_ERR_CUDA: return "CUDA runtime error";
+        case LP_ERR_OOM: return "out of device memory";
+        case LP_ERR_SINGULAR: return "singular basis during reinversion";
+        case LP_ERR_TIMEOUT: return "bounded device wait timed out";
+        case LP_ERR_STATE: return "call not valid in the handle's state";
+        case LP_ERR_DEVICE: return "device-side internal error";
+        default: return "unknown error";
+    }
+}
+
+static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, const double* b,
+                       const double* c, int32_t on_device) {
+    CK(cudaGetDevice(&h->device));
+    h->m = m;
+    h->n = n;
+    h->ld = (m + kLdAlign - 1) / kLdAlign * kLdAlign;
+    const int ld = h->ld;
+    if ((size_t)ld * sizeof(double) * 2 > 200 * 1024) return LP_ERR_INVALID_ARG;  // smem staging limit
+    if (h->opt.cuda_stream) {
+        h->stream = static_cast<cudaStream_t>(h->opt.cuda_stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    CK(cudaEventCreate(&h->ev0));
+    CK(cudaEventCreate(&h->ev1));
+    CK(cudaEventCreate(&h->er0));
+    CK(cudaEventCreate(&h->er1));
+    CK(cudaMallocHost(&h->h_ctrl, sizeof(Ctrl)));
+
+    DevState& s = h->ds;
+    Params& P = h->p;
+    P.m = m; P.n = n; P.ld = ld;
+    P.reinvert_every = h->opt.reinvert_every;
+    P.tabu_tenure = h->opt.tabu_tenure;
+    P.max_iters = h->opt.max_iters;
+    P.bland_after = h->opt.bland_after;
+    P.trace_cap = std::max(0, h->opt.trace_cap);
+    P.tol_d = h->opt.tol_d;
+    P.tol_piv = h->opt.tol_piv;
+    P.tol_tie = h->opt.tol_tie;
+    s.p = P;
+
+    double *A_cm, *cc, *bb, *binv, *bbar, *y, *rho, *alpha, *theta, *upd_part, *rv_M, *rv_f;
+    int32_t *basis, *pos, *tabu, *rv_sp, *rv_rows, *rv_ri, *rv_piv, *rv_done, *rv_slack, *flag;
+    Ctrl* ctrl;
+    PriceCand* price_part;
+    TRY(dalloc(h, &A_cm, (size_t)n * ld));
+    TRY(dalloc(h, &cc, (size_t)n));
+    TRY(dalloc(h, &bb, (size_t)ld));
+    TRY(dalloc(h, &binv, (size_t)m * ld));
+    TRY(dalloc(h, &bbar, (size_t)m));
+    TRY(dalloc(h, &y, (size_t)ld));
+    TRY(dalloc(h, &rho, (size_t)ld));
+    TRY(dalloc(h, &alpha, 2 * (size_t)ld));
+    TRY(dalloc(h, &theta, (size_t)m));
+    TRY(dalloc(h, &basis, (size_t)m));
+    TRY(dalloc(h, &pos, (size_t)(n + m)));
+    TRY(dalloc(h, &tabu, (size_t)(n + m)));
+    TRY(dalloc(h, &ctrl, 1));
+    TRY(dalloc(h, &flag, 1));
+    TRY(dalloc(h, &rv_sp, (size_t)m));
+    TRY(dalloc(h, &rv_rows, (size_t)m));
+    TRY(dalloc(h, &rv_ri, (size_t)m));
+    TRY(dalloc(h, &rv_piv, (size_t)m));
+    TRY(dalloc(h, &rv_done, (size_t)m));
+    TRY(dalloc(h, &rv_slack, (size_t)m));
+    TRY(dalloc(h, &rv_M, (size_t)m * m));
+    TRY(dalloc(h, &rv_f, 2 * (size_t)m));
+    TRY(setup_geometry(h));
+    const int parts = std::max(h->geo.price_blocks, h->geo.update_blocks);
+    TRY(dalloc(h, &price_part, (size_t)parts));
+    TRY(dalloc(h, &upd_part, (size_t)parts));
+    if (P.trace_cap > 0) {
+        TRY(dalloc(h, &s.trace.q, (size_t)P.trace_cap));
+        TRY(dalloc(h, &s.trace.r, (size_t)P.trace_cap));
+        TRY(dalloc(h, &s.trace.theta, (size_t)P.trace_cap));
+        TRY(dalloc(h, &s.trace.dq, (size_t)P.trace_cap));
+        TRY(dalloc(h, &s.trace.flags, (size_t)P.trace_cap));
+    }
+    s.A_cm = A_cm; s.c = cc; s.b = bb; s.binv = binv; s.bbar = bbar; s.y = y; s.rho = rho;
+    s.alpha = alpha; s.theta = theta; s.basis = basis; s.pos = pos; s.tabu_until = tabu;
+    s.ctrl = ctrl; s.price_part = price_part; s.upd_part = upd_part;
+    s.rv_struct_pos = rv_sp; s.rv_rows = rv_rows; s.rv_row_index = rv_ri; s.rv_slack_pos = rv_slack;
+    s.rv_pivrow = rv_piv; s.rv_rowdone = rv_done; s.rv_M = rv_M; s.rv_f = rv_f;
+
+    // upload: A (row-major) -> padded column-major, b padded, c
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const double* A_src = A;
+    double* staging = nullptr;
+    if (!on_device) {
+        CK(cudaMalloc(&staging, (size_t)m * n * sizeof(double)));
+        cudaError_t e = cudaMemcpyAsync(staging, A, (size_t)m * n * sizeof(double), kind, h->stream);
+        if (e != cudaSuccess) { cudaFree(staging); return cuda_fail(e); }
+        A_src = staging;
+    }
+    launch_transpose_pad(A_src, m, n, ld, A_cm, h->stream);
+    CK(cudaMemsetAsync(bb, 0, (size_t)ld * sizeof(double), h->stream));
+    CK(cudaMemcpyAsync(bb, b, (size_t)m * sizeof(double), kind, h->stream));
+    CK(cudaMemcpyAsync(cc, c, (size_t)n * sizeof(double), kind, h->stream));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int32_t), h->stream));
+    launch_validate(A_cm, bb, cc, m, n, ld, flag, h->stream);
+    int32_t hflag = 0;
+    CK(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (staging) CK(cudaFree(staging));
+    if (hflag) return LP_ERR_INVALID_ARG;
+    // b scale for the feasibility check of warm starts
+    {
+        std::vector<double> hb(m);
+        CK(cudaMemcpy(hb.data(), bb, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost));
+        double sc = 1.0;
+        for (double v : hb) sc = std::max(sc, std::fabs(v));
+        P.b_scale = sc;
+        s.p = P;
+    }
+    TRY(reset_state(h));
+    TRY(capture_graph(h));
+    CK(cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const double* b, const double* c,
+              int32_t on_device, const lp_options* opt) {
+    if (!out) return LP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (m < 1 || n < 1 || !A || !b || !c) return LP_ERR_INVALID_ARG;
+    if ((int64_t)n + m > (int64_t)1 << 30) return LP_ERR_INVALID_ARG;
+    lp_options o;
+    lp_default_options(&o);
+    if (opt) o = *opt;
+    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.reserved_ != 0 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 ||
+        o.bland_after < 0 || o.price_mode != 0 || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
+        return LP_ERR_INVALID_ARG;
+    if (!on_device) {
+        if (!finite_all(A, (size_t)m * n) || !finite_all(c, n) || !finite_all(b, m)) return LP_ERR_INVALID_ARG;
+        for (int i = 0; i < m; ++i)
+            if (b[i] < 0) return LP_ERR_INVALID_ARG;
+    }
+    lp_handle* h = new (std::nothrow) lp_handle();
+    if (!h) return LP_ERR_OOM;
+    h->opt = o;
+    int rc = create_impl(h, m, n, A, b, c, on_device);
+    if (rc != LP_OK) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LP_OK;
+}
+
+int lp_set_basis(lp_handle* h, const int32_t* basis) {
+    if (!h || !basis) return LP_ERR_INVALID_ARG;
+    std::vector<char> seen((size_t)h->n + h->m, 0);
+    for (int p = 0; p < h->m; ++p) {
+        const int v = basis[p];
+        if (v < 0 || v >= h->n + h->m || seen[v]) return LP_ERR_INVALID_ARG;
+        seen[v] = 1;
+    }
+    h->warm_basis.assign(basis, basis + h->m);
+    h->warm_pending = true;
+    return LP_OK;
+}
+
+int lp_reset(lp_handle* h) {
+    if (!h) return LP_ERR_INVALID_ARG;
+    h->warm_pending = false;
+    TRY(reset_state(h));
+    CK(cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+int lp_solve(lp_handle* h, lp_result* out) {
+    if (!h) return LP_ERR_INVALID_ARG;
+    CK(cudaEventRecord(h->ev0, h->stream));
+    h->reinvert_seconds = 0.0;
+    h->price_s = h->update_s = h->price_b = h->update_b = 0.0;
+    h->price_n = h->update_n = 0;
+    h->launches = 0;
+    if (h->warm_pending) {
+        TRY(reset_state(h));
+        CK(cudaMemcpyAsync(h->ds.basis, h->warm_basis.data(), sizeof(int32_t) * h->m,
+                           cudaMemcpyHostToDevice, h->stream));
+        launch_load_basis(h->ds, h->stream);
+        CK(cudaGetLastError());
+        h->warm_pending = false;
+        TRY(reinvert(h, 1));
+    }
+    TRY(read_ctrl(h));
+    for (;;) {
+        const Ctrl& C = *h->h_ctrl;
+        if (C.err != kErrNone) return device_err_code(C.err);
+        if (C.status == kReinvert) {
+            TRY(reinvert(h, 0));
+            continue;
+        }
+        if (C.status != kRunning) break;
+        if (!h->primed) {
+            launch_price(h->ds, h->geo, h->stream);
+            launch_update(h->ds, h->geo, h->stream);
+            CK(cudaGetLastError());
+            h->launches += 2;
+            h->primed = true;
+        }
+        const Ctrl before = C;
+        CK(cudaGraphLaunch(h->graph, h->stream));
+        h->launches += 3 * (int64_t)h->opt.graph_iters;
+        TRY(read_ctrl(h));
+        if (!h->tev.empty()) {
+            // kernels that did work occupy the first slots of the graph
+            const Ctrl& A = *h->h_ctrl;
+            const int np = std::min(A.n_price - before.n_price, h->opt.graph_iters);
+            const int nu = std::min(A.n_update - before.n_update, h->opt.graph_iters);
+            for (int t = 0; t < np; ++t) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, h->tev[3 * t], h->tev[3 * t + 1]) == cudaSuccess) h->price_s += ms * 1e-3;
+            }
+            for (int t = 0; t < nu; ++t) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, h->tev[3 * t + 1], h->tev[3 * t + 2]) == cudaSuccess) h->update_s += ms * 1e-3;
+            }
+            h->price_n += np;
+            h->update_n += nu;
+            h->price_b += A.bytes_price - before.bytes_price;
+            h->update_b += A.bytes_update - before.bytes_update;
+        }
+    }
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    h->solved = true;
+    if (out) {
+        const Ctrl& C = *h->h_ctrl;
+        memset(out, 0, sizeof(*out));
+        out->status = C.status;
+        out->iterations = C.it;
+        out->reinversions = C.n_reinv;
+        out->degenerate = C.n_degenerate;
+        out->tabu_pushes = C.n_tabu;
+        out->bland_fallbacks = C.n_bland;
+        out->aspirations = C.n_asp;
+        out->objective = C.z;
+        out->seconds = ms * 1e-3;
+        out->reinvert_seconds = h->reinvert_seconds;
+        out->bytes_moved = C.bytes_price + C.bytes_update;
+        out->price_seconds = h->price_s;
+        out->update_seconds = h->update_s;
+        out->price_bytes = h->price_b;
+        out->update_bytes = h->update_b;
+        out->price_launches = h->price_n;
+        out->update_launches = h->update_n;
+        out->kernel_launches = h->launches;
+    }
+    return LP_OK;
+}
+
+int lp_get_solution(const lp_handle* h, double* x, double* y, double* objective) {
+    if (!h) return LP_ERR_INVALID_ARG;
+    if (!h->solved) return LP_ERR_STATE;
+    const int m = h->m, n = h->n;
+    std::vector<int32_t> basis(m);
+    std::vector<double> bbar(m);
+    CK(cudaMemcpyAsync(basis.data(), h->ds.basis, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(bbar.data(), h->ds.bbar, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+    if (y) CK(cudaMemcpyAsync(y, h->ds.y, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (x) {
+        for (int j = 0; j < n; ++j) x[j] = 0.0;
+        for (int p = 0; p < m; ++p)
+            if (basis[p] < n) x[basis[p]] = bbar[p];
+    }
+    if (objective) *objective = h->h_ctrl->z;
+    return LP_OK;
+}
+
+int lp_get_basis(const lp_handle* h, int32_t* basis) {
+    if (!h || !basis) return LP_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(basis, h->ds.basis, sizeof(int32_t) * h->m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+int lp_get_state(const lp_handle* h, double* binv, double* bbar) {
+    if (!h) return LP_ERR_INVALID_ARG;
+    if (binv)
+        CK(cudaMemcpy2DAsync(binv, sizeof(double) * h->m, h->ds.binv, sizeof(double) * h->ld,
+                             sizeof(double) * h->m, h->m, cudaMemcpyDeviceToHost, h->stream));
+    if (bbar) CK(cudaMemcpyAsync(bbar, h->ds.bbar, sizeof(double) * h->m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+int lp_get_trace(const lp_handle* h, int32_t* q, int32_t* r, double* theta, double* dq, int32_t* flags,
+                 int32_t cap, int32_t* count) {
+    if (!h || cap < 0) return LP_ERR_INVALID_ARG;
+    int avail = std::min(h->h_ctrl->it, h->p.trace_cap);
+    int k = std::min(avail, cap);
+    if (count) *count = k;
+    if (k == 0) return LP_OK;
+    const TraceBuf& t = h->ds.trace;
+    if (q) CK(cudaMemcpyAsync(q, t.q, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, h->stream));
+    if (r) CK(cudaMemcpyAsync(r, t.r, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, h->stream));
+    if (theta) CK(cudaMemcpyAsync(theta, t.theta, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+    if (dq) CK(cudaMemcpyAsync(dq, t.dq, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+    if (flags) CK(cudaMemcpyAsync(flags, t.flags, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+void lp_destroy(lp_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

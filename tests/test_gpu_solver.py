@@ -1,0 +1,196 @@
+"""CUDA solver vs the oracle, through the C ABI (needs a GB300).
+
+Bars (from the method's tolerances): identical pivot sequence wherever ties
+are separated by more than 1e-12 (checked by the oracle's follow mode), optimal
+objective within 1e-9 relative, primal/dual residuals <= 1e-9.  Element-wise
+state (B^-1, bbar) within 1e-9 of the largest entry: FP64 with different
+summation orders over at most 64 rank-1 updates stays far below that.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+from gpu_util import assert_certificate, follow_check, gpu_solve
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1803_04378_gb300 import lpgb  # noqa: F401
+
+
+CASES = [
+    ("int", 200, 200, 0),      # the 200x200 dense integer workload
+    ("int", 37, 61, 5),
+    ("real", 256, 512, 1),
+    ("real", 300, 200, 3),     # n < m
+    ("real", 129, 257, 4),     # ragged against the 64-wide row padding
+    ("degenerate", 64, 128, 2),
+    ("degenerate", 128, 256, 2),
+]
+
+
+@pytest.mark.parametrize("kind,m,n,seed", CASES)
+def test_pivot_sequence_and_objective(kind, m, n, seed):
+    A, b, c = lpgen.make(kind, m, n, seed)
+    lp, res, x, y, z, tr = gpu_solve(A, b, c)
+    assert res.status == 1
+    ref = oracle.solve(A, b, c)
+    assert abs(z - ref.objective) <= 1e-9 * max(1.0, abs(ref.objective))
+    assert_certificate(A, b, c, x, y)
+    follow_check(A, b, c, res, tr)
+    lp.close()
+
+
+def test_klee_minty_pivot_count():
+    for d in (3, 6, 9):
+        A = np.zeros((d, d)); b = np.zeros(d); c = np.zeros(d)
+        for i in range(d):
+            for j in range(i):
+                A[i, j] = 2 * 10.0 ** (i - j)
+            A[i, i] = 1.0
+            b[i] = 100.0 ** i
+            c[i] = 10.0 ** (d - 1 - i)
+        lp, res, x, y, z, tr = gpu_solve(A, b, c)
+        assert res.status == 1 and res.iterations == 2 ** d - 1
+        assert z == pytest.approx(100.0 ** (d - 1), rel=1e-12)
+        lp.close()
+
+
+def test_beale_terminates():
+    g = json.load(open(os.path.join(GOLD, "beale_1955.json")))
+    A, b, c = np.array(g["A"]), np.array(g["b"]), np.array(g["c"])
+    lp, res, x, y, z, tr = gpu_solve(A, b, c)
+    assert res.status == 1 and z == pytest.approx(g["optimum"], abs=1e-15)
+    assert np.allclose(x, g["x_opt"], atol=1e-15)
+    follow_check(A, b, c, res, tr)
+    lp.close()
+
+
+@pytest.mark.parametrize("K,reinv", [(1, 64), (17, 64), (63, 64), (64, 64), (100, 64), (40, 0)])
+def test_state_elementwise(K, reinv):
+    A, b, c = lpgen.dense_real_lp(150, 260, 21)
+    lp, res, x, y, z, tr = gpu_solve(A, b, c, max_iters=K, reinvert_every=reinv)
+    assert res.status == 3 and res.iterations == K
+    o = oracle.Options(max_iters=K, reinvert_every=reinv)
+    follow_check(A, b, c, res, tr, o)
+    ref = oracle.solve(A, b, c, o, want_binv=True)
+    binv, bbar = lp.state()
+    assert np.array_equal(lp.basis(), ref.basis)
+    scale = max(1.0, np.max(np.abs(ref.binv)))
+    assert np.max(np.abs(binv - ref.binv)) <= 1e-9 * scale
+    assert np.max(np.abs(bbar - ref.bbar)) <= 1e-9 * max(1.0, np.max(np.abs(ref.bbar)))
+    assert np.max(np.abs(y - ref.y)) <= 1e-9 * max(1.0, np.max(np.abs(ref.y)))
+    assert z == pytest.approx(ref.objective, rel=1e-12)
+    lp.close()
+
+
+def test_warm_start_reinversion_elementwise():
+    A, b, c = lpgen.dense_real_lp(180, 300, 22)
+    ref_full = oracle.solve(A, b, c)
+    # a feasible intermediate basis from the oracle's own path
+    mid = oracle.solve(A, b, c, oracle.Options(max_iters=ref_full.iterations // 2))
+    from paper_1803_04378_gb300 import lpgb
+    with lpgb.LP(A, b, c, max_iters=0) as lp:
+        lp.set_basis(mid.basis)
+        res = lp.solve()
+        assert res.status == 3 and res.reinversions == 1
+        binv, bbar = lp.state()
+    ref = oracle.solve(A, b, c, oracle.Options(max_iters=0), start_basis=mid.basis, want_binv=True)
+    assert np.max(np.abs(binv - ref.binv)) <= 1e-9 * max(1.0, np.max(np.abs(ref.binv)))
+    assert np.max(np.abs(bbar - ref.bbar)) <= 1e-9 * max(1.0, np.max(np.abs(ref.bbar)))
+    # and a warm solve from the optimal basis takes no pivots
+    with lpgb.LP(A, b, c) as lp:
+        lp.set_basis(ref_full.basis)
+        res = lp.solve()
+        _, _, z = lp.solution()
+        assert res.status == 1 and res.iterations == 0
+        assert z == pytest.approx(ref_full.objective, rel=1e-12)
+
+
+def test_reinvert_every_pivot_same_path():
+    A, b, c = lpgen.dense_real_lp(120, 200, 12)
+    lp, res, x, y, z, tr = gpu_solve(A, b, c, reinvert_every=1)
+    assert res.status == 1 and res.reinversions == res.iterations
+    follow_check(A, b, c, res, tr, oracle.Options(reinvert_every=1))
+    lp.close()
+
+
+def test_edge_shapes():
+    rng = np.random.default_rng(5)
+    for (m, n) in [(1, 1), (1, 7), (7, 1), (63, 64), (64, 63), (65, 65)]:
+        A = rng.random((m, n)) + 0.05
+        b = rng.random(m) * 3
+        c = rng.random(n)
+        lp, res, x, y, z, tr = gpu_solve(A, b, c)
+        ref = oracle.solve(A, b, c)
+        assert res.status == 1 and z == pytest.approx(ref.objective, rel=1e-12, abs=1e-15)
+        follow_check(A, b, c, res, tr)
+        lp.close()
+
+
+def test_trivial_and_unbounded():
+    # c <= 0: the slack basis is optimal
+    A = np.ones((3, 4)); b = np.ones(3); c = -np.ones(4)
+    lp, res, x, y, z, tr = gpu_solve(A, b, c)
+    assert res.status == 1 and res.iterations == 0 and z == 0.0
+    lp.close()
+    # column 1 has no positive entry: unbounded
+    A = np.array([[1.0, -1.0], [2.0, 0.0]]); b = np.array([1.0, 2.0]); c = np.array([1.0, 1.0])
+    lp, res, x, y, z, tr = gpu_solve(A, b, c)
+    ref = oracle.solve(A, b, c)
+    assert res.status == 2 and ref.status == oracle.UNBOUNDED
+    follow_check(A, b, c, res, tr)
+    lp.close()
+
+
+def test_invalid_arguments():
+    from paper_1803_04378_gb300 import lpgb
+    A = np.ones((2, 2))
+    with pytest.raises(lpgb.LPError) as e:
+        lpgb.LP(A, np.array([1.0, -1.0]), np.ones(2))
+    assert e.value.code == lpgb.LP_ERR_INVALID_ARG
+    with pytest.raises(lpgb.LPError):
+        lpgb.LP(np.array([[1.0, np.nan], [1.0, 1.0]]), np.ones(2), np.ones(2))
+    with lpgb.LP(A, np.ones(2), np.ones(2)) as lp:
+        with pytest.raises(lpgb.LPError) as e:
+            lp.set_basis(np.array([0, 0], np.int32))
+        assert e.value.code == lpgb.LP_ERR_INVALID_ARG
+        with pytest.raises(lpgb.LPError) as e:
+            lp.solution()
+        assert e.value.code == lpgb.LP_ERR_STATE
+
+
+def test_device_inputs_match_host_inputs():
+    import torch
+    from paper_1803_04378_gb300 import lpgb
+    A, b, c = lpgen.dense_real_lp(200, 330, 9)
+    with lpgb.LP(A, b, c) as lp:
+        r1 = lp.solve()
+        z1 = lp.solution()[2]
+    At, bt, ct = (torch.from_numpy(v).cuda() for v in (A, b, c))
+    with lpgb.LP(At, bt, ct) as lp:
+        r2 = lp.solve()
+        z2 = lp.solution()[2]
+    assert r1.iterations == r2.iterations and z1 == z2
+
+
+def test_reset_repeats_identically():
+    from paper_1803_04378_gb300 import lpgb
+    A, b, c = lpgen.dense_real_lp(256, 400, 10)
+    with lpgb.LP(A, b, c, trace_cap=10000) as lp:
+        r1 = lp.solve(); t1 = lp.trace(); z1 = lp.solution()[2]
+        lp.reset()
+        r2 = lp.solve(); t2 = lp.trace(); z2 = lp.solution()[2]
+    assert r1.iterations == r2.iterations and z1 == z2
+    assert np.array_equal(t1["q"], t2["q"]) and np.array_equal(t1["r"], t2["r"])
