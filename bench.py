@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark: simplex iterations/s and time-to-optimum of the FP64 dense
+revised simplex on the dense real 4096 x 8192 workload (A_ij ~ U[0,1) with 10%
+zeros, b_i ~ U[n/4, n/2], c_j ~ U[0,1), seed 1; reinversion every 64 pivots,
+tabu tenure 7).
+
+One step = one full solve from the slack basis to optimality (every row of
+the hot path: PRICE+CHUZC, UPDATE+FTRAN+CHUZR, pivot bookkeeping, periodic
+reinversion), with A, b, c already resident in HBM.  value = pivots / second
+over the K timed steps.  The per-iteration working set (A 268 MB + B^-1 134
+MB) is larger than L2, so no flush is needed between iterations.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 (torchrun): every rank solves its own replica (the method has no
+data-parallel exchange on one LP); value = all ranks' pivots / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "simplex iters/s & time-to-optimum, m=4096 n=8192 FP64; batched LPs/s"
+WORKLOAD = dict(name="dense_real_4096x8192", kind="real", m=4096, n=8192, seed=1)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0: float, t1: float) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, line in self.lines:
+            if ts < t0 - 0.25 or ts > t1 + 0.25:
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 FMA peak of the GB300 (1.25 TFLOP/s nominal: 152 SMs x 2 FP64 FMA/clk
+# x ~2.06 GHz); the probe in profiles/fp64_probe.md measured 1.20 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.20
+
+
+def _traffic(kernel: str):
+    """dram bytes per launch from the committed ncu capture, if the kernel's
+    source has not changed since."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_1803_04378_gb300", "csrc", ent["source"])
+    if not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if sha != ent.get("source_sha"):
+        return None
+    return ent.get("dram_bytes_per_launch_full_size")
+
+
+def cpu_baseline(A, b, c, iters: int):
+    """The oracle (single-threaded C, unmodified) on the first `iters` pivots
+    of the same workload (no reinversion inside the sample)."""
+    import oracle
+    t0 = time.perf_counter()
+    s = oracle.solve(A, b, c, oracle.Options(max_iters=iters))
+    dt = time.perf_counter() - t0
+    return {"value": s.iterations / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {s.iterations} pivots of {WORKLOAD['name']} from the slack basis "
+                      f"(single-threaded plain C FP64 revised simplex), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import lpgen
+    import oracle
+    A, b, c = lpgen.make(WORKLOAD["kind"], WORKLOAD["m"], WORKLOAD["n"], WORKLOAD["seed"])
+    oracle.build()
+    sample = 16
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s = oracle.solve(A, b, c, oracle.Options(max_iters=sample))
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = sample * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "m": WORKLOAD["m"], "n": WORKLOAD["n"],
+                       "seed": WORKLOAD["seed"], "step": f"first {sample} pivots from the slack basis"},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {sample} pivots of {WORKLOAD['name']} per step"},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-iters", type=int, default=128, help="pivots of the CPU baseline sample")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--max-iters", type=int, default=0,
+                    help="stop every solve after this many pivots (profiling runs only)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import lpgen
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1803_04378_gb300 import build as _build
+    _build.build()
+    from paper_1803_04378_gb300 import lpgb
+
+    m, n = WORKLOAD["m"], WORKLOAD["n"]
+    A, b, c = lpgen.make(WORKLOAD["kind"], m, n, WORKLOAD["seed"])
+    stream = torch.cuda.current_stream()
+    At, bt, ct = (torch.from_numpy(v).cuda() for v in (A, b, c))
+    extra = {"max_iters": args.max_iters} if args.max_iters > 0 else {}
+    lp = lpgb.LP(At, bt, ct, kernel_timing=1, cuda_stream=stream.cuda_stream, **extra)
+    del At, bt, ct
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        lp.reset()
+        lp.solve()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.5)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    e0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        lp.reset()
+        results.append(lp.solve())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall1 = time.time()
+    clocks = sampler.stop(t_wall0, t_wall1)
+    elapsed = e0.elapsed_time(e1) * 1e-3
+    iters = sum(r.iterations for r in results)
+    x, y, z = lp.solution()
+    if ws > 1:
+        tt = torch.tensor([elapsed], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(tt.item())
+        it_t = torch.tensor([float(iters)], device="cuda")
+        torch.distributed.all_reduce(it_t)
+        iters_all = int(it_t.item())
+    else:
+        iters_all = iters
+
+    # dominant kernel and its live roofline
+    ps = sum(r.price_seconds for r in results)
+    us = sum(r.update_seconds for r in results)
+    pn = sum(r.price_launches for r in results)
+    un = sum(r.update_launches for r in results)
+    pb = sum(r.price_bytes for r in results)
+    ub = sum(r.update_bytes for r in results)
+    if us >= ps:
+        kname, kt, kn, kb, kflops = "k_update", us, un, ub, 4.0 * m * m * un
+    else:
+        kname, kt, kn, kb, kflops = "k_price", ps, pn, pb, 2.0 * pb / 8.0
+    hbm_peak, peak_kind = _peaks()
+    achieved = (kb / kn) / (kt / kn) / 1e9 if kn else None
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": _traffic(kname),
+                "bytes_per_launch": kb / kn if kn else None,
+                "avg_launch_us": 1e6 * kt / kn if kn else None,
+                "share_of_step": kt / sum(r.seconds for r in results),
+                "fp64": {"achieved_tflops": kflops / kt / 1e12 if kt else None,
+                         "peak_tflops": FP64_PEAK_TFLOPS,
+                         "frac": (kflops / kt / 1e12 / FP64_PEAK_TFLOPS) if kt else None}}
+    chain_bytes = sum(r.bytes_moved for r in results)
+    reinv_s = sum(r.reinvert_seconds for r in results)
+    iter_s = sum(r.seconds for r in results) - reinv_s
+
+    # end to end through the public API with host (pinned) buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        Ap = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        bp = torch.empty(m, dtype=torch.float64, pin_memory=True)
+        cp = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        Ap.numpy()[:] = A
+        bp.numpy()[:] = b
+        cp.numpy()[:] = c
+        it_e2e, t_e2e = 0, 0.0
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            with lpgb.LP(Ap.numpy(), bp.numpy(), cp.numpy(), cuda_stream=stream.cuda_stream, **extra) as lp2:
+                r2 = lp2.solve()
+                x2, y2, z2 = lp2.solution()
+            torch.cuda.synchronize()
+            t_e2e += time.perf_counter() - t0
+            it_e2e += r2.iterations
+        e2e = {"value": it_e2e / t_e2e, "unit": "iters/s",
+               "h2d_bytes_per_step": 8 * (m * n + m + n), "d2h_bytes_per_step": 8 * (n + m) + 8,
+               "seconds_per_step": t_e2e / args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(A, b, c, args.cpu_iters)
+
+    launches = sum(r.kernel_launches + 1 for r in results)  # +1: the reset kernel of each step
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": iters_all / elapsed, "unit": "iters/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "m": m, "n": n, "seed": WORKLOAD["seed"],
+                       "A": "U[0,1) with 10% zeros", "reinvert_every": 64, "tabu_tenure": 7,
+                       "step": "one full solve from the slack basis to optimality",
+                       "l2": "no flush: A (268 MB) + B^-1 (134 MB) streamed every pivot exceed L2",
+                       "parallelism": f"replicas x{ws}"},
+            "time_to_optimum_s": elapsed / args.steps,
+            "pivots_per_solve": results[0].iterations,
+            "reinversions_per_solve": results[0].reinversions,
+            "objective": z,
+            "us_per_pivot_excl_reinversion": 1e6 * iter_s / iters,
+            "reinversion_share": reinv_s / sum(r.seconds for r in results),
+            "chain_hbm_gbs_excl_reinversion": chain_bytes / iter_s / 1e9,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    lp.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
