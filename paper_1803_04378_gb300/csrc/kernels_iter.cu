@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kPivotThreads) k_pivot(DevState s) {
 }
 
 // ---- k_price: PRICE + CHUZC -----------------------------------------------------
-__global__ void __launch_bounds__(kPriceThreads) k_price(DevState s) {
+__global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
     Ctrl* C = s.ctrl;
     if (C->status != kRunning) return;
     const Params& P = s.p;
@@ -231,37 +231,65 @@ __global__ void __launch_bounds__(kPriceThreads) k_price(DevState s) {
     __syncthreads();
     const int it = C->it;
     const int lane = threadIdx.x & 31;
-    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int half = P.ld >> 1;
     const double2* y2 = reinterpret_cast<const double2*>(ysh);
     Cand cand;
     cand_init(cand);
-    for (int j = gwarp; j < P.n; j += nwarps) {
-        if (s.pos[j] >= 0) continue;  // basic column: skipped (warp-uniform)
-        const double2* col = reinterpret_cast<const double2*>(s.A_cm + (size_t)j * P.ld);
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int k = lane;
+    // Columns are dealt to blocks round-robin (block b owns j = b, b+G, b+2G,
+    // ...) so every SM gets the same share; each warp takes two owned columns
+    // at a time, so one shared-memory load of y feeds four FMAs.
+    const int G = gridDim.x;
+    const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
+    for (int l = 2 * warp; l < owned; l += 2 * nw) {
+        const int jA = blockIdx.x + G * l;
+        const int jB = (l + 1 < owned) ? jA + G : -1;
+        const bool nbA = s.pos[jA] < 0;
+        const bool nbB = jB >= 0 && s.pos[jB] < 0;
+        if (nbA && nbB) {
+            const double2* ca = reinterpret_cast<const double2*>(s.A_cm + (size_t)jA * P.ld);
+            const double2* cb = reinterpret_cast<const double2*>(s.A_cm + (size_t)jB * P.ld);
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+            int k = lane;
+#pragma unroll 2
+            for (; k + 32 < half; k += 64) {
+                const double2 u0 = __ldcs(ca + k), u1 = __ldcs(ca + k + 32);
+                const double2 v0 = __ldcs(cb + k), v1 = __ldcs(cb + k + 32);
+                const double2 y0 = y2[k], y1 = y2[k + 32];
+                a0 = fma(u0.x, y0.x, a0); a1 = fma(u0.y, y0.y, a1);
+                a2 = fma(u1.x, y1.x, a2); a3 = fma(u1.y, y1.y, a3);
+                b0 = fma(v0.x, y0.x, b0); b1 = fma(v0.y, y0.y, b1);
+                b2 = fma(v1.x, y1.x, b2); b3 = fma(v1.y, y1.y, b3);
+            }
+            for (; k < half; k += 32) {
+                const double2 u0 = __ldcs(ca + k), v0 = __ldcs(cb + k), y0 = y2[k];
+                a0 = fma(u0.x, y0.x, a0); a1 = fma(u0.y, y0.y, a1);
+                b0 = fma(v0.x, y0.x, b0); b1 = fma(v0.y, y0.y, b1);
+            }
+            const double da = s.c[jA] - warp_sum((a0 + a1) + (a2 + a3));
+            const double db = s.c[jB] - warp_sum((b0 + b1) + (b2 + b3));
+            cand_offer(cand, da, jA, s.tabu_until[jA] <= it, P.tol_d);
+            cand_offer(cand, db, jB, s.tabu_until[jB] <= it, P.tol_d);
+        } else if (nbA || nbB) {
+            const int j = nbA ? jA : jB;
+            const double2* col = reinterpret_cast<const double2*>(s.A_cm + (size_t)j * P.ld);
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int k = lane;
 #pragma unroll 4
-        for (; k + 32 < half; k += 64) {
-            const double2 u = __ldcs(col + k);
-            const double2 v = __ldcs(col + k + 32);
-            const double2 yu = y2[k];
-            const double2 yv = y2[k + 32];
-            a0 = fma(u.x, yu.x, a0);
-            a1 = fma(u.y, yu.y, a1);
-            a2 = fma(v.x, yv.x, a2);
-            a3 = fma(v.y, yv.y, a3);
+            for (; k + 32 < half; k += 64) {
+                const double2 u = __ldcs(col + k), v = __ldcs(col + k + 32);
+                const double2 yu = y2[k], yv = y2[k + 32];
+                a0 = fma(u.x, yu.x, a0); a1 = fma(u.y, yu.y, a1);
+                a2 = fma(v.x, yv.x, a2); a3 = fma(v.y, yv.y, a3);
+            }
+            for (; k < half; k += 32) {
+                const double2 u = __ldcs(col + k), yu = y2[k];
+                a0 = fma(u.x, yu.x, a0); a1 = fma(u.y, yu.y, a1);
+            }
+            const double d = s.c[j] - warp_sum((a0 + a1) + (a2 + a3));
+            cand_offer(cand, d, j, s.tabu_until[j] <= it, P.tol_d);
         }
-        for (; k < half; k += 32) {
-            const double2 u = __ldcs(col + k);
-            const double2 yu = y2[k];
-            a0 = fma(u.x, yu.x, a0);
-            a1 = fma(u.y, yu.y, a1);
-        }
-        const double dot = warp_sum((a0 + a1) + (a2 + a3));
-        const double d = s.c[j] - dot;
-        cand_offer(cand, d, j, s.tabu_until[j] <= it, P.tol_d);
     }
     // slack columns: d_{n+i} = -y_i
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.m; i += gridDim.x * blockDim.x) {
@@ -346,58 +374,99 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(DevState s) {
     const double* acur = s.alpha + (size_t)ab * P.ld;
     double* anxt = s.alpha + (size_t)(ab ^ 1) * P.ld;
     const int lane = threadIdx.x & 31;
-    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int half = P.ld >> 1;
     const double2* aq2 = reinterpret_cast<const double2*>(aq);
     const double2* rh2 = reinterpret_cast<const double2*>(rh);
     double tmin = DBL_MAX;
-    for (int i = gwarp; i < P.m; i += nwarps) {
-        double2* row = reinterpret_cast<double2*>(s.binv + (size_t)i * P.ld);
-        double a0 = 0.0, a1 = 0.0;
-        if (do_upd && i == r) {
-            for (int k = lane; k < half; k += 32) {
-                const double2 v = rh2[k];
-                __stcs(row + k, v);
-                const double2 w = aq2[k];
-                a0 = fma(v.x, w.x, a0);
-                a1 = fma(v.y, w.y, a1);
+    // Rows are dealt to blocks round-robin (block b owns i = b, b+G, ...) so
+    // every SM gets the same share; each warp takes two owned rows at a time.
+    const int G = gridDim.x;
+    const int owned = (P.m - (int)blockIdx.x + G - 1) / G;
+    for (int l = 2 * warp; l < owned; l += 2 * nw) {
+        const int i0 = blockIdx.x + G * l;
+        const int i1 = (l + 1 < owned) ? i0 + G : -1;
+        double al0 = 0.0, al1 = 0.0;
+        const bool pair = i1 >= 0 && !(do_upd && (i0 == r || i1 == r));
+        if (pair) {
+            double2* r0 = reinterpret_cast<double2*>(s.binv + (size_t)i0 * P.ld);
+            double2* r1 = reinterpret_cast<double2*>(s.binv + (size_t)i1 * P.ld);
+            double a0 = 0.0, a1 = 0.0, c0 = 0.0, c1 = 0.0;
+            if (do_upd) {
+                const double na0 = -acur[i0], na1 = -acur[i1];
+                const bool st0 = na0 != 0.0, st1 = na1 != 0.0;
+                if (do_ftran) {
+#pragma unroll 2
+                    for (int k = lane; k < half; k += 32) {
+                        double2 v = __ldcs(r0 + k), u = __ldcs(r1 + k);
+                        const double2 p = rh2[k], w = aq2[k];
+                        v.x = fma(na0, p.x, v.x); v.y = fma(na0, p.y, v.y);
+                        u.x = fma(na1, p.x, u.x); u.y = fma(na1, p.y, u.y);
+                        if (st0) __stcs(r0 + k, v);
+                        if (st1) __stcs(r1 + k, u);
+                        a0 = fma(v.x, w.x, a0); a1 = fma(v.y, w.y, a1);
+                        c0 = fma(u.x, w.x, c0); c1 = fma(u.y, w.y, c1);
+                    }
+                } else {
+#pragma unroll 2
+                    for (int k = lane; k < half; k += 32) {
+                        double2 v = __ldcs(r0 + k), u = __ldcs(r1 + k);
+                        const double2 p = rh2[k];
+                        v.x = fma(na0, p.x, v.x); v.y = fma(na0, p.y, v.y);
+                        u.x = fma(na1, p.x, u.x); u.y = fma(na1, p.y, u.y);
+                        if (st0) __stcs(r0 + k, v);
+                        if (st1) __stcs(r1 + k, u);
+                    }
+                }
+            } else {
+#pragma unroll 4
+                for (int k = lane; k < half; k += 32) {
+                    const double2 v = __ldcs(r0 + k), u = __ldcs(r1 + k), w = aq2[k];
+                    a0 = fma(v.x, w.x, a0); a1 = fma(v.y, w.y, a1);
+                    c0 = fma(u.x, w.x, c0); c1 = fma(u.y, w.y, c1);
+                }
             }
-        } else if (do_upd) {
-            const double na = -acur[i];
-            if (na != 0.0) {
-#pragma unroll 4
-                for (int k = lane; k < half; k += 32) {
-                    double2 v = __ldcs(row + k);
-                    const double2 p = rh2[k];
-                    v.x = fma(na, p.x, v.x);
-                    v.y = fma(na, p.y, v.y);
-                    __stcs(row + k, v);
-                    const double2 w = aq2[k];
-                    a0 = fma(v.x, w.x, a0);
-                    a1 = fma(v.y, w.y, a1);
-                }
-            } else if (do_ftran) {
-#pragma unroll 4
-                for (int k = lane; k < half; k += 32) {
-                    const double2 v = __ldcs(row + k);
-                    const double2 w = aq2[k];
-                    a0 = fma(v.x, w.x, a0);
-                    a1 = fma(v.y, w.y, a1);
-                }
+            if (do_ftran) {
+                al0 = warp_sum(a0 + a1);
+                al1 = warp_sum(c0 + c1);
             }
         } else {
-#pragma unroll 4
-            for (int k = lane; k < half; k += 32) {
-                const double2 v = __ldcs(row + k);
-                const double2 w = aq2[k];
-                a0 = fma(v.x, w.x, a0);
-                a1 = fma(v.y, w.y, a1);
+            // single rows: the pivot row, or the odd row left over
+            for (int h = 0; h < 2; ++h) {
+                const int i = h == 0 ? i0 : i1;
+                if (i < 0) continue;
+                double2* row = reinterpret_cast<double2*>(s.binv + (size_t)i * P.ld);
+                double a0 = 0.0, a1 = 0.0;
+                if (do_upd && i == r) {
+                    for (int k = lane; k < half; k += 32) {
+                        const double2 v = rh2[k];
+                        __stcs(row + k, v);
+                        const double2 w = aq2[k];
+                        a0 = fma(v.x, w.x, a0); a1 = fma(v.y, w.y, a1);
+                    }
+                } else {
+                    const double na = do_upd ? -acur[i] : 0.0;
+                    const bool st = na != 0.0;
+                    for (int k = lane; k < half; k += 32) {
+                        double2 v = __ldcs(row + k);
+                        if (st) {
+                            const double2 p = rh2[k];
+                            v.x = fma(na, p.x, v.x); v.y = fma(na, p.y, v.y);
+                            __stcs(row + k, v);
+                        }
+                        const double2 w = aq2[k];
+                        a0 = fma(v.x, w.x, a0); a1 = fma(v.y, w.y, a1);
+                    }
+                }
+                const double al = warp_sum(a0 + a1);
+                if (h == 0) al0 = al; else al1 = al;
             }
         }
-        if (do_ftran) {
-            const double al = warp_sum(a0 + a1);
-            if (lane == 0) {
+        if (do_ftran && lane == 0) {
+            for (int h = 0; h < 2; ++h) {
+                const int i = h == 0 ? i0 : i1;
+                if (i < 0) continue;
+                const double al = h == 0 ? al0 : al1;
                 anxt[i] = al;
                 double th = DBL_MAX;
                 if (al > P.tol_piv) th = s.bbar[i] / al;

@@ -112,15 +112,15 @@ int setup_geometry(lp_handle* h) {
     g.price_threads = 512;
     g.update_threads = 512;
     g.pivot_threads = 256;
-    // PRICE: one warp per nonbasic column; no more warps than columns
-    const int warps_p = g.price_threads / 32;
-    int pb = g.sms * occ_p;
-    pb = std::min(pb, std::max(1, (h->n + warps_p - 1) / warps_p));
+    // PRICE: columns dealt round-robin to sms * min(occupancy, 2) blocks
+    // (a whole number of blocks per SM), two columns per warp.
+    int pb = g.sms * std::min(occ_p, 2);
+    pb = std::min(pb, std::max(1, (h->n + 1) / 2));
     g.price_blocks = std::max(1, pb);
-    // UPDATE: one warp per row
-    const int warps_u = g.update_threads / 32;
-    int ub = g.sms * occ_u;
-    ub = std::min(ub, std::max(1, (h->m + warps_u - 1) / warps_u));
+    // UPDATE: rows dealt round-robin to one block per SM, two rows per warp
+    // (one block per SM keeps the staging of rho and a_q to one copy per SM).
+    (void)occ_u;
+    int ub = std::min(g.sms, std::max(1, (h->m + 1) / 2));
     g.update_blocks = std::max(1, ub);
     g.pivot_blocks = std::max(1, std::min(g.sms, (h->ld + g.pivot_threads - 1) / g.pivot_threads));
     return LP_OK;
