@@ -169,6 +169,44 @@ int lp_get_state(const lp_handle* h, double* binv, double* bbar);
 int lp_get_trace(const lp_handle* h, int32_t* q, int32_t* r, double* theta,
                  double* dq, int32_t* flags, int32_t cap, int32_t* count);
 
+/*
+ * lp_price_static -- reduced costs and Dantzig's entering choice for callers
+ * that cannot allocate memory.  The paper has no counterpart: this entry point
+ * exists for callers such as code that runs inside a CUDA graph it is
+ * capturing itself, or a runtime whose device memory is fixed up front, where
+ * a cudaMalloc (even one hidden inside a library) is not allowed.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Computes d_j = c_j - y^T a_j for every nonbasic structural j and
+ * d_{n+i} = -y_i for every nonbasic slack i, and writes the largest d_j > tol_d
+ * (exact ties to the smallest j) to *q_out with its value in *dq_out;
+ * *q_out = -1 when no d_j exceeds tol_d (the basis is optimal).  The tabu
+ * rule is not applied.
+ *
+ * All pointers are DEVICE pointers owned by the caller:
+ *  A_colmajor  n columns of lda doubles (column j at A_colmajor + j*lda),
+ *              16-byte aligned; only the first m entries of a column are read
+ *  lda         >= m and even
+ *  c (n), y (m), pos (n+m: pos[j] >= 0 marks a basic variable)
+ *  q_out (1 int32), dq_out (1 double)
+ *  cuda_stream cudaStream_t (NULL: the legacy default stream); the call only
+ *              enqueues work and returns
+ * Limits: 1 <= m <= LP_PRICE_STATIC_MAX_M (y is staged in shared memory),
+ * n >= 1; larger sizes return LP_ERR_INVALID_ARG without touching the GPU.
+ *
+ * Scratch: 17 KB of partial results live in a file-scope device array that
+ * every GPU loading this library holds until the process exits.  All calls
+ * share it and it keeps the last call's contents (the counter that must start
+ * at zero is cleared by every call), so calls whose kernels overlap on the GPU
+ * race with each other: serialise them, e.g. on one stream.  The first call
+ * on a device looks up the array's device address and sets the kernel's
+ * shared-memory limit; make that first call before any stream capture.
+ */
+#define LP_PRICE_STATIC_MAX_M 12288
+int lp_price_static(int32_t m, int32_t n, const double* A_colmajor, int32_t lda,
+                    const double* c, const double* y, const int32_t* pos, double tol_d,
+                    int32_t* q_out, double* dq_out, void* cuda_stream);
+
 /* lp_destroy -- frees the handle and its device memory (NULL is ignored). */
 void lp_destroy(lp_handle* h);
 

@@ -85,6 +85,8 @@ def _load():
     lib.lp_destroy.restype = None
     lib.lp_strerror.argtypes = [ctypes.c_int]
     lib.lp_strerror.restype = ctypes.c_char_p
+    lib.lp_price_static.argtypes = [i32, i32, vp, i32, vp, vp, vp, ctypes.c_double, vp, vp, vp]
+    lib.lp_price_static.restype = ctypes.c_int
     return lib
 
 
@@ -235,3 +237,15 @@ class LP:
                                  ctypes.byref(cnt)), "lp_get_trace")
         k = cnt.value
         return dict(q=q[:k], r=r[:k], theta=th[:k], dq=dq[:k], flags=fl[:k])
+
+
+LP_PRICE_STATIC_MAX_M = 12288
+
+
+def price_static(m: int, n: int, A_colmajor, lda: int, c, y, pos, tol_d: float, q_out, dq_out,
+                 stream=None) -> int:
+    """lp_price_static: allocation-free PRICE + Dantzig CHUZC on caller-owned
+    device tensors (torch CUDA tensors); returns the C return code."""
+    st = None if stream is None else ctypes.c_void_p(stream)
+    return _lib.lp_price_static(int(m), int(n), _ptr(A_colmajor), int(lda), _ptr(c), _ptr(y), _ptr(pos),
+                                float(tol_d), _ptr(q_out), _ptr(dq_out), st)
