@@ -146,6 +146,48 @@ def cpu_baseline(A, b, c, iters: int):
                       f"(single-threaded plain C FP64 revised simplex), {dt:.1f} s"}
 
 
+def run_batched(lpgb, args, with_cpu: bool):
+    """4096 independent dense integer LPs (m uniform 16..256, n uniform
+    m..2m, each generated like the 200x200 dense integer workload) solved in
+    persistent launches; per-bucket launch configuration from the autotuner."""
+    import numpy as np
+    import lpgen
+    count = args.batch_count
+    ms, ns = lpgen.batch_sizes(count, seed=3)
+    probs = [lpgen.batch_lp(k, int(ms[k]), int(ns[k])) for k in range(count)]
+    with lpgb.Batch(probs) as bt:
+        table = bt.tune(trials=1)
+        for _ in range(max(1, args.warmup)):
+            bt.solve()
+        secs, its, fl = 0.0, 0, 0.0
+        steps = max(1, args.steps)
+        for _ in range(steps):
+            r = bt.solve()
+            secs += r["seconds"]
+            its += r["iterations"]
+            fl += r["fp64_flops"]
+        st, it, obj, xs, ys = bt.results()
+        solved = int(np.sum(st == 1))
+    out = {"metric": "batched LPs/s", "value": count * steps / secs, "unit": "LPs/s",
+           "config": {"workload": "batch_4096_small", "count": count, "m": "uniform 16..256",
+                      "n": "uniform m..2m", "price": "BF16 screen, top 8 re-priced in FP64",
+                      "tuning": [int(v) for v in table]},
+           "seconds_per_batch": secs / steps, "pivots_per_batch": its // steps, "solved": solved,
+           "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": fl / secs / 1e12,
+                        "peak": FP64_PEAK_TFLOPS, "frac": fl / secs / 1e12 / FP64_PEAK_TFLOPS,
+                        "what": "algorithmic FP64 flops of FTRAN, the B^-1 update and re-pricing"}}
+    if with_cpu:
+        import oracle
+        sample = 32
+        t0 = time.perf_counter()
+        for k in range(sample):
+            oracle.solve(*probs[k])
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": sample / dt, "unit": "LPs/s", "cores": 1, "kind": "oracle",
+                               "sample": f"first {sample} LPs of the batch, single-threaded oracle, {dt:.1f} s"}
+    return out
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -186,6 +228,9 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=128, help="pivots of the CPU baseline sample")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-variants", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--max-iters", type=int, default=0,
                     help="stop every solve after this many pivots (profiling runs only)")
     args = ap.parse_args()
@@ -305,9 +350,40 @@ def main():
                "h2d_bytes_per_step": 8 * (m * n + m + n), "d2h_bytes_per_step": 8 * (n + m) + 8,
                "seconds_per_step": t_e2e / args.e2e_steps}
 
+    # variant: BF16-screened PRICE with the top 16 re-priced in FP64 (same
+    # FP64 UPDATE/FTRAN/ratio test/reinversion; optimality certified in FP64)
+    variants = {}
+    if not args.skip_variants:
+        At, bt, ct = (torch.from_numpy(v).cuda() for v in (A, b, c))
+        with lpgb.LP(At, bt, ct, kernel_timing=1, cuda_stream=stream.cuda_stream, price_mode=1, topk=16,
+                     **extra) as lpv:
+            del At, bt, ct
+            lpv.solve()  # warm-up
+            lpv.reset()
+            torch.cuda.synchronize()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            rv = lpv.solve()
+            v1.record(stream)
+            torch.cuda.synchronize()
+            tv = v0.elapsed_time(v1) * 1e-3
+            zv = lpv.solution()[2]
+        variants["bf16_price_top16"] = {
+            "value": rv.iterations / tv, "unit": "iters/s", "time_to_optimum_s": tv,
+            "pivots_per_solve": rv.iterations, "objective": zv,
+            "objective_rel_err_vs_fp64_path": abs(zv - z) / max(1.0, abs(z)),
+            "us_per_price": 1e6 * rv.price_seconds / max(1, rv.price_launches),
+            "price_hbm_gbs": rv.price_bytes / rv.price_seconds / 1e9 if rv.price_seconds else None,
+            "status": rv.status_name}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
         cpu = cpu_baseline(A, b, c, args.cpu_iters)
+
+    batched = None
+    if not args.skip_batch:
+        batched = run_batched(lpgb, args, rank == 0 and ws == 1 and not args.skip_cpu)
 
     launches = sum(r.kernel_launches + 1 for r in results)  # +1: the reset kernel of each step
     if rank == 0:
@@ -331,6 +407,8 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "variants": variants,
+            "batched": batched,
             "gpu_launches": launches,
             "clocks": clocks,
         }

@@ -52,6 +52,7 @@ extern "C" {
 #define LP_TF_ASPIRATION 4      /* every improving candidate was tabu */
 #define LP_TF_BLAND 8           /* Bland safety net active */
 #define LP_TF_TIE_SET 64        /* the ratio test had more than one tied row */
+#define LP_TF_GUIDED 128        /* the entering variable came from lp_set_priority */
 
 typedef struct lp_handle lp_handle;
 
@@ -66,8 +67,9 @@ typedef struct lp_options {
     int32_t tabu_tenure;    /* iterations a tabu variable may not enter (0: rule off) */
     int32_t max_iters;      /* iteration limit */
     int32_t bland_after;    /* consecutive degenerate pivots before Bland's rule (0: off) */
-    int32_t price_mode;     /* 0: FP64 PRICE (the only mode of this version) */
-    int32_t topk;           /* reserved for price_mode 1 */
+    int32_t price_mode;     /* 0: FP64 PRICE; 1: BF16 screen, top-k re-priced in FP64,
+                               full FP64 PRICE whenever no candidate improves */
+    int32_t topk;           /* price_mode 1: candidates re-priced in FP64 (1..32) */
     int32_t trace_cap;      /* record (q, r, theta, d_q, flags) of the first trace_cap pivots */
     int32_t graph_iters;    /* pivots per captured CUDA graph launch */
     int32_t kernel_timing;  /* 1: time every PRICE and UPDATE launch with CUDA events */
@@ -99,6 +101,8 @@ typedef struct lp_result {
     int32_t price_launches;  /* kernel_timing: PRICE launches timed */
     int32_t update_launches; /* kernel_timing: UPDATE launches timed */
     int64_t kernel_launches; /* all kernels this call launched (graph nodes included) */
+    int32_t warm_repairs;    /* lp_set_basis_repair: repair pivots performed */
+    int32_t warm_fallback;   /* 1: the proposal was unusable, the solve started from the slack basis */
 } lp_result;
 
 /* Fills *opt with the defaults listed above. */
@@ -131,6 +135,43 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A_rowmajor,
  * LP_ERR_SINGULAR.
  */
 int lp_set_basis(lp_handle* h, const int32_t* basis_m);
+
+/*
+ * lp_update_problem -- replaces A, b, c of a handle with a new problem of the
+ * same m and n (same conventions as lp_create) and returns to the slack basis,
+ * reusing every device buffer and the captured graph.  For families of LPs
+ * (for example the perturbed instances a learned warm start is trained on).
+ */
+int lp_update_problem(lp_handle* h, const double* A_rowmajor, const double* b, const double* c,
+                      int32_t inputs_on_device);
+
+/*
+ * lp_set_priority -- guided entering rule for warm starts (price_mode 0 only;
+ * LP_ERR_STATE otherwise).  vars (host) lists `count` distinct variables (a
+ * predicted set).  While any listed variable is nonbasic, not tabu and
+ * improving (d_j > tol_d), CHUZC enters the listed one with the largest d_j
+ * (Dantzig's rule restricted to the list); otherwise the normal rule applies,
+ * so the solve first works on the predicted columns.  Every pivot is still
+ * an ordinary ratio-test pivot, so primal feasibility is never lost and the
+ * optimum is certified by the usual test.  count = 0 clears the list; the
+ * list survives lp_reset and lp_update_problem.
+ */
+int lp_set_priority(lp_handle* h, const int32_t* vars, int32_t count);
+
+/*
+ * lp_set_basis_repair -- warm start from a proposed basis that may be primal
+ * infeasible (the paper has no warm start; this is the repair of the learned
+ * warm start).  When the next lp_solve starts, B^-1 is rebuilt from the
+ * proposal (basis_m: m distinct variables, host pointer).  While some basic
+ * value is negative, the most negative position p leaves and the nonbasic
+ * slack with the most negative B^-1[p][s] enters -- an ordinary tableau pivot
+ * that makes position p positive and keeps B nonsingular -- for at most
+ * max_repairs pivots (counted as iterations).  A singular proposal, or one
+ * still infeasible after max_repairs, is dropped and the solve starts from the
+ * slack basis (lp_result.warm_fallback = 1).  The primal simplex then runs to
+ * the optimum as usual.
+ */
+int lp_set_basis_repair(lp_handle* h, const int32_t* basis_m, int32_t max_repairs);
 
 /* lp_reset -- return to the slack basis and clear all counters. */
 int lp_reset(lp_handle* h);
@@ -206,6 +247,125 @@ int lp_get_trace(const lp_handle* h, int32_t* q, int32_t* r, double* theta,
 int lp_price_static(int32_t m, int32_t n, const double* A_colmajor, int32_t lda,
                     const double* c, const double* y, const int32_t* pos, double tol_d,
                     int32_t* q_out, double* dq_out, void* cuda_stream);
+
+/* ---- batches of small LPs ------------------------------------------------ */
+
+/*
+ * A batch holds many independent small LPs that are solved in persistent
+ * launches: one CTA solves one LP at a time (Steps 1-8 of Section 2.1 with the
+ * tabu rule of Sections 2.2/3.4 and reinversion every reinvert_every pivots),
+ * taking LPs from an atomic work queue per size bucket (m <= 64, 128, 192,
+ * 256).  For batches price_mode defaults to 1: a BF16 screen of the columns,
+ * the top `topk` (at most 8 here) re-priced in FP64, and the full FP64 PRICE
+ * whenever no candidate improves, so optimality is always certified in FP64.
+ */
+typedef struct lp_batch lp_batch;
+
+#define LP_BATCH_MAX_M 256
+#define LP_BATCH_MAX_N 512
+
+typedef struct lp_batch_result {
+    int32_t solved;          /* LPs that ended optimal */
+    int32_t unbounded;
+    int32_t iter_limit;
+    int32_t failed;          /* LPs whose reinversion met a singular basis */
+    int64_t iterations;      /* pivots summed over the batch */
+    double seconds;          /* device time of the solve (CUDA events) */
+    double fp64_flops;       /* algorithmic FP64 flops: FTRAN + update + re-pricing */
+} lp_batch_result;
+
+/*
+ * lp_batch_create -- copies `count` LPs to the GPU.  m[k], n[k] (host arrays)
+ * give the sizes (1 <= m <= LP_BATCH_MAX_M, 1 <= n <= LP_BATCH_MAX_N).  A holds
+ * every A_k row-major, one after another; b every b_k (all >= 0) and c every
+ * c_k, likewise concatenated.  inputs_on_device selects host (0) or device (1)
+ * pointers for A, b, c.  opt: NULL for the defaults (price_mode 1, topk 8);
+ * trace_cap > 0 records each LP's first trace_cap pivots.
+ */
+int lp_batch_create(lp_batch** out, int32_t count, const int32_t* m, const int32_t* n,
+                    const double* A, const double* b, const double* c,
+                    int32_t inputs_on_device, const lp_options* opt);
+
+/* lp_batch_solve -- solves every LP of the batch from its slack basis. */
+int lp_batch_solve(lp_batch* h, lp_batch_result* out);
+
+/*
+ * lp_batch_get -- per-LP results into host arrays (any may be NULL): status
+ * and iterations (count each), objective (count), x (sum of n_k, concatenated)
+ * and duals y (sum of m_k, concatenated).  LP_ERR_STATE before a solve.
+ */
+int lp_batch_get(const lp_batch* h, int32_t* status, int32_t* iterations, double* objective,
+                 double* x, double* y);
+
+/* lp_batch_get_trace -- entering variable q and leaving position r of LP k's
+   first min(cap, recorded) pivots (needs trace_cap > 0). */
+int lp_batch_get_trace(const lp_batch* h, int32_t k, int32_t* q, int32_t* r, int32_t cap,
+                       int32_t* count);
+
+/*
+ * Autotuner.  table[2*b] = threads per CTA (128, 256 or 512) and
+ * table[2*b+1] = 1 to keep B^-1 in shared memory (only where it fits) or 0
+ * for an L2-resident global slot, for size buckets b = 0..3.
+ * lp_batch_tune times every valid configuration of every non-empty bucket on
+ * the batch itself (`trials` solves each), keeps the fastest, and writes the
+ * table if it is not NULL; lp_batch_set_tuning installs a saved table.
+ */
+int lp_batch_tune(lp_batch* h, int32_t* table, int32_t trials);
+int lp_batch_set_tuning(lp_batch* h, const int32_t* table);
+
+/* lp_batch_destroy -- frees the batch (NULL is ignored). */
+void lp_batch_destroy(lp_batch* h);
+
+/* ---- learned warm start: the network ------------------------------------ */
+
+/*
+ * A 3-layer perceptron in -> hidden -> hidden -> out with ReLU, trained with
+ * binary cross-entropy on logits, L = (1/B) sum_b sum_o [softplus(z) - t z],
+ * and Adam (beta 0.9 / 0.999, eps 1e-8).  The GEMMs run on the tensor cores
+ * with FP16 operands and FP32 accumulation; FP32 master weights and Adam
+ * moments are kept on the device.  Parameters are packed W1 (in x hidden,
+ * row-major), b1, W2 (hidden x hidden), b2, W3 (hidden x out), b3.  X and T
+ * are DEVICE pointers to FP32 row-major [batch x in] and [batch x out];
+ * params and grads are HOST pointers; the handle runs on cuda_stream.  The
+ * paper has no learned component: this is the warm start of this design.
+ */
+typedef struct lp_mlp lp_mlp;
+int lp_mlp_create(lp_mlp** out, int32_t in_dim, int32_t hidden, int32_t out_dim,
+                  int32_t max_batch, void* cuda_stream);
+int64_t lp_mlp_num_params(const lp_mlp* h);
+int lp_mlp_set_params(lp_mlp* h, const float* params);        /* also resets Adam */
+int lp_mlp_get_params(const lp_mlp* h, float* params);
+/* logits: DEVICE pointer [batch x out]; enqueued on the handle's stream */
+int lp_mlp_forward(lp_mlp* h, const float* X, int32_t batch, float* logits);
+/* loss and the gradient of every parameter (host), without an update */
+int lp_mlp_gradients(lp_mlp* h, const float* X, const float* T, int32_t batch,
+                     float* grads, float* loss);
+/* one Adam step with learning rate lr; *loss (host, may be NULL) is the batch loss */
+int lp_mlp_train_step(lp_mlp* h, const float* X, const float* T, int32_t batch, float lr,
+                      float* loss);
+void lp_mlp_destroy(lp_mlp* h);
+
+/* ---- learned warm start: LP families ------------------------------------- */
+
+/*
+ * lp_family_perturb -- one instance of the family of a base LP (A0, b0, c0):
+ * every entry of A, b and c is the base entry times an independent N(1, sigma^2)
+ * draw (Box-Muller on SplitMix64 in counter mode under `key`, pairs of draws in
+ * the order A row-major, then b, then c).  All pointers are DEVICE pointers
+ * (A0, A: m x n row-major); nothing is allocated; enqueued on cuda_stream.
+ */
+int lp_family_perturb(int32_t m, int32_t n, const double* A0, const double* b0, const double* c0,
+                      uint64_t key, double sigma, double* A, double* b, double* c, void* cuda_stream);
+
+/*
+ * lp_family_features -- the 2(m+n) network inputs of an instance (DEVICE
+ * float32 out): (b/b0 - 1)/sigma (m), (c/c0 - 1)/sigma (n), then the row (m)
+ * and column (n) means of A/A0 over the nonzero entries of A0, minus 1, times
+ * sqrt(count)/sigma.  Device pointers; nothing is allocated.
+ */
+int lp_family_features(int32_t m, int32_t n, const double* A0, const double* b0, const double* c0,
+                       const double* A, const double* b, const double* c, double sigma,
+                       float* features, void* cuda_stream);
 
 /* lp_destroy -- frees the handle and its device memory (NULL is ignored). */
 void lp_destroy(lp_handle* h);

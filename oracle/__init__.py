@@ -58,7 +58,7 @@ def build(force: bool = False) -> str:
 class _Opts(ctypes.Structure):
     _fields_ = [("reinvert_every", ctypes.c_int32), ("tabu_tenure", ctypes.c_int32),
                 ("max_iters", ctypes.c_int32), ("bland_after", ctypes.c_int32),
-                ("ratio_rule", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("ratio_rule", ctypes.c_int32), ("follow_relaxed", ctypes.c_int32),
                 ("tol_d", ctypes.c_double), ("tol_piv", ctypes.c_double),
                 ("tol_tie", ctypes.c_double), ("tie_cmp", ctypes.c_double)]
 
@@ -111,6 +111,7 @@ class Options:
     max_iters: int = 1_000_000
     bland_after: int = 50
     ratio_rule: int = 0
+    follow_relaxed: int = 0
     tol_d: float = 1e-9
     tol_piv: float = 1e-9
     tol_tie: float = 1e-12
@@ -156,7 +157,7 @@ def solve(A, b, c, opts: Options | None = None, start_basis=None, follow=None,
     c = np.ascontiguousarray(c, dtype=np.float64)
     m, n = A.shape
     assert b.shape == (m,) and c.shape == (n,)
-    copts = _Opts(o.reinvert_every, o.tabu_tenure, o.max_iters, o.bland_after, o.ratio_rule, 0,
+    copts = _Opts(o.reinvert_every, o.tabu_tenure, o.max_iters, o.bland_after, o.ratio_rule, o.follow_relaxed,
                   o.tol_d, o.tol_piv, o.tol_tie, o.tie_cmp)
     sb = None if start_basis is None else np.ascontiguousarray(start_basis, dtype=np.int32)
     fq = fr = None

@@ -54,7 +54,10 @@
  * differently, accepts that choice only if, in the oracle's own arithmetic, it
  * is tied with the oracle's choice to within `tie_cmp` (relative).  An
  * accepted choice is then adopted and the oracle continues from it, so the
- * whole foreign sequence is checked pivot by pivot.
+ * whole foreign sequence is checked pivot by pivot.  With `follow_relaxed`
+ * the entering choice only has to be an improving, eligible column (for
+ * solvers that screen the pricing in lower precision); the leaving row is
+ * still checked against the ratio test.
  */
 #include <math.h>
 #include <stdint.h>
@@ -84,7 +87,7 @@ typedef struct {
     int32_t max_iters;
     int32_t bland_after;    /* 0 = no Bland fallback */
     int32_t ratio_rule;     /* 0 = largest alpha in the tie set, 1 = smallest basic index */
-    int32_t pad_;
+    int32_t follow_relaxed; /* follow mode: accept any improving eligible entering column */
     double tol_d, tol_piv, tol_tie;
     double tie_cmp;         /* follow mode: relative tie window (1e-12) */
 } oracle_opts;
@@ -327,7 +330,12 @@ int oracle_solve(int m, int n, const double* A, const double* b, const double* c
                 } else if (ok) {
                     int asp = (flags & TF_ASPIRATION) != 0;
                     if (!asp && tabu_until[fq] > it) ok = 0;
-                    if (d[fq] < d[q] - eps * dmax(1.0, fabs(d[q]))) ok = 0;
+                    if (o->follow_relaxed) {
+                        /* any improving column is a valid simplex pivot */
+                        if (!(d[fq] > o->tol_d - eps * dmax(1.0, o->tol_d))) ok = 0;
+                    } else if (d[fq] < d[q] - eps * dmax(1.0, fabs(d[q]))) {
+                        ok = 0;
+                    }
                 }
                 if (!ok) {
                     res->status = OR_MISMATCH;

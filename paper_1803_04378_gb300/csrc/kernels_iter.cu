@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kPriceThreads = 512;
 constexpr int kUpdateThreads = 512;
-constexpr int kPivotThreads = 256;
+constexpr int kPivotThreads = 64;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -40,12 +40,14 @@ struct Cand {
     double d_all; int j_all;
     double d_nt;  int j_nt;
     double d_min; int j_min;
+    double d_pr;  int j_pr; int k_pr;
 };
 
 __device__ __forceinline__ void cand_init(Cand& c) {
     c.d_all = -DBL_MAX; c.j_all = -1;
     c.d_nt = -DBL_MAX; c.j_nt = -1;
     c.d_min = 0.0; c.j_min = -1;
+    c.d_pr = 0.0; c.j_pr = -1; c.k_pr = kNoRank;
 }
 
 // a beats b: larger d, exact ties to the smaller index.
@@ -55,16 +57,19 @@ __device__ __forceinline__ bool beats(double da, int ja, double db, int jb) {
     return da > db || (da == db && ja < jb);
 }
 
-__device__ __forceinline__ void cand_offer(Cand& c, double d, int j, bool nontabu, double tol_d) {
+__device__ __forceinline__ void cand_offer(Cand& c, double d, int j, bool nontabu, double tol_d, int rank) {
     if (beats(d, j, c.d_all, c.j_all)) { c.d_all = d; c.j_all = j; }
     if (nontabu && beats(d, j, c.d_nt, c.j_nt)) { c.d_nt = d; c.j_nt = j; }
     if (d > tol_d && (c.j_min < 0 || j < c.j_min)) { c.d_min = d; c.j_min = j; }
+    // guided rule: Dantzig restricted to the listed (priority) columns
+    if (nontabu && d > tol_d && rank != kNoRank && beats(d, j, c.d_pr, c.j_pr)) { c.d_pr = d; c.j_pr = j; c.k_pr = rank; }
 }
 
 __device__ __forceinline__ void cand_merge(Cand& c, const Cand& o) {
     if (beats(o.d_all, o.j_all, c.d_all, c.j_all)) { c.d_all = o.d_all; c.j_all = o.j_all; }
     if (beats(o.d_nt, o.j_nt, c.d_nt, c.j_nt)) { c.d_nt = o.d_nt; c.j_nt = o.j_nt; }
     if (o.j_min >= 0 && (c.j_min < 0 || o.j_min < c.j_min)) { c.d_min = o.d_min; c.j_min = o.j_min; }
+    if (beats(o.d_pr, o.j_pr, c.d_pr, c.j_pr)) { c.d_pr = o.d_pr; c.j_pr = o.j_pr; c.k_pr = o.k_pr; }
 }
 
 __device__ __forceinline__ Cand cand_shfl(const Cand& c, int off) {
@@ -75,6 +80,9 @@ __device__ __forceinline__ Cand cand_shfl(const Cand& c, int off) {
     o.j_nt = __shfl_xor_sync(0xffffffffu, c.j_nt, off);
     o.d_min = __shfl_xor_sync(0xffffffffu, c.d_min, off);
     o.j_min = __shfl_xor_sync(0xffffffffu, c.j_min, off);
+    o.d_pr = __shfl_xor_sync(0xffffffffu, c.d_pr, off);
+    o.j_pr = __shfl_xor_sync(0xffffffffu, c.j_pr, off);
+    o.k_pr = __shfl_xor_sync(0xffffffffu, c.k_pr, off);
     return o;
 }
 
@@ -131,6 +139,7 @@ __global__ void k_init_slack(DevState s) {
     }
     for (size_t i = tid; i < (size_t)P.ld; i += stride) {
         s.y[i] = 0.0;
+        s.y32[i] = 0.f;
         s.rho[i] = 0.0;
         s.alpha[i] = 0.0;
         s.alpha[P.ld + i] = 0.0;
@@ -169,7 +178,9 @@ __global__ void __launch_bounds__(kPivotThreads) k_pivot(DevState s) {
     for (int k = tid; k < P.ld; k += stride) {
         const double rn = brow[k] / ar;
         s.rho[k] = rn;
-        s.y[k] = __dadd_rn(s.y[k], __dmul_rn(dq, rn));
+        const double yn = __dadd_rn(s.y[k], __dmul_rn(dq, rn));
+        s.y[k] = yn;
+        s.y32[k] = (float)yn;
     }
     for (int i = tid; i < P.m; i += stride) {
         if (i == r) s.bbar[i] = th;
@@ -226,6 +237,9 @@ __global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
     Ctrl* C = s.ctrl;
     if (C->status != kRunning) return;
     const Params& P = s.p;
+    // price_mode 1: this full FP64 pass only runs when the BF16 screen found no
+    // improving candidate, or under the Bland safety net
+    if (P.price_mode == 1 && !C->need_full && !C->bland) return;
     extern __shared__ double ysh[];
     for (int k = threadIdx.x; k < P.ld; k += blockDim.x) ysh[k] = s.y[k];
     __syncthreads();
@@ -269,8 +283,8 @@ __global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
             }
             const double da = s.c[jA] - warp_sum((a0 + a1) + (a2 + a3));
             const double db = s.c[jB] - warp_sum((b0 + b1) + (b2 + b3));
-            cand_offer(cand, da, jA, s.tabu_until[jA] <= it, P.tol_d);
-            cand_offer(cand, db, jB, s.tabu_until[jB] <= it, P.tol_d);
+            cand_offer(cand, da, jA, s.tabu_until[jA] <= it, P.tol_d, s.rank[jA]);
+            cand_offer(cand, db, jB, s.tabu_until[jB] <= it, P.tol_d, s.rank[jB]);
         } else if (nbA || nbB) {
             const int j = nbA ? jA : jB;
             const double2* col = reinterpret_cast<const double2*>(s.A_cm + (size_t)j * P.ld);
@@ -288,14 +302,14 @@ __global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
                 a0 = fma(u.x, yu.x, a0); a1 = fma(u.y, yu.y, a1);
             }
             const double d = s.c[j] - warp_sum((a0 + a1) + (a2 + a3));
-            cand_offer(cand, d, j, s.tabu_until[j] <= it, P.tol_d);
+            cand_offer(cand, d, j, s.tabu_until[j] <= it, P.tol_d, s.rank[j]);
         }
     }
     // slack columns: d_{n+i} = -y_i
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.m; i += gridDim.x * blockDim.x) {
         const int j = P.n + i;
         if (s.pos[j] >= 0) continue;
-        cand_offer(cand, -ysh[i], j, s.tabu_until[j] <= it, P.tol_d);
+        cand_offer(cand, -ysh[i], j, s.tabu_until[j] <= it, P.tol_d, s.rank[j]);
     }
     Cand bc = cand_block_reduce(cand);
     if (threadIdx.x == 0) {
@@ -303,6 +317,7 @@ __global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
         pc.d_all = bc.d_all; pc.j_all = bc.j_all;
         pc.d_nt = bc.d_nt; pc.j_nt = bc.j_nt;
         pc.d_min = bc.d_min; pc.j_min = bc.j_min;
+        pc.d_pr = bc.d_pr; pc.j_pr = bc.j_pr; pc.k_pr = bc.k_pr;
         pc.pad_ = 0;
         s.price_part[blockIdx.x] = pc;
     }
@@ -316,6 +331,7 @@ __global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
         o.d_all = __ldcg(&pp->d_all); o.j_all = __ldcg(&pp->j_all);
         o.d_nt = __ldcg(&pp->d_nt); o.j_nt = __ldcg(&pp->j_nt);
         o.d_min = __ldcg(&pp->d_min); o.j_min = __ldcg(&pp->j_min);
+        o.d_pr = __ldcg(&pp->d_pr); o.j_pr = __ldcg(&pp->j_pr); o.k_pr = __ldcg(&pp->k_pr);
         cand_merge(g, o);
     }
     g = cand_block_reduce(g);
@@ -323,6 +339,10 @@ __global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
         C->ticket_price = 0;
         C->bytes_price += 8.0 * P.m * (double)(P.n - C->nsb);
         C->n_price++;
+        if (P.price_mode == 1) {
+            C->need_full = 0;
+            C->n_full++;
+        }
         if (g.j_all < 0 || !(g.d_all > P.tol_d)) {
             C->status = kOptimal;
             C->q = -1;
@@ -332,6 +352,10 @@ __global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
             if (C->bland) {
                 q = g.j_min; dq = g.d_min;
                 C->flags |= kTfBland;
+            } else if (g.j_pr >= 0) {
+                // guided entering rule: Dantzig's choice among the listed columns
+                q = g.j_pr; dq = g.d_pr;
+                C->flags |= kTfGuided;
             } else if (g.j_nt >= 0 && g.d_nt > P.tol_d) {
                 q = g.j_nt; dq = g.d_nt;
             } else {
@@ -530,14 +554,25 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(DevState s) {
     const bool bland = C->bland != 0;
     RowCand best = {0.0, 0, -1};
     int cnt = 0;
-    for (int i = threadIdx.x; i < P.m; i += blockDim.x) {
-        const double al = __ldcg(anxt + i);
-        if (!(al > P.tol_piv)) continue;
-        const double th = __ldcg(s.theta + i);
-        if (!(th <= thr)) continue;
-        cnt++;
-        RowCand c = {al, s.basis[i], i};
-        if (row_beats(c, best, bland)) best = c;
+    // all loads of a chunk are issued before any is tested: one L2 round trip per chunk
+    constexpr int kU = 8;
+    for (int base = 0; base < P.m; base += kU * (int)blockDim.x) {
+        double al[kU], th[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = base + u * blockDim.x + threadIdx.x;
+            al[u] = i < P.m ? __ldcg(anxt + i) : 0.0;
+            th[u] = i < P.m ? __ldcg(s.theta + i) : DBL_MAX;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = base + u * blockDim.x + threadIdx.x;
+            if (i < P.m && al[u] > P.tol_piv && th[u] <= thr) {
+                cnt++;
+                RowCand c = {al[u], s.basis[i], i};
+                if (row_beats(c, best, bland)) best = c;
+            }
+        }
     }
     // block reduce (best, cnt)
     for (int o = 16; o > 0; o >>= 1) {
@@ -595,7 +630,10 @@ void launch_pivot(const DevState& s, const Geometry& g, cudaStream_t st) {
     k_pivot<<<g.pivot_blocks, kPivotThreads, 0, st>>>(s);
 }
 
+void launch_price_lp(const DevState& s, const Geometry& g, cudaStream_t st);
+
 void launch_price(const DevState& s, const Geometry& g, cudaStream_t st) {
+    if (s.p.price_mode == 1) launch_price_lp(s, g, st);
     k_price<<<g.price_blocks, kPriceThreads, price_smem_bytes(s.p.ld), st>>>(s);
 }
 

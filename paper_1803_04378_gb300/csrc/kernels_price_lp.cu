@@ -1,0 +1,282 @@
+// kernels_price_lp.cu -- mixed-precision PRICE (price_mode 1).
+//
+// Step 3 PRICE streams all of A every iteration, and on GB300 the FP64 pipe
+// (about 2 FMA/clock/SM) caps an FP64 GEMV near 70% of HBM bandwidth.  This
+// mode screens the columns with a BF16 copy of A (2 bytes/element, 4x fewer
+// bytes) and FP32 FMAs on the CUDA cores -- a matrix-vector product has no
+// reuse for tensor cores to exploit, so plain FMAs at HBM speed are the right
+// unit -- then re-prices the top k candidates exactly in FP64 and enters the
+// best of them.  Whenever no exactly re-priced candidate improves (or the
+// Bland safety net is on) the full FP64 PRICE runs, so optimality is always
+// certified in FP64 and the final objective equals the FP64 method's.  The
+// entering choice can differ from Dantzig's FP64 argmax when more than k
+// columns sit within the BF16 error of the maximum.
+//
+//   k_price_lp   BF16 screen: approximate d~_j over nonbasic, non-tabu
+//                structural columns; each block keeps its best two; exact
+//                slack candidates (d = -y_i) as well.  In the last block one
+//                warp picks the top k of the block bests.
+//   k_reprice    one block per candidate: exact FP64 d_j; the last block
+//                enters the best exact candidate, or asks for the full PRICE.
+#include "lpgb_internal.cuh"
+
+#include <cfloat>
+
+namespace lpgb {
+
+namespace {
+
+constexpr int kLpThreads = 512;
+constexpr int kSortN = 2048;  // >= 2 * price grid (block bests)
+
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// (d desc, j asc); j < 0 sorts last
+__device__ __forceinline__ bool cand_before(float da, int ja, float db, int jb) {
+    if (ja < 0) return false;
+    if (jb < 0) return true;
+    return da > db || (da == db && ja < jb);
+}
+
+__device__ __forceinline__ bool dbl_before(double da, int ja, double db, int jb) {
+    if (ja < 0) return false;
+    if (jb < 0) return true;
+    return da > db || (da == db && ja < jb);
+}
+
+__device__ __forceinline__ void top2_offer(float d, int j, float& d0, int& j0, float& d1, int& j1) {
+    if (cand_before(d, j, d0, j0)) {
+        d1 = d0; j1 = j0; d0 = d; j0 = j;
+    } else if (cand_before(d, j, d1, j1)) {
+        d1 = d; j1 = j;
+    }
+}
+
+__global__ void k_to_bf16(const double* __restrict__ src, uint16_t* __restrict__ dst, size_t count) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)src[e]);
+        dst[e] = *reinterpret_cast<const uint16_t*>(&h);
+    }
+}
+
+__global__ void __launch_bounds__(kLpThreads, 2) k_price_lp(DevState s) {
+    Ctrl* C = s.ctrl;
+    if (C->status != kRunning || C->bland) return;
+    const Params& P = s.p;
+    extern __shared__ float ysf[];
+    for (int k = threadIdx.x; k < P.ld; k += blockDim.x) ysf[k] = s.y32[k];
+    __syncthreads();
+    const int it = C->it;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int vecs = P.ld >> 3;  // 8 BF16 values per 16-byte load
+    const float4* y4 = reinterpret_cast<const float4*>(ysf);
+    float d0 = -FLT_MAX, d1 = -FLT_MAX;
+    int j0 = -1, j1 = -1;
+    const int G = gridDim.x;
+    const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
+    for (int l = warp; l < owned; l += nw) {
+        const int j = blockIdx.x + G * l;
+        if (s.pos[j] >= 0 || s.tabu_until[j] > it) continue;
+        const uint4* col = reinterpret_cast<const uint4*>(s.A_lp + (size_t)j * P.ld);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 4
+        for (int k = lane; k < vecs; k += 32) {
+            const uint4 u = __ldcs(col + k);
+            const float4 ya = y4[2 * k], yb = y4[2 * k + 1];
+            a0 = fmaf(bf16_lo(u.x), ya.x, a0);
+            a1 = fmaf(bf16_hi(u.x), ya.y, a1);
+            a2 = fmaf(bf16_lo(u.y), ya.z, a2);
+            a3 = fmaf(bf16_hi(u.y), ya.w, a3);
+            a0 = fmaf(bf16_lo(u.z), yb.x, a0);
+            a1 = fmaf(bf16_hi(u.z), yb.y, a1);
+            a2 = fmaf(bf16_lo(u.w), yb.z, a2);
+            a3 = fmaf(bf16_hi(u.w), yb.w, a3);
+        }
+        const float d = (float)s.c[j] - warp_sum_f((a0 + a1) + (a2 + a3));
+        top2_offer(d, j, d0, j0, d1, j1);
+    }
+    // exact slack candidates
+    double ds = -DBL_MAX;
+    int js = -1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.m; i += gridDim.x * blockDim.x) {
+        const int j = P.n + i;
+        if (s.pos[j] >= 0 || s.tabu_until[j] > it) continue;
+        const double d = -s.y[i];
+        if (dbl_before(d, j, ds, js)) { ds = d; js = j; }
+    }
+    // block reduction of (top2, slack best)
+    __shared__ float sd0[32], sd1[32];
+    __shared__ int sj0[32], sj1[32], sjs[32];
+    __shared__ double sds[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ods = __shfl_xor_sync(0xffffffffu, ds, o);
+        const int ojs = __shfl_xor_sync(0xffffffffu, js, o);
+        if (dbl_before(ods, ojs, ds, js)) { ds = ods; js = ojs; }
+    }
+    if (lane == 0) { sd0[warp] = d0; sj0[warp] = j0; sd1[warp] = d1; sj1[warp] = j1; sds[warp] = ds; sjs[warp] = js; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b0 = -FLT_MAX, b1 = -FLT_MAX;
+        int c0 = -1, c1 = -1;
+        double bs = -DBL_MAX;
+        int cs = -1;
+        for (int w = 0; w < nw; ++w) {
+            top2_offer(sd0[w], sj0[w], b0, c0, b1, c1);
+            top2_offer(sd1[w], sj1[w], b0, c0, b1, c1);
+            if (dbl_before(sds[w], sjs[w], bs, cs)) { bs = sds[w]; cs = sjs[w]; }
+        }
+        LpCand pc;
+        pc.d0 = b0; pc.j0 = c0; pc.d1 = b1; pc.j1 = c1; pc.ds = bs; pc.js = cs; pc.pad_ = 0;
+        s.lp_part[blockIdx.x] = pc;
+    }
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&C->ticket_lp, 1) == G - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // last block: warp 0 picks the top k of the 2G block bests (k rounds of a
+    // warp argmax over a shared-memory copy; no block-wide barriers)
+    __shared__ float kd[kSortN];
+    __shared__ int kj[kSortN];
+    const int nc = 2 * G;
+    for (int e = threadIdx.x; e < nc; e += blockDim.x) {
+        const LpCand* pp = s.lp_part + (e >> 1);
+        if (e & 1) { kd[e] = __ldcg(&pp->d1); kj[e] = __ldcg(&pp->j1); }
+        else { kd[e] = __ldcg(&pp->d0); kj[e] = __ldcg(&pp->j0); }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int t = 0; t < kMaxTopk; ++t) {
+            float bd = -FLT_MAX;
+            int bj = -1, be = -1;
+            if (t < P.topk) {
+                for (int e = lane; e < nc; e += 32)
+                    if (cand_before(kd[e], kj[e], bd, bj)) { bd = kd[e]; bj = kj[e]; be = e; }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                    const int oe = __shfl_xor_sync(0xffffffffu, be, o);
+                    if (cand_before(od, oj, bd, bj)) { bd = od; bj = oj; be = oe; }
+                }
+                if (lane == 0 && be >= 0) kj[be] = -1;  // taken
+                __syncwarp();
+            }
+            if (lane == 0) s.cand[t] = bj;
+        }
+    }
+    // best exact slack of the whole grid
+    double ds2 = -DBL_MAX;
+    int js2 = -1;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) {
+        const double od = __ldcg(&s.lp_part[b].ds);
+        const int oj = __ldcg(&s.lp_part[b].js);
+        if (dbl_before(od, oj, ds2, js2)) { ds2 = od; js2 = oj; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, ds2, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, js2, o);
+        if (dbl_before(od, oj, ds2, js2)) { ds2 = od; js2 = oj; }
+    }
+    __syncthreads();
+    if (lane == 0) { sds[warp] = ds2; sjs[warp] = js2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bs = -DBL_MAX;
+        int cs = -1;
+        for (int w = 0; w < nw; ++w)
+            if (dbl_before(sds[w], sjs[w], bs, cs)) { bs = sds[w]; cs = sjs[w]; }
+        s.cand[kMaxTopk] = cs;        // slot kMaxTopk: the best slack (exact already)
+        s.cand_d[kMaxTopk] = bs;
+        C->ticket_lp = 0;
+        C->bytes_price += 2.0 * P.m * (double)(P.n - C->nsb);
+        __threadfence();
+    }
+}
+
+// One block per candidate: exact FP64 reduced cost; the last block decides.
+constexpr int kRpThreads = 256;
+
+__global__ void __launch_bounds__(kRpThreads) k_reprice(DevState s) {
+    Ctrl* C = s.ctrl;
+    if (C->status != kRunning || C->bland) return;
+    const Params& P = s.p;
+    const int j = s.cand[blockIdx.x];
+    __shared__ double part[kRpThreads / 32];
+    if (j >= 0) {
+        const double2* col = reinterpret_cast<const double2*>(s.A_cm + (size_t)j * P.ld);
+        const double2* y2 = reinterpret_cast<const double2*>(s.y);
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll 8
+        for (int k = threadIdx.x; k < (P.ld >> 1); k += kRpThreads) {
+            const double2 u = __ldg(col + k), w = y2[k];
+            a0 = fma(u.x, w.x, a0);
+            a1 = fma(u.y, w.y, a1);
+        }
+        double t = a0 + a1;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < kRpThreads / 32; ++w) sum += part[w];
+            s.cand_d[blockIdx.x] = s.c[j] - sum;
+        }
+    }
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&C->ticket_rp, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    double bd = __ldcg(s.cand_d + kMaxTopk);
+    int bj = __ldcg(s.cand + kMaxTopk);
+    for (int e = 0; e < (int)gridDim.x; ++e) {
+        const int ej = __ldcg(s.cand + e);
+        if (ej < 0) continue;
+        const double ed = __ldcg(s.cand_d + e);
+        if (dbl_before(ed, ej, bd, bj)) { bd = ed; bj = ej; }
+    }
+    C->ticket_rp = 0;
+    C->bytes_price += 8.0 * P.m * (double)gridDim.x;
+    C->n_lp++;
+    if (bj >= 0 && bd > P.tol_d) {
+        C->q = bj;
+        C->dq = bd;
+        C->need_full = 0;
+    } else {
+        C->need_full = 1;
+    }
+    __threadfence();
+}
+
+}  // namespace
+
+void launch_to_bf16(const double* src, uint16_t* dst, size_t count, cudaStream_t st) {
+    k_to_bf16<<<2048, 256, 0, st>>>(src, dst, count);
+}
+
+void launch_price_lp(const DevState& s, const Geometry& g, cudaStream_t st) {
+    k_price_lp<<<g.price_blocks, kLpThreads, (size_t)s.p.ld * sizeof(float), st>>>(s);
+    k_reprice<<<s.p.topk, kRpThreads, 0, st>>>(s);
+}
+
+int occupancy_price_lp(int ld) {
+    cudaFuncSetAttribute(k_price_lp, cudaFuncAttributeMaxDynamicSharedMemorySize, ld * (int)sizeof(float));
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_price_lp, kLpThreads, (size_t)ld * sizeof(float));
+    return nb;
+}
+
+}  // namespace lpgb

@@ -50,6 +50,7 @@ __global__ void k_load_basis(DevState s) {
     }
     for (int i = tid; i < s.p.ld; i += stride) {
         s.rho[i] = 0.0;
+        s.y32[i] = 0.f;
         s.alpha[i] = 0.0;
         s.alpha[s.p.ld + i] = 0.0;
     }
@@ -85,5 +86,104 @@ void launch_load_basis(const DevState& s, cudaStream_t st) {
     k_load_basis<<<256, 256, 0, st>>>(s);
     k_load_basis_pos<<<64, 256, 0, st>>>(s);
 }
+
+}  // namespace lpgb
+
+namespace lpgb {
+namespace {
+
+// Warm-start repair (one block): if some basic value is below -tol, pick the
+// most negative position p and, among nonbasic slacks s, the most negative
+// B^-1[p][s]; stage the pivot (q = n+s, r = p) for k_pivot / k_update.
+// Ctrl::repair becomes 2 when no value is negative, 3 when no slack can fix p.
+__global__ void __launch_bounds__(1024) k_repair_pick(DevState s, double tol) {
+    Ctrl* C = s.ctrl;
+    const Params& P = s.p;
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    __shared__ int p_sh;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) C->repair = 1;
+    __syncthreads();
+    // most negative basic value (ties: smallest position)
+    double v = 0.0;
+    int pi = -1;
+    for (int p = threadIdx.x; p < P.m; p += blockDim.x) {
+        const double bv = s.bbar[p];
+        if (bv < -tol && (pi < 0 || bv < v)) { v = bv; pi = p; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, pi, o);
+        if (oi >= 0 && (pi < 0 || ov < v || (ov == v && oi < pi))) { v = ov; pi = oi; }
+    }
+    if (lane == 0) { sv[w] = v; si[w] = pi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bvv = 0.0;
+        int bp = -1;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
+            if (si[i] >= 0 && (bp < 0 || sv[i] < bvv || (sv[i] == bvv && si[i] < bp))) { bvv = sv[i]; bp = si[i]; }
+        p_sh = bp;
+        if (bp < 0) C->repair = 2;
+    }
+    __syncthreads();
+    const int p = p_sh;
+    if (p < 0) return;
+    // entering slack: most negative B^-1[p][s] over nonbasic slacks s
+    const double* row = s.binv + (size_t)p * P.ld;
+    double best = 0.0;
+    int bs = -1;
+    for (int r = threadIdx.x; r < P.m; r += blockDim.x) {
+        if (s.pos[P.n + r] >= 0) continue;
+        const double e = row[r];
+        if (e < 0.0 && (bs < 0 || e < best)) { best = e; bs = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bs, o);
+        if (oi >= 0 && (bs < 0 || ov < best || (ov == best && oi < bs))) { best = ov; bs = oi; }
+    }
+    __syncthreads();
+    if (lane == 0) { sv[w] = best; si[w] = bs; }
+    __syncthreads();
+    __shared__ int s_sh;
+    __shared__ double e_sh;
+    if (threadIdx.x == 0) {
+        double be = 0.0;
+        int b2 = -1;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
+            if (si[i] >= 0 && (b2 < 0 || sv[i] < be || (sv[i] == be && si[i] < b2))) { be = sv[i]; b2 = si[i]; }
+        s_sh = b2;
+        e_sh = be;
+        if (b2 < 0) C->repair = 3;
+    }
+    __syncthreads();
+    const int sl = s_sh;
+    if (sl < 0) return;
+    // alpha = column sl of B^-1 into the current alpha buffer
+    double* al = s.alpha + (size_t)C->abuf * P.ld;
+    for (int i = threadIdx.x; i < P.m; i += blockDim.x) al[i] = s.binv[(size_t)i * P.ld + sl];
+    if (threadIdx.x == 0) {
+        C->q = P.n + sl;
+        C->r = p;
+        C->dq = -s.y[sl];
+        C->theta = s.bbar[p] / e_sh;
+        C->tcount = 1;
+        C->status = kRunning;
+        C->flags = 0;
+    }
+}
+
+// after the repair pivot's bookkeeping: no FTRAN of a next column
+__global__ void k_repair_clear(DevState s) { s.ctrl->q = -1; }
+
+}  // namespace
+
+void launch_repair_pick(const DevState& s, double tol, cudaStream_t st) {
+    k_repair_pick<<<1, 1024, 0, st>>>(s, tol);
+}
+
+void launch_repair_clear(const DevState& s, cudaStream_t st) { k_repair_clear<<<1, 1, 0, st>>>(s); }
 
 }  // namespace lpgb

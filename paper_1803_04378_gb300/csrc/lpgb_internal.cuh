@@ -17,6 +17,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 namespace lpgb {
 
@@ -48,7 +49,11 @@ struct Params {
     int32_t reinvert_every, tabu_tenure, max_iters, bland_after, trace_cap;
     double tol_d, tol_piv, tol_tie;
     double b_scale;        // max(1, max_i b_i): scale of the feasibility check
+    int32_t price_mode;    // 0: FP64 PRICE; 1: BF16 screen + FP64 re-price of the top k
+    int32_t topk;          // candidates re-priced in FP64 (price_mode 1), <= kMaxTopk
 };
+
+constexpr int kMaxTopk = 32;
 
 struct Ctrl {
     int32_t status;        // kRunning / kOptimal / kUnbounded / kIterLimit / kReinvert
@@ -70,6 +75,12 @@ struct Ctrl {
     int32_t ticket_pivot;
     int32_t nsb;           // structural variables in the basis
     int32_t pad_;
+    int32_t repair;        // warm-start repair: 1 pivot staged, 2 feasible, 3 cannot repair
+    int32_t need_full;     // price_mode 1: the screen found no improving candidate
+    int32_t n_full;        // price_mode 1: full FP64 PRICE passes
+    int32_t n_lp;          // price_mode 1: screen + re-price passes
+    int32_t ticket_lp;     // last-block tickets of the screen and re-price kernels
+    int32_t ticket_rp;
     int32_t n_price;       // PRICE launches that did work
     int32_t n_update;      // UPDATE launches that did work
     double bytes_price;    // algorithmic HBM bytes moved by PRICE
@@ -85,8 +96,21 @@ struct PriceCand {
     double d_all; int32_t j_all;   // best nonbasic (optimality test, aspiration)
     int32_t j_min;                 // smallest improving index (Bland)
     double d_nt;  int32_t j_nt;    // best nonbasic non-tabu
-    int32_t pad_;
+    int32_t k_pr;                  // priority rank of j_pr (guided entering rule)
     double d_min;                  // d of j_min
+    double d_pr;  int32_t j_pr;    // improving non-tabu column with the best priority
+    int32_t pad_;
+};
+
+constexpr int32_t kNoRank = 0x7fffffff;
+constexpr int kTfGuided = 128;
+
+// BF16 screen partial of one block: its best two columns by approximate d,
+// and its best exact slack.
+struct LpCand {
+    float d0; int32_t j0;
+    float d1; int32_t j1;
+    double ds; int32_t js; int32_t pad_;
 };
 
 struct TraceBuf {
@@ -96,6 +120,11 @@ struct TraceBuf {
 struct DevState {
     Params p;
     const double* A_cm;
+    const uint16_t* A_lp;    // price_mode 1: BF16 copy of A_cm (same layout)
+    float* y32;              // FP32 copy of y (ld), for the BF16 screen
+    LpCand* lp_part;         // per-block screen partials
+    int32_t* cand;           // kMaxTopk candidate columns (-1 = none)
+    double* cand_d;          // their exact reduced costs
     const double* c;
     const double* b;
     double* binv;
@@ -107,6 +136,7 @@ struct DevState {
     int32_t* basis;
     int32_t* pos;
     int32_t* tabu_until;
+    int32_t* rank;           // n+m: entering priority (kNoRank = none), lp_set_priority
     Ctrl* ctrl;
     PriceCand* price_part;
     double* upd_part;   // per-block theta minima
@@ -133,7 +163,8 @@ struct Geometry {
 // ---- kernels (kernels_iter.cu) ----------------------------------------------
 void launch_init_slack(const DevState& s, cudaStream_t st);
 void launch_pivot(const DevState& s, const Geometry& g, cudaStream_t st);
-void launch_price(const DevState& s, const Geometry& g, cudaStream_t st);
+void launch_price(const DevState& s, const Geometry& g, cudaStream_t st);  // the whole PRICE + CHUZC of the mode
+void launch_to_bf16(const double* src, uint16_t* dst, size_t count, cudaStream_t st);
 void launch_update(const DevState& s, const Geometry& g, cudaStream_t st);
 size_t price_smem_bytes(int ld);
 size_t update_smem_bytes(int ld);
@@ -146,6 +177,7 @@ void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t s
 void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st);
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible);
 int occupancy_price(int ld);
+int occupancy_price_lp(int ld);
 int occupancy_update(int ld);
 
 // ---- setup (kernels_setup.cu) ---------------------------------------------------
@@ -153,5 +185,7 @@ void launch_transpose_pad(const double* A_rm, int m, int n, int ld, double* A_cm
 void launch_validate(const double* A_cm, const double* b, const double* c, int m, int n, int ld,
                      int32_t* flag, cudaStream_t st);
 void launch_load_basis(const DevState& s, cudaStream_t st);
+void launch_repair_pick(const DevState& s, double tol, cudaStream_t st);
+void launch_repair_clear(const DevState& s, cudaStream_t st);
 
 }  // namespace lpgb

@@ -30,9 +30,11 @@ struct lp_handle {
     Ctrl* h_ctrl = nullptr;          // pinned mirror of the control block
     cudaGraphExec_t graph = nullptr;
     std::vector<void*> allocs;
+    int32_t* flag = nullptr;         // device validation flag
     bool solved = false;
     bool primed = false;             // q and r of the next pivot are on the device
     bool warm_pending = false;
+    int warm_repair_max = -1;         // >= 0: lp_set_basis_repair
     std::vector<int32_t> warm_basis;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr;
     std::vector<cudaEvent_t> tev;    // kernel_timing: 3 events per captured iteration
@@ -107,11 +109,12 @@ int setup_geometry(lp_handle* h) {
     Geometry& g = h->geo;
     g.sms = prop.multiProcessorCount;
     configure_iter_kernels(h->ld);
-    const int occ_p = std::max(1, occupancy_price(h->ld));
+    int occ_p = std::max(1, occupancy_price(h->ld));
+    if (h->opt.price_mode == 1) occ_p = std::min(occ_p, std::max(1, occupancy_price_lp(h->ld)));
     const int occ_u = std::max(1, occupancy_update(h->ld));
     g.price_threads = 512;
     g.update_threads = 512;
-    g.pivot_threads = 256;
+    g.pivot_threads = 64;
     // PRICE: columns dealt round-robin to sms * min(occupancy, 2) blocks
     // (a whole number of blocks per SM), two columns per warp.
     int pb = g.sms * std::min(occ_p, 2);
@@ -122,7 +125,8 @@ int setup_geometry(lp_handle* h) {
     (void)occ_u;
     int ub = std::min(g.sms, std::max(1, (h->m + 1) / 2));
     g.update_blocks = std::max(1, ub);
-    g.pivot_blocks = std::max(1, std::min(g.sms, (h->ld + g.pivot_threads - 1) / g.pivot_threads));
+    // pivot bookkeeping: O(m) vector work, one element per thread spread over the SMs
+    g.pivot_blocks = std::max(1, std::min(2 * g.sms, (h->ld + 63) / 64));
     return LP_OK;
 }
 
@@ -225,6 +229,49 @@ const char* lp_strerror(int code) {
     }
 }
 
+// Copies A (row-major -> padded column-major), b (padded) and c to the device,
+// validates them and refreshes the BF16 copy and the feasibility scale.
+static int upload_problem(lp_handle* h, const double* A, const double* b, const double* c, int32_t on_device) {
+    const int m = h->m, n = h->n, ld = h->ld;
+    DevState& s = h->ds;
+    Params& P = h->p;
+    double* A_cm = const_cast<double*>(s.A_cm);
+    double* bb = const_cast<double*>(s.b);
+    double* cc = const_cast<double*>(s.c);
+    int32_t* flag = h->flag;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const double* A_src = A;
+    double* staging = nullptr;
+    if (!on_device) {
+        CK(cudaMalloc(&staging, (size_t)m * n * sizeof(double)));
+        cudaError_t e = cudaMemcpyAsync(staging, A, (size_t)m * n * sizeof(double), kind, h->stream);
+        if (e != cudaSuccess) { cudaFree(staging); return cuda_fail(e); }
+        A_src = staging;
+    }
+    launch_transpose_pad(A_src, m, n, ld, A_cm, h->stream);
+    CK(cudaMemsetAsync(bb, 0, (size_t)ld * sizeof(double), h->stream));
+    CK(cudaMemcpyAsync(bb, b, (size_t)m * sizeof(double), kind, h->stream));
+    CK(cudaMemcpyAsync(cc, c, (size_t)n * sizeof(double), kind, h->stream));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int32_t), h->stream));
+    launch_validate(A_cm, bb, cc, m, n, ld, flag, h->stream);
+    if (P.price_mode == 1) launch_to_bf16(A_cm, const_cast<uint16_t*>(s.A_lp), (size_t)n * ld, h->stream);
+    int32_t hflag = 0;
+    CK(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (staging) CK(cudaFree(staging));
+    if (hflag) return LP_ERR_INVALID_ARG;
+    // b scale for the feasibility check of warm starts
+    {
+        std::vector<double> hb(m);
+        CK(cudaMemcpy(hb.data(), bb, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost));
+        double sc = 1.0;
+        for (double v : hb) sc = std::max(sc, std::fabs(v));
+        P.b_scale = sc;
+        s.p = P;
+    }
+    return LP_OK;
+}
+
 static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, const double* b,
                        const double* c, int32_t on_device) {
     CK(cudaGetDevice(&h->device));
@@ -256,6 +303,8 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     P.tol_d = h->opt.tol_d;
     P.tol_piv = h->opt.tol_piv;
     P.tol_tie = h->opt.tol_tie;
+    P.price_mode = h->opt.price_mode;
+    P.topk = h->opt.topk;
     s.p = P;
 
     double *A_cm, *cc, *bb, *binv, *bbar, *y, *rho, *alpha, *theta, *upd_part, *rv_M, *rv_f;
@@ -276,6 +325,8 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &tabu, (size_t)(n + m)));
     TRY(dalloc(h, &ctrl, 1));
     TRY(dalloc(h, &flag, 1));
+    h->flag = flag;
+    TRY(dalloc(h, &s.rank, (size_t)(n + m)));
     TRY(dalloc(h, &rv_sp, (size_t)m));
     TRY(dalloc(h, &rv_rows, (size_t)m));
     TRY(dalloc(h, &rv_ri, (size_t)m));
@@ -284,9 +335,18 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &rv_slack, (size_t)m));
     TRY(dalloc(h, &rv_M, (size_t)m * m));
     TRY(dalloc(h, &rv_f, 2 * (size_t)m));
+    TRY(dalloc(h, &s.y32, (size_t)ld));
+    TRY(dalloc(h, &s.cand, (size_t)kMaxTopk + 1));
+    TRY(dalloc(h, &s.cand_d, (size_t)kMaxTopk + 1));
+    if (P.price_mode == 1) {
+        uint16_t* lp = nullptr;
+        TRY(dalloc(h, &lp, (size_t)n * ld));
+        s.A_lp = lp;
+    }
     TRY(setup_geometry(h));
     const int parts = std::max(h->geo.price_blocks, h->geo.update_blocks);
     TRY(dalloc(h, &price_part, (size_t)parts));
+    TRY(dalloc(h, &s.lp_part, (size_t)parts));
     TRY(dalloc(h, &upd_part, (size_t)parts));
     if (P.trace_cap > 0) {
         TRY(dalloc(h, &s.trace.q, (size_t)P.trace_cap));
@@ -301,36 +361,11 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     s.rv_struct_pos = rv_sp; s.rv_rows = rv_rows; s.rv_row_index = rv_ri; s.rv_slack_pos = rv_slack;
     s.rv_pivrow = rv_piv; s.rv_rowdone = rv_done; s.rv_M = rv_M; s.rv_f = rv_f;
 
-    // upload: A (row-major) -> padded column-major, b padded, c
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const double* A_src = A;
-    double* staging = nullptr;
-    if (!on_device) {
-        CK(cudaMalloc(&staging, (size_t)m * n * sizeof(double)));
-        cudaError_t e = cudaMemcpyAsync(staging, A, (size_t)m * n * sizeof(double), kind, h->stream);
-        if (e != cudaSuccess) { cudaFree(staging); return cuda_fail(e); }
-        A_src = staging;
-    }
-    launch_transpose_pad(A_src, m, n, ld, A_cm, h->stream);
-    CK(cudaMemsetAsync(bb, 0, (size_t)ld * sizeof(double), h->stream));
-    CK(cudaMemcpyAsync(bb, b, (size_t)m * sizeof(double), kind, h->stream));
-    CK(cudaMemcpyAsync(cc, c, (size_t)n * sizeof(double), kind, h->stream));
-    CK(cudaMemsetAsync(flag, 0, sizeof(int32_t), h->stream));
-    launch_validate(A_cm, bb, cc, m, n, ld, flag, h->stream);
-    int32_t hflag = 0;
-    CK(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    if (staging) CK(cudaFree(staging));
-    if (hflag) return LP_ERR_INVALID_ARG;
-    // b scale for the feasibility check of warm starts
     {
-        std::vector<double> hb(m);
-        CK(cudaMemcpy(hb.data(), bb, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost));
-        double sc = 1.0;
-        for (double v : hb) sc = std::max(sc, std::fabs(v));
-        P.b_scale = sc;
-        s.p = P;
+        std::vector<int32_t> none((size_t)n + m, kNoRank);
+        CK(cudaMemcpy(s.rank, none.data(), sizeof(int32_t) * none.size(), cudaMemcpyHostToDevice));
     }
+    TRY(upload_problem(h, A, b, c, on_device));
     TRY(reset_state(h));
     TRY(capture_graph(h));
     CK(cudaStreamSynchronize(h->stream));
@@ -347,7 +382,7 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     lp_default_options(&o);
     if (opt) o = *opt;
     if (o.graph_iters < 1 || o.graph_iters > 4096 || o.reserved_ != 0 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 ||
-        o.bland_after < 0 || o.price_mode != 0 || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
+        o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 1 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
         if (!finite_all(A, (size_t)m * n) || !finite_all(c, n) || !finite_all(b, m)) return LP_ERR_INVALID_ARG;
@@ -367,8 +402,16 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     return LP_OK;
 }
 
+int lp_set_basis_repair(lp_handle* h, const int32_t* basis, int32_t max_repairs) {
+    if (max_repairs < 0) return LP_ERR_INVALID_ARG;
+    int rc = lp_set_basis(h, basis);
+    if (rc == LP_OK) h->warm_repair_max = max_repairs;
+    return rc;
+}
+
 int lp_set_basis(lp_handle* h, const int32_t* basis) {
     if (!h || !basis) return LP_ERR_INVALID_ARG;
+    h->warm_repair_max = -1;
     std::vector<char> seen((size_t)h->n + h->m, 0);
     for (int p = 0; p < h->m; ++p) {
         const int v = basis[p];
@@ -377,6 +420,37 @@ int lp_set_basis(lp_handle* h, const int32_t* basis) {
     }
     h->warm_basis.assign(basis, basis + h->m);
     h->warm_pending = true;
+    return LP_OK;
+}
+
+int lp_update_problem(lp_handle* h, const double* A, const double* b, const double* c, int32_t on_device) {
+    if (!h || !A || !b || !c) return LP_ERR_INVALID_ARG;
+    if (!on_device) {
+        if (!finite_all(A, (size_t)h->m * h->n) || !finite_all(c, h->n) || !finite_all(b, h->m))
+            return LP_ERR_INVALID_ARG;
+        for (int i = 0; i < h->m; ++i)
+            if (b[i] < 0) return LP_ERR_INVALID_ARG;
+    }
+    h->warm_pending = false;
+    TRY(upload_problem(h, A, b, c, on_device));
+    TRY(reset_state(h));
+    CK(cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+int lp_set_priority(lp_handle* h, const int32_t* vars, int32_t count) {
+    if (!h || count < 0 || (count > 0 && !vars)) return LP_ERR_INVALID_ARG;
+    if (h->opt.price_mode != 0) return LP_ERR_STATE;
+    const int N = h->n + h->m;
+    if (count > N) return LP_ERR_INVALID_ARG;
+    std::vector<int32_t> rank((size_t)N, kNoRank);
+    for (int t = 0; t < count; ++t) {
+        const int v = vars[t];
+        if (v < 0 || v >= N || rank[v] != kNoRank) return LP_ERR_INVALID_ARG;
+        rank[v] = t;
+    }
+    CK(cudaMemcpyAsync(h->ds.rank, rank.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return LP_OK;
 }
 
@@ -395,6 +469,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
     h->price_s = h->update_s = h->price_b = h->update_b = 0.0;
     h->price_n = h->update_n = 0;
     h->launches = 0;
+    int warm_repairs = 0, warm_fallback = 0;
     if (h->warm_pending) {
         TRY(reset_state(h));
         CK(cudaMemcpyAsync(h->ds.basis, h->warm_basis.data(), sizeof(int32_t) * h->m,
@@ -402,7 +477,33 @@ int lp_solve(lp_handle* h, lp_result* out) {
         launch_load_basis(h->ds, h->stream);
         CK(cudaGetLastError());
         h->warm_pending = false;
-        TRY(reinvert(h, 1));
+        if (h->warm_repair_max < 0) {
+            TRY(reinvert(h, 1));
+        } else {
+            int rc = reinvert(h, 0);
+            bool ok = rc == LP_OK;
+            if (rc != LP_OK && rc != LP_ERR_SINGULAR) return rc;
+            while (ok) {
+                launch_repair_pick(h->ds, 1e-9 * h->p.b_scale, h->stream);
+                TRY(read_ctrl(h));
+                if (h->h_ctrl->repair == 2) break;                  // feasible
+                if (h->h_ctrl->repair == 3 || warm_repairs >= h->warm_repair_max) { ok = false; break; }
+                launch_pivot(h->ds, h->geo, h->stream);
+                launch_repair_clear(h->ds, h->stream);
+                launch_update(h->ds, h->geo, h->stream);
+                CK(cudaGetLastError());
+                h->launches += 4;
+                warm_repairs++;
+                TRY(read_ctrl(h));
+                if (h->h_ctrl->status == kReinvert) TRY(reinvert(h, 0));
+                else if (h->h_ctrl->status != kRunning) break;
+            }
+            if (!ok) {
+                warm_fallback = 1;
+                TRY(reset_state(h));
+            }
+            h->primed = false;
+        }
     }
     TRY(read_ctrl(h));
     for (;;) {
@@ -427,7 +528,10 @@ int lp_solve(lp_handle* h, lp_result* out) {
         if (!h->tev.empty()) {
             // kernels that did work occupy the first slots of the graph
             const Ctrl& A = *h->h_ctrl;
-            const int np = std::min(A.n_price - before.n_price, h->opt.graph_iters);
+            // a PRICE slot did work when the FP64 pass or (price_mode 1) the screen ran
+            const int np = std::min((A.n_price - before.n_price) + (A.n_lp - before.n_lp) -
+                                        (A.n_full - before.n_full),
+                                    h->opt.graph_iters);
             const int nu = std::min(A.n_update - before.n_update, h->opt.graph_iters);
             for (int t = 0; t < np; ++t) {
                 float ms = 0.f;
@@ -469,6 +573,8 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->price_launches = h->price_n;
         out->update_launches = h->update_n;
         out->kernel_launches = h->launches;
+        out->warm_repairs = warm_repairs;
+        out->warm_fallback = warm_fallback;
     }
     return LP_OK;
 }

@@ -27,6 +27,7 @@ LP_ERR_DEVICE = -7
 LP_RUNNING, LP_OPTIMAL, LP_UNBOUNDED, LP_ITER_LIMIT = 0, 1, 2, 3
 STATUS_NAMES = {0: "running", 1: "optimal", 2: "unbounded", 3: "iter_limit"}
 LP_TF_DEGENERATE, LP_TF_TABU_PUSH, LP_TF_ASPIRATION, LP_TF_BLAND, LP_TF_TIE_SET = 1, 2, 4, 8, 64
+LP_TF_GUIDED = 128
 
 
 class lp_options(ctypes.Structure):
@@ -49,7 +50,15 @@ class lp_result(ctypes.Structure):
                 ("price_seconds", ctypes.c_double), ("update_seconds", ctypes.c_double),
                 ("price_bytes", ctypes.c_double), ("update_bytes", ctypes.c_double),
                 ("price_launches", ctypes.c_int32), ("update_launches", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("warm_repairs", ctypes.c_int32),
+                ("warm_fallback", ctypes.c_int32)]
+
+
+class lp_batch_result(ctypes.Structure):
+    _fields_ = [("solved", ctypes.c_int32), ("unbounded", ctypes.c_int32),
+                ("iter_limit", ctypes.c_int32), ("failed", ctypes.c_int32),
+                ("iterations", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("fp64_flops", ctypes.c_double)]
 
 
 class LPError(RuntimeError):
@@ -87,6 +96,46 @@ def _load():
     lib.lp_strerror.restype = ctypes.c_char_p
     lib.lp_price_static.argtypes = [i32, i32, vp, i32, vp, vp, vp, ctypes.c_double, vp, vp, vp]
     lib.lp_price_static.restype = ctypes.c_int
+    lib.lp_set_basis_repair.argtypes = [vp, vp, i32]
+    lib.lp_set_basis_repair.restype = ctypes.c_int
+    lib.lp_update_problem.argtypes = [vp, vp, vp, vp, i32]
+    lib.lp_update_problem.restype = ctypes.c_int
+    lib.lp_set_priority.argtypes = [vp, vp, i32]
+    lib.lp_set_priority.restype = ctypes.c_int
+    lib.lp_mlp_create.argtypes = [P(vp), i32, i32, i32, i32, vp]
+    lib.lp_mlp_create.restype = ctypes.c_int
+    lib.lp_mlp_num_params.argtypes = [vp]
+    lib.lp_mlp_num_params.restype = ctypes.c_int64
+    lib.lp_mlp_set_params.argtypes = [vp, vp]
+    lib.lp_mlp_set_params.restype = ctypes.c_int
+    lib.lp_mlp_get_params.argtypes = [vp, vp]
+    lib.lp_mlp_get_params.restype = ctypes.c_int
+    lib.lp_mlp_forward.argtypes = [vp, vp, i32, vp]
+    lib.lp_mlp_forward.restype = ctypes.c_int
+    lib.lp_mlp_gradients.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.lp_mlp_gradients.restype = ctypes.c_int
+    lib.lp_mlp_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp]
+    lib.lp_mlp_train_step.restype = ctypes.c_int
+    lib.lp_mlp_destroy.argtypes = [vp]
+    lib.lp_mlp_destroy.restype = None
+    lib.lp_family_perturb.argtypes = [i32, i32, vp, vp, vp, ctypes.c_uint64, ctypes.c_double, vp, vp, vp, vp]
+    lib.lp_family_perturb.restype = ctypes.c_int
+    lib.lp_family_features.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, ctypes.c_double, vp, vp]
+    lib.lp_family_features.restype = ctypes.c_int
+    lib.lp_batch_create.argtypes = [P(vp), i32, vp, vp, vp, vp, vp, i32, P(lp_options)]
+    lib.lp_batch_create.restype = ctypes.c_int
+    lib.lp_batch_solve.argtypes = [vp, P(lp_batch_result)]
+    lib.lp_batch_solve.restype = ctypes.c_int
+    lib.lp_batch_get.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.lp_batch_get.restype = ctypes.c_int
+    lib.lp_batch_get_trace.argtypes = [vp, i32, vp, vp, i32, P(i32)]
+    lib.lp_batch_get_trace.restype = ctypes.c_int
+    lib.lp_batch_tune.argtypes = [vp, vp, i32]
+    lib.lp_batch_tune.restype = ctypes.c_int
+    lib.lp_batch_set_tuning.argtypes = [vp, vp]
+    lib.lp_batch_set_tuning.restype = ctypes.c_int
+    lib.lp_batch_destroy.argtypes = [vp]
+    lib.lp_batch_destroy.restype = None
     return lib
 
 
@@ -138,6 +187,8 @@ class Result:
     price_launches: int = 0
     update_launches: int = 0
     kernel_launches: int = 0
+    warm_repairs: int = 0
+    warm_fallback: int = 0
 
     @property
     def status_name(self) -> str:
@@ -196,16 +247,35 @@ class LP:
                       r.bland_fallbacks, r.aspirations, r.objective, r.seconds,
                       r.reinvert_seconds, r.bytes_moved, r.price_seconds, r.update_seconds,
                       r.price_bytes, r.update_bytes, r.price_launches, r.update_launches,
-                      r.kernel_launches)
+                      r.kernel_launches, r.warm_repairs, r.warm_fallback)
 
     def reset(self):
         _check(_lib.lp_reset(self._h), "lp_reset")
+
+    def update_problem(self, A, b, c):
+        on_dev = hasattr(A, "is_cuda") and A.is_cuda
+        if not on_dev:
+            A = np.ascontiguousarray(A, dtype=np.float64)
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            c = np.ascontiguousarray(c, dtype=np.float64)
+        _check(_lib.lp_update_problem(self._h, _ptr(A), _ptr(b), _ptr(c), 1 if on_dev else 0),
+               "lp_update_problem")
+
+    def set_priority(self, vars_in_order):
+        v = np.ascontiguousarray(vars_in_order, dtype=np.int32)
+        _check(_lib.lp_set_priority(self._h, _ptr(v) if len(v) else None, len(v)), "lp_set_priority")
 
     def set_basis(self, basis):
         bb = np.ascontiguousarray(basis, dtype=np.int32)
         if bb.shape != (self.m,):
             raise ValueError("basis must have m entries")
         _check(_lib.lp_set_basis(self._h, _ptr(bb)), "lp_set_basis")
+
+    def set_basis_repair(self, basis, max_repairs: int):
+        bb = np.ascontiguousarray(basis, dtype=np.int32)
+        if bb.shape != (self.m,):
+            raise ValueError("basis must have m entries")
+        _check(_lib.lp_set_basis_repair(self._h, _ptr(bb), int(max_repairs)), "lp_set_basis_repair")
 
     def solution(self):
         x = np.zeros(self.n)
@@ -249,3 +319,171 @@ def price_static(m: int, n: int, A_colmajor, lda: int, c, y, pos, tol_d: float, 
     st = None if stream is None else ctypes.c_void_p(stream)
     return _lib.lp_price_static(int(m), int(n), _ptr(A_colmajor), int(lda), _ptr(c), _ptr(y), _ptr(pos),
                                 float(tol_d), _ptr(q_out), _ptr(dq_out), st)
+
+
+LP_BATCH_MAX_M = 256
+LP_BATCH_MAX_N = 512
+
+
+class Batch:
+    """Many independent small LPs solved in persistent launches (lp_batch_*).
+
+    ``problems`` is a list of (A, b, c) numpy triples (A row-major m x n);
+    they are packed one after another as the C ABI expects.
+    """
+
+    def __init__(self, problems, **options):
+        self._h = ctypes.c_void_p()
+        ms = np.array([p[0].shape[0] for p in problems], np.int32)
+        ns = np.array([p[0].shape[1] for p in problems], np.int32)
+        A = np.concatenate([np.ascontiguousarray(p[0], np.float64).ravel() for p in problems])
+        b = np.concatenate([np.ascontiguousarray(p[1], np.float64) for p in problems])
+        c = np.concatenate([np.ascontiguousarray(p[2], np.float64) for p in problems])
+        self.count = len(problems)
+        self.ms, self.ns = ms, ns
+        opts = default_options(price_mode=1, topk=8)
+        for k, v in options.items():
+            setattr(opts, k, v)
+        self.options = opts
+        _check(_lib.lp_batch_create(ctypes.byref(self._h), self.count, _ptr(ms), _ptr(ns), _ptr(A),
+                                    _ptr(b), _ptr(c), 0, ctypes.byref(opts)), "lp_batch_create")
+
+    def close(self):
+        if self._h:
+            _lib.lp_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self):
+        r = lp_batch_result()
+        _check(_lib.lp_batch_solve(self._h, ctypes.byref(r)), "lp_batch_solve")
+        return dict(solved=r.solved, unbounded=r.unbounded, iter_limit=r.iter_limit, failed=r.failed,
+                    iterations=r.iterations, seconds=r.seconds, fp64_flops=r.fp64_flops)
+
+    def results(self):
+        st = np.zeros(self.count, np.int32)
+        it = np.zeros(self.count, np.int32)
+        obj = np.zeros(self.count)
+        x = np.zeros(int(self.ns.sum()))
+        y = np.zeros(int(self.ms.sum()))
+        _check(_lib.lp_batch_get(self._h, _ptr(st), _ptr(it), _ptr(obj), _ptr(x), _ptr(y)), "lp_batch_get")
+        xs = np.split(x, np.cumsum(self.ns)[:-1])
+        ys = np.split(y, np.cumsum(self.ms)[:-1])
+        return st, it, obj, xs, ys
+
+    def trace(self, k):
+        cap = int(self.options.trace_cap)
+        q = np.zeros(cap, np.int32)
+        r = np.zeros(cap, np.int32)
+        cnt = ctypes.c_int32()
+        _check(_lib.lp_batch_get_trace(self._h, int(k), _ptr(q), _ptr(r), cap, ctypes.byref(cnt)),
+               "lp_batch_get_trace")
+        return dict(q=q[:cnt.value], r=r[:cnt.value])
+
+    def tune(self, trials: int = 1):
+        table = np.zeros(8, np.int32)
+        _check(_lib.lp_batch_tune(self._h, _ptr(table), int(trials)), "lp_batch_tune")
+        return table
+
+    def set_tuning(self, table):
+        t = np.ascontiguousarray(table, np.int32)
+        _check(_lib.lp_batch_set_tuning(self._h, _ptr(t)), "lp_batch_set_tuning")
+
+
+def save_tuning(path: str, table) -> None:
+    """Caches an autotuner table as JSON: bucket -> (threads, B^-1 in shared memory)."""
+    import json
+    t = [int(v) for v in table]
+    json.dump({"buckets_m": [64, 128, 192, 256],
+               "threads": t[0::2], "binv_in_shared_memory": t[1::2]}, open(path, "w"), indent=1)
+
+
+def load_tuning(path: str):
+    import json
+    d = json.load(open(path))
+    out = []
+    for t, s in zip(d["threads"], d["binv_in_shared_memory"]):
+        out += [t, s]
+    return np.array(out, np.int32)
+
+
+class MLP:
+    """The warm start's network (lp_mlp_*): in -> hidden -> hidden -> out.
+
+    X and T are torch CUDA float32 tensors; parameters move as numpy float32.
+    """
+
+    def __init__(self, in_dim: int, hidden: int, out_dim: int, max_batch: int, stream=None):
+        self._h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(stream)
+        _check(_lib.lp_mlp_create(ctypes.byref(self._h), in_dim, hidden, out_dim, max_batch, st), "lp_mlp_create")
+        self.in_dim, self.hidden, self.out_dim, self.max_batch = in_dim, hidden, out_dim, max_batch
+        self.num_params = int(_lib.lp_mlp_num_params(self._h))
+
+    def shapes(self):
+        i, h, o = self.in_dim, self.hidden, self.out_dim
+        return [(i, h), (h,), (h, h), (h,), (h, o), (o,)]
+
+    def close(self):
+        if self._h:
+            _lib.lp_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        f = np.ascontiguousarray(flat, dtype=np.float32)
+        assert f.size == self.num_params
+        _check(_lib.lp_mlp_set_params(self._h, _ptr(f)), "lp_mlp_set_params")
+
+    def get_params(self):
+        f = np.zeros(self.num_params, np.float32)
+        _check(_lib.lp_mlp_get_params(self._h, _ptr(f)), "lp_mlp_get_params")
+        return f
+
+    def forward(self, X, logits):
+        _check(_lib.lp_mlp_forward(self._h, _ptr(X), int(X.shape[0]), _ptr(logits)), "lp_mlp_forward")
+
+    def gradients(self, X, T):
+        g = np.zeros(self.num_params, np.float32)
+        loss = np.zeros(1, np.float32)
+        _check(_lib.lp_mlp_gradients(self._h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(g), _ptr(loss)),
+               "lp_mlp_gradients")
+        return g, float(loss[0])
+
+    def train_step(self, X, T, lr: float) -> float:
+        loss = np.zeros(1, np.float32)
+        _check(_lib.lp_mlp_train_step(self._h, _ptr(X), _ptr(T), int(X.shape[0]), float(lr), _ptr(loss)),
+               "lp_mlp_train_step")
+        return float(loss[0])
+
+
+def family_perturb(A0, b0, c0, key: int, sigma: float, A, b, c, stream=None):
+    """lp_family_perturb on torch CUDA float64 tensors (A0, A: m x n)."""
+    m, n = A0.shape
+    st = None if stream is None else ctypes.c_void_p(stream)
+    _check(_lib.lp_family_perturb(int(m), int(n), _ptr(A0), _ptr(b0), _ptr(c0), ctypes.c_uint64(key),
+                                  float(sigma), _ptr(A), _ptr(b), _ptr(c), st), "lp_family_perturb")
+
+
+def family_features(A0, b0, c0, A, b, c, sigma: float, out, stream=None):
+    """lp_family_features into a torch CUDA float32 tensor of 2(m+n) values."""
+    m, n = A0.shape
+    st = None if stream is None else ctypes.c_void_p(stream)
+    _check(_lib.lp_family_features(int(m), int(n), _ptr(A0), _ptr(b0), _ptr(c0), _ptr(A), _ptr(b), _ptr(c),
+                                   float(sigma), _ptr(out), st), "lp_family_features")

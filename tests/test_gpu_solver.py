@@ -194,3 +194,91 @@ def test_reset_repeats_identically():
         r2 = lp.solve(); t2 = lp.trace(); z2 = lp.solution()[2]
     assert r1.iterations == r2.iterations and z1 == z2
     assert np.array_equal(t1["q"], t2["q"]) and np.array_equal(t1["r"], t2["r"])
+
+
+@pytest.mark.parametrize("kind,m,n,seed", CASES)
+def test_bf16_price_mode(kind, m, n, seed):
+    """price_mode 1: BF16 screen + FP64 re-price of the top k.  The entering
+    choice may differ from Dantzig's FP64 argmax (pivot-sequence parity is not
+    claimed), so every pivot is checked as a valid simplex pivot -- an
+    improving eligible column and the ratio-test row -- and the optimum must
+    match the FP64 oracle to 1e-9."""
+    A, b, c = lpgen.make(kind, m, n, seed)
+    lp, res, x, y, z, tr = gpu_solve(A, b, c, price_mode=1, topk=16)
+    ref = oracle.solve(A, b, c)
+    assert res.status == 1
+    assert abs(z - ref.objective) <= 1e-9 * max(1.0, abs(ref.objective))
+    assert_certificate(A, b, c, x, y)
+    follow_check(A, b, c, res, tr, oracle.Options(follow_relaxed=1))
+    lp.close()
+
+
+def test_bf16_price_mode_small_topk_and_klee_minty():
+    for d in (4, 7):
+        A = np.zeros((d, d)); b = np.zeros(d); c = np.zeros(d)
+        for i in range(d):
+            for j in range(i):
+                A[i, j] = 2 * 10.0 ** (i - j)
+            A[i, i] = 1.0
+            b[i] = 100.0 ** i
+            c[i] = 10.0 ** (d - 1 - i)
+        lp, res, x, y, z, tr = gpu_solve(A, b, c, price_mode=1, topk=1)
+        assert res.status == 1 and z == pytest.approx(100.0 ** (d - 1), rel=1e-12)
+        follow_check(A, b, c, res, tr, oracle.Options(follow_relaxed=1))
+        lp.close()
+
+
+def test_update_problem_equals_fresh_handle():
+    from paper_1803_04378_gb300 import lpgb
+    P1 = lpgen.dense_real_lp(220, 350, 41)
+    P2 = lpgen.perturbed_lp(P1, 7)
+    with lpgb.LP(*P2, trace_cap=5000) as fresh:
+        rf = fresh.solve(); zf = fresh.solution()[2]; tf = fresh.trace()
+    with lpgb.LP(*P1, trace_cap=5000) as lp:
+        lp.solve()
+        lp.update_problem(*P2)
+        r2 = lp.solve(); z2 = lp.solution()[2]; t2 = lp.trace()
+    assert r2.iterations == rf.iterations and z2 == zf
+    assert np.array_equal(t2["q"], tf["q"]) and np.array_equal(t2["r"], tf["r"])
+
+
+def test_guided_priority_warm_start():
+    """lp_set_priority: the optimal basis of a perturbed neighbour, listed as
+    priorities, cuts the pivots; every pivot is still a valid simplex pivot and
+    the optimum is the oracle's."""
+    from paper_1803_04378_gb300 import lpgb
+    base = lpgen.dense_real_lp(300, 600, 42)
+    inst = lpgen.perturbed_lp(base, 11)
+    ref_base = oracle.solve(*base)
+    ref = oracle.solve(*inst)
+    A, b, c = inst
+    hint = [int(v) for v in ref_base.basis if v < A.shape[1]]
+    with lpgb.LP(A, b, c, trace_cap=20000) as lp:
+        cold = lp.solve()
+        lp.reset()
+        lp.set_priority(hint)
+        guided = lp.solve()
+        x, y, z = lp.solution()
+        tr = lp.trace()
+    assert guided.status == 1 and abs(z - ref.objective) <= 1e-9 * abs(ref.objective)
+    assert_certificate(A, b, c, x, y)
+    assert np.any(tr["flags"] & lpgb.LP_TF_GUIDED)
+    follow_check(A, b, c, guided, tr, oracle.Options(follow_relaxed=1))
+    # direct start from the neighbour's optimal basis, repaired where infeasible
+    with lpgb.LP(A, b, c) as lp:
+        lp.set_basis_repair(ref_base.basis, 300)
+        warm = lp.solve()
+        x, y, z = lp.solution()
+    assert warm.status == 1 and warm.warm_fallback == 0
+    assert abs(z - ref.objective) <= 1e-9 * abs(ref.objective)
+    assert_certificate(A, b, c, x, y)
+    assert warm.iterations < cold.iterations
+    # a useless priority list (every column, in index order) still ends optimal
+    with lpgb.LP(A, b, c) as lp:
+        lp.set_priority(np.arange(A.shape[1] + A.shape[0]))
+        r = lp.solve()
+        assert r.status == 1 and abs(lp.solution()[2] - ref.objective) <= 1e-9 * abs(ref.objective)
+    with lpgb.LP(A, b, c, price_mode=1) as lp:
+        with pytest.raises(lpgb.LPError) as e:
+            lp.set_priority(hint)
+        assert e.value.code == lpgb.LP_ERR_STATE

@@ -286,3 +286,39 @@ def test_follow_mode_accepts_exact_ties():
     f = oracle.solve(A, b, c, follow=(q, r))
     assert f.status == oracle.OPTIMAL and f.adopted >= 1
     assert f.objective == pytest.approx(s.objective, rel=1e-15)
+
+
+def test_follow_relaxed_accepts_any_improving_column_only():
+    A, b, c = lpgen.dense_real_lp(100, 180, 14)
+    s = oracle.solve(A, b, c, trace_cap=10000)
+    q = np.append(s.trace["q"], -1)
+    r = np.append(s.trace["r"], -1)
+    # at pivot 0, y = 0 so d = c: take the second-best column, which improves
+    # but is not Dantzig's choice
+    order = np.argsort(-c, kind="stable")
+    assert order[0] == q[0]
+    q2 = q[:1].copy()
+    q2[0] = order[1]
+    strict = oracle.solve(A, b, c, oracle.Options(max_iters=1), follow=(q2, r[:1]))
+    assert strict.status == oracle.MISMATCH and strict.mismatch_kind == 1
+    # relaxed: accepted as an entering choice; the leaving row must still be
+    # the ratio-test row, which does not depend on c -- take it from a run
+    # whose costs make order[1] Dantzig's choice
+    c_alt = c.copy()
+    c_alt[order[1]] = c[order[0]] + 1.0
+    r_alt = oracle.solve(A, b, c_alt, oracle.Options(max_iters=1), trace_cap=1).trace["r"]
+    probe = oracle.solve(A, b, c, oracle.Options(max_iters=1, follow_relaxed=1),
+                         follow=(q2, r_alt), follow_status=oracle.ITER_LIMIT)
+    assert probe.mismatch_at < 0 and probe.adopted >= 1
+    wrong_r = np.array([(r_alt[0] + 1) % 100], np.int32)
+    probe2 = oracle.solve(A, b, c, oracle.Options(max_iters=1, follow_relaxed=1),
+                          follow=(q2, wrong_r), follow_status=oracle.ITER_LIMIT)
+    assert probe2.status == oracle.MISMATCH and probe2.mismatch_kind == 2
+    # a column with d <= 0 is rejected even when relaxed
+    c3 = c.copy()
+    c3[5] = -1.0
+    s3 = oracle.solve(A, b, c3, trace_cap=2)
+    q3 = np.array([5], np.int32)
+    bad = oracle.solve(A, b, c3, oracle.Options(max_iters=1, follow_relaxed=1),
+                       follow=(q3, np.array([0], np.int32)))
+    assert bad.status == oracle.MISMATCH and bad.mismatch_kind == 1
