@@ -230,7 +230,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--price-mode", type=int, default=0, help="PRICE of the timed solves (profiling)")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--only-batch", action="store_true", help="run only the batched leg (profiling)")
+    ap.add_argument("--reinversion-only", type=int, default=0,
+                    help="profiling: solve once, then time this many reinversions of the optimal basis")
     ap.add_argument("--max-iters", type=int, default=0,
                     help="stop every solve after this many pivots (profiling runs only)")
     args = ap.parse_args()
@@ -252,17 +256,39 @@ def main():
     _build.build()
     from paper_1803_04378_gb300 import lpgb
 
+    if args.only_batch:
+        print(json.dumps(run_batched(lpgb, args, False)), flush=True)
+        return 0
     m, n = WORKLOAD["m"], WORKLOAD["n"]
     A, b, c = lpgen.make(WORKLOAD["kind"], m, n, WORKLOAD["seed"])
     stream = torch.cuda.current_stream()
     At, bt, ct = (torch.from_numpy(v).cuda() for v in (A, b, c))
     extra = {"max_iters": args.max_iters} if args.max_iters > 0 else {}
-    lp = lpgb.LP(At, bt, ct, kernel_timing=1, cuda_stream=stream.cuda_stream, **extra)
+    lp = lpgb.LP(At, bt, ct, kernel_timing=1, cuda_stream=stream.cuda_stream, price_mode=args.price_mode, **extra)
     del At, bt, ct
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
+
+    if args.reinversion_only > 0:
+        lp.solve()
+        basis = lp.basis()
+        k = int(sum(1 for v in basis if v < n))
+        with lpgb.LP(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), torch.from_numpy(c).cuda(),
+                     max_iters=0) as lr:
+            times = []
+            for _ in range(args.reinversion_only):
+                lr.set_basis(basis)
+                r = lr.solve()
+                times.append((r.reinvert_seconds, r.reinvert_gj_seconds, r.reinvert_assemble_seconds))
+        t = np.array(times)
+        print(json.dumps({"reinversion_of_optimal_basis": {"k_structural": k, "m": m,
+                                                           "seconds_mean": float(t[:, 0].mean()),
+                                                           "gj_seconds_mean": float(t[:, 1].mean()),
+                                                           "assemble_seconds_mean": float(t[:, 2].mean())}}))
+        lp.close()
+        return 0
 
     for _ in range(args.warmup):
         lp.reset()
@@ -350,12 +376,13 @@ def main():
                "h2d_bytes_per_step": 8 * (m * n + m + n), "d2h_bytes_per_step": 8 * (n + m) + 8,
                "seconds_per_step": t_e2e / args.e2e_steps}
 
-    # variant: BF16-screened PRICE with the top 16 re-priced in FP64 (same
-    # FP64 UPDATE/FTRAN/ratio test/reinversion; optimality certified in FP64)
+    # variant: BF16-screened PRICE, each screening block's best two columns
+    # re-priced in FP64 (same FP64 UPDATE/FTRAN/ratio test/reinversion;
+    # optimality certified in FP64)
     variants = {}
     if not args.skip_variants:
         At, bt, ct = (torch.from_numpy(v).cuda() for v in (A, b, c))
-        with lpgb.LP(At, bt, ct, kernel_timing=1, cuda_stream=stream.cuda_stream, price_mode=1, topk=16,
+        with lpgb.LP(At, bt, ct, kernel_timing=1, cuda_stream=stream.cuda_stream, price_mode=1, topk=2,
                      **extra) as lpv:
             del At, bt, ct
             lpv.solve()  # warm-up
@@ -369,12 +396,13 @@ def main():
             torch.cuda.synchronize()
             tv = v0.elapsed_time(v1) * 1e-3
             zv = lpv.solution()[2]
-        variants["bf16_price_top16"] = {
+        variants["bf16_price"] = {
             "value": rv.iterations / tv, "unit": "iters/s", "time_to_optimum_s": tv,
             "pivots_per_solve": rv.iterations, "objective": zv,
             "objective_rel_err_vs_fp64_path": abs(zv - z) / max(1.0, abs(z)),
             "us_per_price": 1e6 * rv.price_seconds / max(1, rv.price_launches),
             "price_hbm_gbs": rv.price_bytes / rv.price_seconds / 1e9 if rv.price_seconds else None,
+            "screen_passes": rv.screen_passes, "full_fp64_passes": rv.full_passes,
             "status": rv.status_name}
 
     cpu = None

@@ -67,9 +67,10 @@ typedef struct lp_options {
     int32_t tabu_tenure;    /* iterations a tabu variable may not enter (0: rule off) */
     int32_t max_iters;      /* iteration limit */
     int32_t bland_after;    /* consecutive degenerate pivots before Bland's rule (0: off) */
-    int32_t price_mode;     /* 0: FP64 PRICE; 1: BF16 screen, top-k re-priced in FP64,
-                               full FP64 PRICE whenever no candidate improves */
-    int32_t topk;           /* price_mode 1: candidates re-priced in FP64 (1..32) */
+    int32_t price_mode;     /* 0: FP64 PRICE; 1: BF16 screen, the screened best columns
+                               re-priced in FP64, full FP64 PRICE whenever none improves */
+    int32_t topk;           /* price_mode 1: columns re-priced per screening block (1 or 2;
+                               larger values act as 2); batches: candidates per LP (1..8) */
     int32_t trace_cap;      /* record (q, r, theta, d_q, flags) of the first trace_cap pivots */
     int32_t graph_iters;    /* pivots per captured CUDA graph launch */
     int32_t kernel_timing;  /* 1: time every PRICE and UPDATE launch with CUDA events */
@@ -103,6 +104,10 @@ typedef struct lp_result {
     int64_t kernel_launches; /* all kernels this call launched (graph nodes included) */
     int32_t warm_repairs;    /* lp_set_basis_repair: repair pivots performed */
     int32_t warm_fallback;   /* 1: the proposal was unusable, the solve started from the slack basis */
+    int32_t screen_passes;   /* price_mode 1: BF16 screen + re-price passes (cumulative) */
+    int32_t full_passes;     /* price_mode 1: full FP64 PRICE passes (cumulative) */
+    double reinvert_gj_seconds;       /* part of reinvert_seconds: elimination of B11 */
+    double reinvert_assemble_seconds; /* part: B^-1 rows, bbar, duals */
 } lp_result;
 
 /* Fills *opt with the defaults listed above. */

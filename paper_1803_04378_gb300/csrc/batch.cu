@@ -253,14 +253,23 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
         bool have_q = false;
         if (P.price_mode == 1 && !bland && Alp != nullptr) {
             // BF16 screen over nonbasic, non-tabu structural columns
-            for (int j = tid; j < n; j += T) {
-                float v = -FLT_MAX;
-                if (pos[j] < 0 && tabu[j] <= it) {
-                    float acc = 0.f;
-                    for (int i = 0; i < m; ++i) acc = fmaf(y32[i], bf16f(__ldg(Alp + (size_t)i * n + j)), acc);
-                    v = (float)c[j] - acc;
+            // four lanes per column, rows dealt round-robin, two chains each
+            for (int base = 0; base < n; base += T / 4) {
+                const int j = base + (tid >> 2), g = tid & 3;
+                const bool live = j < n && pos[j] < 0 && tabu[j] <= it;
+                float a0 = 0.f, a1 = 0.f;
+                if (live) {
+                    int i = g;
+                    for (; i + 4 < m; i += 8) {
+                        a0 = fmaf(y32[i], bf16f(__ldg(Alp + (size_t)i * n + j)), a0);
+                        a1 = fmaf(y32[i + 4], bf16f(__ldg(Alp + (size_t)(i + 4) * n + j)), a1);
+                    }
+                    for (; i < m; i += 4) a0 = fmaf(y32[i], bf16f(__ldg(Alp + (size_t)i * n + j)), a0);
                 }
-                dts[j] = v;
+                float acc = a0 + a1;
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                if (g == 0 && j < n) dts[j] = live ? (float)c[j] - acc : -FLT_MAX;
             }
             __syncthreads();
             const int K = P.topk < kBatchTopk ? P.topk : kBatchTopk;
@@ -312,20 +321,31 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
             BCand ball = {-DBL_MAX, -1}, bnt = {-DBL_MAX, -1};
             int jmin = -1;
             double dmin = 0.0;
-            for (int j = tid; j < N; j += T) {
-                if (pos[j] >= 0) continue;
-                double d;
-                if (j < n) {
-                    double acc = 0.0;
-                    for (int i = 0; i < m; ++i) acc = fma(y[i], __ldg(A + (size_t)i * n + j), acc);
-                    d = c[j] - acc;
-                } else {
-                    d = -y[j - n];
-                }
+            auto offer = [&](double d, int j) {
                 if (bc_beats(d, j, ball.d, ball.j)) ball = {d, j};
                 if (tabu[j] <= it && bc_beats(d, j, bnt.d, bnt.j)) bnt = {d, j};
                 if (d > P.tol_d && (jmin < 0 || j < jmin)) { jmin = j; dmin = d; }
+            };
+            // structural columns: four lanes per column
+            for (int base = 0; base < n; base += T / 4) {
+                const int j = base + (tid >> 2), g = tid & 3;
+                const bool live = j < n && pos[j] < 0;
+                double a0 = 0.0, a1 = 0.0;
+                if (live) {
+                    int i = g;
+                    for (; i + 4 < m; i += 8) {
+                        a0 = fma(y[i], __ldg(A + (size_t)i * n + j), a0);
+                        a1 = fma(y[i + 4], __ldg(A + (size_t)(i + 4) * n + j), a1);
+                    }
+                    for (; i < m; i += 4) a0 = fma(y[i], __ldg(A + (size_t)i * n + j), a0);
+                }
+                double acc = a0 + a1;
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                if (g == 0 && live) offer(c[j] - acc, j);
             }
+            for (int i = tid; i < m; i += T)
+                if (pos[n + i] < 0) offer(-y[i], n + i);
             ball = block_best<T>(ball, R.bc);
             bnt = block_best<T>(bnt, R.bc);
             // smallest improving index: reduce as argmax of (-j)
@@ -369,15 +389,33 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
         // ---- Step 5: FTRAN alpha = B^-1 a_q
         for (int k = tid; k < m; k += T) aq[k] = q < n ? __ldg(A + (size_t)k * n + q) : (k == q - n ? 1.0 : 0.0);
         __syncthreads();
-        for (int i = tid; i < m; i += T) {
-            double acc = 0.0;
-            if (q < n) {
-                for (int k = 0; k < m; ++k) acc = fma(Binv[(size_t)k * m + i], aq[k], acc);
-            } else {
-                acc = Binv[(size_t)(q - n) * m + i];
+        if (q < n) {
+            // four lanes per row, columns of B^-1 dealt round-robin
+            for (int base = 0; base < m; base += T / 4) {
+                const int i = base + (tid >> 2), g = tid & 3;
+                double a0 = 0.0, a1 = 0.0;
+                if (i < m) {
+                    int k = g;
+                    for (; k + 4 < m; k += 8) {
+                        a0 = fma(Binv[(size_t)k * m + i], aq[k], a0);
+                        a1 = fma(Binv[(size_t)(k + 4) * m + i], aq[k + 4], a1);
+                    }
+                    for (; k < m; k += 4) a0 = fma(Binv[(size_t)k * m + i], aq[k], a0);
+                }
+                double acc = a0 + a1;
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                if (g == 0 && i < m) {
+                    al[i] = acc;
+                    th[i] = acc > P.tol_piv ? bbar[i] / acc : DBL_MAX;
+                }
             }
-            al[i] = acc;
-            th[i] = acc > P.tol_piv ? bbar[i] / acc : DBL_MAX;
+        } else {
+            for (int i = tid; i < m; i += T) {
+                const double acc = Binv[(size_t)(q - n) * m + i];
+                al[i] = acc;
+                th[i] = acc > P.tol_piv ? bbar[i] / acc : DBL_MAX;
+            }
         }
         __syncthreads();
         // ---- Step 6: CHUZR with the tie set
@@ -439,9 +477,16 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
         }
         for (int i = tid; i < m; i += T)
             bbar[i] = (i == r) ? theta : __dsub_rn(bbar[i], __dmul_rn(al[i], theta));
-        for (int e = tid; e < m * m; e += T) {
-            const int k = e / m, i = e - k * m;
-            Binv[e] = (i == r) ? rho[k] : fma(-al[i], rho[k], Binv[e]);
+        {
+            // element e = k*m + i walks by T: advance (k, i) without dividing
+            const int dk = T / m, di = T - dk * m;
+            int k = tid / m, i = tid - k * m;
+            for (int e = tid; e < m * m; e += T) {
+                Binv[e] = (i == r) ? rho[k] : fma(-al[i], rho[k], Binv[e]);
+                k += dk;
+                i += di;
+                if (i >= m) { i -= m; ++k; }
+            }
         }
         __syncthreads();
         // ---- periodic reinversion (structure-aware, as in the single-LP solver)

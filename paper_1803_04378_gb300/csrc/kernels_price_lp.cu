@@ -9,15 +9,18 @@
 // best of them.  Whenever no exactly re-priced candidate improves (or the
 // Bland safety net is on) the full FP64 PRICE runs, so optimality is always
 // certified in FP64 and the final objective equals the FP64 method's.  The
-// entering choice can differ from Dantzig's FP64 argmax when more than k
-// columns sit within the BF16 error of the maximum.
+// entering choice can differ from Dantzig's FP64 argmax when the argmax is
+// not among a block's screened best.
 //
 //   k_price_lp   BF16 screen: approximate d~_j over nonbasic, non-tabu
-//                structural columns; each block keeps its best two; exact
-//                slack candidates (d = -y_i) as well.  In the last block one
-//                warp picks the top k of the block bests.
-//   k_reprice    one block per candidate: exact FP64 d_j; the last block
+//                structural columns; each block re-prices its best `topk`
+//                (1 or 2) columns exactly in FP64 and offers the best exact
+//                candidate, slacks (d = -y_i, exact) included.  The last block
 //                enters the best exact candidate, or asks for the full PRICE.
+//                The candidates re-priced are therefore the union of every
+//                block's screened best (2 x grid columns), a superset of the
+//                global top-k except where one block holds more than two of
+//                them.
 #include "lpgb_internal.cuh"
 
 #include <cfloat>
@@ -27,10 +30,15 @@ namespace lpgb {
 namespace {
 
 constexpr int kLpThreads = 512;
-constexpr int kSortN = 2048;  // >= 2 * price grid (block bests)
 
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -70,8 +78,12 @@ __global__ void __launch_bounds__(kLpThreads, 2) k_price_lp(DevState s) {
     Ctrl* C = s.ctrl;
     if (C->status != kRunning || C->bland) return;
     const Params& P = s.p;
-    extern __shared__ float ysf[];
-    for (int k = threadIdx.x; k < P.ld; k += blockDim.x) ysf[k] = s.y32[k];
+    extern __shared__ double y64[];                 // ld doubles (exact re-price)
+    float* ysf = reinterpret_cast<float*>(y64 + P.ld);  // ld floats (screen)
+    for (int k = threadIdx.x; k < P.ld; k += blockDim.x) {
+        y64[k] = s.y[k];
+        ysf[k] = s.y32[k];
+    }
     __syncthreads();
     const int it = C->it;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -86,7 +98,7 @@ __global__ void __launch_bounds__(kLpThreads, 2) k_price_lp(DevState s) {
         if (s.pos[j] >= 0 || s.tabu_until[j] > it) continue;
         const uint4* col = reinterpret_cast<const uint4*>(s.A_lp + (size_t)j * P.ld);
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 4
+#pragma unroll 8
         for (int k = lane; k < vecs; k += 32) {
             const uint4 u = __ldcs(col + k);
             const float4 ya = y4[2 * k], yb = y4[2 * k + 1];
@@ -108,13 +120,13 @@ __global__ void __launch_bounds__(kLpThreads, 2) k_price_lp(DevState s) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.m; i += gridDim.x * blockDim.x) {
         const int j = P.n + i;
         if (s.pos[j] >= 0 || s.tabu_until[j] > it) continue;
-        const double d = -s.y[i];
+        const double d = -y64[i];
         if (dbl_before(d, j, ds, js)) { ds = d; js = j; }
     }
-    // block reduction of (top2, slack best)
+    // block top-2 of the screen and best slack
     __shared__ float sd0[32], sd1[32];
-    __shared__ int sj0[32], sj1[32], sjs[32];
-    __shared__ double sds[32];
+    __shared__ int sj0[32], sj1[32], sjs[32], cand2[2];
+    __shared__ double sds[32], exact[2];
     for (int o = 16; o > 0; o >>= 1) {
         const double ods = __shfl_xor_sync(0xffffffffu, ds, o);
         const int ojs = __shfl_xor_sync(0xffffffffu, js, o);
@@ -132,8 +144,55 @@ __global__ void __launch_bounds__(kLpThreads, 2) k_price_lp(DevState s) {
             top2_offer(sd1[w], sj1[w], b0, c0, b1, c1);
             if (dbl_before(sds[w], sjs[w], bs, cs)) { bs = sds[w]; cs = sjs[w]; }
         }
+        cand2[0] = c0;
+        cand2[1] = P.topk >= 2 ? c1 : -1;
+        sds[0] = bs;
+        sjs[0] = cs;
+    }
+    __syncthreads();
+    // exact FP64 re-price of the block's two candidates: half of the warps
+    // per column, each warp one segment; segments summed in a fixed order
+    __shared__ double epart[32];
+    {
+        const int wpc = nw >> 1;               // warps per candidate
+        const int which = warp / wpc, seg = warp % wpc;
+        const int j = which < 2 ? cand2[which] : -1;
+        double a0 = 0.0, a1 = 0.0;
+        if (j >= 0) {
+            const int h2 = P.ld >> 1, segl = (h2 + wpc - 1) / wpc;
+            const int k0 = seg * segl, k1 = min(h2, k0 + segl);
+            const double2* col = reinterpret_cast<const double2*>(s.A_cm + (size_t)j * P.ld);
+            const double2* yy = reinterpret_cast<const double2*>(y64);
+#pragma unroll 4
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const double2 u = __ldg(col + k), w = yy[k];
+                a0 = fma(u.x, w.x, a0);
+                a1 = fma(u.y, w.y, a1);
+            }
+        }
+        const double t = warp_sum(a0 + a1);
+        if (lane == 0) epart[warp] = t;
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const int jj = cand2[threadIdx.x];
+            double e = -DBL_MAX;
+            if (jj >= 0) {
+                double sum = 0.0;
+                for (int w = 0; w < wpc; ++w) sum += epart[threadIdx.x * wpc + w];
+                e = s.c[jj] - sum;
+            }
+            exact[threadIdx.x] = e;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bd = sds[0];
+        int bj = sjs[0];
+        for (int t = 0; t < 2; ++t)
+            if (cand2[t] >= 0 && dbl_before(exact[t], cand2[t], bd, bj)) { bd = exact[t]; bj = cand2[t]; }
         LpCand pc;
-        pc.d0 = b0; pc.j0 = c0; pc.d1 = b1; pc.j1 = c1; pc.ds = bs; pc.js = cs; pc.pad_ = 0;
+        pc.d0 = 0.f; pc.j0 = 0; pc.d1 = 0.f; pc.j1 = 0;
+        pc.ds = bd; pc.js = bj; pc.pad_ = (cand2[0] >= 0) + (cand2[1] >= 0);
         s.lp_part[blockIdx.x] = pc;
     }
     __shared__ int last;
@@ -144,121 +203,43 @@ __global__ void __launch_bounds__(kLpThreads, 2) k_price_lp(DevState s) {
     }
     __syncthreads();
     if (!last) return;
-    // last block: warp 0 picks the top k of the 2G block bests (k rounds of a
-    // warp argmax over a shared-memory copy; no block-wide barriers)
-    __shared__ float kd[kSortN];
-    __shared__ int kj[kSortN];
-    const int nc = 2 * G;
-    for (int e = threadIdx.x; e < nc; e += blockDim.x) {
-        const LpCand* pp = s.lp_part + (e >> 1);
-        if (e & 1) { kd[e] = __ldcg(&pp->d1); kj[e] = __ldcg(&pp->j1); }
-        else { kd[e] = __ldcg(&pp->d0); kj[e] = __ldcg(&pp->j0); }
-    }
-    __syncthreads();
-    if (warp == 0) {
-        for (int t = 0; t < kMaxTopk; ++t) {
-            float bd = -FLT_MAX;
-            int bj = -1, be = -1;
-            if (t < P.topk) {
-                for (int e = lane; e < nc; e += 32)
-                    if (cand_before(kd[e], kj[e], bd, bj)) { bd = kd[e]; bj = kj[e]; be = e; }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
-                    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                    const int oe = __shfl_xor_sync(0xffffffffu, be, o);
-                    if (cand_before(od, oj, bd, bj)) { bd = od; bj = oj; be = oe; }
-                }
-                if (lane == 0 && be >= 0) kj[be] = -1;  // taken
-                __syncwarp();
-            }
-            if (lane == 0) s.cand[t] = bj;
-        }
-    }
-    // best exact slack of the whole grid
-    double ds2 = -DBL_MAX;
-    int js2 = -1;
+    // last block: best exact candidate over the blocks
+    double bd = -DBL_MAX;
+    int bj = -1, nrep = 0;
     for (int b = threadIdx.x; b < G; b += blockDim.x) {
         const double od = __ldcg(&s.lp_part[b].ds);
         const int oj = __ldcg(&s.lp_part[b].js);
-        if (dbl_before(od, oj, ds2, js2)) { ds2 = od; js2 = oj; }
+        nrep += __ldcg(&s.lp_part[b].pad_);
+        if (dbl_before(od, oj, bd, bj)) { bd = od; bj = oj; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        const double od = __shfl_xor_sync(0xffffffffu, ds2, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, js2, o);
-        if (dbl_before(od, oj, ds2, js2)) { ds2 = od; js2 = oj; }
+        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        nrep += __shfl_xor_sync(0xffffffffu, nrep, o);
+        if (dbl_before(od, oj, bd, bj)) { bd = od; bj = oj; }
     }
     __syncthreads();
-    if (lane == 0) { sds[warp] = ds2; sjs[warp] = js2; }
+    if (lane == 0) { sds[warp] = bd; sjs[warp] = bj; sj0[warp] = nrep; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double bs = -DBL_MAX;
-        int cs = -1;
-        for (int w = 0; w < nw; ++w)
-            if (dbl_before(sds[w], sjs[w], bs, cs)) { bs = sds[w]; cs = sjs[w]; }
-        s.cand[kMaxTopk] = cs;        // slot kMaxTopk: the best slack (exact already)
-        s.cand_d[kMaxTopk] = bs;
+        double fd = -DBL_MAX;
+        int fj = -1, tot = 0;
+        for (int w = 0; w < nw; ++w) {
+            tot += sj0[w];
+            if (dbl_before(sds[w], sjs[w], fd, fj)) { fd = sds[w]; fj = sjs[w]; }
+        }
         C->ticket_lp = 0;
-        C->bytes_price += 2.0 * P.m * (double)(P.n - C->nsb);
+        C->bytes_price += 2.0 * P.m * (double)(P.n - C->nsb) + 8.0 * P.m * (double)tot;
+        C->n_lp++;
+        if (fj >= 0 && fd > P.tol_d) {
+            C->q = fj;
+            C->dq = fd;
+            C->need_full = 0;
+        } else {
+            C->need_full = 1;
+        }
         __threadfence();
     }
-}
-
-// One block per candidate: exact FP64 reduced cost; the last block decides.
-constexpr int kRpThreads = 256;
-
-__global__ void __launch_bounds__(kRpThreads) k_reprice(DevState s) {
-    Ctrl* C = s.ctrl;
-    if (C->status != kRunning || C->bland) return;
-    const Params& P = s.p;
-    const int j = s.cand[blockIdx.x];
-    __shared__ double part[kRpThreads / 32];
-    if (j >= 0) {
-        const double2* col = reinterpret_cast<const double2*>(s.A_cm + (size_t)j * P.ld);
-        const double2* y2 = reinterpret_cast<const double2*>(s.y);
-        double a0 = 0.0, a1 = 0.0;
-#pragma unroll 8
-        for (int k = threadIdx.x; k < (P.ld >> 1); k += kRpThreads) {
-            const double2 u = __ldg(col + k), w = y2[k];
-            a0 = fma(u.x, w.x, a0);
-            a1 = fma(u.y, w.y, a1);
-        }
-        double t = a0 + a1;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double sum = 0.0;
-            for (int w = 0; w < kRpThreads / 32; ++w) sum += part[w];
-            s.cand_d[blockIdx.x] = s.c[j] - sum;
-        }
-    }
-    __shared__ int last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&C->ticket_rp, 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    double bd = __ldcg(s.cand_d + kMaxTopk);
-    int bj = __ldcg(s.cand + kMaxTopk);
-    for (int e = 0; e < (int)gridDim.x; ++e) {
-        const int ej = __ldcg(s.cand + e);
-        if (ej < 0) continue;
-        const double ed = __ldcg(s.cand_d + e);
-        if (dbl_before(ed, ej, bd, bj)) { bd = ed; bj = ej; }
-    }
-    C->ticket_rp = 0;
-    C->bytes_price += 8.0 * P.m * (double)gridDim.x;
-    C->n_lp++;
-    if (bj >= 0 && bd > P.tol_d) {
-        C->q = bj;
-        C->dq = bd;
-        C->need_full = 0;
-    } else {
-        C->need_full = 1;
-    }
-    __threadfence();
 }
 
 }  // namespace
@@ -268,14 +249,14 @@ void launch_to_bf16(const double* src, uint16_t* dst, size_t count, cudaStream_t
 }
 
 void launch_price_lp(const DevState& s, const Geometry& g, cudaStream_t st) {
-    k_price_lp<<<g.price_blocks, kLpThreads, (size_t)s.p.ld * sizeof(float), st>>>(s);
-    k_reprice<<<s.p.topk, kRpThreads, 0, st>>>(s);
+    k_price_lp<<<g.price_blocks, kLpThreads, (size_t)s.p.ld * (sizeof(float) + sizeof(double)), st>>>(s);
 }
 
 int occupancy_price_lp(int ld) {
-    cudaFuncSetAttribute(k_price_lp, cudaFuncAttributeMaxDynamicSharedMemorySize, ld * (int)sizeof(float));
+    const size_t smem = (size_t)ld * (sizeof(float) + sizeof(double));
+    cudaFuncSetAttribute(k_price_lp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_price_lp, kLpThreads, (size_t)ld * sizeof(float));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_price_lp, kLpThreads, smem);
     return nb;
 }
 

@@ -145,7 +145,12 @@ struct DevState {
     int32_t* rv_struct_pos;  // k structural basis positions (increasing)
     int32_t* rv_rows;        // k rows whose slack is nonbasic (increasing)
     int32_t* rv_row_index;   // m: row -> index in rv_rows, or -1
-    int32_t* rv_slack_pos;   // m-k basis positions holding a slack (increasing)
+    int32_t* rv_slack_pos;   // m-k rows whose slack is basic (increasing row)
+    int32_t* rv_b_of_pos;    // m: basis position -> structural index b, or -1
+    int32_t* rv_g_of_row;    // m: row -> index in rv_slack_pos, or -1
+    int32_t* rv_J;           // k: structural variable of index b
+    double* rv_cJ;           // k: its cost
+    double* rv_W;            // m*m: dense B11^-1 (k x k) then -A[S,J] B11^-1 ((m-k) x k)
     int32_t* rv_pivrow;      // k: pivot row chosen for column t (GJ)
     int32_t* rv_rowdone;     // k: row already used as pivot
     double* rv_M;            // k*k column-major workspace (B11 then its GJ form)
@@ -172,7 +177,6 @@ void configure_iter_kernels(int ld);
 
 // ---- reinversion (kernels_reinv.cu) -------------------------------------------
 void launch_reinv_classify(const DevState& s, cudaStream_t st);
-void launch_reinv_gather(const DevState& s, int k, cudaStream_t st);
 void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t st);
 void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st);
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible);

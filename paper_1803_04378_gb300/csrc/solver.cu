@@ -36,7 +36,8 @@ struct lp_handle {
     bool warm_pending = false;
     int warm_repair_max = -1;         // >= 0: lp_set_basis_repair
     std::vector<int32_t> warm_basis;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr, erg = nullptr, era = nullptr;
+    double reinv_gj_s = 0.0, reinv_asm_s = 0.0;
     std::vector<cudaEvent_t> tev;    // kernel_timing: 3 events per captured iteration
     double reinvert_seconds = 0.0;
     // per-solve accumulators
@@ -98,6 +99,8 @@ void free_all(lp_handle* h) {
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->er0) cudaEventDestroy(h->er0);
     if (h->er1) cudaEventDestroy(h->er1);
+    if (h->erg) cudaEventDestroy(h->erg);
+    if (h->era) cudaEventDestroy(h->era);
     for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
     h->tev.clear();
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -162,17 +165,22 @@ int reinvert(lp_handle* h, int check_feasible) {
     TRY(read_ctrl(h));
     if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
     const int k = h->h_ctrl->k_struct;
-    h->launches += 1 + (k > 0 ? k + 5 : 0) + 5;
-    launch_reinv_gather(h->ds, k, h->stream);
+    h->launches += 1 + (k > 0 ? (k <= 512 ? 4 : k + 4) : 1) + 3;
+    CK(cudaEventRecord(h->erg, h->stream));
     launch_reinv_gj(h->ds, k, h->geo, h->stream);
+    CK(cudaEventRecord(h->era, h->stream));
     launch_reinv_assemble(h->ds, k, h->geo, h->stream);
     launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible);
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->er1, h->stream));
     TRY(read_ctrl(h));
-    float ms = 0.f;
+    float ms = 0.f, mg = 0.f, ma = 0.f;
     CK(cudaEventElapsedTime(&ms, h->er0, h->er1));
+    CK(cudaEventElapsedTime(&mg, h->erg, h->era));
+    CK(cudaEventElapsedTime(&ma, h->era, h->er1));
     h->reinvert_seconds += ms * 1e-3;
+    h->reinv_gj_s += mg * 1e-3;
+    h->reinv_asm_s += ma * 1e-3;
     h->primed = false;
     if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
     return LP_OK;
@@ -280,6 +288,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     h->ld = (m + kLdAlign - 1) / kLdAlign * kLdAlign;
     const int ld = h->ld;
     if ((size_t)ld * sizeof(double) * 2 > 200 * 1024) return LP_ERR_INVALID_ARG;  // smem staging limit
+
     if (h->opt.cuda_stream) {
         h->stream = static_cast<cudaStream_t>(h->opt.cuda_stream);
     } else {
@@ -290,6 +299,8 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     CK(cudaEventCreate(&h->ev1));
     CK(cudaEventCreate(&h->er0));
     CK(cudaEventCreate(&h->er1));
+    CK(cudaEventCreate(&h->erg));
+    CK(cudaEventCreate(&h->era));
     CK(cudaMallocHost(&h->h_ctrl, sizeof(Ctrl)));
 
     DevState& s = h->ds;
@@ -334,6 +345,11 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &rv_done, (size_t)m));
     TRY(dalloc(h, &rv_slack, (size_t)m));
     TRY(dalloc(h, &rv_M, (size_t)m * m));
+    TRY(dalloc(h, &s.rv_W, (size_t)m * m));
+    TRY(dalloc(h, &s.rv_b_of_pos, (size_t)m));
+    TRY(dalloc(h, &s.rv_g_of_row, (size_t)m));
+    TRY(dalloc(h, &s.rv_J, (size_t)m));
+    TRY(dalloc(h, &s.rv_cJ, (size_t)m));
     TRY(dalloc(h, &rv_f, 2 * (size_t)m));
     TRY(dalloc(h, &s.y32, (size_t)ld));
     TRY(dalloc(h, &s.cand, (size_t)kMaxTopk + 1));
@@ -466,6 +482,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
     if (!h) return LP_ERR_INVALID_ARG;
     CK(cudaEventRecord(h->ev0, h->stream));
     h->reinvert_seconds = 0.0;
+    h->reinv_gj_s = h->reinv_asm_s = 0.0;
     h->price_s = h->update_s = h->price_b = h->update_b = 0.0;
     h->price_n = h->update_n = 0;
     h->launches = 0;
@@ -575,6 +592,10 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->kernel_launches = h->launches;
         out->warm_repairs = warm_repairs;
         out->warm_fallback = warm_fallback;
+        out->screen_passes = C.n_lp;
+        out->full_passes = C.n_full;
+        out->reinvert_gj_seconds = h->reinv_gj_s;
+        out->reinvert_assemble_seconds = h->reinv_asm_s;
     }
     return LP_OK;
 }

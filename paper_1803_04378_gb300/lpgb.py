@@ -51,7 +51,9 @@ class lp_result(ctypes.Structure):
                 ("price_bytes", ctypes.c_double), ("update_bytes", ctypes.c_double),
                 ("price_launches", ctypes.c_int32), ("update_launches", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int64), ("warm_repairs", ctypes.c_int32),
-                ("warm_fallback", ctypes.c_int32)]
+                ("warm_fallback", ctypes.c_int32), ("screen_passes", ctypes.c_int32),
+                ("full_passes", ctypes.c_int32), ("reinvert_gj_seconds", ctypes.c_double),
+                ("reinvert_assemble_seconds", ctypes.c_double)]
 
 
 class lp_batch_result(ctypes.Structure):
@@ -189,6 +191,10 @@ class Result:
     kernel_launches: int = 0
     warm_repairs: int = 0
     warm_fallback: int = 0
+    screen_passes: int = 0
+    full_passes: int = 0
+    reinvert_gj_seconds: float = 0.0
+    reinvert_assemble_seconds: float = 0.0
 
     @property
     def status_name(self) -> str:
@@ -247,7 +253,8 @@ class LP:
                       r.bland_fallbacks, r.aspirations, r.objective, r.seconds,
                       r.reinvert_seconds, r.bytes_moved, r.price_seconds, r.update_seconds,
                       r.price_bytes, r.update_bytes, r.price_launches, r.update_launches,
-                      r.kernel_launches, r.warm_repairs, r.warm_fallback)
+                      r.kernel_launches, r.warm_repairs, r.warm_fallback, r.screen_passes,
+                      r.full_passes, r.reinvert_gj_seconds, r.reinvert_assemble_seconds)
 
     def reset(self):
         _check(_lib.lp_reset(self._h), "lp_reset")
