@@ -12,11 +12,10 @@
 // inverted (2k^3 flops) plus one (m-k) x k x k product, instead of 2m^3.
 //
 // B11^-1 comes from in-place Gauss-Jordan elimination with partial pivoting
-// (row pivots chosen among rows not yet used, no physical swaps).  The matrix
-// lives column-major; each CTA owns whole columns, and the CTA that owns
-// column j+1 searches and publishes the pivot of step j+1 while step j is
-// applied, so one launch per elimination step is the only synchronisation.
-// With pivot row p_t for column t, the stored matrix M satisfies
+// (row pivots chosen among rows not yet used, no physical swaps), blocked in
+// panels of columns (k_gj_panel + k_gj_trail below); per-step kernels remain
+// for a device that refuses the cluster launch.  The matrix lives
+// column-major.  With pivot row p_t for column t, the stored matrix M satisfies
 //       B11^-1[b][p_t] = M[p_b][t].
 #include "lpgb_internal.cuh"
 
@@ -170,127 +169,205 @@ __global__ void __launch_bounds__(kStepThreads) k_gj_step(DevState s, int k, int
     }
 }
 
-// Whole Gauss-Jordan elimination of B11 (k <= kClusterMaxK) in one cluster of
-// kCS CTAs.  CTA r keeps the columns t = r, r+kCS, ... in shared memory.  At
-// step j every CTA applies the pivot (p_j, j) to its columns; the owner of
-// column j+1 first updates that column, searches its pivot among rows not yet
-// used and writes the column and the pivot row into every CTA's shared memory
-// (double-buffered), so one hardware cluster barrier per step is the only
-// synchronisation.  Writes B11 in the same column-major form as the
-// per-step kernels, and the pivot rows.
-constexpr int kCS = 16;
-constexpr int kClusterMaxK = 512;
-constexpr int kClusterThreads = 256;
+// Blocked Gauss-Jordan elimination of B11, panels of kNB columns.
+//
+// One cluster of kPCS CTAs eliminates the pivots of a panel on the k x kNB
+// panel alone (its rows split evenly over the CTAs, held in shared memory).
+// The product T of the panel's elementary transforms differs from the
+// identity only in the columns of the panel's pivot rows p_t, and column t of
+// the eliminated panel is T e_{p_t}; so every other column v of the matrix
+// becomes
+//     T v = (v with rows p_t set to 0) + Panel * v[p_0 .. p_{w-1}],
+// a GEMM of inner dimension kNB run over the whole GPU (k_gj_trail).  A
+// panel column has received every earlier transform before its pivot is
+// searched, so the pivots are those of the unblocked elimination.
+//
+// Inside a panel one hardware cluster barrier per step is the only
+// synchronisation: each CTA publishes its best candidate (|value| as an
+// ordered integer key, smaller row on equal keys) in its own shared memory;
+// after the barrier every CTA reads all candidates and the pivot row through
+// distributed shared memory.  The owner of the pivot row leaves it untouched
+// during the step (others are reading it) and folds the scaling into its
+// update of the next step, after the next barrier.
+constexpr int kPCS = 16;
+constexpr int kNB = 32;
+constexpr int kPLD = kNB + 1;  // padded row stride of the panel in shared memory
+constexpr int kPanelThreads = 256;
+constexpr size_t kPanelMaxSmem = 200 * 1024;
 
-__device__ int cl_search(const double* col, const int* rowdone, int k, double* sv, int* si) {
-    double best = -1.0;
-    int bi = -1;
-    for (int a = threadIdx.x; a < k; a += blockDim.x) {
-        if (rowdone[a]) continue;
-        const double v = fabs(col[a]);
-        if (v > best) { best = v; bi = a; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi >= 0 && (ov > best || (ov == best && (bi < 0 || oi < bi)))) { best = ov; bi = oi; }
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) { sv[w] = best; si[w] = bi; }
-    __syncthreads();
-    double b = -1.0;
-    int p = -1;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
-        if (si[i] >= 0 && (sv[i] > b || (sv[i] == b && si[i] < p))) { b = sv[i]; p = si[i]; }
-    return b > 0.0 ? p : -1;
+__device__ __forceinline__ unsigned long long mag_key(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    return u > 0x7ff0000000000000ull ? 0ull : u;  // a NaN never becomes a pivot
 }
 
-__global__ void __launch_bounds__(kClusterThreads) k_gj_cluster(DevState s, int k) {
+__device__ __forceinline__ bool cand_better(unsigned long long ka, int ra, unsigned long long kb, int rb) {
+    return ka > kb || (ka == kb && ra < rb);
+}
+
+__device__ __forceinline__ void warp_best(unsigned long long& bk, int& br) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const int orow = __shfl_xor_sync(0xffffffffu, br, o);
+        if (cand_better(ok, orow, bk, br)) { bk = ok; br = orow; }
+    }
+}
+
+size_t gj_panel_smem(int k) {
+    const size_t rpc = (size_t)((k + kPCS - 1) / kPCS);
+    return rpc * kPLD * sizeof(double) + rpc * sizeof(double) + rpc * sizeof(int);
+}
+
+__global__ void __launch_bounds__(kPanelThreads) k_gj_panel(DevState s, int k, int c0, int w) {
     namespace cg = cooperative_groups;
+    // Read before the first cluster barrier, so all CTAs see the same value
+    // (this kernel writes err only after that barrier).
+    if (s.ctrl->err != kErrNone) return;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int cpc = (k + kCS - 1) / kCS;
-    extern __shared__ double sm[];
-    double* cols = sm;                     // cpc columns of k
-    double* fbuf = cols + (size_t)cpc * k; // 2 x k pivot columns
-    double* gcol = fbuf + 2 * (size_t)k;   // cpc multipliers
-    int* pbuf = reinterpret_cast<int*>(gcol + cpc);  // [2] pivot rows
-    int* rowdone = pbuf + 2;               // k
-    __shared__ double sv[32];
-    __shared__ int si[32];
-    const int ld = s.p.ld;
-    for (int c = 0; c < cpc; ++c) {
-        const int t = rank + c * kCS;
-        if (t >= k) break;
-        const int jcol = s.basis[s.rv_struct_pos[t]];
-        for (int a = threadIdx.x; a < k; a += blockDim.x) cols[(size_t)c * k + a] = s.A_cm[(size_t)jcol * ld + s.rv_rows[a]];
+    const int rpc = (k + kPCS - 1) / kPCS;
+    const int a0 = rank * rpc;
+    const int nr = max(0, min(rpc, k - a0));
+    extern __shared__ double psm[];
+    double* pan = psm;                                          // rpc x kPLD, row-major
+    double* fcol = pan + (size_t)rpc * kPLD;                    // column t of the local rows
+    int* done = reinterpret_cast<int*>(fcol + rpc);             // row already a pivot
+    __shared__ double g[2][kNB];                                // scaled pivot row, by step parity
+    __shared__ unsigned long long ckey[2];
+    __shared__ int crow[2];
+    __shared__ int piv[kNB];
+    __shared__ double rinv_sh;
+    __shared__ int fail_sh;
+    for (int e = threadIdx.x; e < nr * w; e += blockDim.x) {
+        const int r = e % nr, t = e / nr;
+        pan[r * kPLD + t] = s.rv_M[(size_t)(c0 + t) * k + a0 + r];
     }
-    for (int a = threadIdx.x; a < k; a += blockDim.x) rowdone[a] = 0;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) done[r] = s.rv_rowdone[a0 + r];
+    if (threadIdx.x == 0) fail_sh = 0;
     __syncthreads();
-    auto broadcast = [&](const double* col, int p, int buf) {
-        for (int r = 0; r < kCS; ++r) {
-            double* dst = cl.map_shared_rank(fbuf + (size_t)buf * k, r);
-            for (int a = threadIdx.x; a < k; a += blockDim.x) dst[a] = col[a];
-            if (threadIdx.x == 0) *cl.map_shared_rank(pbuf + buf, r) = p;
-        }
-    };
-    if (rank == 0) {
-        const int p0 = cl_search(cols, rowdone, k, sv, si);
-        broadcast(cols, p0, 0);
-    }
-    cl.sync();
-    int fail = 0;
-    for (int j = 0; j < k; ++j) {
-        const int buf = j & 1;
-        const int p = pbuf[buf];
-        if (p < 0) { fail = 1; break; }
-        const double* f = fbuf + (size_t)buf * k;
-        const double pv = f[p];
-        if (threadIdx.x == 0) rowdone[p] = 1;
-        if (rank == 0 && threadIdx.x == 0) s.rv_pivrow[j] = p;
-        // multipliers of the local columns (row p / pivot), read before any write
-        for (int c = threadIdx.x; c < cpc; c += blockDim.x) {
-            const int t = rank + c * kCS;
-            gcol[c] = (t < k && t != j) ? cols[(size_t)c * k + p] / pv : 0.0;
-        }
-        __syncthreads();
-        const int nxt = j + 1;
-        const int own_next = (nxt < k && rank == nxt % kCS) ? nxt / kCS : -1;
-        auto upd = [&](int c) {
-            const int t = rank + c * kCS;
-            double* col = cols + (size_t)c * k;
-            if (t == j) {
-                for (int a = threadIdx.x; a < k; a += blockDim.x) col[a] = (a == p) ? 1.0 / pv : -f[a] / pv;
-            } else {
-                const double g = gcol[c];
-                for (int a = threadIdx.x; a < k; a += blockDim.x) col[a] = (a == p) ? g : fma(-f[a], g, col[a]);
+    int prev_local = -1;  // local row of the previous step's pivot, if owned here
+    for (int t = 0; t < w; ++t) {
+        const int par = t & 1;
+        if (threadIdx.x < 32) {
+            unsigned long long bk = 0ull;
+            int br = 0x7fffffff;
+            for (int r = threadIdx.x; r < nr; r += 32) {
+                if (done[r]) continue;
+                const unsigned long long kk = mag_key(pan[r * kPLD + t]);
+                if (cand_better(kk, a0 + r, bk, br)) { bk = kk; br = a0 + r; }
             }
-        };
-        if (own_next >= 0) {
-            upd(own_next);
-            __syncthreads();
-            const int pn = cl_search(cols + (size_t)own_next * k, rowdone, k, sv, si);
-            broadcast(cols + (size_t)own_next * k, pn, nxt & 1);
-        }
-        for (int c = 0; c < cpc; ++c) {
-            if (c == own_next || rank + c * kCS >= k) continue;
-            upd(c);
+            warp_best(bk, br);
+            if (threadIdx.x == 0) { ckey[par] = bk; crow[par] = br; }
         }
         cl.sync();
+        if (threadIdx.x < 32) {
+            unsigned long long bk = 0ull;
+            int br = 0x7fffffff;
+            if (threadIdx.x < kPCS) {
+                bk = *cl.map_shared_rank(&ckey[par], threadIdx.x);
+                br = *cl.map_shared_rank(&crow[par], threadIdx.x);
+            }
+            warp_best(bk, br);
+            if (bk == 0ull || br < 0 || br >= k) {
+                if (threadIdx.x == 0) fail_sh = 1;
+            } else {
+                const int owner = br / rpc;
+                const double* src = cl.map_shared_rank(pan, owner) + (size_t)(br - owner * rpc) * kPLD;
+                const double pr = threadIdx.x < w ? src[threadIdx.x] : 0.0;
+                const double pv = __shfl_sync(0xffffffffu, pr, t);
+                const double ri = 1.0 / pv;
+                if (threadIdx.x < w) g[par][threadIdx.x] = (threadIdx.x == t) ? ri : pr * ri;
+                if (threadIdx.x == 0) { piv[t] = br; rinv_sh = ri; }
+            }
+        } else {
+            for (int r = threadIdx.x - 32; r < nr; r += blockDim.x - 32)
+                fcol[r] = (r == prev_local) ? g[par ^ 1][t] : pan[r * kPLD + t];
+        }
+        __syncthreads();
+        if (fail_sh) break;
+        const int p = piv[t];
+        const int lp = (p >= a0 && p < a0 + nr) ? p - a0 : -1;
+        const double ri = rinv_sh;
+        for (int e = threadIdx.x; e < nr * w; e += blockDim.x) {
+            const int r = e / w, j = e - r * w;
+            if (r == lp) continue;  // read by the other CTAs during this step
+            const double f = fcol[r];
+            const double old = (r == prev_local) ? g[par ^ 1][j] : pan[r * kPLD + j];
+            pan[r * kPLD + j] = (j == t) ? -f * ri : fma(-f, g[par][j], old);
+        }
+        if (lp >= 0 && threadIdx.x == 0) done[lp] = 1;
+        prev_local = lp;
+        __syncthreads();
     }
-    if (fail && rank == 0 && threadIdx.x == 0) s.ctrl->err = kErrSingular;
-    // columns back to global (column-major), as the assembly kernels expect
-    for (int c = 0; c < cpc; ++c) {
-        const int t = rank + c * kCS;
-        if (t >= k) break;
-        for (int a = threadIdx.x; a < k; a += blockDim.x) s.rv_M[(size_t)t * k + a] = cols[(size_t)c * k + a];
+    cl.sync();  // every CTA has read the last pivot row
+    const int fail = fail_sh;
+    if (!fail && prev_local >= 0) {
+        const int lw = (w - 1) & 1;
+        for (int j = threadIdx.x; j < w; j += blockDim.x) pan[prev_local * kPLD + j] = g[lw][j];
+    }
+    __syncthreads();
+    if (fail) {
+        if (rank == 0 && threadIdx.x == 0) s.ctrl->err = kErrSingular;
+        return;
+    }
+    for (int e = threadIdx.x; e < nr * w; e += blockDim.x) {
+        const int r = e % nr, t = e / nr;
+        s.rv_M[(size_t)(c0 + t) * k + a0 + r] = pan[r * kPLD + t];
+    }
+    if (rank == 0)
+        for (int t = threadIdx.x; t < w; t += blockDim.x) {
+            s.rv_pivrow[c0 + t] = piv[t];
+            s.rv_rowdone[piv[t]] = 1;
+        }
+    // rows p_t of every column outside the panel: copy to rv_W (t-major), then zero
+    const int nout = k - w;
+    const size_t tot = (size_t)w * nout;
+    for (size_t e = (size_t)rank * blockDim.x + threadIdx.x; e < tot; e += (size_t)kPCS * blockDim.x) {
+        const int t = (int)(e / nout), o = (int)(e % nout);
+        const int j = o < c0 ? o : o + w;
+        double* src = s.rv_M + (size_t)j * k + piv[t];
+        s.rv_W[(size_t)t * k + j] = *src;
+        *src = 0.0;
     }
 }
 
-size_t gj_cluster_smem(int k) {
-    const int cpc = (k + kCS - 1) / kCS;
-    return ((size_t)cpc * k + 2 * (size_t)k + cpc) * sizeof(double) + (2 + (size_t)k) * sizeof(int);
+// M[:, j] += Panel * R[:, j] for every column j outside the panel (R = rows
+// p_t of those columns, saved by k_gj_panel); a warp's lanes are 32
+// consecutive rows, each thread accumulates 4 columns over the panel.
+constexpr int kTM = 32, kTN = 16, kTrailThreads = 128;
+__global__ void __launch_bounds__(kTrailThreads) k_gj_trail(DevState s, int k, int c0, int w) {
+    if (s.ctrl->err != kErrNone) return;
+    __shared__ double As[kNB][kTM];
+    __shared__ double Bs[kNB][kTN];
+    const int nout = k - w;
+    const int a0 = blockIdx.y * kTM, o0 = blockIdx.x * kTN;
+    for (int e = threadIdx.x; e < kTM * w; e += blockDim.x) {
+        const int r = e % kTM, t = e / kTM;
+        const int a = a0 + r;
+        As[t][r] = a < k ? s.rv_M[(size_t)(c0 + t) * k + a] : 0.0;
+    }
+    for (int e = threadIdx.x; e < kTN * w; e += blockDim.x) {
+        const int c = e % kTN, t = e / kTN;
+        const int o = o0 + c;
+        Bs[t][c] = o < nout ? s.rv_W[(size_t)t * k + (o < c0 ? o : o + w)] : 0.0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, c4 = (threadIdx.x >> 5) * 4;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = 0; t < w; ++t) {
+        const double av = As[t][lane];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = fma(av, Bs[t][c4 + c], acc[c]);
+    }
+    const int a = a0 + lane;
+    if (a >= k) return;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int o = o0 + c4 + c;
+        if (o >= nout) continue;
+        double* dst = s.rv_M + (size_t)(o < c0 ? o : o + w) * k + a;
+        *dst += acc[c];
+    }
 }
 
 // pinv[pivrow[t]] = t (stored over rv_rowdone, no longer needed)
@@ -481,40 +558,62 @@ void launch_reinv_classify(const DevState& s, cudaStream_t st) {
     k_classify<<<1, kClassifyThreads, 0, st>>>(s);
 }
 
+int reinv_gj_launches(int k) {
+    if (k <= 0) return 0;
+    if (gj_panel_smem(k) > kPanelMaxSmem) return k + 3;
+    const int panels = (k + kNB - 1) / kNB;
+    return 2 + panels + (k > kNB ? panels : 0);
+}
+
 void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t st) {
     if (k <= 0) return;
-    if (k <= kClusterMaxK) {
-        const size_t smem = gj_cluster_smem(k);
-        static bool configured = false;
-        if (!configured) {
-            cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)gj_cluster_smem(kClusterMaxK));
-            configured = true;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(kCS, 1, 1);
-        cfg.blockDim = dim3(kClusterThreads, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = kCS;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, k_gj_cluster, s, k) == cudaSuccess) {
-            k_pivinv<<<(k + 255) / 256, 256, 0, st>>>(s, k);
-            return;
-        }
-        (void)cudaGetLastError();  // cluster launch unavailable: per-step kernels below
-    }
     {
         const size_t total = (size_t)k * k;
         int blocks = (int)((total + 255) / 256);
         if (blocks > 4096) blocks = 4096;
         k_gather<<<blocks, 256, 0, st>>>(s, k);
+    }
+    const size_t smem = gj_panel_smem(k);
+    if (smem <= kPanelMaxSmem) {
+        cudaFuncSetAttribute(k_gj_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(k_gj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelMaxSmem);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kPCS, 1, 1);
+        cfg.blockDim = dim3(kPanelThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kPCS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        bool ok = true;
+        for (int c0 = 0; c0 < k && ok; c0 += kNB) {
+            const int w = k - c0 < kNB ? k - c0 : kNB;
+            if (cudaLaunchKernelEx(&cfg, k_gj_panel, s, k, c0, w) != cudaSuccess) {
+                ok = false;
+                break;
+            }
+            if (w < k) {
+                const dim3 grid((k - w + kTN - 1) / kTN, (k + kTM - 1) / kTM);
+                k_gj_trail<<<grid, kTrailThreads, 0, st>>>(s, k, c0, w);
+            }
+        }
+        if (ok) {
+            k_pivinv<<<(k + 255) / 256, 256, 0, st>>>(s, k);
+            return;
+        }
+        // A refused cluster launch: redo the elimination from a fresh B11
+        // with the per-step kernels.
+        (void)cudaGetLastError();
+        {
+            const size_t total = (size_t)k * k;
+            int blocks = (int)((total + 255) / 256);
+            if (blocks > 4096) blocks = 4096;
+            k_gather<<<blocks, 256, 0, st>>>(s, k);
+        }
     }
     k_gj_search0<<<1, kStepThreads, 0, st>>>(s, k);
     int blocks = k < 2 * g.sms ? k : 2 * g.sms;

@@ -178,6 +178,7 @@ void configure_iter_kernels(int ld);
 // ---- reinversion (kernels_reinv.cu) -------------------------------------------
 void launch_reinv_classify(const DevState& s, cudaStream_t st);
 void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t st);
+int reinv_gj_launches(int k);
 void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st);
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible);
 int occupancy_price(int ld);

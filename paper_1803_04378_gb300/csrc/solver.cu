@@ -165,7 +165,7 @@ int reinvert(lp_handle* h, int check_feasible) {
     TRY(read_ctrl(h));
     if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
     const int k = h->h_ctrl->k_struct;
-    h->launches += 1 + (k > 0 ? (k <= 512 ? 4 : k + 4) : 1) + 3;
+    h->launches += 1 + reinv_gj_launches(k) + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 3;
     CK(cudaEventRecord(h->erg, h->stream));
     launch_reinv_gj(h->ds, k, h->geo, h->stream);
     CK(cudaEventRecord(h->era, h->stream));

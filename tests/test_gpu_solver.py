@@ -118,6 +118,48 @@ def test_warm_start_reinversion_elementwise():
         assert z == pytest.approx(ref_full.objective, rel=1e-12)
 
 
+def _basis_with_k_structurals(m, n, k, seed):
+    """A feasible basis with exactly k structural columns: J (k columns) sit at
+    the positions of k rows R whose slacks are nonbasic; b = A[:, J] x_J + s
+    with x_J > 0 and s > 0 off R, so that bbar = (x_J, s) >= 0."""
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(0.0, 1.0, (m, n))
+    A[rng.uniform(size=(m, n)) < 0.1] = 0.0
+    J = rng.choice(n, k, replace=False)
+    R = np.sort(rng.choice(m, k, replace=False))
+    xJ = rng.uniform(1.0, 2.0, k)
+    s = rng.uniform(1.0, 2.0, m)
+    s[R] = 0.0
+    b = A[:, J] @ xJ + s
+    c = rng.uniform(0.0, 1.0, n)
+    basis = np.arange(n, n + m, dtype=np.int32)
+    basis[R] = J
+    return A, b, c, basis
+
+
+@pytest.mark.parametrize("m,n,k", [(40, 60, 5), (80, 100, 32), (80, 100, 33), (150, 200, 64),
+                                   (150, 200, 65), (700, 900, 600)])
+def test_reinversion_panels(m, n, k):
+    """Fresh B^-1 of a basis with k structurals against the oracle's Gauss-Jordan
+    inverse of the whole basis matrix: covers CTAs that own no rows (k < 16),
+    panel edges (32/33, 64/65) and more rows per CTA than a warp (k = 600)."""
+    A, b, c, basis = _basis_with_k_structurals(m, n, k, 40 + k)
+    from paper_1803_04378_gb300 import lpgb
+    with lpgb.LP(A, b, c, max_iters=0) as lp:
+        lp.set_basis(basis)
+        res = lp.solve()
+        assert res.status == 3 and res.reinversions == 1
+        binv, bbar = lp.state()
+        y = lp.solution()[1]
+    ref = oracle.solve(A, b, c, oracle.Options(max_iters=0), start_basis=basis, want_binv=True)
+    scale = max(1.0, np.max(np.abs(ref.binv)))
+    assert np.max(np.abs(binv - ref.binv)) <= 1e-9 * scale
+    assert np.max(np.abs(bbar - ref.bbar)) <= 1e-9 * max(1.0, np.max(np.abs(ref.bbar)))
+    assert np.max(np.abs(y - ref.y)) <= 1e-9 * max(1.0, np.max(np.abs(ref.y)))
+    B = np.hstack([A, np.eye(m)])[:, basis]
+    assert np.max(np.abs(binv @ B - np.eye(m))) <= 1e-9 * scale
+
+
 def test_reinvert_every_pivot_same_path():
     A, b, c = lpgen.dense_real_lp(120, 200, 12)
     lp, res, x, y, z, tr = gpu_solve(A, b, c, reinvert_every=1)
