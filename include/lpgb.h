@@ -73,7 +73,9 @@ typedef struct lp_options {
                                larger values act as 2); batches: candidates per LP (1..8) */
     int32_t trace_cap;      /* record (q, r, theta, d_q, flags) of the first trace_cap pivots */
     int32_t graph_iters;    /* pivots per captured CUDA graph launch */
-    int32_t kernel_timing;  /* 1: time every PRICE and UPDATE launch with CUDA events */
+    int32_t kernel_timing;  /* s >= 1: time the PRICE and UPDATE launches of every s-th
+                               pivot of each captured graph with CUDA events (1 = all);
+                               timed pivots run without launch overlap */
     int32_t reserved_;      /* must be 0 */
     double tol_d;           /* optimality tolerance on the reduced costs */
     double tol_piv;         /* smallest admissible pivot alpha_r */

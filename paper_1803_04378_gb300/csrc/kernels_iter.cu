@@ -25,14 +25,62 @@ namespace lpgb {
 
 namespace {
 
-constexpr int kPriceThreads = 512;
-constexpr int kUpdateThreads = 512;
+constexpr int kPriceThreads = 1024;
+constexpr int kOct = 4;   // columns per warp in k_price
+constexpr int kSeg = 2;   // row segments per column in k_price
+constexpr int kPriceCols = kPriceThreads / 32 / kSeg * kOct;  // columns per block per round
+constexpr int kUpdateThreads = 1024;
 constexpr int kPivotThreads = 64;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Warp sum in the pairing order of k_price's transposed reduction (lanes
+// 16 apart, then 8, 1, 2, 4), so that a column's d_j does not depend on the
+// width of the group it was priced in.
+__device__ __forceinline__ double pair_sum(double t) {
+    t += __shfl_xor_sync(0xffffffffu, t, 16);
+    t += __shfl_xor_sync(0xffffffffu, t, 8);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 4);
+    return t;
+}
+
+// acc[c] = sum over this lane's elements k0+lane, k0+lane+32, ... < k1 of
+// column cols[c] (double2 units) times y.  Register double buffering: the W
+// loads of the next step are issued before the FMAs of the current one, so a
+// warp always has a step's worth of reads in flight while it computes.
+template <int W>
+__device__ __forceinline__ void dot_cols(const double2* __restrict__ A2, const int* cols, int half,
+                                         const double2* y2, int k0, int k1, int lane, double (&acc)[W]) {
+    const double2* p[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+        p[c] = A2 + (size_t)cols[c] * half;
+        acc[c] = 0.0;
+    }
+    int k = k0 + lane;
+    if (k >= k1) return;
+    double2 nx[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) nx[c] = __ldcs(p[c] + k);
+#pragma unroll 1
+    for (; k < k1; k += 32) {
+        double2 cur[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) cur[c] = nx[c];
+        if (k + 32 < k1) {
+#pragma unroll
+            for (int c = 0; c < W; ++c) nx[c] = __ldcs(p[c] + k + 32);
+        }
+        const double2 yv = y2[k];
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[c] = fma(cur[c].y, yv.y, fma(cur[c].x, yv.x, acc[c]));
+    }
 }
 
 // ---- CHUZC candidate ---------------------------------------------------------
@@ -163,6 +211,7 @@ __global__ void k_init_slack(DevState s) {
 
 // ---- k_pivot -----------------------------------------------------------------------
 __global__ void __launch_bounds__(kPivotThreads) k_pivot(DevState s) {
+    pdl_enter();
     Ctrl* C = s.ctrl;
     const Params& P = s.p;
     if (C->status != kRunning || C->r < 0 || C->r >= P.m || C->q < 0) return;
@@ -233,7 +282,8 @@ __global__ void __launch_bounds__(kPivotThreads) k_pivot(DevState s) {
 }
 
 // ---- k_price: PRICE + CHUZC -----------------------------------------------------
-__global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
+__global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
+    pdl_enter();
     Ctrl* C = s.ctrl;
     if (C->status != kRunning) return;
     const Params& P = s.p;
@@ -245,66 +295,130 @@ __global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
     __syncthreads();
     const int it = C->it;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
     const int half = P.ld >> 1;
     const double2* y2 = reinterpret_cast<const double2*>(ysh);
-    Cand cand;
-    cand_init(cand);
-    // Columns are dealt to blocks round-robin (block b owns j = b, b+G, b+2G,
-    // ...) so every SM gets the same share; each warp takes two owned columns
-    // at a time, so one shared-memory load of y feeds four FMAs.
+    // Columns are dealt to blocks round-robin (block b owns j = b, b+G, ...)
+    // so every SM gets the same share.  The block first lists its nonbasic
+    // columns; then each warp takes kOct listed columns over one of kSeg row
+    // segments, so one shared-memory load of y feeds 2*kOct FMAs, 2*kOct
+    // independent 512-byte loads are in flight per step, and the kOct partial
+    // sums leave the warp through one transposed reduction (6 adds for 4
+    // columns instead of 5 per column).  The segment sums of a column are
+    // added in a fixed order, so d_j does not depend on where j was listed.
+    // Candidates live in shared memory (one per offering thread) so that no
+    // registers are held across the streaming loops.
+    __shared__ Cand csh[kPriceCols];
+    __shared__ int jl[kPriceThreads];
+    __shared__ double part[kSeg][kPriceCols];
+    __shared__ int wcnt[kPriceThreads / 32];
+    if (threadIdx.x < kPriceCols) cand_init(csh[threadIdx.x]);
     const int G = gridDim.x;
     const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
-    for (int l = 2 * warp; l < owned; l += 2 * nw) {
-        const int jA = blockIdx.x + G * l;
-        const int jB = (l + 1 < owned) ? jA + G : -1;
-        const bool nbA = s.pos[jA] < 0;
-        const bool nbB = jB >= 0 && s.pos[jB] < 0;
-        if (nbA && nbB) {
-            const double2* ca = reinterpret_cast<const double2*>(s.A_cm + (size_t)jA * P.ld);
-            const double2* cb = reinterpret_cast<const double2*>(s.A_cm + (size_t)jB * P.ld);
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
-            int k = lane;
-#pragma unroll 2
-            for (; k + 32 < half; k += 64) {
-                const double2 u0 = __ldcs(ca + k), u1 = __ldcs(ca + k + 32);
-                const double2 v0 = __ldcs(cb + k), v1 = __ldcs(cb + k + 32);
-                const double2 y0 = y2[k], y1 = y2[k + 32];
-                a0 = fma(u0.x, y0.x, a0); a1 = fma(u0.y, y0.y, a1);
-                a2 = fma(u1.x, y1.x, a2); a3 = fma(u1.y, y1.y, a3);
-                b0 = fma(v0.x, y0.x, b0); b1 = fma(v0.y, y0.y, b1);
-                b2 = fma(v1.x, y1.x, b2); b3 = fma(v1.y, y1.y, b3);
+    const int nch = half >> 5;  // 32-double2 chunks per column
+    const int seg = warp % kSeg, gi = warp / kSeg;
+    const int k0 = 32 * (seg * nch / kSeg), k1 = 32 * ((seg + 1) * nch / kSeg);
+    const double2* A2 = reinterpret_cast<const double2*>(s.A_cm);
+    for (int lb = 0; lb < owned; lb += kPriceThreads) {
+        // list the nonbasic owned columns lb .. lb+kPriceThreads-1, in order
+        const int l = lb + (int)threadIdx.x;
+        const int jj = (int)blockIdx.x + G * l;
+        const bool nb = l < owned && s.pos[jj] < 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, nb);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, cnt = 0;
+        for (int w = 0; w < kPriceThreads / 32; ++w) {
+            const int cw = wcnt[w];
+            if (w < warp) before += cw;
+            cnt += cw;
+        }
+        if (nb) jl[before + __popc(bal & ((1u << lane) - 1u))] = jj;
+        __syncthreads();
+        // Groups of 4 listed columns, and of 3 where cnt is not a multiple of 4,
+        // so that every warp streams 3 or 4 columns at a time (a lone column
+        // would run latency-bound long after the others); only lists shorter
+        // than the 3-groups they would need fall back to groups of 1 or 2.
+        const int n3 = (4 - (cnt & 3)) & 3;
+        const bool mixed = cnt >= 3 * n3;
+        const int n4 = mixed ? (cnt - 3 * n3) / 4 : cnt / 4;
+        const int ngrp = mixed ? n4 + n3 : (cnt + 3) / 4;
+        for (int gb = 0; gb < ngrp; gb += kPriceThreads / 32 / kSeg) {
+            const int g = gb + gi;
+            int e0 = 0, width = 0;
+            if (g < ngrp) {
+                if (!mixed) { e0 = 4 * g; width = min(4, cnt - e0); }
+                else if (g < n4) { e0 = 4 * g; width = 4; }
+                else { e0 = 4 * n4 + 3 * (g - n4); width = 3; }
             }
-            for (; k < half; k += 32) {
-                const double2 u0 = __ldcs(ca + k), v0 = __ldcs(cb + k), y0 = y2[k];
-                a0 = fma(u0.x, y0.x, a0); a1 = fma(u0.y, y0.y, a1);
-                b0 = fma(v0.x, y0.x, b0); b1 = fma(v0.y, y0.y, b1);
+            const int slot = gi * kOct;  // part[] slots of this warp's group
+            if (width == 4) {
+                double acc[4];
+                dot_cols<4>(A2, jl + e0, half, y2, k0, k1, lane, acc);
+                // transposed reduction: lane L ends with column ((L>>4)&1)*2 + ((L>>3)&1)
+                const bool h16 = lane & 16, h8 = lane & 8;
+                double r2[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const double send = h16 ? acc[i] : acc[2 + i];
+                    const double keep = h16 ? acc[2 + i] : acc[i];
+                    r2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
+                const double send = h8 ? r2[0] : r2[1];
+                double r1 = (h8 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, send, 8);
+                r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
+                r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
+                r1 += __shfl_xor_sync(0xffffffffu, r1, 4);
+                const int c = (h16 ? 2 : 0) + (h8 ? 1 : 0);
+                if ((lane & 7) == 0) part[seg][slot + c] = r1;
+            } else if (width == 3) {
+                double acc[3];
+                dot_cols<3>(A2, jl + e0, half, y2, k0, k1, lane, acc);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double t = pair_sum(acc[c]);
+                    if (lane == 0) part[seg][slot + c] = t;
+                }
+            } else if (width == 2) {
+                double acc[2];
+                dot_cols<2>(A2, jl + e0, half, y2, k0, k1, lane, acc);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const double t = pair_sum(acc[c]);
+                    if (lane == 0) part[seg][slot + c] = t;
+                }
+            } else if (width == 1) {
+                double acc[1];
+                dot_cols<1>(A2, jl + e0, half, y2, k0, k1, lane, acc);
+                const double t = pair_sum(acc[0]);
+                if (lane == 0) part[seg][slot] = t;
             }
-            const double da = s.c[jA] - warp_sum((a0 + a1) + (a2 + a3));
-            const double db = s.c[jB] - warp_sum((b0 + b1) + (b2 + b3));
-            cand_offer(cand, da, jA, s.tabu_until[jA] <= it, P.tol_d, s.rank[jA]);
-            cand_offer(cand, db, jB, s.tabu_until[jB] <= it, P.tol_d, s.rank[jB]);
-        } else if (nbA || nbB) {
-            const int j = nbA ? jA : jB;
-            const double2* col = reinterpret_cast<const double2*>(s.A_cm + (size_t)j * P.ld);
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            int k = lane;
-#pragma unroll 4
-            for (; k + 32 < half; k += 64) {
-                const double2 u = __ldcs(col + k), v = __ldcs(col + k + 32);
-                const double2 yu = y2[k], yv = y2[k + 32];
-                a0 = fma(u.x, yu.x, a0); a1 = fma(u.y, yu.y, a1);
-                a2 = fma(v.x, yv.x, a2); a3 = fma(v.y, yv.y, a3);
+            __syncthreads();
+            // thread t < kPriceCols: column t of this round = group t/4, member t%4
+            if (threadIdx.x < kPriceCols) {
+                const int gg = gb + (int)threadIdx.x / kOct, c = (int)threadIdx.x % kOct;
+                int ee = -1;
+                if (gg < ngrp) {
+                    if (!mixed) ee = (4 * gg + c < cnt) ? 4 * gg + c : -1;
+                    else if (gg < n4) ee = 4 * gg + c;
+                    else ee = c < 3 ? 4 * n4 + 3 * (gg - n4) + c : -1;
+                }
+                if (ee >= 0) {
+                    const int j = jl[ee];
+                    double sum = part[0][threadIdx.x];
+#pragma unroll
+                    for (int t = 1; t < kSeg; ++t) sum += part[t][threadIdx.x];
+                    Cand cc = csh[threadIdx.x];
+                    cand_offer(cc, s.c[j] - sum, j, s.tabu_until[j] <= it, P.tol_d, s.rank[j]);
+                    csh[threadIdx.x] = cc;
+                }
             }
-            for (; k < half; k += 32) {
-                const double2 u = __ldcs(col + k), yu = y2[k];
-                a0 = fma(u.x, yu.x, a0); a1 = fma(u.y, yu.y, a1);
-            }
-            const double d = s.c[j] - warp_sum((a0 + a1) + (a2 + a3));
-            cand_offer(cand, d, j, s.tabu_until[j] <= it, P.tol_d, s.rank[j]);
+            __syncthreads();
         }
     }
+    Cand cand;
+    cand_init(cand);
+    if (threadIdx.x < kPriceCols) cand = csh[threadIdx.x];
     // slack columns: d_{n+i} = -y_i
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.m; i += gridDim.x * blockDim.x) {
         const int j = P.n + i;
@@ -371,7 +485,8 @@ __global__ void __launch_bounds__(kPriceThreads, 2) k_price(DevState s) {
 }
 
 // ---- k_update: B^-1 update + FTRAN + ratio test -------------------------------------
-__global__ void __launch_bounds__(kUpdateThreads) k_update(DevState s) {
+__global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
+    pdl_enter();
     Ctrl* C = s.ctrl;
     const Params& P = s.p;
     const int status = C->status;
@@ -404,93 +519,55 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(DevState s) {
     const double2* rh2 = reinterpret_cast<const double2*>(rh);
     double tmin = DBL_MAX;
     // Rows are dealt to blocks round-robin (block b owns i = b, b+G, ...) so
-    // every SM gets the same share; each warp takes two owned rows at a time.
+    // every SM gets the same share, and to the block's warps one row at a
+    // time, which spreads them evenly over the SM's four schedulers.  Each
+    // warp keeps kS 512-byte reads of its row in flight.
     const int G = gridDim.x;
     const int owned = (P.m - (int)blockIdx.x + G - 1) / G;
-    for (int l = 2 * warp; l < owned; l += 2 * nw) {
-        const int i0 = blockIdx.x + G * l;
-        const int i1 = (l + 1 < owned) ? i0 + G : -1;
-        double al0 = 0.0, al1 = 0.0;
-        const bool pair = i1 >= 0 && !(do_upd && (i0 == r || i1 == r));
-        if (pair) {
-            double2* r0 = reinterpret_cast<double2*>(s.binv + (size_t)i0 * P.ld);
-            double2* r1 = reinterpret_cast<double2*>(s.binv + (size_t)i1 * P.ld);
-            double a0 = 0.0, a1 = 0.0, c0 = 0.0, c1 = 0.0;
-            if (do_upd) {
-                const double na0 = -acur[i0], na1 = -acur[i1];
-                const bool st0 = na0 != 0.0, st1 = na1 != 0.0;
+    for (int l = warp; l < owned; l += nw) {
+        const int i = blockIdx.x + G * l;
+        double2* row = reinterpret_cast<double2*>(s.binv + (size_t)i * P.ld);
+        double a0 = 0.0, a1 = 0.0;
+        if (do_upd && i == r) {
+            // the pivot row becomes rho (no read of the old row)
+            for (int k = lane; k < half; k += 32) {
+                const double2 v = rh2[k];
+                __stcs(row + k, v);
                 if (do_ftran) {
-#pragma unroll 2
-                    for (int k = lane; k < half; k += 32) {
-                        double2 v = __ldcs(r0 + k), u = __ldcs(r1 + k);
-                        const double2 p = rh2[k], w = aq2[k];
-                        v.x = fma(na0, p.x, v.x); v.y = fma(na0, p.y, v.y);
-                        u.x = fma(na1, p.x, u.x); u.y = fma(na1, p.y, u.y);
-                        if (st0) __stcs(r0 + k, v);
-                        if (st1) __stcs(r1 + k, u);
-                        a0 = fma(v.x, w.x, a0); a1 = fma(v.y, w.y, a1);
-                        c0 = fma(u.x, w.x, c0); c1 = fma(u.y, w.y, c1);
-                    }
-                } else {
-#pragma unroll 2
-                    for (int k = lane; k < half; k += 32) {
-                        double2 v = __ldcs(r0 + k), u = __ldcs(r1 + k);
-                        const double2 p = rh2[k];
-                        v.x = fma(na0, p.x, v.x); v.y = fma(na0, p.y, v.y);
-                        u.x = fma(na1, p.x, u.x); u.y = fma(na1, p.y, u.y);
-                        if (st0) __stcs(r0 + k, v);
-                        if (st1) __stcs(r1 + k, u);
-                    }
-                }
-            } else {
-#pragma unroll 4
-                for (int k = lane; k < half; k += 32) {
-                    const double2 v = __ldcs(r0 + k), u = __ldcs(r1 + k), w = aq2[k];
+                    const double2 w = aq2[k];
                     a0 = fma(v.x, w.x, a0); a1 = fma(v.y, w.y, a1);
-                    c0 = fma(u.x, w.x, c0); c1 = fma(u.y, w.y, c1);
                 }
-            }
-            if (do_ftran) {
-                al0 = warp_sum(a0 + a1);
-                al1 = warp_sum(c0 + c1);
             }
         } else {
-            // single rows: the pivot row, or the odd row left over
-            for (int h = 0; h < 2; ++h) {
-                const int i = h == 0 ? i0 : i1;
-                if (i < 0) continue;
-                double2* row = reinterpret_cast<double2*>(s.binv + (size_t)i * P.ld);
-                double a0 = 0.0, a1 = 0.0;
-                if (do_upd && i == r) {
-                    for (int k = lane; k < half; k += 32) {
-                        const double2 v = rh2[k];
-                        __stcs(row + k, v);
-                        const double2 w = aq2[k];
-                        a0 = fma(v.x, w.x, a0); a1 = fma(v.y, w.y, a1);
-                    }
-                } else {
-                    const double na = do_upd ? -acur[i] : 0.0;
-                    const bool st = na != 0.0;
-                    for (int k = lane; k < half; k += 32) {
-                        double2 v = __ldcs(row + k);
+            const double na = do_upd ? -acur[i] : 0.0;
+            const bool st = na != 0.0;
+            if (st || do_ftran) {
+                constexpr int kS = 4;
+                for (int k0 = lane; k0 < half; k0 += 32 * kS) {
+                    double2 v[kS];
+#pragma unroll
+                    for (int t = 0; t < kS; ++t)
+                        if (k0 + 32 * t < half) v[t] = __ldcs(row + k0 + 32 * t);
+#pragma unroll
+                    for (int t = 0; t < kS; ++t) {
+                        const int k = k0 + 32 * t;
+                        if (k >= half) break;
                         if (st) {
                             const double2 p = rh2[k];
-                            v.x = fma(na, p.x, v.x); v.y = fma(na, p.y, v.y);
-                            __stcs(row + k, v);
+                            v[t].x = fma(na, p.x, v[t].x); v[t].y = fma(na, p.y, v[t].y);
+                            __stcs(row + k, v[t]);
                         }
-                        const double2 w = aq2[k];
-                        a0 = fma(v.x, w.x, a0); a1 = fma(v.y, w.y, a1);
+                        if (do_ftran) {
+                            const double2 w = aq2[k];
+                            a0 = fma(v[t].x, w.x, a0); a1 = fma(v[t].y, w.y, a1);
+                        }
                     }
                 }
-                const double al = warp_sum(a0 + a1);
-                if (h == 0) al0 = al; else al1 = al;
             }
         }
-        if (do_ftran && lane == 0) {
-            for (int h = 0; h < 2; ++h) {
-                const int i = h == 0 ? i0 : i1;
-                if (i < 0) continue;
-                const double al = h == 0 ? al0 : al1;
+        if (do_ftran) {
+            const double al = warp_sum(a0 + a1);
+            if (lane == 0) {
                 anxt[i] = al;
                 double th = DBL_MAX;
                 if (al > P.tol_piv) th = s.bbar[i] / al;
@@ -626,19 +703,22 @@ void launch_init_slack(const DevState& s, cudaStream_t st) {
     k_init_slack<<<1024, 256, 0, st>>>(s);
 }
 
-void launch_pivot(const DevState& s, const Geometry& g, cudaStream_t st) {
-    k_pivot<<<g.pivot_blocks, kPivotThreads, 0, st>>>(s);
+void launch_pivot(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl) {
+    launch_k(k_pivot, dim3(g.pivot_blocks), dim3(kPivotThreads), 0, st, pdl, s);
 }
 
-void launch_price_lp(const DevState& s, const Geometry& g, cudaStream_t st);
+void launch_price_lp(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl);
 
-void launch_price(const DevState& s, const Geometry& g, cudaStream_t st) {
-    if (s.p.price_mode == 1) launch_price_lp(s, g, st);
-    k_price<<<g.price_blocks, kPriceThreads, price_smem_bytes(s.p.ld), st>>>(s);
+void launch_price(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl) {
+    if (s.p.price_mode == 1) {
+        launch_price_lp(s, g, st, pdl);
+        pdl = g.pdl != 0;  // k_price directly follows k_price_lp
+    }
+    launch_k(k_price, dim3(g.price_blocks), dim3(kPriceThreads), price_smem_bytes(s.p.ld), st, pdl, s);
 }
 
-void launch_update(const DevState& s, const Geometry& g, cudaStream_t st) {
-    k_update<<<g.update_blocks, kUpdateThreads, update_smem_bytes(s.p.ld), st>>>(s);
+void launch_update(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl) {
+    launch_k(k_update, dim3(g.update_blocks), dim3(kUpdateThreads), update_smem_bytes(s.p.ld), st, pdl, s);
 }
 
 int occupancy_price(int ld) {

@@ -75,6 +75,7 @@ __global__ void k_to_bf16(const double* __restrict__ src, uint16_t* __restrict__
 }
 
 __global__ void __launch_bounds__(kLpThreads, 2) k_price_lp(DevState s) {
+    pdl_enter();
     Ctrl* C = s.ctrl;
     if (C->status != kRunning || C->bland) return;
     const Params& P = s.p;
@@ -248,8 +249,9 @@ void launch_to_bf16(const double* src, uint16_t* dst, size_t count, cudaStream_t
     k_to_bf16<<<2048, 256, 0, st>>>(src, dst, count);
 }
 
-void launch_price_lp(const DevState& s, const Geometry& g, cudaStream_t st) {
-    k_price_lp<<<g.price_blocks, kLpThreads, (size_t)s.p.ld * (sizeof(float) + sizeof(double)), st>>>(s);
+void launch_price_lp(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl) {
+    launch_k(k_price_lp, dim3(g.price_lp_blocks), dim3(kLpThreads), (size_t)s.p.ld * (sizeof(float) + sizeof(double)),
+             st, pdl, s);
 }
 
 int occupancy_price_lp(int ld) {

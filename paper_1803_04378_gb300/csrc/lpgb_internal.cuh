@@ -158,19 +158,49 @@ struct DevState {
 };
 
 // ---- launch geometry -----------------------------------------------------
+// Programmatic dependent launch: wait for the previous kernel of the stream
+// (its completion and memory), then let the next kernel's CTAs be scheduled.
+// Both are no-ops for a kernel launched without the programmatic attribute.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch `kernel` on `st`, with programmatic stream serialization when pdl.
+template <typename... Args>
+inline cudaError_t launch_k(void (*kernel)(Args...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 struct Geometry {
     int sms;
     int price_blocks, price_threads;
+    int price_lp_blocks;  // BF16 screening kernel (price_mode 1)
     int update_blocks, update_threads;
     int pivot_blocks, pivot_threads;
+    int pdl;  // graph kernels use programmatic dependent launch
 };
 
 // ---- kernels (kernels_iter.cu) ----------------------------------------------
 void launch_init_slack(const DevState& s, cudaStream_t st);
-void launch_pivot(const DevState& s, const Geometry& g, cudaStream_t st);
-void launch_price(const DevState& s, const Geometry& g, cudaStream_t st);  // the whole PRICE + CHUZC of the mode
+// pdl: launch with programmatic stream serialization (the kernel may start
+// while the previous kernel of the stream finishes; it waits for that kernel's
+// completion and memory in griddepcontrol.wait before touching any state).
+void launch_pivot(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl = false);
+void launch_price(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl = false);  // the whole PRICE + CHUZC of the mode
 void launch_to_bf16(const double* src, uint16_t* dst, size_t count, cudaStream_t st);
-void launch_update(const DevState& s, const Geometry& g, cudaStream_t st);
+void launch_update(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl = false);
 size_t price_smem_bytes(int ld);
 size_t update_smem_bytes(int ld);
 void configure_iter_kernels(int ld);

@@ -38,7 +38,7 @@ struct lp_handle {
     std::vector<int32_t> warm_basis;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr, erg = nullptr, era = nullptr;
     double reinv_gj_s = 0.0, reinv_asm_s = 0.0;
-    std::vector<cudaEvent_t> tev;    // kernel_timing: 3 events per captured iteration
+    std::vector<cudaEvent_t> tev;    // kernel_timing: 3 events per timed iteration of the graph
     double reinvert_seconds = 0.0;
     // per-solve accumulators
     double price_s = 0.0, update_s = 0.0, price_b = 0.0, update_b = 0.0;
@@ -112,43 +112,56 @@ int setup_geometry(lp_handle* h) {
     Geometry& g = h->geo;
     g.sms = prop.multiProcessorCount;
     configure_iter_kernels(h->ld);
-    int occ_p = std::max(1, occupancy_price(h->ld));
-    if (h->opt.price_mode == 1) occ_p = std::min(occ_p, std::max(1, occupancy_price_lp(h->ld)));
-    const int occ_u = std::max(1, occupancy_update(h->ld));
-    g.price_threads = 512;
-    g.update_threads = 512;
+    const int occ_p = std::max(1, occupancy_price(h->ld));
+    g.price_threads = 1024;
+    g.update_threads = 1024;
     g.pivot_threads = 64;
-    // PRICE: columns dealt round-robin to sms * min(occupancy, 2) blocks
-    // (a whole number of blocks per SM), two columns per warp.
-    int pb = g.sms * std::min(occ_p, 2);
-    pb = std::min(pb, std::max(1, (h->n + 1) / 2));
-    g.price_blocks = std::max(1, pb);
-    // UPDATE: rows dealt round-robin to one block per SM, two rows per warp
+    // PRICE: columns dealt round-robin to one 1024-thread block per SM (the
+    // block's warps spread its column groups evenly over the SM's four
+    // schedulers).
+    g.price_blocks = std::max(1, std::min(g.sms * std::min(occ_p, 1), h->n));
+    // BF16 screen: sms * min(occupancy, 2) blocks, a whole number per SM
+    int lb = g.sms * 2;
+    if (h->opt.price_mode == 1) lb = g.sms * std::min(2, std::max(1, occupancy_price_lp(h->ld)));
+    g.price_lp_blocks = std::max(1, std::min(lb, std::max(1, (h->n + 1) / 2)));
+    // UPDATE: rows dealt round-robin to one block per SM, one row per warp
     // (one block per SM keeps the staging of rho and a_q to one copy per SM).
-    (void)occ_u;
-    int ub = std::min(g.sms, std::max(1, (h->m + 1) / 2));
+    int ub = std::min(g.sms, h->m);
     g.update_blocks = std::max(1, ub);
     // pivot bookkeeping: O(m) vector work, one element per thread spread over the SMs
     g.pivot_blocks = std::max(1, std::min(2 * g.sms, (h->ld + 63) / 64));
     return LP_OK;
 }
 
-int capture_graph(lp_handle* h) {
+// Kernel timing samples every `stride`-th iteration of the graph: events sit
+// around that iteration's kernels, and a kernel that follows an event is
+// launched without the programmatic attribute.
+int timing_stride(const lp_handle* h) { return h->opt.kernel_timing > 0 ? h->opt.kernel_timing : 0; }
+
+int capture_graph_once(lp_handle* h, bool pdl) {
     cudaGraph_t graph = nullptr;
     const int G = h->opt.graph_iters;
-    const bool timing = h->opt.kernel_timing != 0;
-    if (timing) {
-        h->tev.resize(3 * (size_t)G, nullptr);
-        for (auto& e : h->tev) CK(cudaEventCreate(&e));
-    }
+    const int stride = timing_stride(h);
+    int slot = 0;
+    bool after_event = true;  // the graph's first kernel follows no kernel of the graph
+    auto mark = [&](int which, bool timed) {
+        if (!timed) return;
+        cudaEventRecordWithFlags(h->tev[3 * (size_t)slot + which], h->stream, cudaEventRecordExternal);
+        after_event = true;
+    };
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int t = 0; t < G; ++t) {
-        launch_pivot(h->ds, h->geo, h->stream);
-        if (timing) cudaEventRecordWithFlags(h->tev[3 * t], h->stream, cudaEventRecordExternal);
-        launch_price(h->ds, h->geo, h->stream);
-        if (timing) cudaEventRecordWithFlags(h->tev[3 * t + 1], h->stream, cudaEventRecordExternal);
-        launch_update(h->ds, h->geo, h->stream);
-        if (timing) cudaEventRecordWithFlags(h->tev[3 * t + 2], h->stream, cudaEventRecordExternal);
+        const bool timed = stride > 0 && t % stride == 0;
+        launch_pivot(h->ds, h->geo, h->stream, pdl && !after_event);
+        after_event = false;
+        mark(0, timed);
+        launch_price(h->ds, h->geo, h->stream, pdl && !after_event);
+        after_event = false;
+        mark(1, timed);
+        launch_update(h->ds, h->geo, h->stream, pdl && !after_event);
+        after_event = false;
+        mark(2, timed);
+        if (timed) ++slot;
     }
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -156,6 +169,21 @@ int capture_graph(lp_handle* h) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e);
     return LP_OK;
+}
+
+int capture_graph(lp_handle* h) {
+    const int G = h->opt.graph_iters;
+    const int stride = timing_stride(h);
+    if (stride > 0) {
+        h->tev.resize(3 * (size_t)((G + stride - 1) / stride), nullptr);
+        for (auto& e : h->tev) CK(cudaEventCreate(&e));
+    }
+    h->geo.pdl = 1;
+    if (capture_graph_once(h, true) == LP_OK) return LP_OK;
+    // programmatic edges refused by this driver: plain stream order
+    (void)cudaGetLastError();
+    h->geo.pdl = 0;
+    return capture_graph_once(h, false);
 }
 
 // Rebuild B^-1, bbar, y, z from the current basis.
@@ -360,7 +388,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
         s.A_lp = lp;
     }
     TRY(setup_geometry(h));
-    const int parts = std::max(h->geo.price_blocks, h->geo.update_blocks);
+    const int parts = std::max(std::max(h->geo.price_blocks, h->geo.price_lp_blocks), h->geo.update_blocks);
     TRY(dalloc(h, &price_part, (size_t)parts));
     TRY(dalloc(h, &s.lp_part, (size_t)parts));
     TRY(dalloc(h, &upd_part, (size_t)parts));
@@ -397,7 +425,7 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     lp_options o;
     lp_default_options(&o);
     if (opt) o = *opt;
-    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.reserved_ != 0 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 ||
+    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.reserved_ != 0 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
         o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 1 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
@@ -550,18 +578,22 @@ int lp_solve(lp_handle* h, lp_result* out) {
                                         (A.n_full - before.n_full),
                                     h->opt.graph_iters);
             const int nu = std::min(A.n_update - before.n_update, h->opt.graph_iters);
-            for (int t = 0; t < np; ++t) {
+            // timed iterations are 0, stride, 2*stride, ...: slot i times iteration i*stride
+            const int stride = timing_stride(h);
+            const int tp = (np + stride - 1) / stride, tu = (nu + stride - 1) / stride;
+            for (int i = 0; i < tp; ++i) {
                 float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, h->tev[3 * t], h->tev[3 * t + 1]) == cudaSuccess) h->price_s += ms * 1e-3;
+                if (cudaEventElapsedTime(&ms, h->tev[3 * i], h->tev[3 * i + 1]) == cudaSuccess) h->price_s += ms * 1e-3;
             }
-            for (int t = 0; t < nu; ++t) {
+            for (int i = 0; i < tu; ++i) {
                 float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, h->tev[3 * t + 1], h->tev[3 * t + 2]) == cudaSuccess) h->update_s += ms * 1e-3;
+                if (cudaEventElapsedTime(&ms, h->tev[3 * i + 1], h->tev[3 * i + 2]) == cudaSuccess) h->update_s += ms * 1e-3;
             }
-            h->price_n += np;
-            h->update_n += nu;
-            h->price_b += A.bytes_price - before.bytes_price;
-            h->update_b += A.bytes_update - before.bytes_update;
+            h->price_n += tp;
+            h->update_n += tu;
+            // bytes of the timed launches: this graph's bytes in proportion
+            if (np > 0) h->price_b += (A.bytes_price - before.bytes_price) * tp / np;
+            if (nu > 0) h->update_b += (A.bytes_update - before.bytes_update) * tu / nu;
         }
     }
     CK(cudaEventRecord(h->ev1, h->stream));
