@@ -6,9 +6,11 @@
 // same aspiration and Bland safety net as the single-LP solver, and
 // structure-aware reinversion every `reinvert_every` pivots.  LPs are grouped
 // into size buckets (m <= 64, 128, 192, 256); every bucket has its own
-// persistent launch whose thread count and B^-1 residency (shared memory or
-// an L2-resident global slot per CTA) come from the autotuner.  Inside a
-// bucket the largest LPs go first so the tail is made of small ones.
+// persistent kernel whose thread count and B^-1 residency (shared memory or
+// an L2-resident global slot per CTA) come from the autotuner.  The bucket
+// kernels run side by side on forked streams, captured together as one CUDA
+// graph, so the tail of one bucket overlaps the others.  Inside a bucket the
+// largest LPs go first so the tail is made of small ones.
 //
 // PRICE (price_mode 1, the default for batches): a BF16 copy of A screens the
 // columns with FP32 FMAs, the top k are re-priced in FP64, and the full FP64
@@ -55,17 +57,19 @@ struct BatchState {
     double* x;
     double* y;
     int32_t* queue;             // one counter per bucket
-    double* scratch;            // per-CTA slots: [B^-1 if global] [reinversion block]
-    int64_t slot_doubles;
+    double* scratch[4];         // per bucket, per-CTA slots: [B^-1 if global] [reinversion block]
+    int64_t slot_doubles[4];    // 2 * (bucket's largest m)^2
     int32_t* trace_q;
     int32_t* trace_r;
 };
 
 constexpr int kBuckets = 4;
+static_assert(sizeof(BatchState::scratch) / sizeof(double*) == kBuckets, "one scratch area per bucket");
 constexpr int kBucketM[kBuckets] = {64, 128, 192, 256};
 constexpr int kBatchMaxM = 256;
 constexpr int kBatchMaxN = 512;
 constexpr int kBatchTopk = 8;
+constexpr int kSlotsPerSm = 8;  // scratch slots per SM and bucket (CTAs per SM at most)
 
 namespace {
 
@@ -596,9 +600,9 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
 }
 
 template <int T, bool SMEM>
-__global__ void __launch_bounds__(T) k_batch(BatchState s, int bucket, int begin, int count, int mmax, int nmax) {
+__global__ void __launch_bounds__(T, 1024 / T) k_batch(BatchState s, int bucket, int begin, int count, int mmax, int nmax) {
     extern __shared__ __align__(16) unsigned char smem[];
-    double* slot = s.scratch + (size_t)blockIdx.x * s.slot_doubles;
+    double* slot = s.scratch[bucket] + (size_t)blockIdx.x * s.slot_doubles[bucket];
     __shared__ int next;
     for (;;) {
         if (threadIdx.x == 0) next = atomicAdd(s.queue + bucket, 1);
@@ -651,6 +655,11 @@ struct lp_batch {
     int64_t sum_m = 0, sum_n = 0;
     BatchState st{};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // the buckets run side by side on their own streams, forked from and
+    // joined back into `stream`; the whole solve is one captured CUDA graph
+    cudaStream_t bstream[kBuckets] = {};
+    cudaEvent_t fork = nullptr, join[kBuckets] = {};
+    cudaGraphExec_t graph = nullptr;
     bool solved = false;
     double fp64_flops_per_iter_avg = 0.0;
 };
@@ -680,6 +689,12 @@ void bfree(lp_batch* h) {
     h->allocs.clear();
     if (h->e0) cudaEventDestroy(h->e0);
     if (h->e1) cudaEventDestroy(h->e1);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->fork) cudaEventDestroy(h->fork);
+    for (int bk = 0; bk < kBuckets; ++bk) {
+        if (h->join[bk]) cudaEventDestroy(h->join[bk]);
+        if (h->bstream[bk]) cudaStreamDestroy(h->bstream[bk]);
+    }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -701,22 +716,71 @@ int grid_for(const lp_batch* h, int bucket, int* grid, size_t* smem) {
     return LP_OK;
 }
 
-// Launch the buckets in [b0, b1) (largest bucket first).
-int launch_buckets(lp_batch* h, int b0, int b1) {
+struct BucketLaunch {
+    int grid = 0;
+    size_t smem = 0;
+};
+
+// Grid and shared memory of every non-empty bucket in [b0, b1).
+int plan_buckets(lp_batch* h, int b0, int b1, BucketLaunch* out) {
+    for (int bk = b0; bk < b1; ++bk) {
+        const int cnt = h->bucket_begin[bk + 1] - h->bucket_begin[bk];
+        out[bk] = BucketLaunch{};
+        if (cnt == 0) continue;
+        int rc = grid_for(h, bk, &out[bk].grid, &out[bk].smem);
+        if (rc != LP_OK) return rc;
+        out[bk].grid = std::min(std::min(out[bk].grid, h->sms * kSlotsPerSm), cnt);
+    }
+    return LP_OK;
+}
+
+// Launch the buckets in [b0, b1), largest first: one after another on
+// `stream`, or (concurrent) each on its own stream between a fork and a join,
+// so that a bucket's tail overlaps the next bucket.  Every bucket has its own
+// scratch slots, so concurrent buckets never share one.
+int launch_buckets(lp_batch* h, int b0, int b1, const BucketLaunch* plan, bool concurrent) {
     BCK(cudaMemsetAsync(h->st.queue, 0, sizeof(int32_t) * kBuckets, h->stream));
+    if (concurrent) BCK(cudaEventRecord(h->fork, h->stream));
     for (int bk = b1 - 1; bk >= b0; --bk) {
         const int begin = h->bucket_begin[bk], cnt = h->bucket_begin[bk + 1] - begin;
-        if (cnt == 0) continue;
-        int grid = 0;
-        size_t smem = 0;
-        int rc = grid_for(h, bk, &grid, &smem);
-        if (rc != LP_OK) return rc;
-        grid = std::min(grid, (int)(h->st.slot_doubles > 0 ? h->sms * 8 : grid));
-        grid = std::min(grid, cnt);
+        if (cnt == 0 || plan[bk].grid == 0) continue;
+        cudaStream_t st = h->stream;
+        if (concurrent) {
+            st = h->bstream[bk];
+            BCK(cudaStreamWaitEvent(st, h->fork, 0));
+        }
         BatchKernel k = batch_kernel(h->cfg_threads[bk], h->cfg_smem[bk] != 0);
-        k<<<grid, h->cfg_threads[bk], smem, h->stream>>>(h->st, bk, begin, cnt, kBucketM[bk], kBatchMaxN);
+        k<<<plan[bk].grid, h->cfg_threads[bk], plan[bk].smem, st>>>(h->st, bk, begin, cnt, kBucketM[bk], kBatchMaxN);
         BCK(cudaGetLastError());
+        if (concurrent) {
+            BCK(cudaEventRecord(h->join[bk], st));
+            BCK(cudaStreamWaitEvent(h->stream, h->join[bk], 0));
+        }
     }
+    return LP_OK;
+}
+
+// (Re)capture the whole solve as one graph after a change of the tuning.
+int capture_batch_graph(lp_batch* h) {
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    BucketLaunch plan[kBuckets];
+    int rc = plan_buckets(h, 0, kBuckets, plan);
+    if (rc != LP_OK) return rc;
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    rc = launch_buckets(h, 0, kBuckets, plan, true);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc != LP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    BCK(e);
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    BCK(e);
     return LP_OK;
 }
 
@@ -771,6 +835,11 @@ int lp_batch_create(lp_batch** out, int32_t count, const int32_t* m, const int32
         h->own_stream = true;
     }
     if (cudaEventCreate(&h->e0) != cudaSuccess || cudaEventCreate(&h->e1) != cudaSuccess) return fail(LP_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) return fail(LP_ERR_CUDA);
+    for (int bk = 0; bk < kBuckets; ++bk)
+        if (cudaStreamCreateWithFlags(&h->bstream[bk], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->join[bk], cudaEventDisableTiming) != cudaSuccess)
+            return fail(LP_ERR_CUDA);
     // host-side validation of host inputs
     if (!on_device) {
         for (int64_t e = 0; e < aoff; ++e)
@@ -818,12 +887,16 @@ int lp_batch_create(lp_batch** out, int32_t count, const int32_t* m, const int32
         (rc = balloc(h, &db, roff)) || (rc = balloc(h, &dc, coff)) || (rc = balloc(h, &dob, count)) ||
         (rc = balloc(h, &dx, coff)) || (rc = balloc(h, &dy, roff)))
         return fail(rc);
-    // per-CTA slots: B^-1 (global residency) + reinversion block, sized for the largest bucket
-    const int64_t slot = 2 * (int64_t)kBatchMaxM * kBatchMaxM;
-    const int slots = h->sms * 8;
-    if ((rc = balloc(h, &dscr, (size_t)slot * slots))) return fail(rc);
+    // per-CTA slots of each non-empty bucket: B^-1 (global residency) + reinversion block
+    for (int bk = 0; bk < kBuckets; ++bk) {
+        S.slot_doubles[bk] = 2 * (int64_t)kBucketM[bk] * kBucketM[bk];
+        S.scratch[bk] = nullptr;
+        if (h->bucket_begin[bk + 1] == h->bucket_begin[bk]) continue;
+        if ((rc = balloc(h, &dscr, (size_t)S.slot_doubles[bk] * h->sms * kSlotsPerSm))) return fail(rc);
+        S.scratch[bk] = dscr;
+    }
     S.lps = dl; S.order = dord; S.status = dst; S.iters = dit; S.queue = dq;
-    S.A = dA; S.b = db; S.c = dc; S.obj = dob; S.x = dx; S.y = dy; S.scratch = dscr; S.slot_doubles = slot;
+    S.A = dA; S.b = db; S.c = dc; S.obj = dob; S.x = dx; S.y = dy;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (cudaMemcpyAsync(dl, h->lps.data(), sizeof(BatchLP) * count, cudaMemcpyHostToDevice, h->stream) ||
         cudaMemcpyAsync(dord, idx.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, h->stream) ||
@@ -858,9 +931,12 @@ int lp_batch_create(lp_batch** out, int32_t count, const int32_t* m, const int32
 
 int lp_batch_solve(lp_batch* h, lp_batch_result* res) {
     if (!h) return LP_ERR_INVALID_ARG;
+    if (!h->graph) {
+        int rc = capture_batch_graph(h);
+        if (rc != LP_OK) return rc;
+    }
     BCK(cudaEventRecord(h->e0, h->stream));
-    int rc = launch_buckets(h, 0, kBuckets);
-    if (rc != LP_OK) return rc;
+    BCK(cudaGraphLaunch(h->graph, h->stream));
     BCK(cudaEventRecord(h->e1, h->stream));
     BCK(cudaEventSynchronize(h->e1));
     h->solved = true;
@@ -921,11 +997,19 @@ int lp_batch_set_tuning(lp_batch* h, const int32_t* table) {
         h->cfg_threads[bk] = table[2 * bk];
         h->cfg_smem[bk] = table[2 * bk + 1];
     }
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
     return LP_OK;
 }
 
 int lp_batch_tune(lp_batch* h, int32_t* table, int32_t trials) {
     if (!h || trials < 1) return LP_ERR_INVALID_ARG;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
     const int threads[3] = {128, 256, 512};
     for (int bk = 0; bk < kBuckets; ++bk) {
         if (h->bucket_begin[bk + 1] == h->bucket_begin[bk]) continue;
@@ -937,9 +1021,12 @@ int lp_batch_tune(lp_batch* h, int32_t* table, int32_t trials) {
                 h->cfg_threads[bk] = t;
                 h->cfg_smem[bk] = sm;
                 float tot = 0.f;
+                BucketLaunch plan[kBuckets];
+                int rc = plan_buckets(h, bk, bk + 1, plan);
+                if (rc != LP_OK) return rc;
                 for (int r = 0; r < trials; ++r) {
                     BCK(cudaEventRecord(h->e0, h->stream));
-                    int rc = launch_buckets(h, bk, bk + 1);
+                    rc = launch_buckets(h, bk, bk + 1, plan, false);
                     if (rc != LP_OK) return rc;
                     BCK(cudaEventRecord(h->e1, h->stream));
                     BCK(cudaEventSynchronize(h->e1));
