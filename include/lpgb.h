@@ -76,7 +76,9 @@ typedef struct lp_options {
     int32_t kernel_timing;  /* s >= 1: time the PRICE and UPDATE launches of every s-th
                                pivot of each captured graph with CUDA events (1 = all);
                                timed pivots run without launch overlap */
-    int32_t reserved_;      /* must be 0 */
+    int32_t engine;         /* 0: pivots of price_mode 0 run in one persistent cooperative
+                               kernel per graph_iters pivots (captured CUDA graphs where the
+                               device cannot); 1: always captured graphs of three kernels */
     double tol_d;           /* optimality tolerance on the reduced costs */
     double tol_piv;         /* smallest admissible pivot alpha_r */
     double tol_tie;         /* relative width of the ratio-test tie set */
@@ -110,7 +112,22 @@ typedef struct lp_result {
     int32_t full_passes;     /* price_mode 1: full FP64 PRICE passes (cumulative) */
     double reinvert_gj_seconds;       /* part of reinvert_seconds: elimination of B11 */
     double reinvert_assemble_seconds; /* part: B^-1 rows, bbar, duals */
+    double chain_seconds;    /* kernel_timing, persistent engine: device time of its launches */
+    double chain_bytes;      /* algorithmic PRICE + UPDATE bytes of those launches */
+    int32_t chain_launches;  /* persistent launches timed */
+    int32_t persistent;      /* 1: the pivots ran in the persistent kernel */
 } lp_result;
+
+/*
+ * lp_selftest_barrier_timeout -- checks the bounded wait of the persistent
+ * engine's grid barrier (no counterpart in the paper): a cooperative grid of
+ * `blocks` CTAs (1..64) waits at a barrier that expects one CTA more than it
+ * has.  Every CTA gives up after its spin limit (about 2 s), so the call
+ * returns LP_ERR_TIMEOUT and the context stays usable; LP_OK would mean the
+ * wait ended without the barrier completing, LP_ERR_CUDA a refused launch.
+ * Synchronizes `cuda_stream` (NULL = default stream).
+ */
+int lp_selftest_barrier_timeout(int32_t blocks, void* cuda_stream);
 
 /* Fills *opt with the defaults listed above. */
 void lp_default_options(lp_options* opt);

@@ -153,22 +153,27 @@ __device__ __forceinline__ bool rc_beats(const RCand& x, const RCand& y, bool bl
 }
 
 template <int T>
-__device__ RCand block_row(RCand c, bool bland, RCand* sh) {
+__device__ RCand block_row(RCand c, bool bland, RCand* sh, int& cnt, int* shc) {
     for (int o = 16; o > 0; o >>= 1) {
         RCand x;
         x.a = __shfl_xor_sync(0xffffffffu, c.a, o);
         x.var = __shfl_xor_sync(0xffffffffu, c.var, o);
         x.row = __shfl_xor_sync(0xffffffffu, c.row, o);
         if (rc_beats(x, c, bland)) c = x;
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();
-    if (lane == 0) sh[w] = c;
+    if (lane == 0) { sh[w] = c; shc[w] = cnt; }
     __syncthreads();
     RCand r = sh[0];
-    for (int i = 1; i < T / 32; ++i)
+    int total = shc[0];
+    for (int i = 1; i < T / 32; ++i) {
         if (rc_beats(sh[i], r, bland)) r = sh[i];
+        total += shc[i];
+    }
     __syncthreads();
+    cnt = total;
     return r;
 }
 
@@ -185,9 +190,82 @@ struct Red {
     RCand rc[32];
     double dv[32];
     int iv[32];
+    int kj[16 * kBatchTopk];   // top-K selection: each warp's kept columns
+    float kd[16 * kBatchTopk];
 };
 
 // ---------------------------------------------------------------- one LP
+// Top K (K <= kBatchTopk) screened columns, best first, in the order
+// (larger d, then smaller j); entries of -FLT_MAX are not candidates.  Each
+// warp ranks its columns among themselves by counting the columns that beat
+// them (no barrier), keeps ranks below K, and warp 0 ranks the kept columns of
+// all warps the same way: cand[t] is the t-th best (-1 when fewer exist).
+template <int T>
+__device__ void batch_topk(const float* dts, int n, int K, int* cand, int* kj, float* kd) {
+    constexpr int W = T / 32;
+    constexpr int V = (kBatchMaxN + T - 1) / T;  // columns per lane
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    auto beats = [](float da, int ja, float db, int jb) { return da > db || (da == db && ja < jb); };
+    float d[V];
+    int j[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        j[v] = (int)threadIdx.x + T * v;
+        d[v] = j[v] < n ? dts[j[v]] : -FLT_MAX;
+        if (d[v] == -FLT_MAX) j[v] = -1;
+    }
+    if (lane < K) kj[w * K + lane] = -1;
+    __syncwarp();
+    int rank[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) rank[v] = 0;
+    for (int src = 0; src < 32; ++src) {
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const float od = __shfl_sync(0xffffffffu, d[u], src);
+            const int oj = __shfl_sync(0xffffffffu, j[u], src);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (oj >= 0 && j[v] >= 0 && beats(od, oj, d[v], j[v])) rank[v]++;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if (j[v] >= 0 && rank[v] < K) {
+            kj[w * K + rank[v]] = j[v];
+            kd[w * K + rank[v]] = d[v];
+        }
+    __syncthreads();
+    if (w == 0) {
+        constexpr int C = (W * kBatchTopk + 31) / 32;  // kept columns per lane
+        float cd[C];
+        int cj[C], cr[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int e = lane + 32 * c;
+            cj[c] = e < W * K ? kj[e] : -1;
+            cd[c] = cj[c] >= 0 ? kd[e] : -FLT_MAX;
+            cr[c] = 0;
+        }
+        for (int src = 0; src < 32; ++src) {
+#pragma unroll
+            for (int u = 0; u < C; ++u) {
+                const float od = __shfl_sync(0xffffffffu, cd[u], src);
+                const int oj = __shfl_sync(0xffffffffu, cj[u], src);
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    if (oj >= 0 && cj[c] >= 0 && beats(od, oj, cd[c], cj[c])) cr[c]++;
+            }
+        }
+        if (lane < K) cand[lane] = -1;
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+            if (cj[c] >= 0 && cr[c] < K) cand[cr[c]] = cj[c];
+    }
+    __syncthreads();
+}
+
 template <int T, bool SMEM>
 __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, double* slot, int mmax, int nmax) {
     const BatchParams& P = s.p;
@@ -277,15 +355,7 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
             }
             __syncthreads();
             const int K = P.topk < kBatchTopk ? P.topk : kBatchTopk;
-            for (int t = 0; t < K; ++t) {
-                BCand bc = {-DBL_MAX, -1};
-                for (int j = tid; j < n; j += T)
-                    if (dts[j] > -FLT_MAX && bc_beats((double)dts[j], j, bc.d, bc.j)) bc = {(double)dts[j], j};
-                bc = block_best<T>(bc, R.bc);
-                if (tid == 0) cand[t] = bc.j;
-                if (bc.j >= 0 && tid == 0) dts[bc.j] = -FLT_MAX;
-                __syncthreads();
-            }
+            batch_topk<T>(dts, n, K, cand, R.kj, R.kd);
             // exact FP64 re-price: one warp per candidate
             const int warp = tid >> 5, lane = tid & 31;
             for (int t = warp; t < K; t += T / 32) {
@@ -441,8 +511,7 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
                 if (rc_beats(x, rc, bland)) rc = x;
             }
         }
-        rc = block_row<T>(rc, bland, R.rc);
-        cnt = block_sum_int<T>(cnt, R.iv);
+        rc = block_row<T>(rc, bland, R.rc, cnt, R.iv);  // best row and tie-set size together
         const int r = rc.row;
         const double ar = al[r];
         const double theta = th[r];

@@ -18,6 +18,7 @@
 // whole warp owns one row, so the row-r case is a warp-uniform branch and costs
 // nothing.
 #include "lpgb_internal.cuh"
+#include "../../include/lpgb.h"
 
 #include <cfloat>
 
@@ -31,6 +32,7 @@ constexpr int kSeg = 2;   // row segments per column in k_price
 constexpr int kPriceCols = kPriceThreads / 32 / kSeg * kOct;  // columns per block per round
 constexpr int kUpdateThreads = 1024;
 constexpr int kPivotThreads = 64;
+constexpr int kMaxFlagged = 64;  // k_iterate: CTAs scanned for the ratio-test tie set
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -281,19 +283,12 @@ __global__ void __launch_bounds__(kPivotThreads) k_pivot(DevState s) {
     __threadfence();
 }
 
-// ---- k_price: PRICE + CHUZC -----------------------------------------------------
-__global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
-    pdl_enter();
-    Ctrl* C = s.ctrl;
-    if (C->status != kRunning) return;
+// ---- PRICE of one block's columns (k_price and k_iterate) ---------------------------
+// ysh holds y.  pos and tabu_until, which the bookkeeping of a persistent
+// launch writes from another block, are read through L2.  Returns the block's
+// candidate in thread 0.
+__device__ Cand price_block(const DevState& s, int it, const double* ysh) {
     const Params& P = s.p;
-    // price_mode 1: this full FP64 pass only runs when the BF16 screen found no
-    // improving candidate, or under the Bland safety net
-    if (P.price_mode == 1 && !C->need_full && !C->bland) return;
-    extern __shared__ double ysh[];
-    for (int k = threadIdx.x; k < P.ld; k += blockDim.x) ysh[k] = s.y[k];
-    __syncthreads();
-    const int it = C->it;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int half = P.ld >> 1;
@@ -323,7 +318,7 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
         // list the nonbasic owned columns lb .. lb+kPriceThreads-1, in order
         const int l = lb + (int)threadIdx.x;
         const int jj = (int)blockIdx.x + G * l;
-        const bool nb = l < owned && s.pos[jj] < 0;
+        const bool nb = l < owned && __ldcg(s.pos + jj) < 0;
         const unsigned bal = __ballot_sync(0xffffffffu, nb);
         if (lane == 0) wcnt[warp] = __popc(bal);
         __syncthreads();
@@ -409,7 +404,7 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
 #pragma unroll
                     for (int t = 1; t < kSeg; ++t) sum += part[t][threadIdx.x];
                     Cand cc = csh[threadIdx.x];
-                    cand_offer(cc, s.c[j] - sum, j, s.tabu_until[j] <= it, P.tol_d, s.rank[j]);
+                    cand_offer(cc, s.c[j] - sum, j, __ldcg(s.tabu_until + j) <= it, P.tol_d, s.rank[j]);
                     csh[threadIdx.x] = cc;
                 }
             }
@@ -422,25 +417,28 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
     // slack columns: d_{n+i} = -y_i
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.m; i += gridDim.x * blockDim.x) {
         const int j = P.n + i;
-        if (s.pos[j] >= 0) continue;
-        cand_offer(cand, -ysh[i], j, s.tabu_until[j] <= it, P.tol_d, s.rank[j]);
+        if (__ldcg(s.pos + j) >= 0) continue;
+        cand_offer(cand, -ysh[i], j, __ldcg(s.tabu_until + j) <= it, P.tol_d, s.rank[j]);
     }
-    Cand bc = cand_block_reduce(cand);
-    if (threadIdx.x == 0) {
-        PriceCand pc;
-        pc.d_all = bc.d_all; pc.j_all = bc.j_all;
-        pc.d_nt = bc.d_nt; pc.j_nt = bc.j_nt;
-        pc.d_min = bc.d_min; pc.j_min = bc.j_min;
-        pc.d_pr = bc.d_pr; pc.j_pr = bc.j_pr; pc.k_pr = bc.k_pr;
-        pc.pad_ = 0;
-        s.price_part[blockIdx.x] = pc;
-    }
-    if (!is_last_block(&C->ticket_price)) return;
-    // last block: reduce all partials and decide
+    return cand_block_reduce(cand);
+}
+
+__device__ __forceinline__ PriceCand to_price_cand(const Cand& bc) {
+    PriceCand pc;
+    pc.d_all = bc.d_all; pc.j_all = bc.j_all;
+    pc.d_nt = bc.d_nt; pc.j_nt = bc.j_nt;
+    pc.d_min = bc.d_min; pc.j_min = bc.j_min;
+    pc.d_pr = bc.d_pr; pc.j_pr = bc.j_pr; pc.k_pr = bc.k_pr;
+    pc.pad_ = 0;
+    return pc;
+}
+
+// the global candidate from the per-block partials (all threads; result in thread 0)
+__device__ Cand reduce_price_parts(const PriceCand* part, int nparts) {
     Cand g;
     cand_init(g);
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        const PriceCand* pp = s.price_part + b;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const PriceCand* pp = part + b;
         Cand o;
         o.d_all = __ldcg(&pp->d_all); o.j_all = __ldcg(&pp->j_all);
         o.d_nt = __ldcg(&pp->d_nt); o.j_nt = __ldcg(&pp->j_nt);
@@ -448,7 +446,50 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
         o.d_pr = __ldcg(&pp->d_pr); o.j_pr = __ldcg(&pp->j_pr); o.k_pr = __ldcg(&pp->k_pr);
         cand_merge(g, o);
     }
-    g = cand_block_reduce(g);
+    return cand_block_reduce(g);
+}
+
+// Step 4 CHUZC on the global candidate: optimality over all nonbasic columns,
+// then Bland (safety net), the guided rule, Dantzig among non-tabu columns,
+// or aspiration (every improving column tabu).
+struct Chuzc {
+    int optimal, q, flags, asp;
+    double dq;
+};
+
+__device__ Chuzc chuzc_decide(const Cand& g, bool bland, double tol_d) {
+    Chuzc o = {0, -1, 0, 0, 0.0};
+    if (g.j_all < 0 || !(g.d_all > tol_d)) {
+        o.optimal = 1;
+    } else if (bland) {
+        o.q = g.j_min; o.dq = g.d_min; o.flags = kTfBland;
+    } else if (g.j_pr >= 0) {
+        o.q = g.j_pr; o.dq = g.d_pr; o.flags = kTfGuided;
+    } else if (g.j_nt >= 0 && g.d_nt > tol_d) {
+        o.q = g.j_nt; o.dq = g.d_nt;
+    } else {
+        o.q = g.j_all; o.dq = g.d_all; o.flags = kTfAspiration; o.asp = 1;
+    }
+    return o;
+}
+
+// ---- k_price: PRICE + CHUZC -----------------------------------------------------
+__global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
+    pdl_enter();
+    Ctrl* C = s.ctrl;
+    if (C->status != kRunning) return;
+    const Params& P = s.p;
+    // price_mode 1: this full FP64 pass only runs when the BF16 screen found no
+    // improving candidate, or under the Bland safety net
+    if (P.price_mode == 1 && !C->need_full && !C->bland) return;
+    extern __shared__ double ysh[];
+    for (int k = threadIdx.x; k < P.ld; k += blockDim.x) ysh[k] = s.y[k];
+    __syncthreads();
+    const Cand bc = price_block(s, C->it, ysh);
+    if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
+    if (!is_last_block(&C->ticket_price)) return;
+    // last block: reduce all partials and decide
+    const Cand g = reduce_price_parts(s.price_part, gridDim.x);
     if (threadIdx.x == 0) {
         C->ticket_price = 0;
         C->bytes_price += 8.0 * P.m * (double)(P.n - C->nsb);
@@ -457,61 +498,28 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
             C->need_full = 0;
             C->n_full++;
         }
-        if (g.j_all < 0 || !(g.d_all > P.tol_d)) {
+        const Chuzc d = chuzc_decide(g, C->bland != 0, P.tol_d);
+        if (d.optimal) {
             C->status = kOptimal;
             C->q = -1;
         } else {
-            int q;
-            double dq;
-            if (C->bland) {
-                q = g.j_min; dq = g.d_min;
-                C->flags |= kTfBland;
-            } else if (g.j_pr >= 0) {
-                // guided entering rule: Dantzig's choice among the listed columns
-                q = g.j_pr; dq = g.d_pr;
-                C->flags |= kTfGuided;
-            } else if (g.j_nt >= 0 && g.d_nt > P.tol_d) {
-                q = g.j_nt; dq = g.d_nt;
-            } else {
-                q = g.j_all; dq = g.d_all;
-                C->flags |= kTfAspiration;
-                C->n_asp++;
-            }
-            C->q = q;
-            C->dq = dq;
+            C->q = d.q;
+            C->dq = d.dq;
+            C->flags |= d.flags;
+            C->n_asp += d.asp;
         }
         __threadfence();
     }
 }
 
-// ---- k_update: B^-1 update + FTRAN + ratio test -------------------------------------
-__global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
-    pdl_enter();
-    Ctrl* C = s.ctrl;
+// ---- UPDATE of one block's rows (k_update and k_iterate) ----------------------------
+// Step 8 on the block's rows of B^-1 (row r := rho) fused with the FTRAN of
+// the next entering column (aq) and the Step 6 ratios.  Returns, in lane 0 of
+// each warp, the smallest ratio of its rows.  snapshot: also record the basic
+// variable of each row for a ratio test that runs while the basis changes.
+__device__ double update_block(const DevState& s, int r, bool do_upd, bool do_ftran, const double* acur,
+                               double* anxt, const double* aq, const double* rh, bool snapshot) {
     const Params& P = s.p;
-    const int status = C->status;
-    const int q = C->q;
-    const int r = C->r;
-    const int ab = C->abuf;
-    const bool do_upd = C->pending != 0 && r >= 0 && r < P.m;
-    const bool do_ftran = status == kRunning && q >= 0 && q < P.n + P.m;
-    if (!do_upd && !do_ftran) return;
-    extern __shared__ double sh[];
-    double* aq = sh;            // column q' of [A | I]
-    double* rh = sh + P.ld;     // new row r (rho)
-    if (do_ftran) {
-        if (q < P.n) {
-            const double* col = s.A_cm + (size_t)q * P.ld;
-            for (int k = threadIdx.x; k < P.ld; k += blockDim.x) aq[k] = col[k];
-        } else {
-            for (int k = threadIdx.x; k < P.ld; k += blockDim.x) aq[k] = (k == q - P.n) ? 1.0 : 0.0;
-        }
-    }
-    if (do_upd)
-        for (int k = threadIdx.x; k < P.ld; k += blockDim.x) rh[k] = s.rho[k];
-    __syncthreads();
-    const double* acur = s.alpha + (size_t)ab * P.ld;
-    double* anxt = s.alpha + (size_t)(ab ^ 1) * P.ld;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int half = P.ld >> 1;
@@ -539,7 +547,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
                 }
             }
         } else {
-            const double na = do_upd ? -acur[i] : 0.0;
+            const double na = do_upd ? -__ldcg(acur + i) : 0.0;
             const bool st = na != 0.0;
             if (st || do_ftran) {
                 constexpr int kS = 4;
@@ -570,12 +578,84 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
             if (lane == 0) {
                 anxt[i] = al;
                 double th = DBL_MAX;
-                if (al > P.tol_piv) th = s.bbar[i] / al;
+                if (al > P.tol_piv) th = __ldcg(s.bbar + i) / al;
                 s.theta[i] = th;
+                if (snapshot) s.row_var[i] = __ldcg(s.basis + i);
                 tmin = fmin(tmin, th);
             }
         }
     }
+    return tmin;
+}
+
+// block minimum (result in thread 0)
+__device__ double block_min(double v) {
+    __shared__ double shm[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = DBL_MAX;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmin(t, shm[w]);
+    return t;
+}
+
+// block reduce of the ratio-test candidate and the tie-set count (result in thread 0)
+__device__ RowCand block_row_best(RowCand best, int& cnt, bool bland) {
+    __shared__ RowCand shr[32];
+    __shared__ int shc[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        RowCand oc;
+        oc.a = __shfl_xor_sync(0xffffffffu, best.a, o);
+        oc.var = __shfl_xor_sync(0xffffffffu, best.var, o);
+        oc.row = __shfl_xor_sync(0xffffffffu, best.row, o);
+        if (row_beats(oc, best, bland)) best = oc;
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { shr[threadIdx.x >> 5] = best; shc[threadIdx.x >> 5] = cnt; }
+    __syncthreads();
+    RowCand b = shr[0];
+    int total = shc[0];
+    if (threadIdx.x == 0)
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            if (row_beats(shr[w], b, bland)) b = shr[w];
+            total += shc[w];
+        }
+    cnt = total;
+    return b;
+}
+
+// ---- k_update: B^-1 update + FTRAN + ratio test -------------------------------------
+__global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
+    pdl_enter();
+    Ctrl* C = s.ctrl;
+    const Params& P = s.p;
+    const int status = C->status;
+    const int q = C->q;
+    const int r = C->r;
+    const int ab = C->abuf;
+    const bool do_upd = C->pending != 0 && r >= 0 && r < P.m;
+    const bool do_ftran = status == kRunning && q >= 0 && q < P.n + P.m;
+    if (!do_upd && !do_ftran) return;
+    extern __shared__ double sh[];
+    double* aq = sh;            // column q' of [A | I]
+    double* rh = sh + P.ld;     // new row r (rho)
+    if (do_ftran) {
+        if (q < P.n) {
+            const double* col = s.A_cm + (size_t)q * P.ld;
+            for (int k = threadIdx.x; k < P.ld; k += blockDim.x) aq[k] = col[k];
+        } else {
+            for (int k = threadIdx.x; k < P.ld; k += blockDim.x) aq[k] = (k == q - P.n) ? 1.0 : 0.0;
+        }
+    }
+    if (do_upd)
+        for (int k = threadIdx.x; k < P.ld; k += blockDim.x) rh[k] = s.rho[k];
+    __syncthreads();
+    const double* acur = s.alpha + (size_t)ab * P.ld;
+    double* anxt = s.alpha + (size_t)(ab ^ 1) * P.ld;
+    const double tmin = block_min(update_block(s, r, do_upd, do_ftran, acur, anxt, aq, rh, false));
     if (!do_ftran) {
         // only the pending update was applied; the last block clears the flag
         if (!is_last_block(&C->ticket_update)) return;
@@ -588,30 +668,14 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
         }
         return;
     }
-    // block minimum of theta
-    __shared__ double shm[32];
-    for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
-    if (lane == 0) shm[threadIdx.x >> 5] = tmin;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = DBL_MAX;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmin(t, shm[w]);
-        s.upd_part[blockIdx.x] = t;
-    }
+    if (threadIdx.x == 0) s.upd_part[blockIdx.x] = tmin;
     if (!is_last_block(&C->ticket_update)) return;
     // last block: global minimum, tie set and leaving row
     __shared__ double s_tmin;
     double t = DBL_MAX;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t = fmin(t, __ldcg(s.upd_part + b));
-    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
-    __syncthreads();
-    if (lane == 0) shm[threadIdx.x >> 5] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double u = DBL_MAX;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u = fmin(u, shm[w]);
-        s_tmin = u;
-    }
+    t = block_min(t);
+    if (threadIdx.x == 0) s_tmin = t;
     __syncthreads();
     const double gmin = s_tmin;
     if (threadIdx.x == 0) {
@@ -651,26 +715,8 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
             }
         }
     }
-    // block reduce (best, cnt)
-    for (int o = 16; o > 0; o >>= 1) {
-        RowCand oc;
-        oc.a = __shfl_xor_sync(0xffffffffu, best.a, o);
-        oc.var = __shfl_xor_sync(0xffffffffu, best.var, o);
-        oc.row = __shfl_xor_sync(0xffffffffu, best.row, o);
-        if (row_beats(oc, best, bland)) best = oc;
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    }
-    __shared__ RowCand shr[32];
-    __shared__ int shc[32];
-    if (lane == 0) { shr[threadIdx.x >> 5] = best; shc[threadIdx.x >> 5] = cnt; }
-    __syncthreads();
+    const RowCand b = block_row_best(best, cnt, bland);
     if (threadIdx.x == 0) {
-        RowCand b = shr[0];
-        int total = shc[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-            if (row_beats(shr[w], b, bland)) b = shr[w];
-            total += shc[w];
-        }
         C->ticket_update = 0;
         C->pending = 0;
         if (b.row < 0) {  // cannot happen for finite data; stop rather than pivot on garbage
@@ -682,11 +728,338 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
         C->r = b.row;
         C->theta = __ldcg(s.theta + b.row);
         C->alpha_r = b.a;
-        C->tcount = total;
-        if (total > 1) C->flags |= kTfTieSet;
+        C->tcount = cnt;
+        if (cnt > 1) C->flags |= kTfTieSet;
         C->abuf = ab ^ 1;
         __threadfence();
     }
+}
+
+// ---- k_iterate: many pivots in one cooperative launch (price_mode 0) -----------------
+//
+// The three kernels above, as phases of one persistent kernel with one CTA per
+// SM: (1) apply the chosen pivot (rho, y, bbar slices; the bookkeeping), (2)
+// PRICE, (3) CHUZC + UPDATE/FTRAN/ratios, then the ratio test, each phase
+// behind a grid barrier.  Decisions that a last block took alone (CHUZC, the
+// leaving row, the bookkeeping scalars) are computed by every CTA from the
+// same partials in global memory, so all CTAs follow the same path and no
+// single block is left working while the others idle; block 0 alone writes
+// the shared state and the control block.  Data another CTA wrote in this
+// launch is read through L2 (__ldcg).  The ratio test reads the basic
+// variable of each row from the snapshot taken by the FTRAN (row_var), since
+// block 0 may already be exchanging the basis.
+
+struct IterState {
+    int status, it, q, r, tcount, abuf, pending, flags, degen_run, bland;
+    double dq, theta, alpha_r;
+};
+
+constexpr unsigned kBarrierSpins = 1u << 22;  // ~0.2 s of polling, then the launch gives up
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier of a cooperative launch: a cumulative arrival count, and the
+// number of the last barrier every CTA has reached.  Waits are bounded; a CTA
+// that gives up reports it, and the launch ends with kErrTimeout.
+__device__ bool grid_barrier(uint32_t* bar, unsigned& epoch, volatile int* fail, unsigned parties = 0) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ++epoch;
+        __threadfence();
+        const unsigned prev = atomicAdd(bar, 1u);
+        if (prev == epoch * (parties ? parties : gridDim.x) - 1u) {
+            __threadfence();
+            atomicExch(bar + 1, epoch);
+        } else {
+            unsigned spins = 0;
+            while (ld_acquire_u32(bar + 1) < epoch) {
+                if (++spins > kBarrierSpins) {
+                    *fail = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *fail == 0;
+}
+
+// Step 7/8 bookkeeping of the pivot (q, r): identical scalar updates in every
+// CTA; the lead CTA also writes the basis exchange, tabu list, trace and
+// counters (the same rules as k_pivot).
+__device__ void pivot_bookkeeping(const DevState& s, IterState& S, bool lead) {
+    const Params& P = s.p;
+    Ctrl* C = s.ctrl;
+    const int it = S.it, q = S.q, r = S.r;
+    const double th = S.theta, dq = S.dq;
+    int flags = S.flags;
+    const bool degenerate = th <= P.tol_tie;
+    if (degenerate) flags |= kTfDegenerate;
+    const bool push = P.tabu_tenure > 0 && (S.tcount > 1 || degenerate);
+    if (push) flags |= kTfTabuPush;
+    if (lead) {
+        const int leave = s.basis[r];
+        if (degenerate) C->n_degenerate++;
+        if (push) {
+            s.tabu_until[leave] = it + 1 + P.tabu_tenure;
+            C->n_tabu++;
+        }
+        if (it < P.trace_cap) {
+            s.trace.q[it] = q;
+            s.trace.r[it] = r;
+            s.trace.theta[it] = th;
+            s.trace.dq[it] = dq;
+            s.trace.flags[it] = flags;
+        }
+        C->z = __dadd_rn(C->z, __dmul_rn(dq, th));
+        s.pos[leave] = -1;
+        s.basis[r] = q;
+        s.pos[q] = r;
+        C->nsb += (q < P.n ? 1 : 0) - (leave < P.n ? 1 : 0);
+    }
+    const int it1 = it + 1;
+    S.it = it1;
+    S.degen_run = degenerate ? S.degen_run + 1 : 0;
+    if (S.bland && !degenerate) S.bland = 0;
+    if (!S.bland && P.bland_after > 0 && S.degen_run >= P.bland_after) {
+        S.bland = 1;
+        if (lead) C->n_bland++;
+    }
+    S.flags = 0;
+    if (P.reinvert_every > 0 && it1 % P.reinvert_every == 0) {
+        S.status = kReinvert;
+        S.pending = 0;
+    } else {
+        S.pending = 1;
+        if (it1 >= P.max_iters) S.status = kIterLimit;
+    }
+    if (lead) {
+        C->it = S.it;
+        C->degen_run = S.degen_run;
+        C->bland = S.bland;
+        C->flags = 0;
+        C->status = S.status;
+        C->pending = S.pending;
+    }
+}
+
+__global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int iters) {
+    Ctrl* C = s.ctrl;
+    const Params& P = s.p;
+    extern __shared__ double sh[];  // y for PRICE; a_q and rho for UPDATE (2 ld doubles)
+    __shared__ IterState S;
+    __shared__ volatile int fail;
+    __shared__ double gmin_sh;
+    __shared__ int nflag;
+    __shared__ int flg[kMaxFlagged];
+    unsigned epoch = 0;
+    const bool lead = blockIdx.x == 0;
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+        fail = 0;
+        S.status = C->status; S.it = C->it; S.q = C->q; S.r = C->r; S.tcount = C->tcount;
+        S.abuf = C->abuf; S.pending = C->pending; S.flags = C->flags; S.degen_run = C->degen_run;
+        S.bland = C->bland; S.dq = C->dq; S.theta = C->theta; S.alpha_r = C->alpha_r;
+    }
+    // every CTA has its copy of the control block before block 0 changes it
+    if (!grid_barrier(s.gbar, epoch, &fail)) {
+        if (lead && threadIdx.x == 0) C->err = kErrTimeout;
+        return;
+    }
+    for (int step = 0; step < iters; ++step) {
+        // ---- (1) the pivot chosen by the last ratio test: rho, y, bbar, bookkeeping
+        if (S.status == kRunning && S.r >= 0 && S.r < P.m && S.q >= 0) {
+            const int r = S.r;
+            const double* acur = s.alpha + (size_t)S.abuf * P.ld;
+            const double ar = S.alpha_r, th = S.theta, dq = S.dq;
+            const double* brow = s.binv + (size_t)r * P.ld;
+            const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+            const int stride = G * blockDim.x;
+            for (int k = tid; k < P.ld; k += stride) {
+                const double rn = __ldcg(brow + k) / ar;
+                s.rho[k] = rn;
+                const double yn = __dadd_rn(__ldcg(s.y + k), __dmul_rn(dq, rn));
+                s.y[k] = yn;
+                s.y32[k] = (float)yn;
+            }
+            for (int i = tid; i < P.m; i += stride)
+                s.bbar[i] = (i == r) ? th : __dsub_rn(__ldcg(s.bbar + i), __dmul_rn(__ldcg(acur + i), th));
+            __syncthreads();
+            if (threadIdx.x == 0) pivot_bookkeeping(s, S, lead);
+            if (!grid_barrier(s.gbar, epoch, &fail)) break;
+            if (S.status == kReinvert) break;
+        }
+        // ---- (2) PRICE + CHUZC
+        if (S.status == kRunning) {
+            for (int k = threadIdx.x; k < P.ld; k += blockDim.x) sh[k] = __ldcg(s.y + k);
+            __syncthreads();
+            const Cand bc = price_block(s, S.it, sh);
+            if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
+            if (!grid_barrier(s.gbar, epoch, &fail)) break;
+            const Cand g = reduce_price_parts(s.price_part, G);
+            if (threadIdx.x == 0) {
+                const Chuzc d = chuzc_decide(g, S.bland != 0, P.tol_d);
+                if (d.optimal) {
+                    S.status = kOptimal;
+                    S.q = -1;
+                } else {
+                    S.q = d.q;
+                    S.dq = d.dq;
+                    S.flags |= d.flags;
+                }
+                if (lead) {
+                    C->bytes_price += 8.0 * P.m * (double)(P.n - C->nsb);
+                    C->n_price++;
+                    C->n_asp += d.asp;
+                    C->status = S.status;
+                    C->q = S.q;
+                    C->dq = S.dq;
+                    C->flags = S.flags;
+                }
+            }
+            __syncthreads();
+        }
+        // ---- (3) UPDATE of the pending pivot + FTRAN of the new column + ratios
+        const bool do_upd = S.pending != 0 && S.r >= 0 && S.r < P.m;
+        const bool do_ftran = S.status == kRunning && S.q >= 0 && S.q < P.n + P.m;
+        if (!do_upd && !do_ftran) break;
+        double* aq = sh;
+        double* rh = sh + P.ld;
+        if (do_ftran) {
+            const int q = S.q;
+            if (q < P.n) {
+                const double* col = s.A_cm + (size_t)q * P.ld;
+                for (int k = threadIdx.x; k < P.ld; k += blockDim.x) aq[k] = col[k];
+            } else {
+                for (int k = threadIdx.x; k < P.ld; k += blockDim.x) aq[k] = (k == q - P.n) ? 1.0 : 0.0;
+            }
+        }
+        if (do_upd)
+            for (int k = threadIdx.x; k < P.ld; k += blockDim.x) rh[k] = __ldcg(s.rho + k);
+        __syncthreads();
+        const double* acur = s.alpha + (size_t)S.abuf * P.ld;
+        double* anxt = s.alpha + (size_t)(S.abuf ^ 1) * P.ld;
+        const double tb = block_min(update_block(s, S.r, do_upd, do_ftran, acur, anxt, aq, rh, true));
+        if (threadIdx.x == 0) {
+            s.upd_part[blockIdx.x] = tb;
+            if (lead) {
+                C->bytes_update += (do_upd ? 16.0 : (do_ftran ? 8.0 : 0.0)) * P.m * (double)P.m;
+                C->n_update++;
+            }
+        }
+        if (!do_ftran) {
+            // the pending update of the last pivot was applied (optimal or iteration limit)
+            if (threadIdx.x == 0) {
+                S.pending = 0;
+                if (lead) C->pending = 0;
+            }
+            break;
+        }
+        if (!grid_barrier(s.gbar, epoch, &fail)) break;
+        // ---- (4) CHUZR: minimum ratio, tie set, leaving row (every CTA)
+        double tg = DBL_MAX;
+        for (int b = threadIdx.x; b < G; b += blockDim.x) tg = fmin(tg, __ldcg(s.upd_part + b));
+        tg = block_min(tg);
+        if (threadIdx.x == 0) {
+            gmin_sh = tg;
+            nflag = 0;
+        }
+        __syncthreads();
+        const double gmin = gmin_sh;
+        if (gmin == DBL_MAX) {
+            if (threadIdx.x == 0) {
+                S.status = kUnbounded;
+                S.pending = 0;
+                if (lead) {
+                    C->status = kUnbounded;
+                    C->pending = 0;
+                }
+            }
+            break;
+        }
+        const double thr = gmin + P.tol_tie * fmax(1.0, fabs(gmin));
+        // CTAs whose smallest ratio lies within the tie tolerance hold the tie set
+        for (int b = threadIdx.x; b < G; b += blockDim.x)
+            if (__ldcg(s.upd_part + b) <= thr) {
+                const int k = atomicAdd(&nflag, 1);
+                if (k < kMaxFlagged) flg[k] = b;
+            }
+        __syncthreads();
+        const bool bland = S.bland != 0;
+        RowCand best = {0.0, 0, -1};
+        int cnt = 0;
+        if (nflag <= kMaxFlagged) {
+            const int per = (P.m + G - 1) / G;  // rows of the fullest CTA
+            for (int e = threadIdx.x; e < nflag * per; e += blockDim.x) {
+                const int b = flg[e / per], l = e % per;
+                const int i = b + G * l;
+                if (i >= P.m) continue;
+                const double al = __ldcg(anxt + i), th = __ldcg(s.theta + i);
+                if (al > P.tol_piv && th <= thr) {
+                    cnt++;
+                    RowCand c = {al, __ldcg(s.row_var + i), i};
+                    if (row_beats(c, best, bland)) best = c;
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < P.m; i += blockDim.x) {
+                const double al = __ldcg(anxt + i), th = __ldcg(s.theta + i);
+                if (al > P.tol_piv && th <= thr) {
+                    cnt++;
+                    RowCand c = {al, __ldcg(s.row_var + i), i};
+                    if (row_beats(c, best, bland)) best = c;
+                }
+            }
+        }
+        const RowCand b = block_row_best(best, cnt, bland);
+        if (threadIdx.x == 0) {
+            S.pending = 0;
+            if (b.row < 0) {  // cannot happen for finite data; stop rather than pivot on garbage
+                S.status = kUnbounded;
+                if (lead) {
+                    C->status = kUnbounded;
+                    C->err = kErrBadIndex;
+                    C->pending = 0;
+                }
+            } else {
+                S.r = b.row;
+                S.theta = __ldcg(s.theta + b.row);
+                S.alpha_r = b.a;
+                S.tcount = cnt;
+                if (cnt > 1) S.flags |= kTfTieSet;
+                S.abuf ^= 1;
+                if (lead) {
+                    C->r = S.r;
+                    C->theta = S.theta;
+                    C->alpha_r = S.alpha_r;
+                    C->tcount = S.tcount;
+                    C->flags = S.flags;
+                    C->abuf = S.abuf;
+                    C->pending = 0;
+                }
+            }
+        }
+        __syncthreads();
+        if (S.status != kRunning) break;
+    }
+    if (lead && threadIdx.x == 0 && fail) C->err = kErrTimeout;
+}
+
+// Self-test of the bounded wait: the barrier expects one CTA more than the
+// grid has, so no CTA is ever released; every CTA must give up after the spin
+// limit and report kErrTimeout instead of waiting forever.
+__global__ void k_barrier_selftest(uint32_t* bar, int32_t* err) {
+    __shared__ volatile int fail;
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    unsigned epoch = 0;
+    if (!grid_barrier(bar, epoch, &fail, gridDim.x + 1u) && threadIdx.x == 0) atomicExch(err, kErrTimeout);
 }
 
 }  // namespace
@@ -725,6 +1098,61 @@ int occupancy_price(int ld) {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_price, kPriceThreads, price_smem_bytes(ld));
     return nb;
+}
+
+size_t iterate_smem_bytes(int ld) { return 2 * (size_t)ld * sizeof(double); }
+
+int occupancy_iterate(int ld) {
+    cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iterate_smem_bytes(ld));
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iterate, kUpdateThreads, iterate_smem_bytes(ld));
+    return nb;
+}
+
+cudaError_t launch_iterate(const DevState& s, int blocks, int iters, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(s.gbar, 0, 2 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kUpdateThreads);
+    cfg.dynamicSmemBytes = iterate_smem_bytes(s.p.ld);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_iterate, s, iters);
+}
+
+int barrier_selftest(int blocks, cudaStream_t st) {
+    uint32_t* bar = nullptr;
+    int32_t* err = nullptr;
+    if (cudaMallocAsync(&bar, 2 * sizeof(uint32_t), st) != cudaSuccess) return LP_ERR_CUDA;
+    if (cudaMallocAsync(&err, sizeof(int32_t), st) != cudaSuccess) {
+        cudaFreeAsync(bar, st);
+        return LP_ERR_CUDA;
+    }
+    cudaMemsetAsync(bar, 0, 2 * sizeof(uint32_t), st);
+    cudaMemsetAsync(err, 0, sizeof(int32_t), st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(32);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_barrier_selftest, bar, err);
+    int32_t h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(bar, st);
+    cudaFreeAsync(err, st);
+    cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return LP_ERR_CUDA;
+    return h == kErrTimeout ? LP_ERR_TIMEOUT : LP_OK;
 }
 
 int occupancy_update(int ld) {

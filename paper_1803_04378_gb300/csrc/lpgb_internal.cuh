@@ -36,6 +36,7 @@ constexpr int kErrNone = 0;
 constexpr int kErrSingular = 1;
 constexpr int kErrBadIndex = 2;
 constexpr int kErrInfeasibleStart = 3;
+constexpr int kErrTimeout = 4;         // a bounded device wait ran out
 
 // trace flags (same values as LP_TF_*)
 constexpr int kTfDegenerate = 1;
@@ -140,6 +141,8 @@ struct DevState {
     Ctrl* ctrl;
     PriceCand* price_part;
     double* upd_part;   // per-block theta minima
+    int32_t* row_var;   // m: basic variable of each row as seen by the last FTRAN (k_iterate)
+    uint32_t* gbar;     // k_iterate grid barrier: arrivals, released epoch
     TraceBuf trace;
     // reinversion scratch
     int32_t* rv_struct_pos;  // k structural basis positions (increasing)
@@ -201,6 +204,11 @@ void launch_pivot(const DevState& s, const Geometry& g, cudaStream_t st, bool pd
 void launch_price(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl = false);  // the whole PRICE + CHUZC of the mode
 void launch_to_bf16(const double* src, uint16_t* dst, size_t count, cudaStream_t st);
 void launch_update(const DevState& s, const Geometry& g, cudaStream_t st, bool pdl = false);
+// Up to `iters` pivots in one cooperative launch of `blocks` CTAs (price_mode 0).
+cudaError_t launch_iterate(const DevState& s, int blocks, int iters, cudaStream_t st);
+int occupancy_iterate(int ld);
+// Bounded-wait self-test: a grid barrier that cannot complete (lp_selftest_barrier_timeout).
+int barrier_selftest(int blocks, cudaStream_t st);
 size_t price_smem_bytes(int ld);
 size_t update_smem_bytes(int ld);
 void configure_iter_kernels(int ld);

@@ -39,6 +39,11 @@ struct lp_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr, erg = nullptr, era = nullptr;
     double reinv_gj_s = 0.0, reinv_asm_s = 0.0;
     std::vector<cudaEvent_t> tev;    // kernel_timing: 3 events per timed iteration of the graph
+    bool persist = false;            // pivots run in k_iterate (cooperative, one CTA per SM)
+    int persist_blocks = 0;
+    cudaEvent_t evc0 = nullptr, evc1 = nullptr;  // kernel_timing around k_iterate launches
+    double chain_s = 0.0, chain_b = 0.0;
+    int chain_n = 0;
     double reinvert_seconds = 0.0;
     // per-solve accumulators
     double price_s = 0.0, update_s = 0.0, price_b = 0.0, update_b = 0.0;
@@ -80,6 +85,7 @@ int device_err_code(int err) {
         case kErrNone: return LP_OK;
         case kErrSingular: return LP_ERR_SINGULAR;
         case kErrInfeasibleStart: return LP_ERR_INVALID_ARG;
+        case kErrTimeout: return LP_ERR_TIMEOUT;
         default: return LP_ERR_DEVICE;
     }
 }
@@ -103,6 +109,9 @@ void free_all(lp_handle* h) {
     if (h->era) cudaEventDestroy(h->era);
     for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
     h->tev.clear();
+    if (h->evc0) cudaEventDestroy(h->evc0);
+    if (h->evc1) cudaEventDestroy(h->evc1);
+    h->evc0 = h->evc1 = nullptr;
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -233,6 +242,11 @@ bool finite_all(const double* x, size_t n) {
 
 extern "C" {
 
+int lp_selftest_barrier_timeout(int32_t blocks, void* cuda_stream) {
+    if (blocks < 1 || blocks > 64) return LP_ERR_INVALID_ARG;
+    return barrier_selftest(blocks, static_cast<cudaStream_t>(cuda_stream));
+}
+
 void lp_default_options(lp_options* o) {
     if (!o) return;
     o->reinvert_every = 64;
@@ -244,7 +258,7 @@ void lp_default_options(lp_options* o) {
     o->trace_cap = 0;
     o->graph_iters = 64;
     o->kernel_timing = 0;
-    o->reserved_ = 0;
+    o->engine = 0;
     o->tol_d = 1e-9;
     o->tol_piv = 1e-9;
     o->tol_tie = 1e-12;
@@ -388,10 +402,14 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
         s.A_lp = lp;
     }
     TRY(setup_geometry(h));
-    const int parts = std::max(std::max(h->geo.price_blocks, h->geo.price_lp_blocks), h->geo.update_blocks);
+    // per-block partials: every grid, including k_iterate's one CTA per SM
+    const int parts = std::max(std::max(h->geo.price_blocks, h->geo.price_lp_blocks),
+                               std::max(h->geo.update_blocks, h->geo.sms));
     TRY(dalloc(h, &price_part, (size_t)parts));
     TRY(dalloc(h, &s.lp_part, (size_t)parts));
     TRY(dalloc(h, &upd_part, (size_t)parts));
+    TRY(dalloc(h, &s.row_var, (size_t)m));
+    TRY(dalloc(h, &s.gbar, 2));
     if (P.trace_cap > 0) {
         TRY(dalloc(h, &s.trace.q, (size_t)P.trace_cap));
         TRY(dalloc(h, &s.trace.r, (size_t)P.trace_cap));
@@ -412,6 +430,20 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(upload_problem(h, A, b, c, on_device));
     TRY(reset_state(h));
     TRY(capture_graph(h));
+    // persistent engine: price_mode 0 on a device that runs cooperative launches
+    // with one 1024-thread CTA on every SM
+    {
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+        if (h->opt.engine == 0 && h->opt.price_mode == 0 && coop && occupancy_iterate(h->ld) >= 1) {
+            h->persist = true;
+            h->persist_blocks = h->geo.sms;  // the partial arrays hold at least sms entries
+            if (h->opt.kernel_timing > 0) {
+                CK(cudaEventCreate(&h->evc0));
+                CK(cudaEventCreate(&h->evc1));
+            }
+        }
+    }
     CK(cudaStreamSynchronize(h->stream));
     return LP_OK;
 }
@@ -425,7 +457,7 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     lp_options o;
     lp_default_options(&o);
     if (opt) o = *opt;
-    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.reserved_ != 0 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
+    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > 1 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
         o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 1 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
@@ -513,6 +545,8 @@ int lp_solve(lp_handle* h, lp_result* out) {
     h->reinv_gj_s = h->reinv_asm_s = 0.0;
     h->price_s = h->update_s = h->price_b = h->update_b = 0.0;
     h->price_n = h->update_n = 0;
+    h->chain_s = h->chain_b = 0.0;
+    h->chain_n = 0;
     h->launches = 0;
     int warm_repairs = 0, warm_fallback = 0;
     if (h->warm_pending) {
@@ -567,6 +601,27 @@ int lp_solve(lp_handle* h, lp_result* out) {
             h->primed = true;
         }
         const Ctrl before = C;
+        if (h->persist) {
+            if (h->evc0) CK(cudaEventRecord(h->evc0, h->stream));
+            const cudaError_t e = launch_iterate(h->ds, h->persist_blocks, h->opt.graph_iters, h->stream);
+            if (e == cudaSuccess) {
+                h->launches += 1;
+                if (h->evc1) CK(cudaEventRecord(h->evc1, h->stream));
+                TRY(read_ctrl(h));
+                if (h->evc1) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, h->evc0, h->evc1));
+                    const Ctrl& A = *h->h_ctrl;
+                    h->chain_s += ms * 1e-3;
+                    h->chain_b += (A.bytes_price - before.bytes_price) + (A.bytes_update - before.bytes_update);
+                    h->chain_n++;
+                }
+                continue;
+            }
+            // the cooperative launch was refused: captured graphs from here on
+            (void)cudaGetLastError();
+            h->persist = false;
+        }
         CK(cudaGraphLaunch(h->graph, h->stream));
         h->launches += 3 * (int64_t)h->opt.graph_iters;
         TRY(read_ctrl(h));
@@ -628,6 +683,10 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->full_passes = C.n_full;
         out->reinvert_gj_seconds = h->reinv_gj_s;
         out->reinvert_assemble_seconds = h->reinv_asm_s;
+        out->chain_seconds = h->chain_s;
+        out->chain_bytes = h->chain_b;
+        out->chain_launches = h->chain_n;
+        out->persistent = h->persist ? 1 : 0;
     }
     return LP_OK;
 }

@@ -35,7 +35,7 @@ class lp_options(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("bland_after", ctypes.c_int32),
                 ("price_mode", ctypes.c_int32), ("topk", ctypes.c_int32),
                 ("trace_cap", ctypes.c_int32), ("graph_iters", ctypes.c_int32),
-                ("kernel_timing", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("kernel_timing", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("tol_d", ctypes.c_double), ("tol_piv", ctypes.c_double),
                 ("tol_tie", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
 
@@ -53,7 +53,9 @@ class lp_result(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("warm_repairs", ctypes.c_int32),
                 ("warm_fallback", ctypes.c_int32), ("screen_passes", ctypes.c_int32),
                 ("full_passes", ctypes.c_int32), ("reinvert_gj_seconds", ctypes.c_double),
-                ("reinvert_assemble_seconds", ctypes.c_double)]
+                ("reinvert_assemble_seconds", ctypes.c_double), ("chain_seconds", ctypes.c_double),
+                ("chain_bytes", ctypes.c_double), ("chain_launches", ctypes.c_int32),
+                ("persistent", ctypes.c_int32)]
 
 
 class lp_batch_result(ctypes.Structure):
@@ -75,6 +77,8 @@ def _load():
     lib = ctypes.CDLL(LIB_PATH)
     vp, i32, P = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER
     lib.lp_default_options.argtypes = [P(lp_options)]
+    lib.lp_selftest_barrier_timeout.argtypes = [i32, vp]
+    lib.lp_selftest_barrier_timeout.restype = ctypes.c_int
     lib.lp_default_options.restype = None
     lib.lp_create.argtypes = [P(vp), i32, i32, vp, vp, vp, i32, P(lp_options)]
     lib.lp_create.restype = ctypes.c_int
@@ -195,6 +199,10 @@ class Result:
     full_passes: int = 0
     reinvert_gj_seconds: float = 0.0
     reinvert_assemble_seconds: float = 0.0
+    chain_seconds: float = 0.0
+    chain_bytes: float = 0.0
+    chain_launches: int = 0
+    persistent: int = 0
 
     @property
     def status_name(self) -> str:
@@ -254,7 +262,8 @@ class LP:
                       r.reinvert_seconds, r.bytes_moved, r.price_seconds, r.update_seconds,
                       r.price_bytes, r.update_bytes, r.price_launches, r.update_launches,
                       r.kernel_launches, r.warm_repairs, r.warm_fallback, r.screen_passes,
-                      r.full_passes, r.reinvert_gj_seconds, r.reinvert_assemble_seconds)
+                      r.full_passes, r.reinvert_gj_seconds, r.reinvert_assemble_seconds,
+                      r.chain_seconds, r.chain_bytes, r.chain_launches, r.persistent)
 
     def reset(self):
         _check(_lib.lp_reset(self._h), "lp_reset")
@@ -314,6 +323,13 @@ class LP:
                                  ctypes.byref(cnt)), "lp_get_trace")
         k = cnt.value
         return dict(q=q[:k], r=r[:k], theta=th[:k], dq=dq[:k], flags=fl[:k])
+
+
+def selftest_barrier_timeout(blocks: int = 4, stream=None) -> int:
+    """lp_selftest_barrier_timeout: return code of a grid barrier that cannot
+    complete (LP_ERR_TIMEOUT when its bounded wait works)."""
+    st = None if stream is None else ctypes.c_void_p(stream)
+    return _lib.lp_selftest_barrier_timeout(int(blocks), st)
 
 
 LP_PRICE_STATIC_MAX_M = 12288

@@ -160,6 +160,47 @@ def test_reinversion_panels(m, n, k):
     assert np.max(np.abs(binv @ B - np.eye(m))) <= 1e-9 * scale
 
 
+@pytest.mark.parametrize("kind,m,n,seed,K", [("real", 256, 512, 1, 0), ("degenerate", 128, 256, 2, 0),
+                                          ("int", 200, 200, 0, 0), ("real", 300, 200, 3, 100)])
+def test_persistent_engine_matches_graph_engine(kind, m, n, seed, K):
+    """The persistent cooperative kernel and the captured three-kernel graphs
+    run the same arithmetic in the same order: identical pivots and
+    bit-identical B^-1, bbar, x, y (K > 0 stops at an iteration limit that is
+    not a multiple of the pivots per launch)."""
+    A, b, c = lpgen.make(kind, m, n, seed)
+    from paper_1803_04378_gb300 import lpgb
+    runs = []
+    for engine in (0, 1):
+        extra = {"max_iters": K} if K else {}
+        with lpgb.LP(A, b, c, engine=engine, trace_cap=1 << 14, **extra) as lp:
+            res = lp.solve()
+            tr = lp.trace()
+            binv, bbar = lp.state()
+            x, y, z = lp.solution()
+            runs.append((res, tr, binv, bbar, x, y, z))
+    (r0, t0, B0, bb0, x0, y0, z0), (r1, t1, B1, bb1, x1, y1, z1) = runs
+    assert r0.persistent == 1 and r1.persistent == 0
+    assert r0.status == r1.status and r0.iterations == r1.iterations
+    assert r0.reinversions == r1.reinversions and r0.tabu_pushes == r1.tabu_pushes
+    assert np.array_equal(t0["q"], t1["q"]) and np.array_equal(t0["r"], t1["r"])
+    assert np.array_equal(B0, B1) and np.array_equal(bb0, bb1)
+    assert np.array_equal(x0, x1) and np.array_equal(y0, y1) and z0 == z1
+
+
+def test_grid_barrier_wait_is_bounded():
+    """The persistent engine's grid barrier gives up after its spin limit: a
+    barrier that cannot complete (it expects one CTA more than the grid has)
+    returns LP_ERR_TIMEOUT within seconds, and the context stays usable."""
+    import time
+    from paper_1803_04378_gb300 import lpgb
+    t0 = time.time()
+    assert lpgb.selftest_barrier_timeout(4) == lpgb.LP_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    A, b, c = lpgen.dense_int_lp(20, 30, 0)
+    with lpgb.LP(A, b, c) as lp:
+        assert lp.solve().status == 1
+
+
 def test_reinvert_every_pivot_same_path():
     A, b, c = lpgen.dense_real_lp(120, 200, 12)
     lp, res, x, y, z, tr = gpu_solve(A, b, c, reinvert_every=1)
