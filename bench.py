@@ -239,6 +239,8 @@ def main():
     ap.add_argument("--only-batch", action="store_true", help="run only the batched leg (profiling)")
     ap.add_argument("--reinversion-only", type=int, default=0,
                     help="profiling: solve once, then time this many reinversions of the optimal basis")
+    ap.add_argument("--graph-iters", type=int, default=0,
+                    help="pivots per persistent launch or captured graph (profiling; default 64)")
     ap.add_argument("--max-iters", type=int, default=0,
                     help="stop every solve after this many pivots (profiling runs only)")
     args = ap.parse_args()
@@ -268,6 +270,8 @@ def main():
     stream = torch.cuda.current_stream()
     At, bt, ct = (torch.from_numpy(v).cuda() for v in (A, b, c))
     extra = {"max_iters": args.max_iters} if args.max_iters > 0 else {}
+    if args.graph_iters > 0:
+        extra["graph_iters"] = args.graph_iters
     lp = lpgb.LP(At, bt, ct, kernel_timing=KERNEL_TIMING_STRIDE, cuda_stream=stream.cuda_stream, price_mode=args.price_mode, **extra)
     del At, bt, ct
 
@@ -336,7 +340,14 @@ def main():
     un = sum(r.update_launches for r in results)
     pb = sum(r.price_bytes for r in results)
     ub = sum(r.update_bytes for r in results)
-    if us >= ps:
+    cs = sum(r.chain_seconds for r in results)
+    cn = sum(r.chain_launches for r in results)
+    cb = sum(r.chain_bytes for r in results)
+    if cn > 0:
+        # persistent engine: every launch runs PRICE + UPDATE/FTRAN of up to 64
+        # pivots; both do one FP64 FMA per 8 algorithmic bytes
+        kname, kt, kn, kb, kflops = "k_iterate", cs, cn, cb, cb / 4.0
+    elif us >= ps:
         kname, kt, kn, kb, kflops = "k_update", us, un, ub, 4.0 * m * m * un
     else:
         kname, kt, kn, kb, kflops = "k_price", ps, pn, pb, 2.0 * pb / 8.0

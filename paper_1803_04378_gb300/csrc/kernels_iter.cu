@@ -156,7 +156,7 @@ __device__ Cand cand_block_reduce(Cand c) {
 
 // Leaving-row candidate of the ratio test: largest alpha, exact ties to the
 // smallest basic variable index (Bland mode: smallest basic variable index).
-struct RowCand { double a; int var; int row; };
+struct RowCand { double a; int var; int row; double th; };  // th: the row's ratio
 
 __device__ __forceinline__ bool row_beats(const RowCand& x, const RowCand& y, bool bland) {
     if (x.row < 0) return false;
@@ -517,14 +517,22 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
 // the next entering column (aq) and the Step 6 ratios.  Returns, in lane 0 of
 // each warp, the smallest ratio of its rows.  snapshot: also record the basic
 // variable of each row for a ratio test that runs while the basis changes.
+// aq_unit >= 0: the entering column is the slack unit vector e_{aq_unit}
+// (generated, aq unused).
+constexpr int kS = 4;  // 512-byte reads in flight per warp
+
 __device__ double update_block(const DevState& s, int r, bool do_upd, bool do_ftran, const double* acur,
-                               double* anxt, const double* aq, const double* rh, bool snapshot) {
+                               double* anxt, const double* aq, const double* rh, bool snapshot, int aq_unit = -1) {
     const Params& P = s.p;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int half = P.ld >> 1;
     const double2* aq2 = reinterpret_cast<const double2*>(aq);
     const double2* rh2 = reinterpret_cast<const double2*>(rh);
+    auto aqv = [&](int k) -> double2 {
+        if (aq_unit < 0) return aq2[k];
+        return make_double2(2 * k == aq_unit ? 1.0 : 0.0, 2 * k + 1 == aq_unit ? 1.0 : 0.0);
+    };
     double tmin = DBL_MAX;
     // Rows are dealt to blocks round-robin (block b owns i = b, b+G, ...) so
     // every SM gets the same share, and to the block's warps one row at a
@@ -542,7 +550,7 @@ __device__ double update_block(const DevState& s, int r, bool do_upd, bool do_ft
                 const double2 v = rh2[k];
                 __stcs(row + k, v);
                 if (do_ftran) {
-                    const double2 w = aq2[k];
+                    const double2 w = aqv(k);
                     a0 = fma(v.x, w.x, a0); a1 = fma(v.y, w.y, a1);
                 }
             }
@@ -550,7 +558,6 @@ __device__ double update_block(const DevState& s, int r, bool do_upd, bool do_ft
             const double na = do_upd ? -__ldcg(acur + i) : 0.0;
             const bool st = na != 0.0;
             if (st || do_ftran) {
-                constexpr int kS = 4;
                 for (int k0 = lane; k0 < half; k0 += 32 * kS) {
                     double2 v[kS];
 #pragma unroll
@@ -566,7 +573,7 @@ __device__ double update_block(const DevState& s, int r, bool do_upd, bool do_ft
                             __stcs(row + k, v[t]);
                         }
                         if (do_ftran) {
-                            const double2 w = aq2[k];
+                            const double2 w = aqv(k);
                             a0 = fma(v[t].x, w.x, a0); a1 = fma(v[t].y, w.y, a1);
                         }
                     }
@@ -610,6 +617,7 @@ __device__ RowCand block_row_best(RowCand best, int& cnt, bool bland) {
         oc.a = __shfl_xor_sync(0xffffffffu, best.a, o);
         oc.var = __shfl_xor_sync(0xffffffffu, best.var, o);
         oc.row = __shfl_xor_sync(0xffffffffu, best.row, o);
+        oc.th = __shfl_xor_sync(0xffffffffu, best.th, o);
         if (row_beats(oc, best, bland)) best = oc;
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     }
@@ -693,7 +701,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
     }
     const double thr = gmin + P.tol_tie * fmax(1.0, fabs(gmin));
     const bool bland = C->bland != 0;
-    RowCand best = {0.0, 0, -1};
+    RowCand best = {0.0, 0, -1, 0.0};
     int cnt = 0;
     // all loads of a chunk are issued before any is tested: one L2 round trip per chunk
     constexpr int kU = 8;
@@ -710,7 +718,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
             const int i = base + u * blockDim.x + threadIdx.x;
             if (i < P.m && al[u] > P.tol_piv && th[u] <= thr) {
                 cnt++;
-                RowCand c = {al[u], s.basis[i], i};
+                RowCand c = {al[u], s.basis[i], i, th[u]};
                 if (row_beats(c, best, bland)) best = c;
             }
         }
@@ -726,7 +734,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
             return;
         }
         C->r = b.row;
-        C->theta = __ldcg(s.theta + b.row);
+        C->theta = b.th;
         C->alpha_r = b.a;
         C->tcount = cnt;
         if (cnt > 1) C->flags |= kTfTieSet;
@@ -750,11 +758,14 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
 // block 0 may already be exchanging the basis.
 
 struct IterState {
-    int status, it, q, r, tcount, abuf, pending, flags, degen_run, bland;
+    int status, it, q, r, leave, tcount, abuf, pending, flags, degen_run, bland;
     double dq, theta, alpha_r;
+    // kept by block 0 during the launch, written back to the control block at its end
+    int nsb, n_degenerate, n_tabu, n_bland, n_asp, n_price, n_update;
+    double z, bytes_price, bytes_update;
 };
 
-constexpr unsigned kBarrierSpins = 1u << 22;  // ~0.2 s of polling, then the launch gives up
+constexpr unsigned kBarrierSpins = 1u << 21;  // about a second of polling, then the launch gives up
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -762,29 +773,28 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     return v;
 }
 
-// Grid barrier of a cooperative launch: a cumulative arrival count, and the
-// number of the last barrier every CTA has reached.  Waits are bounded; a CTA
-// that gives up reports it, and the launch ends with kErrTimeout.
+// Grid barrier of a cooperative launch: one cumulative arrival counter.  Each
+// CTA adds its arrival with a release reduction (no round trip) and polls the
+// counter with acquire loads until every CTA of this barrier has arrived
+// (epoch * CTAs).  Waits are bounded; a CTA that gives up reports it, and the
+// launch ends with kErrTimeout.
+__device__ __forceinline__ void red_release_add(uint32_t* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ bool grid_barrier(uint32_t* bar, unsigned& epoch, volatile int* fail, unsigned parties = 0) {
     __syncthreads();
     if (threadIdx.x == 0) {
         ++epoch;
-        __threadfence();
-        const unsigned prev = atomicAdd(bar, 1u);
-        if (prev == epoch * (parties ? parties : gridDim.x) - 1u) {
-            __threadfence();
-            atomicExch(bar + 1, epoch);
-        } else {
-            unsigned spins = 0;
-            while (ld_acquire_u32(bar + 1) < epoch) {
-                if (++spins > kBarrierSpins) {
-                    *fail = 1;
-                    break;
-                }
-                __nanosleep(32);
+        const unsigned target = epoch * (parties ? parties : gridDim.x);
+        red_release_add(bar, 1u);
+        unsigned spins = 0;
+        while (ld_acquire_u32(bar) < target) {
+            if (++spins > kBarrierSpins) {
+                *fail = 1;
+                break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return *fail == 0;
@@ -795,8 +805,7 @@ __device__ bool grid_barrier(uint32_t* bar, unsigned& epoch, volatile int* fail,
 // counters (the same rules as k_pivot).
 __device__ void pivot_bookkeeping(const DevState& s, IterState& S, bool lead) {
     const Params& P = s.p;
-    Ctrl* C = s.ctrl;
-    const int it = S.it, q = S.q, r = S.r;
+    const int it = S.it, q = S.q, r = S.r, leave = S.leave;
     const double th = S.theta, dq = S.dq;
     int flags = S.flags;
     const bool degenerate = th <= P.tol_tie;
@@ -804,11 +813,12 @@ __device__ void pivot_bookkeeping(const DevState& s, IterState& S, bool lead) {
     const bool push = P.tabu_tenure > 0 && (S.tcount > 1 || degenerate);
     if (push) flags |= kTfTabuPush;
     if (lead) {
-        const int leave = s.basis[r];
-        if (degenerate) C->n_degenerate++;
+        // stores only: the leaving variable comes from the ratio test, the
+        // counters and the objective stay in S until the launch ends
+        if (degenerate) S.n_degenerate++;
         if (push) {
             s.tabu_until[leave] = it + 1 + P.tabu_tenure;
-            C->n_tabu++;
+            S.n_tabu++;
         }
         if (it < P.trace_cap) {
             s.trace.q[it] = q;
@@ -817,11 +827,11 @@ __device__ void pivot_bookkeeping(const DevState& s, IterState& S, bool lead) {
             s.trace.dq[it] = dq;
             s.trace.flags[it] = flags;
         }
-        C->z = __dadd_rn(C->z, __dmul_rn(dq, th));
+        S.z = __dadd_rn(S.z, __dmul_rn(dq, th));
         s.pos[leave] = -1;
         s.basis[r] = q;
         s.pos[q] = r;
-        C->nsb += (q < P.n ? 1 : 0) - (leave < P.n ? 1 : 0);
+        S.nsb += (q < P.n ? 1 : 0) - (leave < P.n ? 1 : 0);
     }
     const int it1 = it + 1;
     S.it = it1;
@@ -829,7 +839,7 @@ __device__ void pivot_bookkeeping(const DevState& s, IterState& S, bool lead) {
     if (S.bland && !degenerate) S.bland = 0;
     if (!S.bland && P.bland_after > 0 && S.degen_run >= P.bland_after) {
         S.bland = 1;
-        if (lead) C->n_bland++;
+        if (lead) S.n_bland++;
     }
     S.flags = 0;
     if (P.reinvert_every > 0 && it1 % P.reinvert_every == 0) {
@@ -839,20 +849,23 @@ __device__ void pivot_bookkeeping(const DevState& s, IterState& S, bool lead) {
         S.pending = 1;
         if (it1 >= P.max_iters) S.status = kIterLimit;
     }
-    if (lead) {
-        C->it = S.it;
-        C->degen_run = S.degen_run;
-        C->bland = S.bland;
-        C->flags = 0;
-        C->status = S.status;
-        C->pending = S.pending;
-    }
+}
+
+// The state block 0 kept during the launch, into the control block.
+__device__ void iterate_flush(const DevState& s, const IterState& S) {
+    Ctrl* C = s.ctrl;
+    C->status = S.status; C->it = S.it; C->q = S.q; C->r = S.r; C->tcount = S.tcount; C->abuf = S.abuf;
+    C->pending = S.pending; C->flags = S.flags; C->degen_run = S.degen_run; C->bland = S.bland;
+    C->dq = S.dq; C->theta = S.theta; C->alpha_r = S.alpha_r;
+    C->nsb = S.nsb; C->n_degenerate = S.n_degenerate; C->n_tabu = S.n_tabu; C->n_bland = S.n_bland;
+    C->n_asp = S.n_asp; C->n_price = S.n_price; C->n_update = S.n_update;
+    C->z = S.z; C->bytes_price = S.bytes_price; C->bytes_update = S.bytes_update;
 }
 
 __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int iters) {
     Ctrl* C = s.ctrl;
     const Params& P = s.p;
-    extern __shared__ double sh[];  // y for PRICE; a_q and rho for UPDATE (2 ld doubles)
+    extern __shared__ double sh[];  // y and rho (ld doubles each)
     __shared__ IterState S;
     __shared__ volatile int fail;
     __shared__ double gmin_sh;
@@ -866,6 +879,10 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
         S.status = C->status; S.it = C->it; S.q = C->q; S.r = C->r; S.tcount = C->tcount;
         S.abuf = C->abuf; S.pending = C->pending; S.flags = C->flags; S.degen_run = C->degen_run;
         S.bland = C->bland; S.dq = C->dq; S.theta = C->theta; S.alpha_r = C->alpha_r;
+        S.leave = (S.r >= 0 && S.r < P.m) ? s.basis[S.r] : -1;
+        S.nsb = C->nsb; S.n_degenerate = C->n_degenerate; S.n_tabu = C->n_tabu; S.n_bland = C->n_bland;
+        S.n_asp = C->n_asp; S.n_price = C->n_price; S.n_update = C->n_update;
+        S.z = C->z; S.bytes_price = C->bytes_price; S.bytes_update = C->bytes_update;
     }
     // every CTA has its copy of the control block before block 0 changes it
     if (!grid_barrier(s.gbar, epoch, &fail)) {
@@ -874,10 +891,14 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
     }
     for (int step = 0; step < iters; ++step) {
         // ---- (1) the pivot chosen by the last ratio test: rho, y, bbar, bookkeeping
+        bool rh_staged = false;
         if (S.status == kRunning && S.r >= 0 && S.r < P.m && S.q >= 0) {
             const int r = S.r;
             const double* acur = s.alpha + (size_t)S.abuf * P.ld;
             const double ar = S.alpha_r, th = S.theta, dq = S.dq;
+            __syncthreads();  // every thread has read the state before thread 0 advances it
+            // the bookkeeping's dependent loads overlap the slices below
+            if (threadIdx.x == 0) pivot_bookkeeping(s, S, lead);
             const double* brow = s.binv + (size_t)r * P.ld;
             const int tid = blockIdx.x * blockDim.x + threadIdx.x;
             const int stride = G * blockDim.x;
@@ -890,14 +911,18 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
             }
             for (int i = tid; i < P.m; i += stride)
                 s.bbar[i] = (i == r) ? th : __dsub_rn(__ldcg(s.bbar + i), __dmul_rn(__ldcg(acur + i), th));
-            __syncthreads();
-            if (threadIdx.x == 0) pivot_bookkeeping(s, S, lead);
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             if (S.status == kReinvert) break;
         }
+        double* rh = sh + P.ld;  // rho for UPDATE, staged with y
         // ---- (2) PRICE + CHUZC
         if (S.status == kRunning) {
-            for (int k = threadIdx.x; k < P.ld; k += blockDim.x) sh[k] = __ldcg(s.y + k);
+            const bool stage_rh = S.pending != 0;
+            for (int k = threadIdx.x; k < P.ld; k += blockDim.x) {
+                sh[k] = __ldcg(s.y + k);
+                if (stage_rh) rh[k] = __ldcg(s.rho + k);
+            }
+            rh_staged = stage_rh;
             __syncthreads();
             const Cand bc = price_block(s, S.it, sh);
             if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
@@ -914,13 +939,9 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
                     S.flags |= d.flags;
                 }
                 if (lead) {
-                    C->bytes_price += 8.0 * P.m * (double)(P.n - C->nsb);
-                    C->n_price++;
-                    C->n_asp += d.asp;
-                    C->status = S.status;
-                    C->q = S.q;
-                    C->dq = S.dq;
-                    C->flags = S.flags;
+                    S.bytes_price += 8.0 * P.m * (double)(P.n - S.nsb);
+                    S.n_price++;
+                    S.n_asp += d.asp;
                 }
             }
             __syncthreads();
@@ -929,43 +950,32 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
         const bool do_upd = S.pending != 0 && S.r >= 0 && S.r < P.m;
         const bool do_ftran = S.status == kRunning && S.q >= 0 && S.q < P.n + P.m;
         if (!do_upd && !do_ftran) break;
-        double* aq = sh;
-        double* rh = sh + P.ld;
-        if (do_ftran) {
-            const int q = S.q;
-            if (q < P.n) {
-                const double* col = s.A_cm + (size_t)q * P.ld;
-                for (int k = threadIdx.x; k < P.ld; k += blockDim.x) aq[k] = col[k];
-            } else {
-                for (int k = threadIdx.x; k < P.ld; k += blockDim.x) aq[k] = (k == q - P.n) ? 1.0 : 0.0;
-            }
-        }
-        if (do_upd)
+        // a structural entering column is read by every warp straight from A
+        // (it stays in L1); a slack column e_i is generated
+        const double* aq = (do_ftran && S.q < P.n) ? s.A_cm + (size_t)S.q * P.ld : nullptr;
+        const int aq_unit = (do_ftran && S.q >= P.n) ? S.q - P.n : -1;
+        if (do_upd && !rh_staged)
             for (int k = threadIdx.x; k < P.ld; k += blockDim.x) rh[k] = __ldcg(s.rho + k);
         __syncthreads();
         const double* acur = s.alpha + (size_t)S.abuf * P.ld;
         double* anxt = s.alpha + (size_t)(S.abuf ^ 1) * P.ld;
-        const double tb = block_min(update_block(s, S.r, do_upd, do_ftran, acur, anxt, aq, rh, true));
+        const double tb = block_min(update_block(s, S.r, do_upd, do_ftran, acur, anxt, aq, rh, true, aq_unit));
         if (threadIdx.x == 0) {
             s.upd_part[blockIdx.x] = tb;
             if (lead) {
-                C->bytes_update += (do_upd ? 16.0 : (do_ftran ? 8.0 : 0.0)) * P.m * (double)P.m;
-                C->n_update++;
+                S.bytes_update += (do_upd ? 16.0 : (do_ftran ? 8.0 : 0.0)) * P.m * (double)P.m;
+                S.n_update++;
             }
         }
         if (!do_ftran) {
             // the pending update of the last pivot was applied (optimal or iteration limit)
-            if (threadIdx.x == 0) {
-                S.pending = 0;
-                if (lead) C->pending = 0;
-            }
+            if (threadIdx.x == 0) S.pending = 0;
             break;
         }
         if (!grid_barrier(s.gbar, epoch, &fail)) break;
         // ---- (4) CHUZR: minimum ratio, tie set, leaving row (every CTA)
-        double tg = DBL_MAX;
-        for (int b = threadIdx.x; b < G; b += blockDim.x) tg = fmin(tg, __ldcg(s.upd_part + b));
-        tg = block_min(tg);
+        const double mine = (int)threadIdx.x < G ? __ldcg(s.upd_part + threadIdx.x) : DBL_MAX;  // G <= blockDim
+        double tg = block_min(mine);
         if (threadIdx.x == 0) {
             gmin_sh = tg;
             nflag = 0;
@@ -976,23 +986,18 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
             if (threadIdx.x == 0) {
                 S.status = kUnbounded;
                 S.pending = 0;
-                if (lead) {
-                    C->status = kUnbounded;
-                    C->pending = 0;
-                }
             }
             break;
         }
         const double thr = gmin + P.tol_tie * fmax(1.0, fabs(gmin));
         // CTAs whose smallest ratio lies within the tie tolerance hold the tie set
-        for (int b = threadIdx.x; b < G; b += blockDim.x)
-            if (__ldcg(s.upd_part + b) <= thr) {
-                const int k = atomicAdd(&nflag, 1);
-                if (k < kMaxFlagged) flg[k] = b;
-            }
+        if ((int)threadIdx.x < G && mine <= thr) {
+            const int k = atomicAdd(&nflag, 1);
+            if (k < kMaxFlagged) flg[k] = threadIdx.x;
+        }
         __syncthreads();
         const bool bland = S.bland != 0;
-        RowCand best = {0.0, 0, -1};
+        RowCand best = {0.0, 0, -1, 0.0};
         int cnt = 0;
         if (nflag <= kMaxFlagged) {
             const int per = (P.m + G - 1) / G;  // rows of the fullest CTA
@@ -1003,7 +1008,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
                 const double al = __ldcg(anxt + i), th = __ldcg(s.theta + i);
                 if (al > P.tol_piv && th <= thr) {
                     cnt++;
-                    RowCand c = {al, __ldcg(s.row_var + i), i};
+                    RowCand c = {al, __ldcg(s.row_var + i), i, th};
                     if (row_beats(c, best, bland)) best = c;
                 }
             }
@@ -1012,7 +1017,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
                 const double al = __ldcg(anxt + i), th = __ldcg(s.theta + i);
                 if (al > P.tol_piv && th <= thr) {
                     cnt++;
-                    RowCand c = {al, __ldcg(s.row_var + i), i};
+                    RowCand c = {al, __ldcg(s.row_var + i), i, th};
                     if (row_beats(c, best, bland)) best = c;
                 }
             }
@@ -1022,33 +1027,24 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
             S.pending = 0;
             if (b.row < 0) {  // cannot happen for finite data; stop rather than pivot on garbage
                 S.status = kUnbounded;
-                if (lead) {
-                    C->status = kUnbounded;
-                    C->err = kErrBadIndex;
-                    C->pending = 0;
-                }
+                if (lead) C->err = kErrBadIndex;
             } else {
                 S.r = b.row;
-                S.theta = __ldcg(s.theta + b.row);
+                S.leave = b.var;
+                S.theta = b.th;
                 S.alpha_r = b.a;
                 S.tcount = cnt;
                 if (cnt > 1) S.flags |= kTfTieSet;
                 S.abuf ^= 1;
-                if (lead) {
-                    C->r = S.r;
-                    C->theta = S.theta;
-                    C->alpha_r = S.alpha_r;
-                    C->tcount = S.tcount;
-                    C->flags = S.flags;
-                    C->abuf = S.abuf;
-                    C->pending = 0;
-                }
             }
         }
         __syncthreads();
         if (S.status != kRunning) break;
     }
-    if (lead && threadIdx.x == 0 && fail) C->err = kErrTimeout;
+    if (lead && threadIdx.x == 0) {
+        iterate_flush(s, S);
+        if (fail) C->err = kErrTimeout;
+    }
 }
 
 // Self-test of the bounded wait: the barrier expects one CTA more than the

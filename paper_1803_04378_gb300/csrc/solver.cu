@@ -435,7 +435,9 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     {
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
-        if (h->opt.engine == 0 && h->opt.price_mode == 0 && coop && occupancy_iterate(h->ld) >= 1) {
+        // (k_iterate's ratio test holds one CTA partial per thread: at most 1024 CTAs)
+        if (h->opt.engine == 0 && h->opt.price_mode == 0 && coop && h->geo.sms <= 1024 &&
+            occupancy_iterate(h->ld) >= 1) {
             h->persist = true;
             h->persist_blocks = h->geo.sms;  // the partial arrays hold at least sms entries
             if (h->opt.kernel_timing > 0) {
