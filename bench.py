@@ -138,6 +138,22 @@ def _traffic(kernel: str):
     return ent.get("dram_bytes_per_launch_full_size")
 
 
+def _certificate(A, b, c, x, y):
+    """Optimality residuals of the returned solution (host, numpy): primal
+    infeasibility of Ax <= b, x >= 0 and dual infeasibility of A^T y >= c,
+    y >= 0, relative to max|b| and max|c|, and the relative duality gap."""
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    s = b - A @ x
+    primal = max(float(np.max(-s, initial=0.0)), float(np.max(-x, initial=0.0)))
+    dual = max(float(np.max(c - A.T @ y, initial=0.0)), float(np.max(-y, initial=0.0)))
+    pz, dz = float(c @ x), float(b @ y)
+    return {"primal_residual": primal / max(1.0, float(np.max(np.abs(b)))) + 0.0,
+            "dual_residual": dual / max(1.0, float(np.max(np.abs(c)))),
+            "gap_rel": abs(pz - dz) / max(1.0, abs(pz))}
+
+
 def cpu_baseline(A, b, c, iters: int):
     """The oracle (single-threaded C, unmodified) on the first `iters` pivots
     of the same workload (no reinversion inside the sample)."""
@@ -444,6 +460,7 @@ def main():
             "pivots_per_solve": results[0].iterations,
             "reinversions_per_solve": results[0].reinversions,
             "objective": z,
+            "certificate": _certificate(A, b, c, x, y),
             "us_per_pivot_excl_reinversion": 1e6 * iter_s / iters,
             "reinversion_share": reinv_s / sum(r.seconds for r in results),
             "chain_hbm_gbs_excl_reinversion": chain_bytes / iter_s / 1e9,

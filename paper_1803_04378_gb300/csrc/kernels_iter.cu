@@ -871,6 +871,8 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
     __shared__ double gmin_sh;
     __shared__ int nflag;
     __shared__ int flg[kMaxFlagged];
+    __shared__ double tb_sh;
+    __shared__ RowPart rec_sh;
     unsigned epoch = 0;
     const bool lead = blockIdx.x == 0;
     const int G = gridDim.x;
@@ -903,14 +905,16 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
             const int tid = blockIdx.x * blockDim.x + threadIdx.x;
             const int stride = G * blockDim.x;
             for (int k = tid; k < P.ld; k += stride) {
-                const double rn = __ldcg(brow + k) / ar;
+                // all four loads first: one round trip (m <= ld)
+                const double bk = __ldcg(brow + k), yk = __ldcg(s.y + k);
+                const double bb = k < P.m ? __ldcg(s.bbar + k) : 0.0, ak = k < P.m ? __ldcg(acur + k) : 0.0;
+                const double rn = bk / ar;
                 s.rho[k] = rn;
-                const double yn = __dadd_rn(__ldcg(s.y + k), __dmul_rn(dq, rn));
+                const double yn = __dadd_rn(yk, __dmul_rn(dq, rn));
                 s.y[k] = yn;
                 s.y32[k] = (float)yn;
+                if (k < P.m) s.bbar[k] = (k == r) ? th : __dsub_rn(bb, __dmul_rn(ak, th));
             }
-            for (int i = tid; i < P.m; i += stride)
-                s.bbar[i] = (i == r) ? th : __dsub_rn(__ldcg(s.bbar + i), __dmul_rn(__ldcg(acur + i), th));
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             if (S.status == kReinvert) break;
         }
@@ -961,10 +965,38 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
         double* anxt = s.alpha + (size_t)(S.abuf ^ 1) * P.ld;
         const double tb = block_min(update_block(s, S.r, do_upd, do_ftran, acur, anxt, aq, rh, true, aq_unit));
         if (threadIdx.x == 0) {
-            s.upd_part[blockIdx.x] = tb;
+            tb_sh = tb;
             if (lead) {
                 S.bytes_update += (do_upd ? 16.0 : (do_ftran ? 8.0 : 0.0)) * P.m * (double)P.m;
                 S.n_update++;
+            }
+        }
+        __syncthreads();
+        if (do_ftran) {
+            // this CTA's best row and tie count under its own smallest ratio's
+            // threshold; when one CTA holds the global minimum this is the answer
+            const double tbl = tb_sh;
+            const double thr_b = tbl + P.tol_tie * fmax(1.0, fabs(tbl));
+            const bool blandb = S.bland != 0;
+            RowCand lb = {0.0, 0, -1, 0.0};
+            int lc = 0;
+            if (tbl != DBL_MAX) {
+                const int owned = (P.m - (int)blockIdx.x + G - 1) / G;
+                for (int l = threadIdx.x; l < owned; l += blockDim.x) {
+                    const int i = blockIdx.x + G * l;
+                    const double al = anxt[i], th = s.theta[i];  // written by this CTA
+                    if (al > P.tol_piv && th <= thr_b) {
+                        lc++;
+                        RowCand c = {al, s.row_var[i], i, th};
+                        if (row_beats(c, lb, blandb)) lb = c;
+                    }
+                }
+            }
+            lb = block_row_best(lb, lc, blandb);
+            if (threadIdx.x == 0) {
+                RowPart rp;
+                rp.tmin = tbl; rp.a = lb.a; rp.th = lb.th; rp.var = lb.var; rp.row = lb.row; rp.cnt = lc; rp.pad_ = 0;
+                s.row_part[blockIdx.x] = rp;
             }
         }
         if (!do_ftran) {
@@ -974,7 +1006,15 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
         }
         if (!grid_barrier(s.gbar, epoch, &fail)) break;
         // ---- (4) CHUZR: minimum ratio, tie set, leaving row (every CTA)
-        const double mine = (int)threadIdx.x < G ? __ldcg(s.upd_part + threadIdx.x) : DBL_MAX;  // G <= blockDim
+        // one record per CTA (G <= blockDim): smallest ratio, best row, tie count
+        RowPart rec;
+        rec.tmin = DBL_MAX;
+        if ((int)threadIdx.x < G) {
+            const RowPart* rp = s.row_part + threadIdx.x;
+            rec.tmin = __ldcg(&rp->tmin); rec.a = __ldcg(&rp->a); rec.th = __ldcg(&rp->th);
+            rec.var = __ldcg(&rp->var); rec.row = __ldcg(&rp->row); rec.cnt = __ldcg(&rp->cnt);
+        }
+        const double mine = rec.tmin;
         double tg = block_min(mine);
         if (threadIdx.x == 0) {
             gmin_sh = tg;
@@ -994,12 +1034,20 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
         if ((int)threadIdx.x < G && mine <= thr) {
             const int k = atomicAdd(&nflag, 1);
             if (k < kMaxFlagged) flg[k] = threadIdx.x;
+            rec_sh = rec;  // read only when this CTA is the only one (nflag == 1)
         }
         __syncthreads();
         const bool bland = S.bland != 0;
         RowCand best = {0.0, 0, -1, 0.0};
         int cnt = 0;
-        if (nflag <= kMaxFlagged) {
+        if (nflag == 1) {
+            // one CTA holds the minimum, so its threshold is the global one and
+            // its record is the tie set's best row and size
+            if (threadIdx.x == 0) {
+                best.a = rec_sh.a; best.var = rec_sh.var; best.row = rec_sh.row; best.th = rec_sh.th;
+                cnt = rec_sh.cnt;
+            }
+        } else if (nflag <= kMaxFlagged) {
             const int per = (P.m + G - 1) / G;  // rows of the fullest CTA
             for (int e = threadIdx.x; e < nflag * per; e += blockDim.x) {
                 const int b = flg[e / per], l = e % per;
@@ -1022,7 +1070,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
                 }
             }
         }
-        const RowCand b = block_row_best(best, cnt, bland);
+        const RowCand b = nflag == 1 ? best : block_row_best(best, cnt, bland);
         if (threadIdx.x == 0) {
             S.pending = 0;
             if (b.row < 0) {  // cannot happen for finite data; stop rather than pivot on garbage

@@ -397,7 +397,10 @@ __global__ void k_b11i(DevState s, int k) {
 
 // C (nslack x k, after B11^-1 in rv_W) = -A[S, J] B11^-1; S rows in increasing
 // order so that a tile's gathers from a column of A are close together.
-constexpr int kGM = 64, kGN = 64, kGK = 16;
+// 32 x 32 tiles (2 x 2 outputs per thread): with k of a few hundred, the
+// (m-k) x k output gives several tiles per SM, so the SMs' shares differ by a
+// small fraction of a tile.
+constexpr int kGM = 32, kGN = 32, kGK = 16;
 __global__ void __launch_bounds__(256) k_slack_gemm(DevState s, int k, int nslack) {
     if (s.ctrl->err != kErrNone) return;
     __shared__ double As[kGK][kGM + 1];
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(256) k_slack_gemm(DevState s, int k, int nslac
     double* Cs = s.rv_W + (size_t)k * k;
     const int row0 = blockIdx.y * kGM, col0 = blockIdx.x * kGN;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4] = {};
+    double acc[2][2] = {};
     const int ld = s.p.ld;
     for (int b0 = 0; b0 < k; b0 += kGK) {
         for (int e = threadIdx.x; e < kGM * kGK; e += blockDim.x) {
@@ -422,25 +425,20 @@ __global__ void __launch_bounds__(256) k_slack_gemm(DevState s, int k, int nslac
         __syncthreads();
 #pragma unroll
         for (int bb = 0; bb < kGK; ++bb) {
-            double av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[bb][ty * 4 + i];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) bv[jj] = Bs[bb][tx * 4 + jj];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(av[i], bv[jj], acc[i][jj]);
+            const double a0 = As[bb][ty * 2], a1 = As[bb][ty * 2 + 1];
+            const double b0v = Bs[bb][tx * 2], b1v = Bs[bb][tx * 2 + 1];
+            acc[0][0] = fma(a0, b0v, acc[0][0]); acc[0][1] = fma(a0, b1v, acc[0][1]);
+            acc[1][0] = fma(a1, b0v, acc[1][0]); acc[1][1] = fma(a1, b1v, acc[1][1]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int gr = row0 + ty * 4 + i;
+    for (int i = 0; i < 2; ++i) {
+        const int gr = row0 + ty * 2 + i;
         if (gr >= nslack) continue;
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            const int gc = col0 + tx * 4 + jj;
+        for (int jj = 0; jj < 2; ++jj) {
+            const int gc = col0 + tx * 2 + jj;
             if (gc < k) Cs[(size_t)gr * k + gc] = -acc[i][jj];
         }
     }

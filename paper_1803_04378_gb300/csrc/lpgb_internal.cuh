@@ -92,6 +92,13 @@ struct Ctrl {
     double z;              // objective c_B^T bbar
 };
 
+// Per-CTA ratio-test record of k_iterate: the CTA's smallest ratio, and its
+// best row and tie count under the tie threshold of that ratio.
+struct RowPart {
+    double tmin, a, th;
+    int32_t var, row, cnt, pad_;
+};
+
 // Candidate triple of CHUZC (per block partial).
 struct PriceCand {
     double d_all; int32_t j_all;   // best nonbasic (optimality test, aspiration)
@@ -141,6 +148,7 @@ struct DevState {
     Ctrl* ctrl;
     PriceCand* price_part;
     double* upd_part;   // per-block theta minima
+    RowPart* row_part;  // k_iterate: per-CTA ratio-test record
     int32_t* row_var;   // m: basic variable of each row as seen by the last FTRAN (k_iterate)
     uint32_t* gbar;     // k_iterate grid barrier: arrivals, released epoch
     TraceBuf trace;

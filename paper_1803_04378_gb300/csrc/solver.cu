@@ -409,6 +409,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &s.lp_part, (size_t)parts));
     TRY(dalloc(h, &upd_part, (size_t)parts));
     TRY(dalloc(h, &s.row_var, (size_t)m));
+    TRY(dalloc(h, &s.row_part, (size_t)parts));
     TRY(dalloc(h, &s.gbar, 2));
     if (P.trace_cap > 0) {
         TRY(dalloc(h, &s.trace.q, (size_t)P.trace_cap));
