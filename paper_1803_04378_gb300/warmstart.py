@@ -64,17 +64,21 @@ class Family:
     def features(self, out):
         lpgb.family_features(self.A0, self.b0, self.c0, self.A, self.b, self.c, self.sigma, out, self.stream)
 
-    def solve(self, start=None):
-        """Solve the current instance; start = (basis, structural set) warm
-        starts from `basis` (repaired if infeasible) with the guided rule on
-        the structural set, None solves cold from the slack basis."""
+    def solve(self, start=None, mode: str = "repair"):
+        """Solve the current instance.  start = (basis, structural set):
+        mode "repair" starts from `basis` (repaired if infeasible) with the
+        guided rule on the structural set; mode "guided" starts from the slack
+        basis and only applies the guided rule.  None solves cold."""
         self.lp.update_problem(self.A, self.b, self.c)
         if start is None:
             self.lp.set_priority([])
         else:
             basis, structurals = start
             self.lp.set_priority(structurals)
-            self.lp.set_basis_repair(basis, self.m)
+            if mode == "repair":
+                self.lp.set_basis_repair(basis, self.m)
+            elif mode != "guided":
+                raise ValueError(mode)
         res = self.lp.solve()
         return res, self.lp.basis()
 
@@ -171,8 +175,9 @@ def predicted_start(net, features, m: int, n: int):
     return basis_from_scores(logits[0].cpu().numpy(), m, n)
 
 
-def evaluate(family: Family, net, instances):
-    """Cold vs warm solves of host instances: pivots, device seconds, objectives."""
+def evaluate(family: Family, net, instances, guided: bool = False):
+    """Cold vs warm solves of host instances: pivots, device seconds, objectives
+    (guided: also the slack-basis start with the guided rule only)."""
     import torch
     feat = torch.empty(family.n_features, dtype=torch.float32, device="cuda")
     rows = []
@@ -186,11 +191,16 @@ def evaluate(family: Family, net, instances):
         t_pred = time.perf_counter() - t0
         warm, _ = family.solve(start)
         z_warm = family.lp.solution()[2]
-        rows.append(dict(cold_pivots=cold.iterations, warm_pivots=warm.iterations,
-                         cold_s=cold.seconds, warm_s=warm.seconds + t_pred, predict_s=t_pred,
-                         z_cold=z_cold, z_warm=z_warm, predicted=len(start[1]),
-                         repairs=warm.warm_repairs, fallback=warm.warm_fallback,
-                         status=(cold.status, warm.status)))
+        row = dict(cold_pivots=cold.iterations, warm_pivots=warm.iterations,
+                   cold_s=cold.seconds, warm_s=warm.seconds + t_pred, predict_s=t_pred,
+                   z_cold=z_cold, z_warm=z_warm, predicted=len(start[1]),
+                   repairs=warm.warm_repairs, fallback=warm.warm_fallback,
+                   status=(cold.status, warm.status))
+        if guided:
+            gd, _ = family.solve(start, mode="guided")
+            row.update(guided_pivots=gd.iterations, guided_s=gd.seconds + t_pred,
+                       z_guided=family.lp.solution()[2], guided_status=gd.status)
+        rows.append(row)
     return rows
 
 
@@ -203,11 +213,19 @@ def summarize(rows):
     zw = np.array([r["z_warm"] for r in rows])
     fb = np.array([r.get("fallback", 0) for r in rows])
     rp = np.array([r.get("repairs", 0) for r in rows])
-    return dict(instances=len(rows), cold_pivots_mean=float(cp.mean()), warm_pivots_mean=float(wp.mean()),
-                fallbacks=int(fb.sum()), repairs_mean=float(rp.mean()),
-                pivot_ratio=float(wp.sum() / cp.sum()), cold_time_to_optimum_s=float(cs.mean()),
-                warm_time_to_optimum_s=float(wsec.mean()), speedup=float(cs.sum() / wsec.sum()),
-                max_rel_objective_gap=float(np.max(np.abs(zw - zc) / np.maximum(1.0, np.abs(zc)))))
+    out = dict(instances=len(rows), cold_pivots_mean=float(cp.mean()), warm_pivots_mean=float(wp.mean()),
+               fallbacks=int(fb.sum()), repairs_mean=float(rp.mean()),
+               pivot_ratio=float(wp.sum() / cp.sum()), cold_time_to_optimum_s=float(cs.mean()),
+               warm_time_to_optimum_s=float(wsec.mean()), speedup=float(cs.sum() / wsec.sum()),
+               max_rel_objective_gap=float(np.max(np.abs(zw - zc) / np.maximum(1.0, np.abs(zc)))))
+    if rows and "guided_pivots" in rows[0]:
+        gp = np.array([r["guided_pivots"] for r in rows], float)
+        gs = np.array([r["guided_s"] for r in rows])
+        zg = np.array([r["z_guided"] for r in rows])
+        out.update(guided_pivots_mean=float(gp.mean()), guided_pivot_ratio=float(gp.sum() / cp.sum()),
+                   guided_time_to_optimum_s=float(gs.mean()), guided_speedup=float(cs.sum() / gs.sum()),
+                   guided_max_rel_objective_gap=float(np.max(np.abs(zg - zc) / np.maximum(1.0, np.abs(zc)))))
+    return out
 
 
 def main():
@@ -224,12 +242,16 @@ def main():
     ap.add_argument("--m", type=int, default=1024)
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--out", default="")
+    ap.add_argument("--labels", default="hint", choices=["hint", "cold"],
+                    help="label solves start from the base LP's optimal basis (hint) or the slack basis")
+    ap.add_argument("--guided", action="store_true",
+                    help="also evaluate the slack-basis start with the guided rule only")
     args = ap.parse_args()
     from . import build
     build.build()
     base = lpgen.dense_real_lp(args.m, args.n, 4)
     fam = Family(base)
-    hint = base_hint(fam)
+    hint = base_hint(fam) if args.labels == "hint" else None
     t0 = time.perf_counter()
     X, Y, piv = generate_labels(fam, range(1, args.train + 1), hint, log_every=1000)
     t_labels = time.perf_counter() - t0
@@ -237,9 +259,9 @@ def main():
     net, losses = train(X, Y, epochs=args.epochs, log=True)
     t_train = time.perf_counter() - t0
     held = [lpgen.perturbed_lp(base, 10_000_000 + k) for k in range(args.heldout)]
-    rows = evaluate(fam, net, held)
+    rows = evaluate(fam, net, held, guided=args.guided)
     out = dict(summarize(rows), train_pairs=args.train, label_seconds=t_labels, train_seconds=t_train,
-               label_pivots_mean=float(piv.mean()), losses=losses, m=args.m, n=args.n)
+               label_pivots_mean=float(piv.mean()), losses=losses, m=args.m, n=args.n, labels=args.labels)
     print(json.dumps(out))
     if args.out:
         json.dump(out, open(args.out, "w"), indent=1)
