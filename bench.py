@@ -196,6 +196,19 @@ def run_batched(lpgb, args, with_cpu: bool):
            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": fl / secs / 1e12,
                         "peak": FP64_PEAK_TFLOPS, "frac": fl / secs / 1e12 / FP64_PEAK_TFLOPS,
                         "what": "algorithmic FP64 flops of FTRAN, the B^-1 update and re-pricing"}}
+    # the plain single-LP GPU solver on a sample of the same LPs (one handle
+    # per LP, FP64 PRICE, device solve time only)
+    sample, t_plain, gap = 64, 0.0, 0.0
+    for k in range(min(sample, count)):
+        with lpgb.LP(*probs[k]) as lp1:
+            r1 = lp1.solve()
+            z1 = lp1.solution()[2]
+        t_plain += r1.seconds
+        gap = max(gap, abs(z1 - float(obj[k])) / max(1.0, abs(z1)))
+    out["plain_gpu_solver"] = {"value": min(sample, count) / t_plain, "unit": "LPs/s",
+                               "sample": f"first {min(sample, count)} LPs of the batch, one lp_solve each",
+                               "batched_speedup": out["value"] / (min(sample, count) / t_plain),
+                               "max_rel_objective_gap_vs_batched": gap}
     if with_cpu:
         import oracle
         sample = 32

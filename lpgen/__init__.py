@@ -37,6 +37,8 @@ TAG_C = 4
 TAG_B_ZERO_ROWS = 5
 TAG_SIZES = 6
 TAG_NOISE = 7
+TAG_XSTAR = 8
+TAG_NEG_ROWS = 9
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -132,6 +134,29 @@ def degenerate_lp(m: int, n: int, seed: int, zero_row_frac: float = 0.3):
     return A, b, c
 
 
+def general_lp(m: int, n: int, seed: int, neg_row_frac: float = 0.3):
+    """Dense LP with some negative b_i (needs Phase I), feasible and bounded by
+    construction.  Rows are dealt "negative" with probability neg_row_frac:
+    their A_ij are in {-10..2}, the other rows' in {-2..10}.  A point
+    x* ~ U[0, 1)^n gives b = A x* + s with s ~ U[0, 1), so x* is feasible and
+    the mostly negative rows get b_i < 0.  The last row is all ones with
+    b = sum x* + n, which bounds every objective.  c_j in {1..20}."""
+    if m < 2:
+        raise ValueError("general_lp needs m >= 2")
+    neg = uniform(stream_key(seed, TAG_NEG_ROWS), m) < neg_row_frac
+    lo = np.where(neg, -10, -2)[:, None]
+    hi = np.where(neg, 2, 10)[:, None]
+    u = uniform(stream_key(seed, TAG_A), m * n).reshape(m, n)
+    A = np.floor(lo + u * (hi - lo + 1)).astype(np.float64)
+    A = np.minimum(A, hi)
+    xs = uniform(stream_key(seed, TAG_XSTAR), n)
+    A[m - 1, :] = 1.0
+    b = A @ xs + uniform(stream_key(seed, TAG_B), m)
+    b[m - 1] = float(np.sum(xs)) + n
+    c = randint(stream_key(seed, TAG_C), n, 1, 20)
+    return A, b, c
+
+
 def batch_sizes(count: int, seed: int = 3, m_lo: int = 16, m_hi: int = 256):
     """Sizes of a batch: m_k uniform integer in [m_lo, m_hi], n_k in [m_k, 2 m_k]."""
     key = stream_key(seed, TAG_SIZES)
@@ -179,6 +204,8 @@ def make(kind: str, m: int, n: int, seed: int):
         return dense_int_lp(m, n, seed)
     if kind == "real":
         return dense_real_lp(m, n, seed)
+    if kind == "general":
+        return general_lp(m, n, seed)
     if kind == "degenerate":
         return degenerate_lp(m, n, seed)
     if kind == "warm":

@@ -10,6 +10,9 @@ it.  It shares no code with the CUDA path.
 * ``reduced_costs``    -- d = c - A^T y and d_slack = -y (C).
 * ``brute_force``      -- vertex enumeration for tiny LPs (numpy).
 * ``certificate``      -- primal/dual feasibility and duality-gap residuals.
+* ``solve_two_phase``  -- Phase I with one artificial variable for b with
+                          negative entries (Section 3.4, "Finding the initial
+                          feasible solution"), then ``solve`` as Phase II.
 
 Every floating-point function here is FP64.  Parity status: every function is
 pinned by tests in ``tests/test_oracle.py`` (brute force, closed forms,
@@ -35,6 +38,7 @@ _lock = threading.Lock()
 _lib = None
 
 OPTIMAL, UNBOUNDED, ITER_LIMIT, SINGULAR, MISMATCH = 1, 2, 3, 4, 5
+INFEASIBLE = 7  # two-phase only: the auxiliary optimum is below -tol (no feasible x)
 STATUS_NAMES = {0: "running", 1: "optimal", 2: "unbounded", 3: "iter_limit",
                 4: "singular", 5: "mismatch", 6: "nomem"}
 TF_DEGENERATE, TF_TABU_PUSH, TF_ASPIRATION, TF_BLAND = 1, 2, 4, 8
@@ -267,3 +271,92 @@ def certificate(A, b, c, x, y) -> dict:
     scale_c = max(1.0, float(np.max(np.abs(c), initial=0.0)))
     return dict(primal=primal / scale_b, dual=dual / scale_c, gap=gap,
                 cs=cs / max(1.0, abs(pz)), primal_obj=pz, dual_obj=dz)
+
+
+@dataclass
+class TwoPhaseSolution:
+    status: int
+    objective: float
+    x: np.ndarray | None
+    y: np.ndarray | None
+    basis: np.ndarray | None
+    phase1: Solution | None     # the auxiliary problem's solve (None when b >= 0)
+    phase2: Solution | None
+    exchanged: bool = False     # the artificial was basic at zero and swapped for a slack
+    start_basis: np.ndarray | None = None  # Phase II start (original variable numbering)
+
+
+def auxiliary_problem(A, b):
+    """Phase I problem for max c^T x, Ax <= b, x >= 0 with some b_i < 0
+    (Section 3.4 asks for artificial variables and the two-phase method; this
+    uses the textbook single artificial x0): maximize -x0 subject to
+    A x - x0 e <= b, x, x0 >= 0, where e_i = 1 on the rows with b_i < 0.
+    x0 is structural column n; the slacks become n+1 .. n+m.  Returns
+    (A_aux, c_aux, start_basis): the start basis is the slack basis with x0 in
+    the row of the most negative b_i (the smallest such row on ties), which is
+    feasible: x0 = -min b and slack_i = b_i - min b >= 0 on the negative rows."""
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    m, n = A.shape
+    e = (b < 0).astype(np.float64)
+    A_aux = np.hstack([A, -e[:, None]])
+    c_aux = np.zeros(n + 1)
+    c_aux[n] = -1.0
+    istar = int(np.argmin(b))
+    start = np.arange(n + 1, n + 1 + m, dtype=np.int32)
+    start[istar] = n
+    return A_aux, c_aux, start
+
+
+def phase2_start(basis_aux, binv_row_of_x0, n: int):
+    """Phase II start from the auxiliary optimum (original numbering: the aux
+    slack n+1+i is the slack n+i).  If x0 is still basic (at value zero), it is
+    exchanged for the nonbasic slack s with the largest |B^-1[p][s]| (p = x0's
+    row; ties to the smallest s): that entry is the pivot of bringing slack s
+    into row p, so the new basis is nonsingular.  Returns (basis, exchanged)."""
+    basis = np.array(basis_aux, dtype=np.int64)
+    m = len(basis)
+    exchanged = False
+    where = np.nonzero(basis == n)[0]
+    if len(where):
+        p = int(where[0])
+        in_basis = set(int(v) for v in basis)
+        best, s = -1.0, -1
+        for i in range(m):
+            if n + 1 + i in in_basis:
+                continue
+            v = abs(float(binv_row_of_x0[i]))
+            if v > best:
+                best, s = v, i
+        if s < 0 or best <= 1e-12:
+            raise np.linalg.LinAlgError("artificial cannot leave the basis")
+        basis[p] = n + 1 + s
+        exchanged = True
+    return np.array([v if v < n else v - 1 for v in basis], dtype=np.int32), exchanged
+
+
+def solve_two_phase(A, b, c, opts: Options | None = None) -> TwoPhaseSolution:
+    """max c^T x, Ax <= b, x >= 0 for any b: with b >= 0 this is ``solve``;
+    otherwise Phase I maximises -x0 over the auxiliary problem from its
+    feasible start basis, reports INFEASIBLE when the optimum is below
+    -1e-9 max(1, max|b|), and Phase II runs the method on the original problem
+    from the final auxiliary basis.  Both phases use the same rules (Dantzig,
+    tabu, reinversion every 64 pivots, Bland net)."""
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    m, n = A.shape
+    if np.min(b) >= 0:
+        s = solve(A, b, c, opts)
+        return TwoPhaseSolution(s.status, s.objective, s.x, s.y, s.basis, None, s)
+    A_aux, c_aux, start = auxiliary_problem(A, b)
+    p1 = solve(A_aux, b, c_aux, opts, start_basis=start, want_binv=True)
+    if p1.status != OPTIMAL:
+        return TwoPhaseSolution(p1.status, float("nan"), None, None, None, p1, None)
+    if p1.objective < -1e-9 * max(1.0, float(np.max(np.abs(b)))):
+        return TwoPhaseSolution(INFEASIBLE, float("nan"), None, None, None, p1, None)
+    where = np.nonzero(p1.basis == n)[0]
+    row = p1.binv[int(where[0])] if len(where) else None
+    start2, exchanged = phase2_start(p1.basis, row, n)
+    p2 = solve(A, b, c, opts, start_basis=start2)
+    return TwoPhaseSolution(p2.status, p2.objective, p2.x, p2.y, p2.basis, p1, p2, exchanged, start2)
