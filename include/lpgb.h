@@ -1,12 +1,14 @@
 /*
  * lpgb.h -- C ABI of the GB300 dense revised simplex solver.
  *
- * Solves   max c^T x   s.t.   A x <= b,  x >= 0,  b >= 0
+ * Solves   max c^T x   s.t.   A x <= b,  x >= 0
  * with the revised simplex method of Section 2.1 (Steps 1-8): slack columns
  * A = (A', I_m) form the starting basis, Dantzig pricing (Step 3/4), the ratio
  * test (Step 6), and the explicit-inverse tableau pivot (Step 8, Figure 1),
- * with the tabu anti-cycling rule of Sections 2.2 and 3.4.  Every step runs in
- * the library's own CUDA kernels (sm_103a); there is no CPU fallback.
+ * with the tabu anti-cycling rule of Sections 2.2 and 3.4.  When some b_i < 0
+ * the slack basis is infeasible and a solve starts with Phase I (the
+ * two-phase method of Section 3.4, one artificial variable).  Every step runs
+ * in the library's own CUDA kernels (sm_103a); there is no CPU fallback.
  *
  * Conventions
  *  - m = number of constraints (rows of A), n = number of structural
@@ -17,7 +19,7 @@
  *    keeps ownership of every buffer it passes.
  *  - Return codes: LP_OK (0) or a negative LP_ERR_*.  A solve that ends
  *    optimal, unbounded or at the iteration limit returns LP_OK and reports
- *    the outcome in lp_result.status.
+ *    the outcome in lp_result.status (LP_INFEASIBLE too).
  *  - A handle owns all of its device memory.  One handle must not be used
  *    from two host threads at once; different handles are independent.
  */
@@ -45,6 +47,7 @@ extern "C" {
 #define LP_OPTIMAL 1            /* Step 4: every reduced cost <= tol_d */
 #define LP_UNBOUNDED 2          /* Step 5: no alpha_i > tol_piv */
 #define LP_ITER_LIMIT 3
+#define LP_INFEASIBLE 4         /* Phase I (b with negative entries): no x >= 0 with Ax <= b */
 
 /* ---- trace flags (lp_get_trace) ----------------------------------------- */
 #define LP_TF_DEGENERATE 1      /* step length theta <= tol_tie */
@@ -87,7 +90,7 @@ typedef struct lp_options {
 
 /* Outcome and counters of one lp_solve call. */
 typedef struct lp_result {
-    int32_t status;          /* LP_OPTIMAL, LP_UNBOUNDED or LP_ITER_LIMIT */
+    int32_t status;          /* LP_OPTIMAL, LP_UNBOUNDED, LP_ITER_LIMIT or LP_INFEASIBLE */
     int32_t iterations;      /* pivots performed (cumulative over the handle) */
     int32_t reinversions;    /* reinversions performed */
     int32_t degenerate;      /* pivots with theta <= tol_tie */
@@ -116,6 +119,8 @@ typedef struct lp_result {
     double chain_bytes;      /* algorithmic PRICE + UPDATE bytes of those launches */
     int32_t chain_launches;  /* persistent launches timed */
     int32_t persistent;      /* 1: the pivots ran in the persistent kernel */
+    int32_t phase1_iterations; /* b with negative entries: pivots of the Phase I problem */
+    int32_t phase1_exchanged;  /* 1: the artificial ended basic at zero and was exchanged */
 } lp_result;
 
 /*
@@ -139,11 +144,20 @@ void lp_default_options(lp_options* opt);
  *  out              receives the new handle (set to NULL on error)
  *  m, n             constraints and structural variables, both >= 1
  *  A_rowmajor       m x n FP64, row-major
- *  b, c             m and n FP64 values; every b_i must be >= 0 (no Phase I)
+ *  b, c             m and n FP64 values.  If some b_i < 0, every lp_solve
+ *                   that starts from the slack basis first solves the Phase I
+ *                   problem  max -x0  s.t.  A x - x0 e <= b,  x, x0 >= 0
+ *                   (e_i = 1 where b_i < 0) on a second, internal handle with
+ *                   the same options, from the slack basis with x0 in the row
+ *                   of the most negative b_i.  An optimum below
+ *                   -1e-9 max(1, max|b_i|) ends the solve with LP_INFEASIBLE;
+ *                   otherwise its final basis (x0 exchanged for the nonbasic
+ *                   slack s with the largest |B^-1[p][s]| if it is still basic
+ *                   at zero in row p) is the Phase II start.
  *  inputs_on_device 0: A, b, c are host pointers; 1: device pointers, which
  *                   must stay valid until lp_create returns
  *  opt              options, or NULL for the defaults
- * Errors: LP_ERR_INVALID_ARG (sizes, NULL, NaN/Inf, b_i < 0), LP_ERR_OOM,
+ * Errors: LP_ERR_INVALID_ARG (sizes, NULL, NaN/Inf), LP_ERR_OOM,
  * LP_ERR_CUDA.  The handle is on the current CUDA device.
  */
 int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A_rowmajor,
@@ -211,7 +225,7 @@ int lp_solve(lp_handle* h, lp_result* out);
 /*
  * lp_get_solution -- x (n values), duals y = c_B^T B^-1 (m values; y_i >= 0 at
  * an optimum), objective.  Any output pointer may be NULL.  LP_ERR_STATE
- * before the first lp_solve.
+ * before the first lp_solve and after a solve that ended LP_INFEASIBLE.
  */
 int lp_get_solution(const lp_handle* h, double* x_n, double* y_m, double* objective);
 

@@ -33,8 +33,10 @@ __global__ void k_validate(const double* A_cm, const double* b, const double* c,
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x)
         if (!isfinite(A_cm[e])) f |= 1;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-        if (!isfinite(b[i]) || b[i] < 0.0) f |= 2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        if (!isfinite(b[i])) f |= 2;
+        if (b[i] < 0.0) f |= 8;  // not an error: the solve starts with Phase I
+    }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
         if (!isfinite(c[j])) f |= 4;
     if (f) atomicOr(flag, f);
@@ -80,6 +82,24 @@ void launch_transpose_pad(const double* A_rm, int m, int n, int ld, double* A_cm
 void launch_validate(const double* A_cm, const double* b, const double* c, int m, int n, int ld,
                      int32_t* flag, cudaStream_t st) {
     k_validate<<<1024, 256, 0, st>>>(A_cm, b, c, m, n, ld, flag);
+}
+
+// Phase I problem (Section 3.4): [A | -e] row-major, e_i = 1 where b_i < 0,
+// and the objective -x0 on the artificial column n.
+__global__ void k_build_aux(const double* __restrict__ A_cm, int ld, int m, int n, const double* __restrict__ b,
+                            double* __restrict__ A_aux, double* __restrict__ c_aux) {
+    const size_t total = (size_t)m * (n + 1);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / (n + 1)), j = (int)(e % (n + 1));
+        A_aux[e] = j < n ? A_cm[(size_t)j * ld + i] : (b[i] < 0.0 ? -1.0 : 0.0);
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += gridDim.x * blockDim.x)
+        c_aux[j] = j < n ? 0.0 : -1.0;
+}
+
+void launch_build_aux(const double* A_cm, int ld, int m, int n, const double* b, double* A_aux, double* c_aux,
+                      cudaStream_t st) {
+    k_build_aux<<<1024, 256, 0, st>>>(A_cm, ld, m, n, b, A_aux, c_aux);
 }
 
 void launch_load_basis(const DevState& s, cudaStream_t st) {

@@ -233,6 +233,8 @@ int occupancy_update(int ld);
 
 // ---- setup (kernels_setup.cu) ---------------------------------------------------
 void launch_transpose_pad(const double* A_rm, int m, int n, int ld, double* A_cm, cudaStream_t st);
+void launch_build_aux(const double* A_cm, int ld, int m, int n, const double* b, double* A_aux, double* c_aux,
+                      cudaStream_t st);
 void launch_validate(const double* A_cm, const double* b, const double* c, int m, int n, int ld,
                      int32_t* flag, cudaStream_t st);
 void launch_load_basis(const DevState& s, cudaStream_t st);

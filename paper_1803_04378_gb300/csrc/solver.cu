@@ -33,6 +33,9 @@ struct lp_handle {
     int32_t* flag = nullptr;         // device validation flag
     bool solved = false;
     bool primed = false;             // q and r of the next pivot are on the device
+    bool neg_b = false;               // some b_i < 0: every solve from the slack basis starts with Phase I
+    bool infeasible = false;          // the last solve found no feasible point (Phase I)
+    std::vector<double> h_b;          // b on the host (Phase I start row)
     bool warm_pending = false;
     int warm_repair_max = -1;         // >= 0: lp_set_basis_repair
     std::vector<int32_t> warm_basis;
@@ -238,6 +241,89 @@ bool finite_all(const double* x, size_t n) {
     return true;
 }
 
+// Phase I (Section 3.4: artificial variables and the two-phase method), with
+// the textbook single artificial x0: maximise -x0 over [A | -e] x' <= b, where
+// e marks the rows with b_i < 0, from the slack basis with x0 in the row of
+// the most negative b_i (feasible: x0 = -min b).  The auxiliary LP runs on a
+// second handle with the same kernels and options.  On an optimum of 0 the
+// final basis becomes the Phase II start of `h` (an artificial left basic at
+// zero is exchanged for the nonbasic slack with the largest |B^-1[p][s]|, the
+// pivot of that exchange); below -1e-9 max(1, max|b|) the LP is infeasible.
+// *status: LP_OPTIMAL (start staged), LP_INFEASIBLE, or the auxiliary solve's
+// own status (iteration limit).
+int run_phase1(lp_handle* h, int* iters, int* status, int* exchanged) {
+    const int m = h->m, n = h->n;
+    *iters = 0;
+    *exchanged = 0;
+    double* A_aux = nullptr;
+    double* c_aux = nullptr;
+    CK(cudaMalloc(&A_aux, sizeof(double) * (size_t)m * (n + 1)));
+    if (cudaMalloc(&c_aux, sizeof(double) * (size_t)(n + 1)) != cudaSuccess) {
+        cudaFree(A_aux);
+        return LP_ERR_OOM;
+    }
+    launch_build_aux(h->ds.A_cm, h->ld, m, n, h->ds.b, A_aux, c_aux, h->stream);
+    lp_options o = h->opt;
+    o.cuda_stream = h->stream;
+    o.trace_cap = 0;
+    o.kernel_timing = 0;
+    lp_handle* aux = nullptr;
+    int rc = lp_create(&aux, m, n + 1, A_aux, h->ds.b, c_aux, 1, &o);  // copies, synchronises
+    cudaFree(A_aux);
+    cudaFree(c_aux);
+    if (rc != LP_OK) return rc;
+    int istar = 0;
+    for (int i = 1; i < m; ++i)
+        if (h->h_b[i] < h->h_b[istar]) istar = i;
+    std::vector<int32_t> basis(m);
+    for (int i = 0; i < m; ++i) basis[i] = n + 1 + i;
+    basis[istar] = n;
+    lp_result r1;
+    rc = lp_set_basis(aux, basis.data());
+    if (rc == LP_OK) rc = lp_solve(aux, &r1);
+    if (rc == LP_OK) {
+        *iters = r1.iterations;
+        if (r1.status != LP_OPTIMAL) {
+            *status = r1.status;
+        } else if (r1.objective < -1e-9 * h->p.b_scale) {
+            *status = LP_INFEASIBLE;
+        } else {
+            rc = lp_get_basis(aux, basis.data());
+            int p = -1;
+            for (int i = 0; i < m && rc == LP_OK; ++i)
+                if (basis[i] == n) p = i;
+            if (rc == LP_OK && p >= 0) {
+                std::vector<double> row(m);
+                std::vector<char> in_basis((size_t)n + 1 + m, 0);
+                for (int i = 0; i < m; ++i) in_basis[basis[i]] = 1;
+                if (cudaMemcpy(row.data(), aux->ds.binv + (size_t)p * aux->ld, sizeof(double) * m,
+                               cudaMemcpyDeviceToHost) != cudaSuccess) {
+                    rc = LP_ERR_CUDA;
+                } else {
+                    double best = -1.0;
+                    int s = -1;
+                    for (int i = 0; i < m; ++i) {
+                        if (in_basis[(size_t)n + 1 + i]) continue;
+                        const double v = std::fabs(row[i]);
+                        if (v > best) { best = v; s = i; }
+                    }
+                    if (s < 0 || !(best > 1e-12)) rc = LP_ERR_SINGULAR;
+                    else { basis[p] = n + 1 + s; *exchanged = 1; }
+                }
+            }
+            if (rc == LP_OK) {
+                h->warm_basis.resize(m);
+                for (int i = 0; i < m; ++i) h->warm_basis[i] = basis[i] < n ? basis[i] : basis[i] - 1;
+                h->warm_pending = true;
+                h->warm_repair_max = -1;
+                *status = LP_OPTIMAL;
+            }
+        }
+    }
+    lp_destroy(aux);
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -309,13 +395,14 @@ static int upload_problem(lp_handle* h, const double* A, const double* b, const 
     CK(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (staging) CK(cudaFree(staging));
-    if (hflag) return LP_ERR_INVALID_ARG;
+    if (hflag & 7) return LP_ERR_INVALID_ARG;
+    h->neg_b = (hflag & 8) != 0;
     // b scale for the feasibility check of warm starts
     {
-        std::vector<double> hb(m);
-        CK(cudaMemcpy(hb.data(), bb, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost));
+        h->h_b.resize(m);
+        CK(cudaMemcpy(h->h_b.data(), bb, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost));
         double sc = 1.0;
-        for (double v : hb) sc = std::max(sc, std::fabs(v));
+        for (double v : h->h_b) sc = std::max(sc, std::fabs(v));
         P.b_scale = sc;
         s.p = P;
     }
@@ -465,8 +552,6 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
         if (!finite_all(A, (size_t)m * n) || !finite_all(c, n) || !finite_all(b, m)) return LP_ERR_INVALID_ARG;
-        for (int i = 0; i < m; ++i)
-            if (b[i] < 0) return LP_ERR_INVALID_ARG;
     }
     lp_handle* h = new (std::nothrow) lp_handle();
     if (!h) return LP_ERR_OOM;
@@ -507,8 +592,6 @@ int lp_update_problem(lp_handle* h, const double* A, const double* b, const doub
     if (!on_device) {
         if (!finite_all(A, (size_t)h->m * h->n) || !finite_all(c, h->n) || !finite_all(b, h->m))
             return LP_ERR_INVALID_ARG;
-        for (int i = 0; i < h->m; ++i)
-            if (b[i] < 0) return LP_ERR_INVALID_ARG;
     }
     h->warm_pending = false;
     TRY(upload_problem(h, A, b, c, on_device));
@@ -551,7 +634,29 @@ int lp_solve(lp_handle* h, lp_result* out) {
     h->chain_s = h->chain_b = 0.0;
     h->chain_n = 0;
     h->launches = 0;
+    h->infeasible = false;
     int warm_repairs = 0, warm_fallback = 0;
+    int phase1_iters = 0, phase1_status = 0, phase1_exch = 0;
+    if (h->neg_b && !h->warm_pending) {
+        TRY(run_phase1(h, &phase1_iters, &phase1_status, &phase1_exch));
+        if (phase1_status != LP_OPTIMAL) {
+            // no feasible start: the LP is infeasible, or Phase I hit its iteration limit
+            CK(cudaEventRecord(h->ev1, h->stream));
+            CK(cudaEventSynchronize(h->ev1));
+            float ms1 = 0.f;
+            CK(cudaEventElapsedTime(&ms1, h->ev0, h->ev1));
+            h->solved = true;
+            h->infeasible = phase1_status == LP_INFEASIBLE;
+            if (out) {
+                memset(out, 0, sizeof(*out));
+                out->status = phase1_status;
+                out->seconds = ms1 * 1e-3;
+                out->phase1_iterations = phase1_iters;
+                out->persistent = h->persist ? 1 : 0;
+            }
+            return LP_OK;
+        }
+    }
     if (h->warm_pending) {
         TRY(reset_state(h));
         CK(cudaMemcpyAsync(h->ds.basis, h->warm_basis.data(), sizeof(int32_t) * h->m,
@@ -690,13 +795,15 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->chain_bytes = h->chain_b;
         out->chain_launches = h->chain_n;
         out->persistent = h->persist ? 1 : 0;
+        out->phase1_iterations = phase1_iters;
+        out->phase1_exchanged = phase1_exch;
     }
     return LP_OK;
 }
 
 int lp_get_solution(const lp_handle* h, double* x, double* y, double* objective) {
     if (!h) return LP_ERR_INVALID_ARG;
-    if (!h->solved) return LP_ERR_STATE;
+    if (!h->solved || h->infeasible) return LP_ERR_STATE;
     const int m = h->m, n = h->n;
     std::vector<int32_t> basis(m);
     std::vector<double> bbar(m);

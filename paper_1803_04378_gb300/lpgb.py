@@ -24,8 +24,8 @@ LP_ERR_TIMEOUT = -5
 LP_ERR_STATE = -6
 LP_ERR_DEVICE = -7
 
-LP_RUNNING, LP_OPTIMAL, LP_UNBOUNDED, LP_ITER_LIMIT = 0, 1, 2, 3
-STATUS_NAMES = {0: "running", 1: "optimal", 2: "unbounded", 3: "iter_limit"}
+LP_RUNNING, LP_OPTIMAL, LP_UNBOUNDED, LP_ITER_LIMIT, LP_INFEASIBLE = 0, 1, 2, 3, 4
+STATUS_NAMES = {0: "running", 1: "optimal", 2: "unbounded", 3: "iter_limit", 4: "infeasible"}
 LP_TF_DEGENERATE, LP_TF_TABU_PUSH, LP_TF_ASPIRATION, LP_TF_BLAND, LP_TF_TIE_SET = 1, 2, 4, 8, 64
 LP_TF_GUIDED = 128
 
@@ -55,7 +55,8 @@ class lp_result(ctypes.Structure):
                 ("full_passes", ctypes.c_int32), ("reinvert_gj_seconds", ctypes.c_double),
                 ("reinvert_assemble_seconds", ctypes.c_double), ("chain_seconds", ctypes.c_double),
                 ("chain_bytes", ctypes.c_double), ("chain_launches", ctypes.c_int32),
-                ("persistent", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("phase1_iterations", ctypes.c_int32),
+                ("phase1_exchanged", ctypes.c_int32)]
 
 
 class lp_batch_result(ctypes.Structure):
@@ -203,6 +204,8 @@ class Result:
     chain_bytes: float = 0.0
     chain_launches: int = 0
     persistent: int = 0
+    phase1_iterations: int = 0
+    phase1_exchanged: int = 0
 
     @property
     def status_name(self) -> str:
@@ -263,7 +266,8 @@ class LP:
                       r.price_bytes, r.update_bytes, r.price_launches, r.update_launches,
                       r.kernel_launches, r.warm_repairs, r.warm_fallback, r.screen_passes,
                       r.full_passes, r.reinvert_gj_seconds, r.reinvert_assemble_seconds,
-                      r.chain_seconds, r.chain_bytes, r.chain_launches, r.persistent)
+                      r.chain_seconds, r.chain_bytes, r.chain_launches, r.persistent,
+                      r.phase1_iterations, r.phase1_exchanged)
 
     def reset(self):
         _check(_lib.lp_reset(self._h), "lp_reset")

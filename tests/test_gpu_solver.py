@@ -241,7 +241,7 @@ def test_invalid_arguments():
     from paper_1803_04378_gb300 import lpgb
     A = np.ones((2, 2))
     with pytest.raises(lpgb.LPError) as e:
-        lpgb.LP(A, np.array([1.0, -1.0]), np.ones(2))
+        lpgb.LP(A, np.array([1.0, np.inf]), np.ones(2))
     assert e.value.code == lpgb.LP_ERR_INVALID_ARG
     with pytest.raises(lpgb.LPError):
         lpgb.LP(np.array([[1.0, np.nan], [1.0, 1.0]]), np.ones(2), np.ones(2))
