@@ -264,6 +264,8 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--price-mode", type=int, default=0, help="PRICE of the timed solves (profiling)")
+    ap.add_argument("--engine", type=int, default=0,
+                    help="LP_ENGINE_* of the timed solves: 0 dense persistent, 1 graphs, 2 slack-structured")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--only-batch", action="store_true", help="run only the batched leg (profiling)")
     ap.add_argument("--reinversion-only", type=int, default=0,
@@ -301,6 +303,7 @@ def main():
     extra = {"max_iters": args.max_iters} if args.max_iters > 0 else {}
     if args.graph_iters > 0:
         extra["graph_iters"] = args.graph_iters
+    extra["engine"] = args.engine
     lp = lpgb.LP(At, bt, ct, kernel_timing=KERNEL_TIMING_STRIDE, cuda_stream=stream.cuda_stream, price_mode=args.price_mode, **extra)
     del At, bt, ct
 
@@ -375,7 +378,8 @@ def main():
     if cn > 0:
         # persistent engine: every launch runs PRICE + UPDATE/FTRAN of up to 64
         # pivots; both do one FP64 FMA per 8 algorithmic bytes
-        kname, kt, kn, kb, kflops = "k_iterate", cs, cn, cb, cb / 4.0
+        kname = "k_iterate_s" if results[0].persistent == 2 else "k_iterate"
+        kt, kn, kb, kflops = cs, cn, cb, cb / 4.0
     elif us >= ps:
         kname, kt, kn, kb, kflops = "k_update", us, un, ub, 4.0 * m * m * un
     else:
@@ -424,6 +428,33 @@ def main():
     # re-priced in FP64 (same FP64 UPDATE/FTRAN/ratio test/reinversion;
     # optimality certified in FP64)
     variants = {}
+    if not args.skip_variants and args.engine != 2:
+        # variant: the slack-structured persistent engine (same pivots; only
+        # the rows whose slack is nonbasic carry PRICE and UPDATE/FTRAN work)
+        At, bt, ct = (torch.from_numpy(v).cuda() for v in (A, b, c))
+        xs = dict(extra, engine=2)
+        with lpgb.LP(At, bt, ct, kernel_timing=KERNEL_TIMING_STRIDE, cuda_stream=stream.cuda_stream, **xs) as lps:
+            del At, bt, ct
+            lps.solve()  # warm-up
+            lps.reset()
+            torch.cuda.synchronize()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            rs_ = lps.solve()
+            v1.record(stream)
+            torch.cuda.synchronize()
+            ts_ = v0.elapsed_time(v1) * 1e-3
+            zs_ = lps.solution()[2]
+        variants["structured_engine"] = {
+            "value": rs_.iterations / ts_, "unit": "iters/s", "time_to_optimum_s": ts_,
+            "pivots_per_solve": rs_.iterations, "reinversions_per_solve": rs_.reinversions,
+            "objective": zs_, "objective_rel_err_vs_dense_engine": abs(zs_ - z) / max(1.0, abs(z)),
+            "reinversion_seconds": rs_.reinvert_seconds,
+            "us_per_pivot_excl_reinversion": 1e6 * (ts_ - rs_.reinvert_seconds) / max(1, rs_.iterations),
+            "chain_seconds": rs_.chain_seconds, "chain_launches": rs_.chain_launches,
+            "chain_gbs": rs_.chain_bytes / rs_.chain_seconds / 1e9 if rs_.chain_seconds else None,
+            "engine": rs_.persistent, "status": rs_.status_name}
     if not args.skip_variants:
         At, bt, ct = (torch.from_numpy(v).cuda() for v in (A, b, c))
         with lpgb.LP(At, bt, ct, kernel_timing=KERNEL_TIMING_STRIDE, cuda_stream=stream.cuda_stream, price_mode=1, topk=2,

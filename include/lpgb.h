@@ -57,6 +57,16 @@ extern "C" {
 #define LP_TF_TIE_SET 64        /* the ratio test had more than one tied row */
 #define LP_TF_GUIDED 128        /* the entering variable came from lp_set_priority */
 
+/* lp_options.engine: how the pivots of price_mode 0 run. */
+#define LP_ENGINE_DENSE 0       /* persistent cooperative kernel on the m x m B^-1, graph_iters
+                                   pivots per launch: PRICE reads all of A, UPDATE all of B^-1 */
+#define LP_ENGINE_GRAPH 1       /* captured CUDA graphs of three kernels per pivot */
+#define LP_ENGINE_STRUCTURED 2  /* persistent kernel on the slack-structured B^-1: only the k
+                                   rows whose slack is nonbasic carry nonzero y and non-unit
+                                   B^-1 columns, so PRICE reads k rows of A and UPDATE/FTRAN
+                                   k columns of B^-1 (exactly the same pivots up to the
+                                   order of summation; extra device memory: 8 ld (n + m) bytes) */
+
 typedef struct lp_handle lp_handle;
 
 /*
@@ -79,9 +89,8 @@ typedef struct lp_options {
     int32_t kernel_timing;  /* s >= 1: time the PRICE and UPDATE launches of every s-th
                                pivot of each captured graph with CUDA events (1 = all);
                                timed pivots run without launch overlap */
-    int32_t engine;         /* 0: pivots of price_mode 0 run in one persistent cooperative
-                               kernel per graph_iters pivots (captured CUDA graphs where the
-                               device cannot); 1: always captured graphs of three kernels */
+    int32_t engine;         /* LP_ENGINE_*: how the pivots of price_mode 0 run (captured
+                               CUDA graphs wherever the device refuses a cooperative launch) */
     double tol_d;           /* optimality tolerance on the reduced costs */
     double tol_piv;         /* smallest admissible pivot alpha_r */
     double tol_tie;         /* relative width of the ratio-test tie set */
@@ -118,7 +127,8 @@ typedef struct lp_result {
     double chain_seconds;    /* kernel_timing, persistent engine: device time of its launches */
     double chain_bytes;      /* algorithmic PRICE + UPDATE bytes of those launches */
     int32_t chain_launches;  /* persistent launches timed */
-    int32_t persistent;      /* 1: the pivots ran in the persistent kernel */
+    int32_t persistent;      /* 1: the pivots ran in the dense persistent kernel, 2: in the
+                                slack-structured one, 0: in captured graphs */
     int32_t phase1_iterations; /* b with negative entries: pivots of the Phase I problem */
     int32_t phase1_exchanged;  /* 1: the artificial ended basic at zero and was exchanged */
 } lp_result;

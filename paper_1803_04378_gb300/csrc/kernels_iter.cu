@@ -18,6 +18,7 @@
 // whole warp owns one row, so the row-r case is a warp-uniform branch and costs
 // nothing.
 #include "lpgb_internal.cuh"
+#include "iter_common.cuh"
 #include "../../include/lpgb.h"
 
 #include <cfloat>
@@ -26,156 +27,6 @@ namespace lpgb {
 
 namespace {
 
-constexpr int kPriceThreads = 1024;
-constexpr int kOct = 4;   // columns per warp in k_price
-constexpr int kSeg = 2;   // row segments per column in k_price
-constexpr int kPriceCols = kPriceThreads / 32 / kSeg * kOct;  // columns per block per round
-constexpr int kUpdateThreads = 1024;
-constexpr int kPivotThreads = 64;
-constexpr int kMaxFlagged = 64;  // k_iterate: CTAs scanned for the ratio-test tie set
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Warp sum in the pairing order of k_price's transposed reduction (lanes
-// 16 apart, then 8, 1, 2, 4), so that a column's d_j does not depend on the
-// width of the group it was priced in.
-__device__ __forceinline__ double pair_sum(double t) {
-    t += __shfl_xor_sync(0xffffffffu, t, 16);
-    t += __shfl_xor_sync(0xffffffffu, t, 8);
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
-    t += __shfl_xor_sync(0xffffffffu, t, 2);
-    t += __shfl_xor_sync(0xffffffffu, t, 4);
-    return t;
-}
-
-// acc[c] = sum over this lane's elements k0+lane, k0+lane+32, ... < k1 of
-// column cols[c] (double2 units) times y.  Register double buffering: the W
-// loads of the next step are issued before the FMAs of the current one, so a
-// warp always has a step's worth of reads in flight while it computes.
-template <int W>
-__device__ __forceinline__ void dot_cols(const double2* __restrict__ A2, const int* cols, int half,
-                                         const double2* y2, int k0, int k1, int lane, double (&acc)[W]) {
-    const double2* p[W];
-#pragma unroll
-    for (int c = 0; c < W; ++c) {
-        p[c] = A2 + (size_t)cols[c] * half;
-        acc[c] = 0.0;
-    }
-    int k = k0 + lane;
-    if (k >= k1) return;
-    double2 nx[W];
-#pragma unroll
-    for (int c = 0; c < W; ++c) nx[c] = __ldcs(p[c] + k);
-#pragma unroll 1
-    for (; k < k1; k += 32) {
-        double2 cur[W];
-#pragma unroll
-        for (int c = 0; c < W; ++c) cur[c] = nx[c];
-        if (k + 32 < k1) {
-#pragma unroll
-            for (int c = 0; c < W; ++c) nx[c] = __ldcs(p[c] + k + 32);
-        }
-        const double2 yv = y2[k];
-#pragma unroll
-        for (int c = 0; c < W; ++c) acc[c] = fma(cur[c].y, yv.y, fma(cur[c].x, yv.x, acc[c]));
-    }
-}
-
-// ---- CHUZC candidate ---------------------------------------------------------
-struct Cand {
-    double d_all; int j_all;
-    double d_nt;  int j_nt;
-    double d_min; int j_min;
-    double d_pr;  int j_pr; int k_pr;
-};
-
-__device__ __forceinline__ void cand_init(Cand& c) {
-    c.d_all = -DBL_MAX; c.j_all = -1;
-    c.d_nt = -DBL_MAX; c.j_nt = -1;
-    c.d_min = 0.0; c.j_min = -1;
-    c.d_pr = 0.0; c.j_pr = -1; c.k_pr = kNoRank;
-}
-
-// a beats b: larger d, exact ties to the smaller index.
-__device__ __forceinline__ bool beats(double da, int ja, double db, int jb) {
-    if (ja < 0) return false;
-    if (jb < 0) return true;
-    return da > db || (da == db && ja < jb);
-}
-
-__device__ __forceinline__ void cand_offer(Cand& c, double d, int j, bool nontabu, double tol_d, int rank) {
-    if (beats(d, j, c.d_all, c.j_all)) { c.d_all = d; c.j_all = j; }
-    if (nontabu && beats(d, j, c.d_nt, c.j_nt)) { c.d_nt = d; c.j_nt = j; }
-    if (d > tol_d && (c.j_min < 0 || j < c.j_min)) { c.d_min = d; c.j_min = j; }
-    // guided rule: Dantzig restricted to the listed (priority) columns
-    if (nontabu && d > tol_d && rank != kNoRank && beats(d, j, c.d_pr, c.j_pr)) { c.d_pr = d; c.j_pr = j; c.k_pr = rank; }
-}
-
-__device__ __forceinline__ void cand_merge(Cand& c, const Cand& o) {
-    if (beats(o.d_all, o.j_all, c.d_all, c.j_all)) { c.d_all = o.d_all; c.j_all = o.j_all; }
-    if (beats(o.d_nt, o.j_nt, c.d_nt, c.j_nt)) { c.d_nt = o.d_nt; c.j_nt = o.j_nt; }
-    if (o.j_min >= 0 && (c.j_min < 0 || o.j_min < c.j_min)) { c.d_min = o.d_min; c.j_min = o.j_min; }
-    if (beats(o.d_pr, o.j_pr, c.d_pr, c.j_pr)) { c.d_pr = o.d_pr; c.j_pr = o.j_pr; c.k_pr = o.k_pr; }
-}
-
-__device__ __forceinline__ Cand cand_shfl(const Cand& c, int off) {
-    Cand o;
-    o.d_all = __shfl_xor_sync(0xffffffffu, c.d_all, off);
-    o.j_all = __shfl_xor_sync(0xffffffffu, c.j_all, off);
-    o.d_nt = __shfl_xor_sync(0xffffffffu, c.d_nt, off);
-    o.j_nt = __shfl_xor_sync(0xffffffffu, c.j_nt, off);
-    o.d_min = __shfl_xor_sync(0xffffffffu, c.d_min, off);
-    o.j_min = __shfl_xor_sync(0xffffffffu, c.j_min, off);
-    o.d_pr = __shfl_xor_sync(0xffffffffu, c.d_pr, off);
-    o.j_pr = __shfl_xor_sync(0xffffffffu, c.j_pr, off);
-    o.k_pr = __shfl_xor_sync(0xffffffffu, c.k_pr, off);
-    return o;
-}
-
-// Block-wide reduction; the result is valid in thread 0.
-__device__ Cand cand_block_reduce(Cand c) {
-    __shared__ Cand sh[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cand_merge(c, cand_shfl(c, o));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = c;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-        if (lane < nw) c = sh[lane]; else cand_init(c);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cand_merge(c, cand_shfl(c, o));
-    }
-    return c;
-}
-
-// Leaving-row candidate of the ratio test: largest alpha, exact ties to the
-// smallest basic variable index (Bland mode: smallest basic variable index).
-struct RowCand { double a; int var; int row; double th; };  // th: the row's ratio
-
-__device__ __forceinline__ bool row_beats(const RowCand& x, const RowCand& y, bool bland) {
-    if (x.row < 0) return false;
-    if (y.row < 0) return true;
-    if (bland) return x.var < y.var;
-    return x.a > y.a || (x.a == y.a && x.var < y.var);
-}
-
-__device__ __forceinline__ bool is_last_block(int32_t* ticket) {
-    __shared__ int last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        int t = atomicAdd(ticket, 1);
-        last = (t == (int)gridDim.x - 1);
-    }
-    __syncthreads();
-    return last != 0;
-}
 
 // ---- initial slack basis (Step 1 with B = I) -------------------------------------
 __global__ void k_init_slack(DevState s) {
@@ -204,6 +55,7 @@ __global__ void k_init_slack(DevState s) {
     }
     if (tid == 0) {
         Ctrl c = {};
+        c.map_par = s.ctrl->map_par;  // the slot map copy that matches A_p survives a reset
         c.status = P.max_iters > 0 ? kRunning : kIterLimit;
         c.q = -1;
         c.r = -1;
@@ -283,196 +135,6 @@ __global__ void __launch_bounds__(kPivotThreads) k_pivot(DevState s) {
     __threadfence();
 }
 
-// ---- PRICE of one block's columns (k_price and k_iterate) ---------------------------
-// ysh holds y.  pos and tabu_until, which the bookkeeping of a persistent
-// launch writes from another block, are read through L2.  Returns the block's
-// candidate in thread 0.
-__device__ Cand price_block(const DevState& s, int it, const double* ysh) {
-    const Params& P = s.p;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int half = P.ld >> 1;
-    const double2* y2 = reinterpret_cast<const double2*>(ysh);
-    // Columns are dealt to blocks round-robin (block b owns j = b, b+G, ...)
-    // so every SM gets the same share.  The block first lists its nonbasic
-    // columns; then each warp takes kOct listed columns over one of kSeg row
-    // segments, so one shared-memory load of y feeds 2*kOct FMAs, 2*kOct
-    // independent 512-byte loads are in flight per step, and the kOct partial
-    // sums leave the warp through one transposed reduction (6 adds for 4
-    // columns instead of 5 per column).  The segment sums of a column are
-    // added in a fixed order, so d_j does not depend on where j was listed.
-    // Candidates live in shared memory (one per offering thread) so that no
-    // registers are held across the streaming loops.
-    __shared__ Cand csh[kPriceCols];
-    __shared__ int jl[kPriceThreads];
-    __shared__ double part[kSeg][kPriceCols];
-    __shared__ int wcnt[kPriceThreads / 32];
-    if (threadIdx.x < kPriceCols) cand_init(csh[threadIdx.x]);
-    const int G = gridDim.x;
-    const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
-    const int nch = half >> 5;  // 32-double2 chunks per column
-    const int seg = warp % kSeg, gi = warp / kSeg;
-    const int k0 = 32 * (seg * nch / kSeg), k1 = 32 * ((seg + 1) * nch / kSeg);
-    const double2* A2 = reinterpret_cast<const double2*>(s.A_cm);
-    for (int lb = 0; lb < owned; lb += kPriceThreads) {
-        // list the nonbasic owned columns lb .. lb+kPriceThreads-1, in order
-        const int l = lb + (int)threadIdx.x;
-        const int jj = (int)blockIdx.x + G * l;
-        const bool nb = l < owned && __ldcg(s.pos + jj) < 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, nb);
-        if (lane == 0) wcnt[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, cnt = 0;
-        for (int w = 0; w < kPriceThreads / 32; ++w) {
-            const int cw = wcnt[w];
-            if (w < warp) before += cw;
-            cnt += cw;
-        }
-        if (nb) jl[before + __popc(bal & ((1u << lane) - 1u))] = jj;
-        __syncthreads();
-        // Groups of 4 listed columns, and of 3 where cnt is not a multiple of 4,
-        // so that every warp streams 3 or 4 columns at a time (a lone column
-        // would run latency-bound long after the others); only lists shorter
-        // than the 3-groups they would need fall back to groups of 1 or 2.
-        const int n3 = (4 - (cnt & 3)) & 3;
-        const bool mixed = cnt >= 3 * n3;
-        const int n4 = mixed ? (cnt - 3 * n3) / 4 : cnt / 4;
-        const int ngrp = mixed ? n4 + n3 : (cnt + 3) / 4;
-        for (int gb = 0; gb < ngrp; gb += kPriceThreads / 32 / kSeg) {
-            const int g = gb + gi;
-            int e0 = 0, width = 0;
-            if (g < ngrp) {
-                if (!mixed) { e0 = 4 * g; width = min(4, cnt - e0); }
-                else if (g < n4) { e0 = 4 * g; width = 4; }
-                else { e0 = 4 * n4 + 3 * (g - n4); width = 3; }
-            }
-            const int slot = gi * kOct;  // part[] slots of this warp's group
-            if (width == 4) {
-                double acc[4];
-                dot_cols<4>(A2, jl + e0, half, y2, k0, k1, lane, acc);
-                // transposed reduction: lane L ends with column ((L>>4)&1)*2 + ((L>>3)&1)
-                const bool h16 = lane & 16, h8 = lane & 8;
-                double r2[2];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const double send = h16 ? acc[i] : acc[2 + i];
-                    const double keep = h16 ? acc[2 + i] : acc[i];
-                    r2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                }
-                const double send = h8 ? r2[0] : r2[1];
-                double r1 = (h8 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, send, 8);
-                r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
-                r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
-                r1 += __shfl_xor_sync(0xffffffffu, r1, 4);
-                const int c = (h16 ? 2 : 0) + (h8 ? 1 : 0);
-                if ((lane & 7) == 0) part[seg][slot + c] = r1;
-            } else if (width == 3) {
-                double acc[3];
-                dot_cols<3>(A2, jl + e0, half, y2, k0, k1, lane, acc);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double t = pair_sum(acc[c]);
-                    if (lane == 0) part[seg][slot + c] = t;
-                }
-            } else if (width == 2) {
-                double acc[2];
-                dot_cols<2>(A2, jl + e0, half, y2, k0, k1, lane, acc);
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const double t = pair_sum(acc[c]);
-                    if (lane == 0) part[seg][slot + c] = t;
-                }
-            } else if (width == 1) {
-                double acc[1];
-                dot_cols<1>(A2, jl + e0, half, y2, k0, k1, lane, acc);
-                const double t = pair_sum(acc[0]);
-                if (lane == 0) part[seg][slot] = t;
-            }
-            __syncthreads();
-            // thread t < kPriceCols: column t of this round = group t/4, member t%4
-            if (threadIdx.x < kPriceCols) {
-                const int gg = gb + (int)threadIdx.x / kOct, c = (int)threadIdx.x % kOct;
-                int ee = -1;
-                if (gg < ngrp) {
-                    if (!mixed) ee = (4 * gg + c < cnt) ? 4 * gg + c : -1;
-                    else if (gg < n4) ee = 4 * gg + c;
-                    else ee = c < 3 ? 4 * n4 + 3 * (gg - n4) + c : -1;
-                }
-                if (ee >= 0) {
-                    const int j = jl[ee];
-                    double sum = part[0][threadIdx.x];
-#pragma unroll
-                    for (int t = 1; t < kSeg; ++t) sum += part[t][threadIdx.x];
-                    Cand cc = csh[threadIdx.x];
-                    cand_offer(cc, s.c[j] - sum, j, __ldcg(s.tabu_until + j) <= it, P.tol_d, s.rank[j]);
-                    csh[threadIdx.x] = cc;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    Cand cand;
-    cand_init(cand);
-    if (threadIdx.x < kPriceCols) cand = csh[threadIdx.x];
-    // slack columns: d_{n+i} = -y_i
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.m; i += gridDim.x * blockDim.x) {
-        const int j = P.n + i;
-        if (__ldcg(s.pos + j) >= 0) continue;
-        cand_offer(cand, -ysh[i], j, __ldcg(s.tabu_until + j) <= it, P.tol_d, s.rank[j]);
-    }
-    return cand_block_reduce(cand);
-}
-
-__device__ __forceinline__ PriceCand to_price_cand(const Cand& bc) {
-    PriceCand pc;
-    pc.d_all = bc.d_all; pc.j_all = bc.j_all;
-    pc.d_nt = bc.d_nt; pc.j_nt = bc.j_nt;
-    pc.d_min = bc.d_min; pc.j_min = bc.j_min;
-    pc.d_pr = bc.d_pr; pc.j_pr = bc.j_pr; pc.k_pr = bc.k_pr;
-    pc.pad_ = 0;
-    return pc;
-}
-
-// the global candidate from the per-block partials (all threads; result in thread 0)
-__device__ Cand reduce_price_parts(const PriceCand* part, int nparts) {
-    Cand g;
-    cand_init(g);
-    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
-        const PriceCand* pp = part + b;
-        Cand o;
-        o.d_all = __ldcg(&pp->d_all); o.j_all = __ldcg(&pp->j_all);
-        o.d_nt = __ldcg(&pp->d_nt); o.j_nt = __ldcg(&pp->j_nt);
-        o.d_min = __ldcg(&pp->d_min); o.j_min = __ldcg(&pp->j_min);
-        o.d_pr = __ldcg(&pp->d_pr); o.j_pr = __ldcg(&pp->j_pr); o.k_pr = __ldcg(&pp->k_pr);
-        cand_merge(g, o);
-    }
-    return cand_block_reduce(g);
-}
-
-// Step 4 CHUZC on the global candidate: optimality over all nonbasic columns,
-// then Bland (safety net), the guided rule, Dantzig among non-tabu columns,
-// or aspiration (every improving column tabu).
-struct Chuzc {
-    int optimal, q, flags, asp;
-    double dq;
-};
-
-__device__ Chuzc chuzc_decide(const Cand& g, bool bland, double tol_d) {
-    Chuzc o = {0, -1, 0, 0, 0.0};
-    if (g.j_all < 0 || !(g.d_all > tol_d)) {
-        o.optimal = 1;
-    } else if (bland) {
-        o.q = g.j_min; o.dq = g.d_min; o.flags = kTfBland;
-    } else if (g.j_pr >= 0) {
-        o.q = g.j_pr; o.dq = g.d_pr; o.flags = kTfGuided;
-    } else if (g.j_nt >= 0 && g.d_nt > tol_d) {
-        o.q = g.j_nt; o.dq = g.d_nt;
-    } else {
-        o.q = g.j_all; o.dq = g.d_all; o.flags = kTfAspiration; o.asp = 1;
-    }
-    return o;
-}
-
 // ---- k_price: PRICE + CHUZC -----------------------------------------------------
 __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
     pdl_enter();
@@ -485,7 +147,7 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
     extern __shared__ double ysh[];
     for (int k = threadIdx.x; k < P.ld; k += blockDim.x) ysh[k] = s.y[k];
     __syncthreads();
-    const Cand bc = price_block(s, C->it, ysh);
+    const Cand bc = price_block(s, C->it, ysh, s.A_cm, P.ld >> 1, nullptr, P.m);
     if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
     if (!is_last_block(&C->ticket_price)) return;
     // last block: reduce all partials and decide
@@ -519,7 +181,6 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
 // variable of each row for a ratio test that runs while the basis changes.
 // aq_unit >= 0: the entering column is the slack unit vector e_{aq_unit}
 // (generated, aq unused).
-constexpr int kS = 4;  // 512-byte reads in flight per warp
 
 __device__ double update_block(const DevState& s, int r, bool do_upd, bool do_ftran, const double* acur,
                                double* anxt, const double* aq, const double* rh, bool snapshot, int aq_unit = -1) {
@@ -596,45 +257,6 @@ __device__ double update_block(const DevState& s, int r, bool do_upd, bool do_ft
 }
 
 // block minimum (result in thread 0)
-__device__ double block_min(double v) {
-    __shared__ double shm[32];
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = DBL_MAX;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmin(t, shm[w]);
-    return t;
-}
-
-// block reduce of the ratio-test candidate and the tie-set count (result in thread 0)
-__device__ RowCand block_row_best(RowCand best, int& cnt, bool bland) {
-    __shared__ RowCand shr[32];
-    __shared__ int shc[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        RowCand oc;
-        oc.a = __shfl_xor_sync(0xffffffffu, best.a, o);
-        oc.var = __shfl_xor_sync(0xffffffffu, best.var, o);
-        oc.row = __shfl_xor_sync(0xffffffffu, best.row, o);
-        oc.th = __shfl_xor_sync(0xffffffffu, best.th, o);
-        if (row_beats(oc, best, bland)) best = oc;
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    }
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) { shr[threadIdx.x >> 5] = best; shc[threadIdx.x >> 5] = cnt; }
-    __syncthreads();
-    RowCand b = shr[0];
-    int total = shc[0];
-    if (threadIdx.x == 0)
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-            if (row_beats(shr[w], b, bland)) b = shr[w];
-            total += shc[w];
-        }
-    cnt = total;
-    return b;
-}
-
 // ---- k_update: B^-1 update + FTRAN + ratio test -------------------------------------
 __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
     pdl_enter();
@@ -757,111 +379,6 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
 // variable of each row from the snapshot taken by the FTRAN (row_var), since
 // block 0 may already be exchanging the basis.
 
-struct IterState {
-    int status, it, q, r, leave, tcount, abuf, pending, flags, degen_run, bland;
-    double dq, theta, alpha_r;
-    // kept by block 0 during the launch, written back to the control block at its end
-    int nsb, n_degenerate, n_tabu, n_bland, n_asp, n_price, n_update;
-    double z, bytes_price, bytes_update;
-};
-
-constexpr unsigned kBarrierSpins = 1u << 21;  // about a second of polling, then the launch gives up
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Grid barrier of a cooperative launch: one cumulative arrival counter.  Each
-// CTA adds its arrival with a release reduction (no round trip) and polls the
-// counter with acquire loads until every CTA of this barrier has arrived
-// (epoch * CTAs).  Waits are bounded; a CTA that gives up reports it, and the
-// launch ends with kErrTimeout.
-__device__ __forceinline__ void red_release_add(uint32_t* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ bool grid_barrier(uint32_t* bar, unsigned& epoch, volatile int* fail, unsigned parties = 0) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ++epoch;
-        const unsigned target = epoch * (parties ? parties : gridDim.x);
-        red_release_add(bar, 1u);
-        unsigned spins = 0;
-        while (ld_acquire_u32(bar) < target) {
-            if (++spins > kBarrierSpins) {
-                *fail = 1;
-                break;
-            }
-        }
-    }
-    __syncthreads();
-    return *fail == 0;
-}
-
-// Step 7/8 bookkeeping of the pivot (q, r): identical scalar updates in every
-// CTA; the lead CTA also writes the basis exchange, tabu list, trace and
-// counters (the same rules as k_pivot).
-__device__ void pivot_bookkeeping(const DevState& s, IterState& S, bool lead) {
-    const Params& P = s.p;
-    const int it = S.it, q = S.q, r = S.r, leave = S.leave;
-    const double th = S.theta, dq = S.dq;
-    int flags = S.flags;
-    const bool degenerate = th <= P.tol_tie;
-    if (degenerate) flags |= kTfDegenerate;
-    const bool push = P.tabu_tenure > 0 && (S.tcount > 1 || degenerate);
-    if (push) flags |= kTfTabuPush;
-    if (lead) {
-        // stores only: the leaving variable comes from the ratio test, the
-        // counters and the objective stay in S until the launch ends
-        if (degenerate) S.n_degenerate++;
-        if (push) {
-            s.tabu_until[leave] = it + 1 + P.tabu_tenure;
-            S.n_tabu++;
-        }
-        if (it < P.trace_cap) {
-            s.trace.q[it] = q;
-            s.trace.r[it] = r;
-            s.trace.theta[it] = th;
-            s.trace.dq[it] = dq;
-            s.trace.flags[it] = flags;
-        }
-        S.z = __dadd_rn(S.z, __dmul_rn(dq, th));
-        s.pos[leave] = -1;
-        s.basis[r] = q;
-        s.pos[q] = r;
-        S.nsb += (q < P.n ? 1 : 0) - (leave < P.n ? 1 : 0);
-    }
-    const int it1 = it + 1;
-    S.it = it1;
-    S.degen_run = degenerate ? S.degen_run + 1 : 0;
-    if (S.bland && !degenerate) S.bland = 0;
-    if (!S.bland && P.bland_after > 0 && S.degen_run >= P.bland_after) {
-        S.bland = 1;
-        if (lead) S.n_bland++;
-    }
-    S.flags = 0;
-    if (P.reinvert_every > 0 && it1 % P.reinvert_every == 0) {
-        S.status = kReinvert;
-        S.pending = 0;
-    } else {
-        S.pending = 1;
-        if (it1 >= P.max_iters) S.status = kIterLimit;
-    }
-}
-
-// The state block 0 kept during the launch, into the control block.
-__device__ void iterate_flush(const DevState& s, const IterState& S) {
-    Ctrl* C = s.ctrl;
-    C->status = S.status; C->it = S.it; C->q = S.q; C->r = S.r; C->tcount = S.tcount; C->abuf = S.abuf;
-    C->pending = S.pending; C->flags = S.flags; C->degen_run = S.degen_run; C->bland = S.bland;
-    C->dq = S.dq; C->theta = S.theta; C->alpha_r = S.alpha_r;
-    C->nsb = S.nsb; C->n_degenerate = S.n_degenerate; C->n_tabu = S.n_tabu; C->n_bland = S.n_bland;
-    C->n_asp = S.n_asp; C->n_price = S.n_price; C->n_update = S.n_update;
-    C->z = S.z; C->bytes_price = S.bytes_price; C->bytes_update = S.bytes_update;
-}
-
 __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int iters) {
     Ctrl* C = s.ctrl;
     const Params& P = s.p;
@@ -885,6 +402,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
         S.nsb = C->nsb; S.n_degenerate = C->n_degenerate; S.n_tabu = C->n_tabu; S.n_bland = C->n_bland;
         S.n_asp = C->n_asp; S.n_price = C->n_price; S.n_update = C->n_update;
         S.z = C->z; S.bytes_price = C->bytes_price; S.bytes_update = C->bytes_update;
+        S.k = C->k_live; S.par = C->map_par;
     }
     // every CTA has its copy of the control block before block 0 changes it
     if (!grid_barrier(s.gbar, epoch, &fail)) {
@@ -928,7 +446,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
             }
             rh_staged = stage_rh;
             __syncthreads();
-            const Cand bc = price_block(s, S.it, sh);
+            const Cand bc = price_block(s, S.it, sh, s.A_cm, P.ld >> 1, nullptr, P.m);
             if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             const Cand g = reduce_price_parts(s.price_part, G);

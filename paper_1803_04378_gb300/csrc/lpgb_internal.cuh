@@ -75,7 +75,7 @@ struct Ctrl {
     int32_t k_struct;      // reinversion: number of structural basic columns
     int32_t ticket_pivot;
     int32_t nsb;           // structural variables in the basis
-    int32_t pad_;
+    int32_t k_live;        // slack-structured engine: rows whose slack is nonbasic (live slots)
     int32_t repair;        // warm-start repair: 1 pivot staged, 2 feasible, 3 cannot repair
     int32_t need_full;     // price_mode 1: the screen found no improving candidate
     int32_t n_full;        // price_mode 1: full FP64 PRICE passes
@@ -84,6 +84,8 @@ struct Ctrl {
     int32_t ticket_rp;
     int32_t n_price;       // PRICE launches that did work
     int32_t n_update;      // UPDATE launches that did work
+    int32_t map_par;       // slack-structured engine: which slot map is current
+    int32_t pad2_;
     double bytes_price;    // algorithmic HBM bytes moved by PRICE
     double bytes_update;   // algorithmic HBM bytes moved by UPDATE/FTRAN
     double dq;             // d_q of the pending pivot
@@ -151,6 +153,14 @@ struct DevState {
     RowPart* row_part;  // k_iterate: per-CTA ratio-test record
     int32_t* row_var;   // m: basic variable of each row as seen by the last FTRAN (k_iterate)
     uint32_t* gbar;     // k_iterate grid barrier: arrivals, released epoch
+    // slack-structured engine (k_iterate_s): the constraint rows in slot order,
+    // the rows whose slack is nonbasic in slots [0, k_live)
+    double* A_p;        // n columns of ld doubles: A with its rows in slot order
+    double* bp;         // m rows of ld doubles: B^-1 columns of the live slots
+    double* yp;         // ld: y in slot order (zero outside the live slots)
+    int32_t* slot_row;  // 2*m: slot -> row, two copies (current, next) by map_par
+    int32_t* row_slot;  // 2*m: row -> slot, same two copies
+    int32_t* uslot;     // m: basis position -> slot of its basic slack, or -1
     TraceBuf trace;
     // reinversion scratch
     int32_t* rv_struct_pos;  // k structural basis positions (increasing)
@@ -215,6 +225,14 @@ void launch_update(const DevState& s, const Geometry& g, cudaStream_t st, bool p
 // Up to `iters` pivots in one cooperative launch of `blocks` CTAs (price_mode 0).
 cudaError_t launch_iterate(const DevState& s, int blocks, int iters, cudaStream_t st);
 int occupancy_iterate(int ld);
+// The same on the slack-structured form of B^-1 (kernels_struct.cu).
+cudaError_t launch_iterate_s(const DevState& s, int blocks, int iters, cudaStream_t st);
+int occupancy_iterate_s(int ld);
+// Dense state -> structured state: slot map check (rebuilt when force or
+// inconsistent, then A_p regathered), live B^-1 columns and y, start at PRICE.
+void launch_struct_enter(const DevState& s, int force, int32_t* relayout, cudaStream_t st);
+void launch_struct_scatter_y(const DevState& s, cudaStream_t st);  // yp -> y (row order)
+void launch_struct_init_maps(const DevState& s, cudaStream_t st);
 // Bounded-wait self-test: a grid barrier that cannot complete (lp_selftest_barrier_timeout).
 int barrier_selftest(int blocks, cudaStream_t st);
 size_t price_smem_bytes(int ld);

@@ -45,6 +45,11 @@ struct lp_handle {
     bool persist = false;            // pivots run in k_iterate (cooperative, one CTA per SM)
     int persist_blocks = 0;
     cudaEvent_t evc0 = nullptr, evc1 = nullptr;  // kernel_timing around k_iterate launches
+    bool structured = false;         // pivots run in k_iterate_s (LP_ENGINE_STRUCTURED)
+    bool s_ready = false;            // the structured state (bp, yp, slot maps) is current; the dense
+                                     // B^-1 and y are stale while it is
+    bool s_force = true;             // rebuild the slot map and A_p on the next entry
+    int32_t* s_relayout = nullptr;   // device flag: the entry rebuilt the slot map
     double chain_s = 0.0, chain_b = 0.0;
     int chain_n = 0;
     double reinvert_seconds = 0.0;
@@ -222,6 +227,7 @@ int reinvert(lp_handle* h, int check_feasible) {
     h->reinv_gj_s += mg * 1e-3;
     h->reinv_asm_s += ma * 1e-3;
     h->primed = false;
+    h->s_ready = false;
     if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
     return LP_OK;
 }
@@ -230,6 +236,8 @@ int reset_state(lp_handle* h) {
     launch_init_slack(h->ds, h->stream);
     CK(cudaGetLastError());
     h->primed = false;
+    h->s_ready = false;
+    h->s_force = true;  // canonical slot order: a solve from the slack basis repeats bit for bit
     h->solved = false;
     h->reinvert_seconds = 0.0;
     return LP_OK;
@@ -239,6 +247,32 @@ bool finite_all(const double* x, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(x[i])) return false;
     return true;
+}
+
+// Rows p0 .. p0+np-1 of B^-1 (indexed by constraint row) into out[np][m],
+// from the dense inverse or, while the structured engine's state is current,
+// from its live columns and the unit columns of the basic slacks.
+int binv_rows(const lp_handle* h, int p0, int np, double* out) {
+    const int m = h->m;
+    if (!(h->structured && h->s_ready)) {
+        CK(cudaMemcpy2D(out, sizeof(double) * m, h->ds.binv + (size_t)p0 * h->ld, sizeof(double) * h->ld,
+                        sizeof(double) * m, np, cudaMemcpyDeviceToHost));
+        return LP_OK;
+    }
+    Ctrl c;
+    CK(cudaMemcpy(&c, h->ds.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    const int k = c.k_live, par = c.map_par;
+    std::vector<double> live((size_t)np * std::max(k, 1));
+    std::vector<int32_t> rs((size_t)m), bv((size_t)np);
+    if (k > 0)
+        CK(cudaMemcpy2D(live.data(), sizeof(double) * k, h->ds.bp + (size_t)p0 * h->ld, sizeof(double) * h->ld,
+                        sizeof(double) * k, np, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rs.data(), h->ds.row_slot + (size_t)par * m, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(bv.data(), h->ds.basis + p0, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+    for (int p = 0; p < np; ++p)
+        for (int i = 0; i < m; ++i)
+            out[(size_t)p * m + i] = rs[i] < k ? live[(size_t)p * k + rs[i]] : (bv[p] == h->n + i ? 1.0 : 0.0);
+    return LP_OK;
 }
 
 // Phase I (Section 3.4: artificial variables and the two-phase method), with
@@ -296,8 +330,7 @@ int run_phase1(lp_handle* h, int* iters, int* status, int* exchanged) {
                 std::vector<double> row(m);
                 std::vector<char> in_basis((size_t)n + 1 + m, 0);
                 for (int i = 0; i < m; ++i) in_basis[basis[i]] = 1;
-                if (cudaMemcpy(row.data(), aux->ds.binv + (size_t)p * aux->ld, sizeof(double) * m,
-                               cudaMemcpyDeviceToHost) != cudaSuccess) {
+                if (binv_rows(aux, p, 1, row.data()) != LP_OK) {
                     rc = LP_ERR_CUDA;
                 } else {
                     double best = -1.0;
@@ -464,6 +497,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &pos, (size_t)(n + m)));
     TRY(dalloc(h, &tabu, (size_t)(n + m)));
     TRY(dalloc(h, &ctrl, 1));
+    CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), h->stream));
     TRY(dalloc(h, &flag, 1));
     h->flag = flag;
     TRY(dalloc(h, &s.rank, (size_t)(n + m)));
@@ -533,6 +567,28 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
                 CK(cudaEventCreate(&h->evc1));
             }
         }
+        if (h->opt.engine == LP_ENGINE_STRUCTURED && h->opt.price_mode == 0 && coop && h->geo.sms <= 1024 &&
+            occupancy_iterate_s(h->ld) >= 1) {
+            const int m = h->m, n = h->n, ld = h->ld;
+            TRY(dalloc(h, &s.A_p, (size_t)n * ld));
+            TRY(dalloc(h, &s.bp, (size_t)m * ld));
+            TRY(dalloc(h, &s.yp, (size_t)ld));
+            TRY(dalloc(h, &s.slot_row, 2 * (size_t)m));
+            TRY(dalloc(h, &s.row_slot, 2 * (size_t)m));
+            TRY(dalloc(h, &s.uslot, (size_t)m));
+            TRY(dalloc(h, &h->s_relayout, 1));
+            CK(cudaMemsetAsync(s.bp, 0, sizeof(double) * (size_t)m * ld, h->stream));
+            CK(cudaMemsetAsync(s.yp, 0, sizeof(double) * (size_t)ld, h->stream));
+            launch_struct_init_maps(s, h->stream);
+            CK(cudaGetLastError());
+            h->structured = true;
+            h->persist_blocks = h->geo.sms;
+            h->s_force = true;
+            if (h->opt.kernel_timing > 0 && !h->evc0) {
+                CK(cudaEventCreate(&h->evc0));
+                CK(cudaEventCreate(&h->evc1));
+            }
+        }
     }
     CK(cudaStreamSynchronize(h->stream));
     return LP_OK;
@@ -547,7 +603,7 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     lp_options o;
     lp_default_options(&o);
     if (opt) o = *opt;
-    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > 1 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
+    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > LP_ENGINE_STRUCTURED || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
         o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 1 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
@@ -595,6 +651,7 @@ int lp_update_problem(lp_handle* h, const double* A, const double* b, const doub
     }
     h->warm_pending = false;
     TRY(upload_problem(h, A, b, c, on_device));
+    h->s_force = true;
     TRY(reset_state(h));
     CK(cudaStreamSynchronize(h->stream));
     return LP_OK;
@@ -652,7 +709,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
                 out->status = phase1_status;
                 out->seconds = ms1 * 1e-3;
                 out->phase1_iterations = phase1_iters;
-                out->persistent = h->persist ? 1 : 0;
+                out->persistent = h->structured ? 2 : (h->persist ? 1 : 0);
             }
             return LP_OK;
         }
@@ -701,6 +758,39 @@ int lp_solve(lp_handle* h, lp_result* out) {
             continue;
         }
         if (C.status != kRunning) break;
+        if (h->structured) {
+            if (!h->s_ready) {
+                // enter the structured form from the dense state (rebuilt B^-1 or slack basis)
+                launch_struct_enter(h->ds, h->s_force ? 1 : 0, h->s_relayout, h->stream);
+                CK(cudaGetLastError());
+                h->launches += 3;
+                h->s_force = false;
+                h->s_ready = true;
+            }
+            const Ctrl before = C;
+            if (h->evc0) CK(cudaEventRecord(h->evc0, h->stream));
+            const cudaError_t e = launch_iterate_s(h->ds, h->persist_blocks, h->opt.graph_iters, h->stream);
+            if (e == cudaSuccess) {
+                h->launches += 1;
+                if (h->evc1) CK(cudaEventRecord(h->evc1, h->stream));
+                TRY(read_ctrl(h));
+                if (h->evc1) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, h->evc0, h->evc1));
+                    const Ctrl& A = *h->h_ctrl;
+                    h->chain_s += ms * 1e-3;
+                    h->chain_b += (A.bytes_price - before.bytes_price) + (A.bytes_update - before.bytes_update);
+                    h->chain_n++;
+                }
+                continue;
+            }
+            // the cooperative launch was refused: rebuild the dense state and
+            // continue on the dense engines
+            (void)cudaGetLastError();
+            h->structured = false;
+            TRY(reinvert(h, 0));
+            continue;
+        }
         if (!h->primed) {
             launch_price(h->ds, h->geo, h->stream);
             launch_update(h->ds, h->geo, h->stream);
@@ -759,6 +849,12 @@ int lp_solve(lp_handle* h, lp_result* out) {
             if (nu > 0) h->update_b += (A.bytes_update - before.bytes_update) * tu / nu;
         }
     }
+    if (h->structured && h->s_ready) {
+        // the duals of the solution, in row order
+        launch_struct_scatter_y(h->ds, h->stream);
+        CK(cudaGetLastError());
+        h->launches += 1;
+    }
     CK(cudaEventRecord(h->ev1, h->stream));
     CK(cudaEventSynchronize(h->ev1));
     float ms = 0.f;
@@ -794,7 +890,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->chain_seconds = h->chain_s;
         out->chain_bytes = h->chain_b;
         out->chain_launches = h->chain_n;
-        out->persistent = h->persist ? 1 : 0;
+        out->persistent = h->structured ? 2 : (h->persist ? 1 : 0);
         out->phase1_iterations = phase1_iters;
         out->phase1_exchanged = phase1_exch;
     }
@@ -829,9 +925,8 @@ int lp_get_basis(const lp_handle* h, int32_t* basis) {
 
 int lp_get_state(const lp_handle* h, double* binv, double* bbar) {
     if (!h) return LP_ERR_INVALID_ARG;
-    if (binv)
-        CK(cudaMemcpy2DAsync(binv, sizeof(double) * h->m, h->ds.binv, sizeof(double) * h->ld,
-                             sizeof(double) * h->m, h->m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (binv) TRY(binv_rows(h, 0, h->m, binv));
     if (bbar) CK(cudaMemcpyAsync(bbar, h->ds.bbar, sizeof(double) * h->m, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return LP_OK;

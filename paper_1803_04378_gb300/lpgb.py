@@ -28,6 +28,7 @@ LP_RUNNING, LP_OPTIMAL, LP_UNBOUNDED, LP_ITER_LIMIT, LP_INFEASIBLE = 0, 1, 2, 3,
 STATUS_NAMES = {0: "running", 1: "optimal", 2: "unbounded", 3: "iter_limit", 4: "infeasible"}
 LP_TF_DEGENERATE, LP_TF_TABU_PUSH, LP_TF_ASPIRATION, LP_TF_BLAND, LP_TF_TIE_SET = 1, 2, 4, 8, 64
 LP_TF_GUIDED = 128
+LP_ENGINE_DENSE, LP_ENGINE_GRAPH, LP_ENGINE_STRUCTURED = 0, 1, 2
 
 
 class lp_options(ctypes.Structure):
