@@ -272,6 +272,8 @@ def main():
                     help="profiling: solve once, then time this many reinversions of the optimal basis")
     ap.add_argument("--graph-iters", type=int, default=0,
                     help="pivots per persistent launch or captured graph (profiling; default 64)")
+    ap.add_argument("--reinvert-every", type=int, default=-1,
+                    help="profiling: pivots between reinversions (0: none; default: the solver's 64)")
     ap.add_argument("--max-iters", type=int, default=0,
                     help="stop every solve after this many pivots (profiling runs only)")
     args = ap.parse_args()
@@ -304,6 +306,8 @@ def main():
     if args.graph_iters > 0:
         extra["graph_iters"] = args.graph_iters
     extra["engine"] = args.engine
+    if args.reinvert_every >= 0:
+        extra["reinvert_every"] = args.reinvert_every
     lp = lpgb.LP(At, bt, ct, kernel_timing=KERNEL_TIMING_STRIDE, cuda_stream=stream.cuda_stream, price_mode=args.price_mode, **extra)
     del At, bt, ct
 

@@ -9,6 +9,7 @@
 #include "lpgb_internal.cuh"
 
 #include <cfloat>
+#include <climits>
 
 namespace lpgb {
 namespace {
@@ -81,33 +82,50 @@ __device__ __forceinline__ void dot_cols(const double2* __restrict__ A2, const i
 }
 
 // ---- CHUZC candidate ---------------------------------------------------------
+// Reduced costs are compared through an order-preserving integer image: on
+// this chip every FP64 instruction (compares and min/max included) shares the
+// slow FP64 pipe with the FMAs, while the integer compares below do not.
+// dkey(a) > dkey(b) exactly when a > b, and -0 and +0 share one key (no NaN
+// reaches a candidate).
+__device__ __forceinline__ long long dkey(double d) {
+    long long b = __double_as_longlong(d);
+    if ((b & 0x7fffffffffffffffLL) == 0) b = 0;
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double kdouble(long long k) {
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+
+// d_* fields hold dkey images of reduced costs.
 struct Cand {
-    double d_all; int j_all;
-    double d_nt;  int j_nt;
-    double d_min; int j_min;
-    double d_pr;  int j_pr; int k_pr;
+    long long d_all; int j_all;
+    long long d_nt;  int j_nt;
+    long long d_min; int j_min;
+    long long d_pr;  int j_pr; int k_pr;
 };
 
 __device__ __forceinline__ void cand_init(Cand& c) {
-    c.d_all = -DBL_MAX; c.j_all = -1;
-    c.d_nt = -DBL_MAX; c.j_nt = -1;
-    c.d_min = 0.0; c.j_min = -1;
-    c.d_pr = 0.0; c.j_pr = -1; c.k_pr = kNoRank;
+    c.d_all = LLONG_MIN; c.j_all = -1;
+    c.d_nt = LLONG_MIN; c.j_nt = -1;
+    c.d_min = 0; c.j_min = -1;
+    c.d_pr = 0; c.j_pr = -1; c.k_pr = kNoRank;
 }
 
 // a beats b: larger d, exact ties to the smaller index.
-__device__ __forceinline__ bool beats(double da, int ja, double db, int jb) {
+__device__ __forceinline__ bool beats(long long da, int ja, long long db, int jb) {
     if (ja < 0) return false;
     if (jb < 0) return true;
     return da > db || (da == db && ja < jb);
 }
 
-__device__ __forceinline__ void cand_offer(Cand& c, double d, int j, bool nontabu, double tol_d, int rank) {
+// ktol = dkey(tol_d)
+__device__ __forceinline__ void cand_offer(Cand& c, double dval, int j, bool nontabu, long long ktol, int rank) {
+    const long long d = dkey(dval);
     if (beats(d, j, c.d_all, c.j_all)) { c.d_all = d; c.j_all = j; }
     if (nontabu && beats(d, j, c.d_nt, c.j_nt)) { c.d_nt = d; c.j_nt = j; }
-    if (d > tol_d && (c.j_min < 0 || j < c.j_min)) { c.d_min = d; c.j_min = j; }
+    if (d > ktol && (c.j_min < 0 || j < c.j_min)) { c.d_min = d; c.j_min = j; }
     // guided rule: Dantzig restricted to the listed (priority) columns
-    if (nontabu && d > tol_d && rank != kNoRank && beats(d, j, c.d_pr, c.j_pr)) { c.d_pr = d; c.j_pr = j; c.k_pr = rank; }
+    if (nontabu && d > ktol && rank != kNoRank && beats(d, j, c.d_pr, c.j_pr)) { c.d_pr = d; c.j_pr = j; c.k_pr = rank; }
 }
 
 __device__ __forceinline__ void cand_merge(Cand& c, const Cand& o) {
@@ -171,23 +189,68 @@ __device__ __forceinline__ bool is_last_block(int32_t* ticket) {
     __syncthreads();
     return last != 0;
 }
-// ---- PRICE of one block's columns (k_price and k_iterate) ---------------------------
+// ---- PRICE of one block's columns (k_price, k_iterate, k_iterate_s) ------------------
+// Changes of the pivot being applied that a CTA has not necessarily seen in
+// memory yet (k_iterate_s applies a pivot without a grid barrier before
+// PRICE): column basic_j entered the basis, column free_j left it and is tabu
+// until tabu_until when tabu_j == free_j, and the slot -> row entries listed
+// in sp_* override the slot map (first match wins).
+struct PricePatch {
+    int basic_j, free_j, tabu_j, tabu_until;
+    int nsp;
+    int sp_slot[4], sp_row[4];
+};
+
+__device__ __forceinline__ PricePatch no_patch() {
+    PricePatch p;
+    p.basic_j = p.free_j = p.tabu_j = -1;
+    p.tabu_until = 0;
+    p.nsp = 0;
+    return p;
+}
+
+__device__ __forceinline__ int patched_tabu(const DevState& s, const PricePatch& pp, int j) {
+    return j == pp.tabu_j ? pp.tabu_until : __ldcg(s.tabu_until + j);
+}
+
 // ysh holds y; each column j contributes its first 2*len_half rows of Acol
-// (column stride ld; kL2: read through L2).  pos and tabu_until, which the bookkeeping of a persistent
-// launch writes from another block, are read through L2.  Returns the block's
-// candidate in thread 0.
+// (column stride ld; kL2: read through L2).  pos and tabu_until, which the
+// bookkeeping of a persistent launch writes from another block, are read
+// through L2.  slack_rows: the rows of the nonbasic slacks, entry i holding
+// the row of ysh[i] (nslack of them); otherwise every row is a slack
+// candidate and basic slacks are skipped.  Returns the block's candidate in
+// thread 0.
 template <bool kL2 = false>
 __device__ Cand price_block(const DevState& s, int it, const double* ysh, const double* Acol, int len_half,
-                            const int32_t* slack_rows, int nslack) {
+                            const int32_t* slack_rows, int nslack, const PricePatch& pp) {
     const Params& P = s.p;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int half = P.ld >> 1;  // column stride in double2
     const double2* y2 = reinterpret_cast<const double2*>(ysh);
+    const int G = gridDim.x;
+    const long long ktol = dkey(P.tol_d);
+    // Slack candidates are dealt to blocks round-robin too; their loads are
+    // issued first so that they complete under the column work.
+    int sj = -1;
+    {
+        const int i = blockIdx.x + G * threadIdx.x;
+        if (i < nslack) {
+            int row = i;
+            if (slack_rows) {
+                row = -1;
+                for (int e = 0; e < pp.nsp && row < 0; ++e)
+                    if (pp.sp_slot[e] == i) row = pp.sp_row[e];
+                if (row < 0) row = __ldcg(slack_rows + i);
+            }
+            sj = P.n + row;
+        }
+    }
     // Columns are dealt to blocks round-robin (block b owns j = b, b+G, ...)
     // so every SM gets the same share.  The block first lists its nonbasic
-    // columns; then each warp takes kOct listed columns over one of kSeg row
-    // segments, so one shared-memory load of y feeds 2*kOct FMAs, 2*kOct
+    // columns (with their cost, tabu state and priority, loaded in the same
+    // round trip); then each warp takes kOct listed columns over one of kSeg
+    // row segments, so one shared-memory load of y feeds 2*kOct FMAs, 2*kOct
     // independent 512-byte loads are in flight per step, and the kOct partial
     // sums leave the warp through one transposed reduction (6 adds for 4
     // columns instead of 5 per column).  The segment sums of a column are
@@ -196,10 +259,11 @@ __device__ Cand price_block(const DevState& s, int it, const double* ysh, const 
     // registers are held across the streaming loops.
     __shared__ Cand csh[kPriceCols];
     __shared__ int jl[kPriceThreads];
+    __shared__ double jc[kPriceThreads];
+    __shared__ int jt[kPriceThreads], jr[kPriceThreads];
     __shared__ double part[kSeg][kPriceCols];
     __shared__ int wcnt[kPriceThreads / 32];
     if (threadIdx.x < kPriceCols) cand_init(csh[threadIdx.x]);
-    const int G = gridDim.x;
     const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
     const int nch = len_half >> 5;  // 32-double2 chunks priced per column
     const int seg = warp % kSeg, gi = warp / kSeg;
@@ -209,7 +273,16 @@ __device__ Cand price_block(const DevState& s, int it, const double* ysh, const 
         // list the nonbasic owned columns lb .. lb+kPriceThreads-1, in order
         const int l = lb + (int)threadIdx.x;
         const int jj = (int)blockIdx.x + G * l;
-        const bool nb = l < owned && __ldcg(s.pos + jj) < 0;
+        bool nb = false;
+        double cj = 0.0;
+        int tj = 0, rj = kNoRank;
+        if (l < owned) {
+            const int pj = __ldcg(s.pos + jj);
+            cj = s.c[jj];
+            tj = patched_tabu(s, pp, jj);
+            rj = s.rank[jj];
+            nb = jj == pp.basic_j ? false : (jj == pp.free_j ? true : pj < 0);
+        }
         const unsigned bal = __ballot_sync(0xffffffffu, nb);
         if (lane == 0) wcnt[warp] = __popc(bal);
         __syncthreads();
@@ -219,7 +292,13 @@ __device__ Cand price_block(const DevState& s, int it, const double* ysh, const 
             if (w < warp) before += cw;
             cnt += cw;
         }
-        if (nb) jl[before + __popc(bal & ((1u << lane) - 1u))] = jj;
+        if (nb) {
+            const int e = before + __popc(bal & ((1u << lane) - 1u));
+            jl[e] = jj;
+            jc[e] = cj;
+            jt[e] = tj;
+            jr[e] = rj;
+        }
         __syncthreads();
         // Groups of 4 listed columns, and of 3 where cnt is not a multiple of 4,
         // so that every warp streams 3 or 4 columns at a time (a lone column
@@ -290,12 +369,11 @@ __device__ Cand price_block(const DevState& s, int it, const double* ysh, const 
                     else ee = c < 3 ? 4 * n4 + 3 * (gg - n4) + c : -1;
                 }
                 if (ee >= 0) {
-                    const int j = jl[ee];
                     double sum = part[0][threadIdx.x];
 #pragma unroll
                     for (int t = 1; t < kSeg; ++t) sum += part[t][threadIdx.x];
                     Cand cc = csh[threadIdx.x];
-                    cand_offer(cc, s.c[j] - sum, j, __ldcg(s.tabu_until + j) <= it, P.tol_d, s.rank[j]);
+                    cand_offer(cc, jc[ee] - sum, jl[ee], jt[ee] <= it, ktol, jr[ee]);
                     csh[threadIdx.x] = cc;
                 }
             }
@@ -305,23 +383,31 @@ __device__ Cand price_block(const DevState& s, int it, const double* ysh, const 
     Cand cand;
     cand_init(cand);
     if (threadIdx.x < kPriceCols) cand = csh[threadIdx.x];
-    // slack columns: d_{n+i} = -y_i (slack_rows: the rows of the nonbasic
-    // slacks, entry i holding the row of ysh[i]; otherwise every row, basic
-    // slacks skipped)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nslack; i += gridDim.x * blockDim.x) {
-        const int j = P.n + (slack_rows ? __ldcg(slack_rows + i) : i);
-        if (!slack_rows && __ldcg(s.pos + j) >= 0) continue;
-        cand_offer(cand, -ysh[i], j, __ldcg(s.tabu_until + j) <= it, P.tol_d, s.rank[j]);
+    // slack columns: d_{n+i} = -y_i
+    for (int i = blockIdx.x + G * threadIdx.x; i < nslack; i += G * blockDim.x) {
+        int j = sj;
+        if (i != (int)(blockIdx.x + G * threadIdx.x)) {
+            int row = i;
+            if (slack_rows) {
+                row = -1;
+                for (int e = 0; e < pp.nsp && row < 0; ++e)
+                    if (pp.sp_slot[e] == i) row = pp.sp_row[e];
+                if (row < 0) row = __ldcg(slack_rows + i);
+            }
+            j = P.n + row;
+        }
+        if (!slack_rows && (j == pp.basic_j ? true : (j == pp.free_j ? false : __ldcg(s.pos + j) >= 0))) continue;
+        cand_offer(cand, -ysh[i], j, patched_tabu(s, pp, j) <= it, ktol, s.rank[j]);
     }
     return cand_block_reduce(cand);
 }
 
 __device__ __forceinline__ PriceCand to_price_cand(const Cand& bc) {
     PriceCand pc;
-    pc.d_all = bc.d_all; pc.j_all = bc.j_all;
-    pc.d_nt = bc.d_nt; pc.j_nt = bc.j_nt;
-    pc.d_min = bc.d_min; pc.j_min = bc.j_min;
-    pc.d_pr = bc.d_pr; pc.j_pr = bc.j_pr; pc.k_pr = bc.k_pr;
+    pc.d_all = kdouble(bc.d_all); pc.j_all = bc.j_all;
+    pc.d_nt = kdouble(bc.d_nt); pc.j_nt = bc.j_nt;
+    pc.d_min = kdouble(bc.d_min); pc.j_min = bc.j_min;
+    pc.d_pr = kdouble(bc.d_pr); pc.j_pr = bc.j_pr; pc.k_pr = bc.k_pr;
     pc.pad_ = 0;
     return pc;
 }
@@ -333,10 +419,10 @@ __device__ Cand reduce_price_parts(const PriceCand* part, int nparts) {
     for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
         const PriceCand* pp = part + b;
         Cand o;
-        o.d_all = __ldcg(&pp->d_all); o.j_all = __ldcg(&pp->j_all);
-        o.d_nt = __ldcg(&pp->d_nt); o.j_nt = __ldcg(&pp->j_nt);
-        o.d_min = __ldcg(&pp->d_min); o.j_min = __ldcg(&pp->j_min);
-        o.d_pr = __ldcg(&pp->d_pr); o.j_pr = __ldcg(&pp->j_pr); o.k_pr = __ldcg(&pp->k_pr);
+        o.d_all = dkey(__ldcg(&pp->d_all)); o.j_all = __ldcg(&pp->j_all);
+        o.d_nt = dkey(__ldcg(&pp->d_nt)); o.j_nt = __ldcg(&pp->j_nt);
+        o.d_min = dkey(__ldcg(&pp->d_min)); o.j_min = __ldcg(&pp->j_min);
+        o.d_pr = dkey(__ldcg(&pp->d_pr)); o.j_pr = __ldcg(&pp->j_pr); o.k_pr = __ldcg(&pp->k_pr);
         cand_merge(g, o);
     }
     return cand_block_reduce(g);
@@ -352,16 +438,17 @@ struct Chuzc {
 
 __device__ Chuzc chuzc_decide(const Cand& g, bool bland, double tol_d) {
     Chuzc o = {0, -1, 0, 0, 0.0};
-    if (g.j_all < 0 || !(g.d_all > tol_d)) {
+    const long long ktol = dkey(tol_d);
+    if (g.j_all < 0 || !(g.d_all > ktol)) {
         o.optimal = 1;
     } else if (bland) {
-        o.q = g.j_min; o.dq = g.d_min; o.flags = kTfBland;
+        o.q = g.j_min; o.dq = kdouble(g.d_min); o.flags = kTfBland;
     } else if (g.j_pr >= 0) {
-        o.q = g.j_pr; o.dq = g.d_pr; o.flags = kTfGuided;
-    } else if (g.j_nt >= 0 && g.d_nt > tol_d) {
-        o.q = g.j_nt; o.dq = g.d_nt;
+        o.q = g.j_pr; o.dq = kdouble(g.d_pr); o.flags = kTfGuided;
+    } else if (g.j_nt >= 0 && g.d_nt > ktol) {
+        o.q = g.j_nt; o.dq = kdouble(g.d_nt);
     } else {
-        o.q = g.j_all; o.dq = g.d_all; o.flags = kTfAspiration; o.asp = 1;
+        o.q = g.j_all; o.dq = kdouble(g.d_all); o.flags = kTfAspiration; o.asp = 1;
     }
     return o;
 }

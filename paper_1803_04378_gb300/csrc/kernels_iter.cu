@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
     extern __shared__ double ysh[];
     for (int k = threadIdx.x; k < P.ld; k += blockDim.x) ysh[k] = s.y[k];
     __syncthreads();
-    const Cand bc = price_block(s, C->it, ysh, s.A_cm, P.ld >> 1, nullptr, P.m);
+    const Cand bc = price_block(s, C->it, ysh, s.A_cm, P.ld >> 1, nullptr, P.m, no_patch());
     if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
     if (!is_last_block(&C->ticket_price)) return;
     // last block: reduce all partials and decide
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
             }
             rh_staged = stage_rh;
             __syncthreads();
-            const Cand bc = price_block(s, S.it, sh, s.A_cm, P.ld >> 1, nullptr, P.m);
+            const Cand bc = price_block(s, S.it, sh, s.A_cm, P.ld >> 1, nullptr, P.m, no_patch());
             if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             const Cand g = reduce_price_parts(s.price_part, G);

@@ -103,32 +103,39 @@ __device__ __forceinline__ int vec_src(const SlotMoves& v, int t) {
     return t;
 }
 
+constexpr int kMaxOwnedRows = 256;  // rows of B^-1 per CTA (ratio-test records kept in shared memory)
+
 // Step 8 on the block's rows of the live B^-1 columns (new slot order), fused
 // with the FTRAN of the next entering column and the Step 6 ratios.  A CTA
-// always owns the same rows, so its own rows are read through L1; A_p, whose
-// rows move during the launch, is read through L2.  aq: the
-// entering structural column of A_p (nullptr for a slack, whose unit vector
-// sits at live slot aq_unit).  rh: rho / alpha_r in new slot order, zero past
-// kn.  Returns, in lane 0 of each warp, the smallest ratio of its rows.
-__device__ double update_block_s(const DevState& s, const SlotMoves& v, int r, bool do_upd, bool do_ftran,
-                                 const double* acur, double* anxt, const double* aq, int aq_unit, const double* rh) {
+// always owns the same rows (i = b, b + G, ...), so it reads its own rows
+// through L1.  aqs: the entering structural column of A_p staged in shared
+// memory (all m slots: the live ones for the dot product, the others for the
+// unit columns of the basic slacks), or nullptr for a slack, whose unit vector
+// sits at live slot aq_unit.  rh: rho / alpha_r in new slot order, zero past
+// kn.  Row l of the CTA leaves alpha', its ratio and its basic variable in
+// ral/rth/rvar[l] (and in global memory for the ratio test of other CTAs).
+__device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int q_new, bool do_upd, bool do_ftran,
+                               const double* acur, double* anxt, const double* aqs, int aq_unit, const double* rh,
+                               double* ral, double* rth, int* rvar) {
     const Params& P = s.p;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int kn = v.kn;
     const int kh = (kn + 1) >> 1;  // double2 units covering the live slots
-    const double2* aq2 = reinterpret_cast<const double2*>(aq);
+    const double2* aq2 = reinterpret_cast<const double2*>(aqs);
     const double2* rh2 = reinterpret_cast<const double2*>(rh);
-    double tmin = DBL_MAX;
     const int G = gridDim.x;
     const int owned = (P.m - (int)blockIdx.x + G - 1) / G;
     for (int l = warp; l < owned; l += nw) {
         const int i = blockIdx.x + G * l;
         double* rowd = s.bp + (size_t)i * P.ld;
         double2* row = reinterpret_cast<double2*>(rowd);
-        // the unit term of FTRAN: the row of the slack basic at position i
-        const int us = (do_ftran && aq) ? __ldcg(s.uslot + i) : -1;
-        const double aus = us >= 0 ? __ldcg(aq + us) : 0.0;
+        // per-row scalars, all issued before the row streams in
+        const int us = (do_ftran && aqs) ? __ldcg(s.uslot + i) : -1;
+        const double na = (do_upd && i != r) ? -__ldcg(acur + i) : 0.0;
+        const double bte = (do_upd && i != r && v.src_te >= 0) ? __ldcg(rowd + v.src_te) : 0.0;
+        const double bb = do_ftran ? __ldcg(s.bbar + i) : 0.0;
+        const int var = do_ftran ? (i == r && do_upd ? q_new : __ldcg(s.basis + i)) : 0;
         double a0 = 0.0, a1 = 0.0;
         if (do_upd && i == r) {
             // row r becomes rho / alpha_r (every slot, the moved ones included)
@@ -137,16 +144,13 @@ __device__ double update_block_s(const DevState& s, const SlotMoves& v, int r, b
                 __stcs(row + k, nv);
                 if (do_ftran) {
                     const int t0 = 2 * k, t1 = t0 + 1;
-                    const double2 w = aq ? __ldcg(aq2 + k) : make_double2(t0 == aq_unit ? 1.0 : 0.0, t1 == aq_unit ? 1.0 : 0.0);
+                    const double2 w = aqs ? aq2[k] : make_double2(t0 == aq_unit ? 1.0 : 0.0, t1 == aq_unit ? 1.0 : 0.0);
                     a0 = fma(nv.x, w.x, a0);
                     if (t1 < kn) a1 = fma(nv.y, w.y, a1);
                 }
             }
         } else {
-            const double na = do_upd ? -__ldcg(acur + i) : 0.0;
             const bool st = na != 0.0;
-            // old value of the column that moves into slot te (read before any store)
-            const double bte = (do_upd && v.src_te >= 0) ? __ldcg(rowd + v.src_te) : 0.0;
             for (int k0 = lane; k0 < kh; k0 += 32 * kS) {
                 double2 o[kS];
 #pragma unroll
@@ -167,7 +171,7 @@ __device__ double update_block_s(const DevState& s, const SlotMoves& v, int r, b
                         if (st) __stcs(row + k, nv);
                     }
                     if (do_ftran) {
-                        const double2 w = aq ? __ldcg(aq2 + k) : make_double2(t0 == aq_unit ? 1.0 : 0.0, t1 == aq_unit ? 1.0 : 0.0);
+                        const double2 w = aqs ? aq2[k] : make_double2(t0 == aq_unit ? 1.0 : 0.0, t1 == aq_unit ? 1.0 : 0.0);
                         a0 = fma(nv.x, w.x, a0);
                         if (t1 < kn) a1 = fma(nv.y, w.y, a1);
                     }
@@ -180,37 +184,154 @@ __device__ double update_block_s(const DevState& s, const SlotMoves& v, int r, b
             }
         }
         if (do_ftran) {
-            const double al = warp_sum(a0 + a1) + aus;
+            const double al = warp_sum(a0 + a1);
             if (lane == 0) {
-                anxt[i] = al;
+                const double alf = al + (us >= 0 ? aqs[us] : 0.0);
                 double th = DBL_MAX;
-                if (al > P.tol_piv) th = __ldcg(s.bbar + i) / al;
+                if (alf > P.tol_piv) th = bb / alf;
+                anxt[i] = alf;
                 s.theta[i] = th;
-                s.row_var[i] = __ldcg(s.basis + i);
-                tmin = fmin(tmin, th);
+                s.row_var[i] = var;
+                ral[l] = alf;
+                rth[l] = th;
+                rvar[l] = var;
             }
         }
     }
-    return tmin;
 }
 
+// The CTA's ratio-test record from its rows' (alpha', ratio, variable): its
+// smallest ratio, and its best row and tie count under that ratio's tie
+// threshold (one warp; result written by lane 0).
+__device__ void row_record(const Params& P, int owned, bool bland, const double* ral, const double* rth,
+                           const int* rvar, RowRec* out) {
+    const int lane = threadIdx.x & 31;
+    const int G = gridDim.x;
+    long long kmin = dkey(DBL_MAX);
+    for (int l = lane; l < owned; l += 32) kmin = min(kmin, dkey(rth[l]));
+    for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    const double tmin = kdouble(kmin);
+    RowCand best = {0.0, 0, -1, 0.0};
+    int cnt = 0;
+    double thr = DBL_MAX;
+    if (tmin != DBL_MAX) {
+        thr = tmin + P.tol_tie * fmax(1.0, fabs(tmin));
+        for (int l = lane; l < owned; l += 32) {
+            const double al = ral[l], th = rth[l];
+            if (al > P.tol_piv && th <= thr) {
+                cnt++;
+                RowCand c = {al, rvar[l], (int)blockIdx.x + G * l, th};
+                if (row_beats(c, best, bland)) best = c;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        RowCand oc;
+        oc.a = __shfl_xor_sync(0xffffffffu, best.a, o);
+        oc.var = __shfl_xor_sync(0xffffffffu, best.var, o);
+        oc.row = __shfl_xor_sync(0xffffffffu, best.row, o);
+        oc.th = __shfl_xor_sync(0xffffffffu, best.th, o);
+        if (row_beats(oc, best, bland)) best = oc;
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+        RowRec rp;
+        rp.tmin = kmin; rp.thr = dkey(thr); rp.a = best.a; rp.th = best.th;
+        rp.var = best.var; rp.row = best.row; rp.cnt = cnt; rp.pad_ = 0;
+        *out = rp;
+    }
+}
+
+__device__ __forceinline__ PriceRec to_price_rec(const Cand& c) {
+    PriceRec r;
+    r.d_all = c.d_all; r.d_nt = c.d_nt;  // keys
+    r.j_all = c.j_all; r.j_nt = c.j_nt; r.j_min = c.j_min; r.j_pr = c.j_pr;
+    r.d_min = c.d_min; r.d_pr = c.d_pr;
+    r.k_pr = c.k_pr; r.pad_[0] = r.pad_[1] = r.pad_[2] = 0;
+    return r;
+}
+
+// CHUZC over the per-CTA partials with the warps that hold them (result in
+// thread 0); each record arrives in four 16-byte loads.
+__device__ Cand reduce_price_parts_s(const PriceRec* part, int nparts) {
+    __shared__ Cand wsh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwu = (nparts + 31) >> 5;  // warps holding partials
+    Cand g;
+    cand_init(g);
+    if (warp < nwu) {
+        for (int b = threadIdx.x; b < nparts; b += nwu * 32) {
+            const longlong2* p2 = reinterpret_cast<const longlong2*>(part + b);
+            const int4* p4 = reinterpret_cast<const int4*>(part + b);
+            const longlong2 w0 = __ldcg(p2);
+            const int4 w1 = __ldcg(p4 + 1);
+            const longlong2 w2 = __ldcg(p2 + 2);
+            const int4 w3 = __ldcg(p4 + 3);
+            Cand o;
+            o.d_all = w0.x; o.d_nt = w0.y;
+            o.j_all = w1.x; o.j_nt = w1.y; o.j_min = w1.z; o.j_pr = w1.w;
+            o.d_min = w2.x; o.d_pr = w2.y;
+            o.k_pr = w3.x;
+            cand_merge(g, o);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cand_merge(g, cand_shfl(g, o));
+        if (lane == 0) wsh[warp] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < nwu; ++w) cand_merge(g, wsh[w]);
+    return g;
+}
+
+// The pivot's changes to the data PRICE reads, for a CTA that may not see
+// the lead CTA's bookkeeping stores yet.
+__device__ PricePatch pivot_patch(const SlotMoves& v, int q, int leave, bool push, int tabu_until) {
+    PricePatch p = no_patch();
+    p.basic_j = q;
+    p.free_j = leave;
+    if (push) { p.tabu_j = leave; p.tabu_until = tabu_until; }
+    // the slot -> row entries that differ from the current map, in the
+    // precedence order of moved_slot_row
+    if (v.ent >= 0) {
+        p.sp_slot[p.nsp] = v.te; p.sp_row[p.nsp] = v.w; ++p.nsp;
+        p.sp_slot[p.nsp] = v.k1 - 1; p.sp_row[p.nsp] = v.ent; ++p.nsp;
+    }
+    if (v.join >= 0) {
+        p.sp_slot[p.nsp] = v.k0; p.sp_row[p.nsp] = v.join; ++p.nsp;
+        p.sp_slot[p.nsp] = v.tl; p.sp_row[p.nsp] = v.u; ++p.nsp;
+    }
+    return p;
+}
+
+// One step = apply the pivot chosen by the last ratio test and price (A),
+// grid barrier, CHUZC + UPDATE/FTRAN + the CTA's ratio-test record (B), grid
+// barrier, CHUZR (C).  Step (A) needs no barrier of its own: every CTA
+// computes y and rho / alpha_r in the new slot order for itself from the
+// pivot row of B^-1 (final since the last barrier), moves the A_p rows of the
+// columns it prices and updates bbar on the rows it owns; the pivot's
+// changes to pos, tabu_until and the slot map reach PRICE as a patch while
+// the lead CTA writes them to memory (visible to all after the next barrier).
+// The y of the next step is written by the lead CTA to the other half of a
+// double buffer.
 __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int iters) {
     Ctrl* C = s.ctrl;
     const Params& P = s.p;
-    extern __shared__ double sh[];  // y and rho / alpha_r in slot order (ld doubles each)
+    extern __shared__ double sh[];  // y, rho / alpha_r, entering column (ld doubles each)
     __shared__ IterState S;
     __shared__ volatile int fail;
-    __shared__ double gmin_sh;
-    __shared__ int nflag;
-    __shared__ int flg[kMaxFlagged];
-    __shared__ double tb_sh;
-    __shared__ RowPart rec_sh;
-    __shared__ SlotMoves mv;  // this step's slot moves (thread 0 writes them in phase 1)
+    __shared__ SlotMoves mv;
+    __shared__ PricePatch ppat;
+    __shared__ int nflag, flagged;
+    __shared__ long long wmin_sh[32], wthr_sh[32];
+    __shared__ double rinv_sh;
+    __shared__ int wcnt_sh[32];
+    __shared__ double ral[kMaxOwnedRows], rth[kMaxOwnedRows];
+    __shared__ int rvar[kMaxOwnedRows];
     unsigned epoch = 0;
     const bool lead = blockIdx.x == 0;
     const int G = gridDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = G * blockDim.x;
+    const int owned = (P.m - (int)blockIdx.x + G - 1) / G;
     if (threadIdx.x == 0) {
         fail = 0;
         S.status = C->status; S.it = C->it; S.q = C->q; S.r = C->r; S.tcount = C->tcount;
@@ -228,59 +349,89 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
     }
     double* ysh = sh;
     double* rh = sh + P.ld;
+    double* aqs = sh + 2 * (size_t)P.ld;
     for (int step = 0; step < iters; ++step) {
-        // ---- (1) the pivot chosen by the last ratio test: slot moves, rho, y, bbar, bookkeeping
+        // ---- (A) apply the pivot chosen by the last ratio test, then PRICE
         const bool piv = S.status == kRunning && S.r >= 0 && S.r < P.m && S.q >= 0;
-        {
-            const int r = S.r;
-            const double* acur = s.alpha + (size_t)S.abuf * P.ld;
-            const double ar = S.alpha_r, th = S.theta, dq = S.dq;
-            const int par = S.par;
-            if (threadIdx.x == 0) {
-                if (piv) {
-                    mv = slot_moves(s, S.leave, S.q, S.k, par);
-                } else {
-                    mv.join = mv.ent = -1;
-                    mv.k0 = mv.k1 = mv.kn = S.k;
-                    mv.tl = mv.u = mv.te = mv.w = mv.J = mv.src_te = -1;
-                }
-            }
-            __syncthreads();  // the moves are visible and every thread has read the state
+        const int r = S.r, q = S.q, par = S.par;
+        const double* acur = s.alpha + (size_t)S.abuf * P.ld;
+        const double ar = S.alpha_r, th = S.theta, dq = S.dq;
+        if (threadIdx.x == 0) {
             if (piv) {
-            if (threadIdx.x == 0) {
+                mv = slot_moves(s, S.leave, S.q, S.k, par);
+                const bool degenerate = th <= P.tol_tie;
+                const bool push = P.tabu_tenure > 0 && (S.tcount > 1 || degenerate);
+                ppat = pivot_patch(mv, S.q, S.leave, push, S.it + 1 + P.tabu_tenure);
+                rinv_sh = 1.0 / ar;
+            } else {
+                mv.join = mv.ent = -1;
+                mv.k0 = mv.k1 = mv.kn = S.k;
+                mv.tl = mv.u = mv.te = mv.w = mv.J = mv.src_te = -1;
+                ppat = no_patch();
+            }
+        }
+        __syncthreads();  // the moves are visible and every thread has read the state
+        const int kn = mv.kn;
+        const int kk = min(P.ld, (kn + 63) & ~63);  // live slots rounded up to a double2 sweep
+        const double rinv = rinv_sh;
+        if (threadIdx.x == 0) {
+            if (piv) {
                 if (lead) {
                     // the positions whose basic slack changed slot
                     s.uslot[r] = mv.ent >= 0 ? mv.k1 - 1 : -1;
                     if (mv.join >= 0 && mv.tl != mv.k0) s.uslot[__ldcg(s.pos + P.n + mv.u)] = mv.tl;
                 }
                 pivot_bookkeeping(s, S, lead);
-                S.k = mv.kn;
+                S.k = kn;
                 S.par = par ^ 1;
             }
-            const int32_t* sr0 = s.slot_row + (size_t)par * P.m;
-            const int32_t* rs0 = s.row_slot + (size_t)par * P.m;
-            int32_t* sr1 = s.slot_row + (size_t)(par ^ 1) * P.m;
-            int32_t* rs1 = s.row_slot + (size_t)(par ^ 1) * P.m;
-            const double* brow = s.bp + (size_t)r * P.ld;
-            for (int x = tid; x < P.m; x += stride) {
-                // next slot maps; bbar (by basis position)
-                const int a = __ldcg(sr0 + x), b = __ldcg(rs0 + x);
-                const double bb = __ldcg(s.bbar + x), ak = __ldcg(acur + x);
-                sr1[x] = moved_slot_row(mv, x, a);
-                rs1[x] = moved_row_slot(mv, x, b);
-                s.bbar[x] = (x == r) ? th : __dsub_rn(bb, __dmul_rn(ak, th));
+        }
+        {
+            // y and rho / alpha_r in the new slot order (every CTA, into shared memory)
+            const double* yold = s.yp + (size_t)par * P.ld;
+            double* ynew = s.yp + (size_t)(par ^ 1) * P.ld;
+            const double* brow = s.bp + (size_t)(piv ? r : 0) * P.ld;
+            // slot pairs in 16-byte loads; a moved slot reads its source itself
+            for (int p = threadIdx.x; 2 * p < kk; p += blockDim.x) {
+                const double2 rb = piv ? __ldcg(reinterpret_cast<const double2*>(brow) + p) : make_double2(0.0, 0.0);
+                const double2 yb = __ldcg(reinterpret_cast<const double2*>(yold) + p);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int t = 2 * p + e;
+                    double rn = 0.0, yv = 0.0;
+                    if (t < kn) {
+                        const int src = piv ? vec_src(mv, t) : t;
+                        double rv = e ? rb.y : rb.x, yo = e ? yb.y : yb.x;
+                        if (src == -2) { rv = 1.0; yo = 0.0; }
+                        else if (src != t) { rv = __ldcg(brow + src); yo = __ldcg(yold + src); }
+                        if (piv) {
+                            rn = rv * rinv;  // one reciprocal per pivot: a division per slot in every CTA would load the FP64 pipe
+                            yv = __dadd_rn(yo, __dmul_rn(dq, rn));
+                        } else {
+                            yv = yo;
+                        }
+                        if (lead && piv) ynew[t] = yv;
+                    }
+                    rh[t] = rn;
+                    ysh[t] = yv;
+                }
             }
-            for (int t = tid; t < mv.kn; t += stride) {
-                // rho / alpha_r and y in the new slot order
-                const int src = vec_src(mv, t);
-                const double rv = src >= 0 ? __ldcg(brow + src) : 1.0;
-                const double yv = src >= 0 ? __ldcg(s.yp + src) : 0.0;
-                const double rn = rv / ar;
-                s.rho[t] = rn;
-                s.yp[t] = __dadd_rn(yv, __dmul_rn(dq, rn));
+        }
+        if (piv) {
+            if (lead) {
+                // the next copy of the slot maps
+                const int32_t* sr0 = s.slot_row + (size_t)par * P.m;
+                const int32_t* rs0 = s.row_slot + (size_t)par * P.m;
+                int32_t* sr1 = s.slot_row + (size_t)(par ^ 1) * P.m;
+                int32_t* rs1 = s.row_slot + (size_t)(par ^ 1) * P.m;
+                for (int x = threadIdx.x; x < P.m; x += blockDim.x) {
+                    const int a = __ldcg(sr0 + x), b = __ldcg(rs0 + x);
+                    sr1[x] = moved_slot_row(mv, x, a);
+                    rs1[x] = moved_row_slot(mv, x, b);
+                }
             }
             if (mv.join >= 0 || mv.ent >= 0) {
-                // A_p rows follow their slots (at most three slots change)
+                // A_p rows of the columns this CTA prices follow their slots
                 int dst[3], src[3], nm = 0;
                 if (mv.ent >= 0 && mv.join >= 0) {
                     dst[0] = mv.te; src[0] = mv.tl;
@@ -292,32 +443,29 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
                 } else if (mv.tl != mv.k0) {
                     dst[0] = mv.k0; src[0] = mv.tl; dst[1] = mv.tl; src[1] = mv.k0; nm = 2;
                 }
-                for (int j = tid; j < P.n && nm > 0; j += stride) {
+                for (int j = blockIdx.x + G * threadIdx.x; j < P.n && nm > 0; j += G * blockDim.x) {
                     double* col = s.A_p + (size_t)j * P.ld;
                     double val[3];
                     for (int e = 0; e < nm; ++e) val[e] = __ldcg(col + src[e]);
                     for (int e = 0; e < nm; ++e) col[dst[e]] = val[e];
                 }
             }
-            if (!grid_barrier(s.gbar, epoch, &fail)) break;
-            if (S.status == kReinvert) break;
+            // bbar on the rows this CTA owns (their ratios are computed here too)
+            for (int l = threadIdx.x; l < owned; l += blockDim.x) {
+                const int i = blockIdx.x + G * l;
+                const double bb = __ldcg(s.bbar + i), ak = __ldcg(acur + i);
+                s.bbar[i] = (i == r) ? th : __dsub_rn(bb, __dmul_rn(ak, th));
             }
         }
-        const int kn = S.k;
-        const int kk = min(P.ld, (kn + 63) & ~63);  // live slots rounded up to a double2 sweep
-        // ---- (2) PRICE + CHUZC over the live slots
+        __syncthreads();  // y, rho, the A_p moves and thread 0's bookkeeping are done
+        if (S.status == kReinvert) break;  // the slot moves are complete; B^-1 is rebuilt
         if (S.status == kRunning) {
-            const bool stage_rh = S.pending != 0;
-            for (int t = threadIdx.x; t < kk; t += blockDim.x) {
-                ysh[t] = t < kn ? __ldcg(s.yp + t) : 0.0;
-                if (stage_rh) rh[t] = t < kn ? __ldcg(s.rho + t) : 0.0;
-            }
-            __syncthreads();
-            const int32_t* sr = s.slot_row + (size_t)S.par * P.m;
-            const Cand bc = price_block<true>(s, S.it, ysh, s.A_p, kk >> 1, sr, kn);
-            if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
+            const int32_t* sr = s.slot_row + (size_t)par * P.m;  // + the patch: the map after the moves
+            const Cand bc = price_block<true>(s, S.it, ysh, s.A_p, kk >> 1, sr, kn, ppat);
+            if (threadIdx.x == 0) s.price_rec[blockIdx.x] = to_price_rec(bc);
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
-            const Cand g = reduce_price_parts(s.price_part, G);
+            // ---- (B) CHUZC (every CTA), then UPDATE + FTRAN + ratios
+            const Cand g = reduce_price_parts_s(s.price_rec, G);
             if (threadIdx.x == 0) {
                 const Chuzc d = chuzc_decide(g, S.bland != 0, P.tol_d);
                 if (d.optimal) {
@@ -335,132 +483,131 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
                 }
             }
             __syncthreads();
-        } else if (S.pending != 0) {
-            for (int t = threadIdx.x; t < kk; t += blockDim.x) rh[t] = t < kn ? __ldcg(s.rho + t) : 0.0;
-            __syncthreads();
         }
-        // ---- (3) UPDATE of the pending pivot + FTRAN of the new column + ratios
-        const bool do_upd = S.pending != 0 && S.r >= 0 && S.r < P.m;
+        const bool do_upd = piv;
         const bool do_ftran = S.status == kRunning && S.q >= 0 && S.q < P.n + P.m;
         if (!do_upd && !do_ftran) break;
-        const double* aq = (do_ftran && S.q < P.n) ? s.A_p + (size_t)S.q * P.ld : nullptr;
-        const int aq_unit = (do_ftran && S.q >= P.n) ? __ldcg(s.row_slot + (size_t)S.par * P.m + (S.q - P.n)) : -1;
-        const double* acur = s.alpha + (size_t)S.abuf * P.ld;
-        double* anxt = s.alpha + (size_t)(S.abuf ^ 1) * P.ld;
-        const double tb = block_min(update_block_s(s, mv, S.r, do_upd, do_ftran, acur, anxt, aq, aq_unit, rh));
-        if (threadIdx.x == 0) {
-            tb_sh = tb;
-            if (lead) {
-                S.bytes_update += (do_upd ? 16.0 : (do_ftran ? 8.0 : 0.0)) * P.m * (double)kn;
-                S.n_update++;
+        const double* aqp = nullptr;
+        int aq_unit = -1;
+        if (do_ftran) {
+            if (S.q < P.n) {
+                // the entering column of A_p (every slot), staged in shared memory
+                const double2* col = reinterpret_cast<const double2*>(s.A_p + (size_t)S.q * P.ld);
+                double2* a2 = reinterpret_cast<double2*>(aqs);
+                for (int t = threadIdx.x; t < (P.ld >> 1); t += blockDim.x) a2[t] = __ldcg(col + t);
+                aqp = aqs;
+            } else {
+                const int row = S.q - P.n;
+                aq_unit = moved_row_slot(mv, row, __ldcg(s.row_slot + (size_t)par * P.m + row));
             }
         }
         __syncthreads();
-        if (do_ftran) {
-            const double tbl = tb_sh;
-            const double thr_b = tbl + P.tol_tie * fmax(1.0, fabs(tbl));
-            const bool blandb = S.bland != 0;
-            RowCand lb = {0.0, 0, -1, 0.0};
-            int lc = 0;
-            if (tbl != DBL_MAX) {
-                const int owned = (P.m - (int)blockIdx.x + G - 1) / G;
-                for (int l = threadIdx.x; l < owned; l += blockDim.x) {
-                    const int i = blockIdx.x + G * l;
-                    const double al = anxt[i], th = s.theta[i];  // written by this CTA
-                    if (al > P.tol_piv && th <= thr_b) {
-                        lc++;
-                        RowCand c = {al, s.row_var[i], i, th};
-                        if (row_beats(c, lb, blandb)) lb = c;
-                    }
-                }
-            }
-            lb = block_row_best(lb, lc, blandb);
-            if (threadIdx.x == 0) {
-                RowPart rp;
-                rp.tmin = tbl; rp.a = lb.a; rp.th = lb.th; rp.var = lb.var; rp.row = lb.row; rp.cnt = lc; rp.pad_ = 0;
-                s.row_part[blockIdx.x] = rp;
-            }
+        const double* acur2 = s.alpha + (size_t)S.abuf * P.ld;
+        double* anxt = s.alpha + (size_t)(S.abuf ^ 1) * P.ld;
+        update_block_s(s, mv, r, q, do_upd, do_ftran, acur2, anxt, aqp, aq_unit, rh, ral, rth, rvar);
+        if (lead && threadIdx.x == 0) {
+            S.bytes_update += (do_upd ? 16.0 : (do_ftran ? 8.0 : 0.0)) * P.m * (double)kn;
+            S.n_update++;
         }
         if (!do_ftran) {
             if (threadIdx.x == 0) S.pending = 0;
             break;
         }
+        __syncthreads();
+        if (threadIdx.x < 32) row_record(P, owned, S.bland != 0, ral, rth, rvar, s.row_rec + blockIdx.x);
         if (!grid_barrier(s.gbar, epoch, &fail)) break;
-        // ---- (4) CHUZR: minimum ratio, tie set, leaving row (every CTA)
-        RowPart rec;
-        rec.tmin = DBL_MAX;
+        // ---- (C) CHUZR: minimum ratio, tie set, leaving row (every CTA), on
+        // integer keys; the tie threshold comes with the record that holds
+        // the minimum
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        RowRec rec;
+        rec.tmin = dkey(DBL_MAX);
+        rec.thr = rec.tmin;
         if ((int)threadIdx.x < G) {
-            const RowPart* rp = s.row_part + threadIdx.x;
-            rec.tmin = __ldcg(&rp->tmin); rec.a = __ldcg(&rp->a); rec.th = __ldcg(&rp->th);
-            rec.var = __ldcg(&rp->var); rec.row = __ldcg(&rp->row); rec.cnt = __ldcg(&rp->cnt);
+            const longlong2* p2 = reinterpret_cast<const longlong2*>(s.row_rec + threadIdx.x);
+            const longlong2 w0 = __ldcg(p2);
+            const double2 w1 = __ldcg(reinterpret_cast<const double2*>(p2 + 1));
+            const int4 w2 = __ldcg(reinterpret_cast<const int4*>(p2 + 2));
+            rec.tmin = w0.x; rec.thr = w0.y; rec.a = w1.x; rec.th = w1.y;
+            rec.var = w2.x; rec.row = w2.y; rec.cnt = w2.z;
         }
-        const double mine = rec.tmin;
-        double tg = block_min(mine);
-        if (threadIdx.x == 0) {
-            gmin_sh = tg;
-            nflag = 0;
+        const int nwu = (G + 31) >> 5;
+        long long wm = rec.tmin, wt = rec.thr;
+        if (warp < nwu) {
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long om = __shfl_xor_sync(0xffffffffu, wm, o), ot = __shfl_xor_sync(0xffffffffu, wt, o);
+                if (om < wm) { wm = om; wt = ot; }
+            }
+            if (lane == 0) { wmin_sh[warp] = wm; wthr_sh[warp] = wt; }
         }
         __syncthreads();
-        const double gmin = gmin_sh;
-        if (gmin == DBL_MAX) {
+        long long gmin = wmin_sh[0], gthr = wthr_sh[0];
+        for (int w = 1; w < nwu; ++w)
+            if (wmin_sh[w] < gmin) { gmin = wmin_sh[w]; gthr = wthr_sh[w]; }
+        if (gmin == dkey(DBL_MAX)) {
             if (threadIdx.x == 0) {
                 S.status = kUnbounded;
                 S.pending = 0;
             }
             break;
         }
-        const double thr = gmin + P.tol_tie * fmax(1.0, fabs(gmin));
-        if ((int)threadIdx.x < G && mine <= thr) {
-            const int k = atomicAdd(&nflag, 1);
-            if (k < kMaxFlagged) flg[k] = threadIdx.x;
-            rec_sh = rec;
-        }
+        const double thr = kdouble(gthr);
+        // CTAs whose smallest ratio lies within the tie tolerance hold the tie set
+        const bool fl = (int)threadIdx.x < G && rec.tmin <= gthr;
+        const unsigned bal = __ballot_sync(0xffffffffu, fl);
+        if (lane == 0 && warp < nwu) wcnt_sh[warp] = __popc(bal);
+        if (fl) flagged = threadIdx.x;  // read only when this CTA is the only one
         __syncthreads();
+        int nf = 0;
+        for (int w = 0; w < nwu; ++w) nf += wcnt_sh[w];
         const bool bland = S.bland != 0;
-        RowCand best = {0.0, 0, -1, 0.0};
+        RowCand b = {0.0, 0, -1, 0.0};
         int cnt = 0;
-        if (nflag == 1) {
-            if (threadIdx.x == 0) {
-                best.a = rec_sh.a; best.var = rec_sh.var; best.row = rec_sh.row; best.th = rec_sh.th;
-                cnt = rec_sh.cnt;
+        if (nf == 1) {
+            // one CTA holds the minimum, so its threshold is the global one and
+            // its record is the tie set's best row and size
+            if ((int)threadIdx.x == flagged) {
+                nflag = rec.row < 0 ? -1 : 1;
+                if (rec.row >= 0) {
+                    S.r = rec.row; S.leave = rec.var; S.theta = rec.th; S.alpha_r = rec.a; S.tcount = rec.cnt;
+                }
             }
-        } else if (nflag <= kMaxFlagged) {
-            const int per = (P.m + G - 1) / G;
-            for (int e = threadIdx.x; e < nflag * per; e += blockDim.x) {
-                const int b = flg[e / per], l = e % per;
-                const int i = b + G * l;
-                if (i >= P.m) continue;
-                const double al = __ldcg(anxt + i), th = __ldcg(s.theta + i);
-                if (al > P.tol_piv && th <= thr) {
-                    cnt++;
-                    RowCand c = {al, __ldcg(s.row_var + i), i, th};
-                    if (row_beats(c, best, bland)) best = c;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                S.pending = 0;
+                if (nflag < 0) {
+                    S.status = kUnbounded;
+                    if (lead) C->err = kErrBadIndex;
+                } else {
+                    if (S.tcount > 1) S.flags |= kTfTieSet;
+                    S.abuf ^= 1;
                 }
             }
         } else {
+            // the tie set spans several CTAs: scan the rows of all CTAs
             for (int i = threadIdx.x; i < P.m; i += blockDim.x) {
-                const double al = __ldcg(anxt + i), th = __ldcg(s.theta + i);
-                if (al > P.tol_piv && th <= thr) {
+                const double al = __ldcg(anxt + i), th2 = __ldcg(s.theta + i);
+                if (al > P.tol_piv && th2 <= thr) {
                     cnt++;
-                    RowCand c = {al, __ldcg(s.row_var + i), i, th};
-                    if (row_beats(c, best, bland)) best = c;
+                    RowCand c = {al, __ldcg(s.row_var + i), i, th2};
+                    if (row_beats(c, b, bland)) b = c;
                 }
             }
-        }
-        const RowCand b = nflag == 1 ? best : block_row_best(best, cnt, bland);
-        if (threadIdx.x == 0) {
-            S.pending = 0;
-            if (b.row < 0) {
-                S.status = kUnbounded;
-                if (lead) C->err = kErrBadIndex;
-            } else {
-                S.r = b.row;
-                S.leave = b.var;
-                S.theta = b.th;
-                S.alpha_r = b.a;
-                S.tcount = cnt;
-                if (cnt > 1) S.flags |= kTfTieSet;
-                S.abuf ^= 1;
+            b = block_row_best(b, cnt, bland);
+            if (threadIdx.x == 0) {
+                S.pending = 0;
+                if (b.row < 0) {
+                    S.status = kUnbounded;
+                    if (lead) C->err = kErrBadIndex;
+                } else {
+                    S.r = b.row;
+                    S.leave = b.var;
+                    S.theta = b.th;
+                    S.alpha_r = b.a;
+                    S.tcount = cnt;
+                    if (cnt > 1) S.flags |= kTfTieSet;
+                    S.abuf ^= 1;
+                }
             }
         }
         __syncthreads();
@@ -569,8 +716,9 @@ __global__ void k_struct_gather_B(DevState s) {
         const int t = (int)(e % k);
         s.bp[i * P.ld + t] = s.binv[i * P.ld + sr[t]];
     }
+    double* yp = s.yp + (size_t)s.ctrl->map_par * P.ld;  // the current half of the double buffer
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P.ld; t += gridDim.x * blockDim.x)
-        s.yp[t] = t < k ? s.y[sr[t]] : 0.0;
+        yp[t] = t < k ? s.y[sr[t]] : 0.0;
 }
 
 // dense y (and its FP32 copy) from the slot-order y, for the solution and every
@@ -579,11 +727,12 @@ __global__ void k_struct_scatter_y(DevState s) {
     const Params& P = s.p;
     const int k = s.ctrl->k_live;
     const int32_t* rs = s.row_slot + (size_t)s.ctrl->map_par * P.m;
+    const double* yp = s.yp + (size_t)s.ctrl->map_par * P.ld;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.ld; i += gridDim.x * blockDim.x) {
         double v = 0.0;
         if (i < P.m) {
             const int t = rs[i];
-            if (t < k) v = s.yp[t];
+            if (t < k) v = yp[t];
         }
         s.y[i] = v;
         s.y32[i] = (float)v;
@@ -601,7 +750,11 @@ __global__ void k_struct_init_maps(DevState s) {
 
 }  // namespace
 
-size_t iterate_s_smem_bytes(int ld) { return 2 * (size_t)ld * sizeof(double); }
+size_t iterate_s_smem_bytes(int ld) { return 3 * (size_t)ld * sizeof(double); }
+
+bool struct_engine_fits(int m, int ld, int ctas) {
+    return iterate_s_smem_bytes(ld) <= 200 * 1024 && (m + ctas - 1) / ctas <= kMaxOwnedRows;
+}
 
 int occupancy_iterate_s(int ld) {
     cudaFuncSetAttribute(k_iterate_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iterate_s_smem_bytes(ld));

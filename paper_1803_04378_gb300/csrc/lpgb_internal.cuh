@@ -101,6 +101,21 @@ struct RowPart {
     int32_t var, row, cnt, pad_;
 };
 
+// The same two records packed for 16-byte loads (k_iterate_s, where every CTA
+// reads every CTA's record after a grid barrier).
+// Values to be ordered are stored as order-preserving 64-bit integer images.
+struct alignas(16) PriceRec {
+    long long d_all, d_nt;
+    int32_t j_all, j_nt, j_min, j_pr;
+    long long d_min, d_pr;
+    int32_t k_pr, pad_[3];
+};
+struct alignas(16) RowRec {
+    long long tmin, thr;   // smallest ratio and its tie threshold
+    double a, th;          // best row: pivot element and ratio
+    int32_t var, row, cnt, pad_;
+};
+
 // Candidate triple of CHUZC (per block partial).
 struct PriceCand {
     double d_all; int32_t j_all;   // best nonbasic (optimality test, aspiration)
@@ -157,10 +172,12 @@ struct DevState {
     // the rows whose slack is nonbasic in slots [0, k_live)
     double* A_p;        // n columns of ld doubles: A with its rows in slot order
     double* bp;         // m rows of ld doubles: B^-1 columns of the live slots
-    double* yp;         // ld: y in slot order (zero outside the live slots)
+    double* yp;         // 2*ld: y in slot order (zero outside the live slots), two copies by map_par
     int32_t* slot_row;  // 2*m: slot -> row, two copies (current, next) by map_par
     int32_t* row_slot;  // 2*m: row -> slot, same two copies
     int32_t* uslot;     // m: basis position -> slot of its basic slack, or -1
+    PriceRec* price_rec;  // per-CTA CHUZC partials of k_iterate_s
+    RowRec* row_rec;      // per-CTA ratio-test records of k_iterate_s
     TraceBuf trace;
     // reinversion scratch
     int32_t* rv_struct_pos;  // k structural basis positions (increasing)
@@ -228,6 +245,7 @@ int occupancy_iterate(int ld);
 // The same on the slack-structured form of B^-1 (kernels_struct.cu).
 cudaError_t launch_iterate_s(const DevState& s, int blocks, int iters, cudaStream_t st);
 int occupancy_iterate_s(int ld);
+bool struct_engine_fits(int m, int ld, int ctas);  // shared-memory and per-CTA row limits
 // Dense state -> structured state: slot map check (rebuilt when force or
 // inconsistent, then A_p regathered), live B^-1 columns and y, start at PRICE.
 void launch_struct_enter(const DevState& s, int force, int32_t* relayout, cudaStream_t st);

@@ -568,17 +568,19 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
             }
         }
         if (h->opt.engine == LP_ENGINE_STRUCTURED && h->opt.price_mode == 0 && coop && h->geo.sms <= 1024 &&
-            occupancy_iterate_s(h->ld) >= 1) {
+            struct_engine_fits(h->m, h->ld, h->geo.sms) && occupancy_iterate_s(h->ld) >= 1) {
             const int m = h->m, n = h->n, ld = h->ld;
             TRY(dalloc(h, &s.A_p, (size_t)n * ld));
             TRY(dalloc(h, &s.bp, (size_t)m * ld));
-            TRY(dalloc(h, &s.yp, (size_t)ld));
+            TRY(dalloc(h, &s.yp, 2 * (size_t)ld));
             TRY(dalloc(h, &s.slot_row, 2 * (size_t)m));
             TRY(dalloc(h, &s.row_slot, 2 * (size_t)m));
             TRY(dalloc(h, &s.uslot, (size_t)m));
             TRY(dalloc(h, &h->s_relayout, 1));
+            TRY(dalloc(h, &s.price_rec, (size_t)h->geo.sms));
+            TRY(dalloc(h, &s.row_rec, (size_t)h->geo.sms));
             CK(cudaMemsetAsync(s.bp, 0, sizeof(double) * (size_t)m * ld, h->stream));
-            CK(cudaMemsetAsync(s.yp, 0, sizeof(double) * (size_t)ld, h->stream));
+            CK(cudaMemsetAsync(s.yp, 0, sizeof(double) * 2 * (size_t)ld, h->stream));
             launch_struct_init_maps(s, h->stream);
             CK(cudaGetLastError());
             h->structured = true;
@@ -769,7 +771,9 @@ int lp_solve(lp_handle* h, lp_result* out) {
             }
             const Ctrl before = C;
             if (h->evc0) CK(cudaEventRecord(h->evc0, h->stream));
-            const cudaError_t e = launch_iterate_s(h->ds, h->persist_blocks, h->opt.graph_iters, h->stream);
+            // one step more than graph_iters: the first step after an entry only
+            // prices and runs the ratio test, so a reinversion period fits one launch
+            const cudaError_t e = launch_iterate_s(h->ds, h->persist_blocks, h->opt.graph_iters + 1, h->stream);
             if (e == cudaSuccess) {
                 h->launches += 1;
                 if (h->evc1) CK(cudaEventRecord(h->evc1, h->stream));
