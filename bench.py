@@ -264,7 +264,7 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--price-mode", type=int, default=0, help="PRICE of the timed solves (profiling)")
-    ap.add_argument("--engine", type=int, default=0,
+    ap.add_argument("--engine", type=int, default=2,
                     help="LP_ENGINE_* of the timed solves: 0 dense persistent, 1 graphs, 2 slack-structured")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--only-batch", action="store_true", help="run only the batched leg (profiling)")
@@ -390,16 +390,22 @@ def main():
         kname, kt, kn, kb, kflops = "k_price", ps, pn, pb, 2.0 * pb / 8.0
     hbm_peak, peak_kind = _peaks()
     achieved = (kb / kn) / (kt / kn) / 1e9 if kn else None
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None,
-                "peak_source": f"{peak_kind} hbm_gbs",
-                "traffic": _traffic(kname),
-                "bytes_per_launch": kb / kn if kn else None,
-                "avg_launch_us": 1e6 * kt / kn if kn else None,
-                "share_of_step": kt / sum(r.seconds for r in results),
-                "fp64": {"achieved_tflops": kflops / kt / 1e12 if kt else None,
-                         "peak_tflops": FP64_PEAK_TFLOPS,
-                         "frac": (kflops / kt / 1e12 / FP64_PEAK_TFLOPS) if kt else None}}
+    hbm = {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+           "frac": (achieved / hbm_peak) if achieved else None, "peak_source": f"{peak_kind} hbm_gbs"}
+    fp64 = {"achieved": kflops / kt / 1e12 if kt else None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (kflops / kt / 1e12 / FP64_PEAK_TFLOPS) if kt else None,
+            "peak_source": "measured FP64 FMA issue rate (2 FMA/clock/SM)"}
+    if kname == "k_iterate_s":
+        # the live rows of A and columns of B^-1 stay in L2 across pivots: the
+        # bound is the FP64 pipe, and the HBM figure is given beside it
+        roofline = dict(bound="alu", kernel=kname, **fp64, hbm=hbm)
+    else:
+        roofline = dict(bound="hbm", kernel=kname, **hbm, fp64=fp64)
+    roofline.update({"traffic": _traffic(kname),
+                     "bytes_per_launch": kb / kn if kn else None,
+                     "flops_per_launch": kflops / kn if kn else None,
+                     "avg_launch_us": 1e6 * kt / kn if kn else None,
+                     "share_of_step": kt / sum(r.seconds for r in results)})
     chain_bytes = sum(r.bytes_moved for r in results)
     reinv_s = sum(r.reinvert_seconds for r in results)
     iter_s = sum(r.seconds for r in results) - reinv_s
@@ -432,11 +438,12 @@ def main():
     # re-priced in FP64 (same FP64 UPDATE/FTRAN/ratio test/reinversion;
     # optimality certified in FP64)
     variants = {}
-    if not args.skip_variants and args.engine != 2:
-        # variant: the slack-structured persistent engine (same pivots; only
-        # the rows whose slack is nonbasic carry PRICE and UPDATE/FTRAN work)
+    if not args.skip_variants:
+        # variant: the other persistent engine (same pivots): the dense m x m
+        # inverse when the structured one is timed, and the reverse
+        other = 0 if args.engine == 2 else 2
         At, bt, ct = (torch.from_numpy(v).cuda() for v in (A, b, c))
-        xs = dict(extra, engine=2)
+        xs = dict(extra, engine=other)
         with lpgb.LP(At, bt, ct, kernel_timing=KERNEL_TIMING_STRIDE, cuda_stream=stream.cuda_stream, **xs) as lps:
             del At, bt, ct
             lps.solve()  # warm-up
@@ -450,10 +457,10 @@ def main():
             torch.cuda.synchronize()
             ts_ = v0.elapsed_time(v1) * 1e-3
             zs_ = lps.solution()[2]
-        variants["structured_engine"] = {
+        variants["dense_engine" if other == 0 else "structured_engine"] = {
             "value": rs_.iterations / ts_, "unit": "iters/s", "time_to_optimum_s": ts_,
             "pivots_per_solve": rs_.iterations, "reinversions_per_solve": rs_.reinversions,
-            "objective": zs_, "objective_rel_err_vs_dense_engine": abs(zs_ - z) / max(1.0, abs(z)),
+            "objective": zs_, "objective_rel_err_vs_timed_engine": abs(zs_ - z) / max(1.0, abs(z)),
             "reinversion_seconds": rs_.reinvert_seconds,
             "us_per_pivot_excl_reinversion": 1e6 * (ts_ - rs_.reinvert_seconds) / max(1, rs_.iterations),
             "chain_seconds": rs_.chain_seconds, "chain_launches": rs_.chain_launches,
@@ -502,7 +509,13 @@ def main():
             "config": {"workload": WORKLOAD["name"], "m": m, "n": n, "seed": WORKLOAD["seed"],
                        "A": "U[0,1) with 10% zeros", "reinvert_every": 64, "tabu_tenure": 7,
                        "step": "one full solve from the slack basis to optimality",
-                       "l2": "no flush: A (268 MB) + B^-1 (134 MB) streamed every pivot exceed L2",
+                       "l2": ("no flush: the inputs (A 268 MB, its slot-ordered copy 268 MB, B^-1 134 MB) exceed "
+                              "L2 and every step's reset rebuilds the slot-ordered copy; within a solve the "
+                              "structured engine keeps its live rows and columns L2-resident by design"
+                              if results[0].persistent == 2 else
+                              "no flush: A (268 MB) + B^-1 (134 MB) streamed every pivot exceed L2"),
+                       "engine": {2: "slack-structured persistent", 1: "dense persistent",
+                                  0: "captured graphs"}[results[0].persistent],
                        "parallelism": f"replicas x{ws}"},
             "time_to_optimum_s": elapsed / args.steps,
             "pivots_per_solve": results[0].iterations,

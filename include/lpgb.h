@@ -73,6 +73,7 @@ typedef struct lp_handle lp_handle;
  * Options.  lp_default_options() fills the method's settings:
  * reinvert_every 64, tabu_tenure 7, bland_after 50, max_iters 50,000,000,
  * price_mode 0, topk 16, trace_cap 0, graph_iters 64, kernel_timing 0,
+ * engine LP_ENGINE_STRUCTURED (LP_ENGINE_DENSE where it does not fit),
  * tol_d 1e-9, tol_piv 1e-9, tol_tie 1e-12, cuda_stream NULL.
  */
 typedef struct lp_options {

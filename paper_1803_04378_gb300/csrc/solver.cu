@@ -377,7 +377,7 @@ void lp_default_options(lp_options* o) {
     o->trace_cap = 0;
     o->graph_iters = 64;
     o->kernel_timing = 0;
-    o->engine = 0;
+    o->engine = LP_ENGINE_STRUCTURED;
     o->tol_d = 1e-9;
     o->tol_piv = 1e-9;
     o->tol_tie = 1e-12;
