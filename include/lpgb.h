@@ -57,6 +57,15 @@ extern "C" {
 #define LP_TF_TIE_SET 64        /* the ratio test had more than one tied row */
 #define LP_TF_GUIDED 128        /* the entering variable came from lp_set_priority */
 
+/* lp_options.anticycling. */
+#define LP_ANTICYCLING_TABU 0           /* CHUZC masks tabu variables, the tie set's largest alpha
+                                           leaves, Bland safety net after bland_after degenerate
+                                           pivots (the method) */
+#define LP_ANTICYCLING_LEXICOGRAPHIC 1  /* no tabu list and no safety net; the tie set's row whose
+                                           row of B^-1 / alpha_i is lexicographically smallest
+                                           leaves (entries within tol_tie relative count as equal);
+                                           runs on the captured-graph engine */
+
 /* lp_options.engine: how the pivots of price_mode 0 run. */
 #define LP_ENGINE_DENSE 0       /* persistent cooperative kernel on the m x m B^-1, graph_iters
                                    pivots per launch: PRICE reads all of A, UPDATE all of B^-1 */
@@ -74,6 +83,7 @@ typedef struct lp_handle lp_handle;
  * reinvert_every 64, tabu_tenure 7, bland_after 50, max_iters 50,000,000,
  * price_mode 0, topk 16, trace_cap 0, graph_iters 64, kernel_timing 0,
  * engine LP_ENGINE_STRUCTURED (LP_ENGINE_DENSE where it does not fit),
+ * anticycling LP_ANTICYCLING_TABU,
  * tol_d 1e-9, tol_piv 1e-9, tol_tie 1e-12, cuda_stream NULL.
  */
 typedef struct lp_options {
@@ -92,6 +102,8 @@ typedef struct lp_options {
                                timed pivots run without launch overlap */
     int32_t engine;         /* LP_ENGINE_*: how the pivots of price_mode 0 run (captured
                                CUDA graphs wherever the device refuses a cooperative launch) */
+    int32_t anticycling;    /* LP_ANTICYCLING_*: the tabu rule of Sections 2.2/3.4 (default) or
+                               the lexicographic rule it is compared with */
     double tol_d;           /* optimality tolerance on the reduced costs */
     double tol_piv;         /* smallest admissible pivot alpha_r */
     double tol_tie;         /* relative width of the ratio-test tie set */

@@ -105,11 +105,15 @@ def _p(a):
     return None if a is None else a.ctypes.data
 
 
+RATIO_LARGEST_ALPHA, RATIO_SMALLEST_INDEX, RATIO_LEXICOGRAPHIC = 0, 1, 2
+
+
 @dataclass
 class Options:
     """Solver options; the defaults are the method's settings: reinversion
     every 64 iterations, tabu tenure 7, Bland fallback after 50 consecutive
-    degenerate pivots, tolerances 1e-9 / 1e-9 / 1e-12."""
+    degenerate pivots, tolerances 1e-9 / 1e-9 / 1e-12.  ratio_rule: the
+    leaving row among the ratio-test tie set (RATIO_*)."""
     reinvert_every: int = 64
     tabu_tenure: int = 7
     max_iters: int = 1_000_000
@@ -120,6 +124,16 @@ class Options:
     tol_piv: float = 1e-9
     tol_tie: float = 1e-12
     tie_cmp: float = 1e-12
+
+
+def lexicographic_options(**kw) -> "Options":
+    """The lexicographic anti-cycling rule in place of the tabu rule: the
+    leaving row is the lexicographically smallest row of B^-1 / alpha_i in the
+    tie set; no tabu list and no Bland safety net."""
+    kw.setdefault("ratio_rule", RATIO_LEXICOGRAPHIC)
+    kw.setdefault("tabu_tenure", 0)
+    kw.setdefault("bland_after", 0)
+    return Options(**kw)
 
 
 @dataclass

@@ -44,6 +44,15 @@
  * basis columns by Gauss-Jordan elimination with partial pivoting, and bbar,
  * y and z are recomputed from it.  (The paper only updates; periodic
  * reinversion is an addition of this design.)
+ * Lexicographic rule (ratio_rule 2; the textbook anti-cycling rule the
+ * paper's tabu rule is compared with, Sections 2.2 and 3.4): among the tie set
+ * T the leaving row is the one whose row of B^-1 divided by alpha_i is
+ * lexicographically smallest, columns compared in increasing order; two
+ * entries count as equal when they differ by at most tol_tie times the
+ * larger of 1 and their magnitudes (an exact zero of the update and its
+ * reinverted counterpart must not decide).  Rows of a nonsingular B^-1 are
+ * independent, so the rule always decides.  Callers switch the tabu list
+ * and the safety net off with it.
  * Cycling safety net: after `bland_after` consecutive degenerate pivots both
  * rules become Bland's (entering: smallest improving index, tabu ignored;
  * leaving: smallest basic variable index in the tie set) until the next
@@ -86,7 +95,8 @@ typedef struct {
     int32_t tabu_tenure;    /* 0 = tabu rule off */
     int32_t max_iters;
     int32_t bland_after;    /* 0 = no Bland fallback */
-    int32_t ratio_rule;     /* 0 = largest alpha in the tie set, 1 = smallest basic index */
+    int32_t ratio_rule;     /* 0 = largest alpha in the tie set, 1 = smallest basic index,
+                               2 = lexicographic (rows of B^-1 / alpha_i) */
     int32_t follow_relaxed; /* follow mode: accept any improving eligible entering column */
     double tol_d, tol_piv, tol_tie;
     double tie_cmp;         /* follow mode: relative tie window (1e-12) */
@@ -179,6 +189,21 @@ void oracle_reduced_costs(int m, int n, const double* A, const double* c, const 
 }
 
 static double cost(int n, const double* c, int j) { return j < n ? c[j] : 0.0; }
+
+/* Lexicographic comparison of rows i and r of B^-1, each divided by its
+ * alpha: -1 if row i comes first, +1 if row r does, 0 if every column is equal
+ * within tau (relative to the larger of 1 and the two magnitudes). */
+static int lex_cmp(const double* Binv, int m, const double* alpha, int i, int r, double tau) {
+    const double* bi = Binv + (size_t)i * m;
+    const double* br = Binv + (size_t)r * m;
+    for (int c = 0; c < m; ++c) {
+        double vi = bi[c] / alpha[i], vr = br[c] / alpha[r];
+        double sc = dmax(1.0, dmax(fabs(vi), fabs(vr)));
+        if (fabs(vi - vr) <= tau * sc) continue;
+        return vi < vr ? -1 : 1;
+    }
+    return 0;
+}
 
 /* Rebuild B^-1, bbar, y and z from the basis. */
 static int reinvert(int m, int n, const double* A, const double* b, const double* c,
@@ -385,6 +410,9 @@ int oracle_solve(int m, int n, const double* A, const double* b, const double* c
                 if (r < 0) { r = i; continue; }
                 if (o->ratio_rule == 1 || bland) {
                     if (basis[i] < basis[r]) r = i;
+                } else if (o->ratio_rule == 2) {
+                    int cmp = lex_cmp(Binv, m, alpha, i, r, o->tol_tie);
+                    if (cmp < 0 || (cmp == 0 && basis[i] < basis[r])) r = i;
                 } else if (alpha[i] > alpha[r] || (alpha[i] == alpha[r] && basis[i] < basis[r])) {
                     r = i;
                 }
@@ -395,7 +423,8 @@ int oracle_solve(int m, int n, const double* A, const double* b, const double* c
             for (int i = 0; i < m; ++i) {
                 if (i == r || !(alpha[i] > o->tol_piv)) continue;
                 double sep;
-                if (theta[i] <= thr) sep = (alpha[r] - alpha[i]) / dmax(1.0, alpha[r]);
+                if (theta[i] <= thr && o->ratio_rule == 2) sep = INFINITY;  /* lexicographic: no alpha margin */
+                else if (theta[i] <= thr) sep = (alpha[r] - alpha[i]) / dmax(1.0, alpha[r]);
                 else sep = (theta[i] - thr) / dmax(1.0, fabs(tmin));
                 if (sep < margin_r) margin_r = sep;
             }
@@ -433,6 +462,8 @@ int oracle_solve(int m, int n, const double* A, const double* b, const double* c
                     int r_border = theta[r] >= thr - eps * sc;
                     int a_tie = alpha[fr] >= alpha[r] - eps * dmax(1.0, alpha[r]);
                     if (o->ratio_rule == 1 || bland) a_tie = 1;
+                    /* lexicographic: fr may not come after r beyond the follow tolerance */
+                    if (o->ratio_rule == 2) a_tie = lex_cmp(Binv, m, alpha, fr, r, eps) <= 0;
                     if (!(a_tie || r_border)) ok = 0;
                     if (ok) theta[fr] = th;
                 }

@@ -257,6 +257,40 @@ __device__ double update_block(const DevState& s, int r, bool do_upd, bool do_ft
 }
 
 // block minimum (result in thread 0)
+// Lexicographic comparison of rows i and r of B^-1, each divided by its alpha
+// (alpha' of the current FTRAN), by one warp: -1 if row i comes first, +1 if
+// row r does, 0 if every column is equal within tau relative (the result in
+// every lane).  64 columns per round trip; a column where both entries are
+// zero is passed on integer tests, the others are compared as x_i a_r vs
+// x_r a_i (both alphas are positive), so no division runs on the FP64 pipe.
+__device__ int lex_cmp_warp(const DevState& s, const double* anxt, int i, int r, double tau) {
+    const int lane = threadIdx.x & 31;
+    const double ai = __ldcg(anxt + i), ar = __ldcg(anxt + r);
+    const double2* bi = reinterpret_cast<const double2*>(s.binv + (size_t)i * s.p.ld);
+    const double2* br = reinterpret_cast<const double2*>(s.binv + (size_t)r * s.p.ld);
+    const double aa = ai * ar;
+    for (int c0 = 0; c0 < s.p.m; c0 += 64) {
+        const double2 xi = __ldcg(bi + (c0 >> 1) + lane), xr = __ldcg(br + (c0 >> 1) + lane);
+        int code = 0;  // 1 + element index of the first difference; sign in bit 2
+#pragma unroll
+        for (int e = 1; e >= 0; --e) {
+            const double x = e ? xi.y : xi.x, y = e ? xr.y : xr.x;
+            const bool zz = ((__double_as_longlong(x) | __double_as_longlong(y)) << 1) == 0;
+            if (!zz) {
+                const double u = x * ar, v = y * ai;
+                if (fabs(u - v) > tau * fmax(aa, fmax(fabs(u), fabs(v)))) code = (e + 1) | (u < v ? 4 : 0);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, code != 0);
+        if (bal) {
+            const int src = __ffs(bal) - 1;
+            const int cd = __shfl_sync(0xffffffffu, code, src);
+            return (cd & 4) ? -1 : 1;
+        }
+    }
+    return 0;
+}
+
 // ---- k_update: B^-1 update + FTRAN + ratio test -------------------------------------
 __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
     pdl_enter();
@@ -345,7 +379,39 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
             }
         }
     }
-    const RowCand b = block_row_best(best, cnt, bland);
+    RowCand b = block_row_best(best, cnt, bland);
+    if (P.lex) {
+        // Lexicographic rule: the tie set's row of B^-1 / alpha_i that is
+        // lexicographically smallest leaves; a pairwise tournament over the
+        // tied rows (listed in lex_rows), exact ties to the smaller basic index.
+        __shared__ int lex_n;
+        if (threadIdx.x == 0) lex_n = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < P.m; i += blockDim.x) {
+            const double al = __ldcg(anxt + i), th = __ldcg(s.theta + i);
+            if (al > P.tol_piv && th <= thr) s.lex_rows[atomicAdd(&lex_n, 1)] = i;
+        }
+        __syncthreads();
+        const int nt = lex_n;
+        if (nt > 1) {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            for (int w = 1; w < nt; w *= 2) {
+                for (int e = warp * 2 * w; e + w < nt; e += nw * 2 * w) {
+                    const int i = __ldcg(s.lex_rows + e), r2 = __ldcg(s.lex_rows + e + w);
+                    const int cmp = lex_cmp_warp(s, anxt, i, r2, P.tol_tie);
+                    if (lane == 0 && (cmp > 0 || (cmp == 0 && s.basis[r2] < s.basis[i]))) s.lex_rows[e] = r2;
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                const int rr = __ldcg(s.lex_rows);
+                b.row = rr;
+                b.a = __ldcg(anxt + rr);
+                b.th = __ldcg(s.theta + rr);
+                b.var = s.basis[rr];
+            }
+        }
+    }
     if (threadIdx.x == 0) {
         C->ticket_update = 0;
         C->pending = 0;

@@ -52,6 +52,7 @@ struct Params {
     double b_scale;        // max(1, max_i b_i): scale of the feasibility check
     int32_t price_mode;    // 0: FP64 PRICE; 1: BF16 screen + FP64 re-price of the top k
     int32_t topk;          // candidates re-priced in FP64 (price_mode 1), <= kMaxTopk
+    int32_t lex;           // 1: lexicographic leaving rule (no tabu list, no safety net)
 };
 
 constexpr int kMaxTopk = 32;
@@ -167,6 +168,7 @@ struct DevState {
     double* upd_part;   // per-block theta minima
     RowPart* row_part;  // k_iterate: per-CTA ratio-test record
     int32_t* row_var;   // m: basic variable of each row as seen by the last FTRAN (k_iterate)
+    int32_t* lex_rows;  // m: rows of the ratio-test tie set (lexicographic rule)
     uint32_t* gbar;     // k_iterate grid barrier: arrivals, released epoch
     // slack-structured engine (k_iterate_s): the constraint rows in slot order,
     // the rows whose slack is nonbasic in slots [0, k_live)

@@ -378,6 +378,7 @@ void lp_default_options(lp_options* o) {
     o->graph_iters = 64;
     o->kernel_timing = 0;
     o->engine = LP_ENGINE_STRUCTURED;
+    o->anticycling = LP_ANTICYCLING_TABU;
     o->tol_d = 1e-9;
     o->tol_piv = 1e-9;
     o->tol_tie = 1e-12;
@@ -478,6 +479,12 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     P.tol_tie = h->opt.tol_tie;
     P.price_mode = h->opt.price_mode;
     P.topk = h->opt.topk;
+    P.lex = h->opt.anticycling == LP_ANTICYCLING_LEXICOGRAPHIC ? 1 : 0;
+    if (P.lex) {
+        // the lexicographic rule needs neither the tabu list nor the safety net
+        P.tabu_tenure = 0;
+        P.bland_after = 0;
+    }
     s.p = P;
 
     double *A_cm, *cc, *bb, *binv, *bbar, *y, *rho, *alpha, *theta, *upd_part, *rv_M, *rv_f;
@@ -530,6 +537,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &s.lp_part, (size_t)parts));
     TRY(dalloc(h, &upd_part, (size_t)parts));
     TRY(dalloc(h, &s.row_var, (size_t)m));
+    TRY(dalloc(h, &s.lex_rows, (size_t)m));
     TRY(dalloc(h, &s.row_part, (size_t)parts));
     TRY(dalloc(h, &s.gbar, 2));
     if (P.trace_cap > 0) {
@@ -558,7 +566,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
         // (k_iterate's ratio test holds one CTA partial per thread: at most 1024 CTAs)
-        if (h->opt.engine == 0 && h->opt.price_mode == 0 && coop && h->geo.sms <= 1024 &&
+        if (h->opt.engine == 0 && h->opt.price_mode == 0 && !P.lex && coop && h->geo.sms <= 1024 &&
             occupancy_iterate(h->ld) >= 1) {
             h->persist = true;
             h->persist_blocks = h->geo.sms;  // the partial arrays hold at least sms entries
@@ -567,7 +575,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
                 CK(cudaEventCreate(&h->evc1));
             }
         }
-        if (h->opt.engine == LP_ENGINE_STRUCTURED && h->opt.price_mode == 0 && coop && h->geo.sms <= 1024 &&
+        if (h->opt.engine == LP_ENGINE_STRUCTURED && h->opt.price_mode == 0 && !P.lex && coop && h->geo.sms <= 1024 &&
             struct_engine_fits(h->m, h->ld, h->geo.sms) && occupancy_iterate_s(h->ld) >= 1) {
             const int m = h->m, n = h->n, ld = h->ld;
             TRY(dalloc(h, &s.A_p, (size_t)n * ld));
@@ -605,7 +613,7 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     lp_options o;
     lp_default_options(&o);
     if (opt) o = *opt;
-    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > LP_ENGINE_STRUCTURED || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
+    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > LP_ENGINE_STRUCTURED || o.anticycling < 0 || o.anticycling > 1 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
         o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 1 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {

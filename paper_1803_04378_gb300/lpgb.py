@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "running", 1: "optimal", 2: "unbounded", 3: "iter_limit", 4: 
 LP_TF_DEGENERATE, LP_TF_TABU_PUSH, LP_TF_ASPIRATION, LP_TF_BLAND, LP_TF_TIE_SET = 1, 2, 4, 8, 64
 LP_TF_GUIDED = 128
 LP_ENGINE_DENSE, LP_ENGINE_GRAPH, LP_ENGINE_STRUCTURED = 0, 1, 2
+LP_ANTICYCLING_TABU, LP_ANTICYCLING_LEXICOGRAPHIC = 0, 1
 
 
 class lp_options(ctypes.Structure):
@@ -37,6 +38,7 @@ class lp_options(ctypes.Structure):
                 ("price_mode", ctypes.c_int32), ("topk", ctypes.c_int32),
                 ("trace_cap", ctypes.c_int32), ("graph_iters", ctypes.c_int32),
                 ("kernel_timing", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("anticycling", ctypes.c_int32),
                 ("tol_d", ctypes.c_double), ("tol_piv", ctypes.c_double),
                 ("tol_tie", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
 
