@@ -92,7 +92,10 @@ typedef struct lp_options {
     int32_t max_iters;      /* iteration limit */
     int32_t bland_after;    /* consecutive degenerate pivots before Bland's rule (0: off) */
     int32_t price_mode;     /* 0: FP64 PRICE; 1: BF16 screen, the screened best columns
-                               re-priced in FP64, full FP64 PRICE whenever none improves */
+                               re-priced in FP64, full FP64 PRICE whenever none improves
+                               (captured-graph engine); 2: FP64 PRICE over a compressed
+                               sparse column copy of A, built on the device (dense
+                               engines; extra device memory 12 m n bytes) */
     int32_t topk;           /* price_mode 1: columns re-priced per screening block (1 or 2;
                                larger values act as 2); batches: candidates per LP (1..8) */
     int32_t trace_cap;      /* record (q, r, theta, d_q, flags) of the first trace_cap pivots */

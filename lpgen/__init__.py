@@ -194,6 +194,9 @@ WORKLOADS = {
     "dense_int_200x200": dict(kind="int", m=200, n=200, seed=0),
     "dense_real_4096x8192": dict(kind="real", m=4096, n=8192, seed=1),
     "degenerate_2048x4096": dict(kind="degenerate", m=2048, n=4096, seed=2),
+    # the paper's sparser dense classes (its S20/S60 problems have 20% and 60% zeros)
+    "s20_4096x8192": dict(kind="s20", m=4096, n=8192, seed=1),
+    "s60_4096x8192": dict(kind="s60", m=4096, n=8192, seed=1),
     "batch_4096_small": dict(kind="batch", count=4096, seed=3),
     "warm_family_1024x2048": dict(kind="warm", m=1024, n=2048, seed=4),
 }
@@ -210,4 +213,8 @@ def make(kind: str, m: int, n: int, seed: int):
         return degenerate_lp(m, n, seed)
     if kind == "warm":
         return dense_real_lp(m, n, seed)
+    if kind == "s20":
+        return dense_real_lp(m, n, seed, zero_frac=0.2)
+    if kind == "s60":
+        return dense_real_lp(m, n, seed, zero_frac=0.6)
     raise ValueError(f"unknown LP kind {kind!r}")

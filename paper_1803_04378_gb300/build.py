@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(BUILD, "liblpgb.so")
-SOURCES = ["kernels_iter.cu", "kernels_struct.cu", "kernels_reinv.cu", "kernels_setup.cu", "kernels_price_lp.cu", "solver.cu",
+SOURCES = ["kernels_iter.cu", "kernels_struct.cu", "kernels_sparse.cu", "kernels_reinv.cu", "kernels_setup.cu", "kernels_price_lp.cu", "solver.cu",
            "price_static.cu", "batch.cu", "mlp.cu",
            "family.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

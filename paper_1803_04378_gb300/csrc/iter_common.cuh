@@ -213,6 +213,46 @@ __device__ __forceinline__ int patched_tabu(const DevState& s, const PricePatch&
     return j == pp.tabu_j ? pp.tabu_until : __ldcg(s.tabu_until + j);
 }
 
+// Lists, in order, the nonbasic columns among the block's owned columns
+// lb .. lb+kPriceThreads-1 (block b owns j = b, b+G, ...), with their cost,
+// tabu expiry and priority, all loaded in the same round trip.  Returns the
+// count; ends with a block barrier.
+__device__ int list_nonbasic(const DevState& s, const PricePatch& pp, int lb, int owned, int* jl, double* jc,
+                             int* jt, int* jr, int* wcnt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int G = gridDim.x;
+    const int l = lb + (int)threadIdx.x;
+    const int jj = (int)blockIdx.x + G * l;
+    bool nb = false;
+    double cj = 0.0;
+    int tj = 0, rj = kNoRank;
+    if (l < owned) {
+        const int pj = __ldcg(s.pos + jj);
+        cj = s.c[jj];
+        tj = patched_tabu(s, pp, jj);
+        rj = s.rank[jj];
+        nb = jj == pp.basic_j ? false : (jj == pp.free_j ? true : pj < 0);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, nb);
+    if (lane == 0) wcnt[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, cnt = 0;
+    for (int w = 0; w < kPriceThreads / 32; ++w) {
+        const int cw = wcnt[w];
+        if (w < warp) before += cw;
+        cnt += cw;
+    }
+    if (nb) {
+        const int e = before + __popc(bal & ((1u << lane) - 1u));
+        jl[e] = jj;
+        jc[e] = cj;
+        jt[e] = tj;
+        jr[e] = rj;
+    }
+    __syncthreads();
+    return cnt;
+}
+
 // ysh holds y; each column j contributes its first 2*len_half rows of Acol
 // (column stride ld; kL2: read through L2).  pos and tabu_until, which the
 // bookkeeping of a persistent launch writes from another block, are read
@@ -270,36 +310,7 @@ __device__ Cand price_block(const DevState& s, int it, const double* ysh, const 
     const int k0 = 32 * (seg * nch / kSeg), k1 = 32 * ((seg + 1) * nch / kSeg);
     const double2* A2 = reinterpret_cast<const double2*>(Acol);
     for (int lb = 0; lb < owned; lb += kPriceThreads) {
-        // list the nonbasic owned columns lb .. lb+kPriceThreads-1, in order
-        const int l = lb + (int)threadIdx.x;
-        const int jj = (int)blockIdx.x + G * l;
-        bool nb = false;
-        double cj = 0.0;
-        int tj = 0, rj = kNoRank;
-        if (l < owned) {
-            const int pj = __ldcg(s.pos + jj);
-            cj = s.c[jj];
-            tj = patched_tabu(s, pp, jj);
-            rj = s.rank[jj];
-            nb = jj == pp.basic_j ? false : (jj == pp.free_j ? true : pj < 0);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, nb);
-        if (lane == 0) wcnt[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, cnt = 0;
-        for (int w = 0; w < kPriceThreads / 32; ++w) {
-            const int cw = wcnt[w];
-            if (w < warp) before += cw;
-            cnt += cw;
-        }
-        if (nb) {
-            const int e = before + __popc(bal & ((1u << lane) - 1u));
-            jl[e] = jj;
-            jc[e] = cj;
-            jt[e] = tj;
-            jr[e] = rj;
-        }
-        __syncthreads();
+        const int cnt = list_nonbasic(s, pp, lb, owned, jl, jc, jt, jr, wcnt);
         // Groups of 4 listed columns, and of 3 where cnt is not a multiple of 4,
         // so that every warp streams 3 or 4 columns at a time (a lone column
         // would run latency-bound long after the others); only lists shorter
@@ -397,6 +408,54 @@ __device__ Cand price_block(const DevState& s, int it, const double* ysh, const 
             j = P.n + row;
         }
         if (!slack_rows && (j == pp.basic_j ? true : (j == pp.free_j ? false : __ldcg(s.pos + j) >= 0))) continue;
+        cand_offer(cand, -ysh[i], j, patched_tabu(s, pp, j) <= it, ktol, s.rank[j]);
+    }
+    return cand_block_reduce(cand);
+}
+
+// PRICE of the block's columns from the compressed sparse column copy of A
+// (price_mode 2): each warp takes one listed column at a time and its lanes
+// stride over the column's nonzeros (four independent loads in flight per
+// lane), gathering y by row index from shared memory; the lane sums are added
+// in a fixed order.  Slack candidates as in price_block.
+__device__ Cand price_block_csc(const DevState& s, int it, const double* ysh, const PricePatch& pp) {
+    const Params& P = s.p;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int G = gridDim.x;
+    const long long ktol = dkey(P.tol_d);
+    __shared__ int jl[kPriceThreads];
+    __shared__ double jc[kPriceThreads];
+    __shared__ int jt[kPriceThreads], jr[kPriceThreads];
+    __shared__ int wcnt[kPriceThreads / 32];
+    Cand cand;
+    cand_init(cand);
+    const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
+    for (int lb = 0; lb < owned; lb += kPriceThreads) {
+        const int cnt = list_nonbasic(s, pp, lb, owned, jl, jc, jt, jr, wcnt);
+        for (int e = warp; e < cnt; e += nw) {
+            const int j = jl[e];
+            const long long p0 = __ldg(s.csc_ptr + j), p1 = __ldg(s.csc_ptr + j + 1);
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            long long p = p0 + lane;
+            for (; p + 96 < p1; p += 128) {
+                const int r0 = __ldg(s.csc_row + p), r1 = __ldg(s.csc_row + p + 32);
+                const int r2 = __ldg(s.csc_row + p + 64), r3 = __ldg(s.csc_row + p + 96);
+                const double v0 = __ldg(s.csc_val + p), v1 = __ldg(s.csc_val + p + 32);
+                const double v2 = __ldg(s.csc_val + p + 64), v3 = __ldg(s.csc_val + p + 96);
+                a0 = fma(v0, ysh[r0], a0);
+                a1 = fma(v1, ysh[r1], a1);
+                a2 = fma(v2, ysh[r2], a2);
+                a3 = fma(v3, ysh[r3], a3);
+            }
+            for (; p < p1; p += 32) a0 = fma(__ldg(s.csc_val + p), ysh[__ldg(s.csc_row + p)], a0);
+            const double t = pair_sum((a0 + a1) + (a2 + a3));
+            if (lane == 0) cand_offer(cand, jc[e] - t, j, jt[e] <= it, ktol, jr[e]);
+        }
+        __syncthreads();  // the list is rebuilt for the next round
+    }
+    for (int i = blockIdx.x + G * threadIdx.x; i < P.m; i += G * blockDim.x) {
+        const int j = P.n + i;
+        if (j == pp.basic_j ? true : (j == pp.free_j ? false : __ldcg(s.pos + j) >= 0)) continue;
         cand_offer(cand, -ysh[i], j, patched_tabu(s, pp, j) <= it, ktol, s.rank[j]);
     }
     return cand_block_reduce(cand);

@@ -147,14 +147,14 @@ __global__ void __launch_bounds__(kPriceThreads, 1) k_price(DevState s) {
     extern __shared__ double ysh[];
     for (int k = threadIdx.x; k < P.ld; k += blockDim.x) ysh[k] = s.y[k];
     __syncthreads();
-    const Cand bc = price_block(s, C->it, ysh, s.A_cm, P.ld >> 1, nullptr, P.m, no_patch());
+    const Cand bc = (P.price_mode == 2 ? price_block_csc(s, C->it, ysh, no_patch()) : price_block(s, C->it, ysh, s.A_cm, P.ld >> 1, nullptr, P.m, no_patch()));
     if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
     if (!is_last_block(&C->ticket_price)) return;
     // last block: reduce all partials and decide
     const Cand g = reduce_price_parts(s.price_part, gridDim.x);
     if (threadIdx.x == 0) {
         C->ticket_price = 0;
-        C->bytes_price += 8.0 * P.m * (double)(P.n - C->nsb);
+        C->bytes_price += (P.price_mode == 2 ? 12.0 * P.nnz / P.n : 8.0 * P.m) * (double)(P.n - C->nsb);
         C->n_price++;
         if (P.price_mode == 1) {
             C->need_full = 0;
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
             }
             rh_staged = stage_rh;
             __syncthreads();
-            const Cand bc = price_block(s, S.it, sh, s.A_cm, P.ld >> 1, nullptr, P.m, no_patch());
+            const Cand bc = (P.price_mode == 2 ? price_block_csc(s, S.it, sh, no_patch()) : price_block(s, S.it, sh, s.A_cm, P.ld >> 1, nullptr, P.m, no_patch()));
             if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             const Cand g = reduce_price_parts(s.price_part, G);
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
                     S.flags |= d.flags;
                 }
                 if (lead) {
-                    S.bytes_price += 8.0 * P.m * (double)(P.n - S.nsb);
+                    S.bytes_price += (P.price_mode == 2 ? 12.0 * P.nnz / P.n : 8.0 * P.m) * (double)(P.n - S.nsb);
                     S.n_price++;
                     S.n_asp += d.asp;
                 }

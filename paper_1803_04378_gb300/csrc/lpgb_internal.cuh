@@ -53,6 +53,7 @@ struct Params {
     int32_t price_mode;    // 0: FP64 PRICE; 1: BF16 screen + FP64 re-price of the top k
     int32_t topk;          // candidates re-priced in FP64 (price_mode 1), <= kMaxTopk
     int32_t lex;           // 1: lexicographic leaving rule (no tabu list, no safety net)
+    double nnz;            // price_mode 2: nonzeros of A
 };
 
 constexpr int kMaxTopk = 32;
@@ -149,6 +150,9 @@ struct DevState {
     const uint16_t* A_lp;    // price_mode 1: BF16 copy of A_cm (same layout)
     float* y32;              // FP32 copy of y (ld), for the BF16 screen
     LpCand* lp_part;         // per-block screen partials
+    const int64_t* csc_ptr;  // price_mode 2: n+1 column starts of the sparse copy of A
+    const int32_t* csc_row;  // its row indices (increasing within a column)
+    const double* csc_val;   // its values
     int32_t* cand;           // kMaxTopk candidate columns (-1 = none)
     double* cand_d;          // their exact reduced costs
     const double* c;
@@ -258,6 +262,12 @@ int barrier_selftest(int blocks, cudaStream_t st);
 size_t price_smem_bytes(int ld);
 size_t update_smem_bytes(int ld);
 void configure_iter_kernels(int ld);
+
+// ---- sparse copy of A (kernels_sparse.cu) ----------------------------------------
+// cnt: n int32 scratch; ptr: n+1 column starts (ptr[n] = nonzeros).
+void launch_csc_count(const double* A_cm, int m, int n, int ld, int32_t* cnt, int64_t* ptr, cudaStream_t st);
+void launch_csc_fill(const double* A_cm, int m, int n, int ld, const int64_t* ptr, int32_t* row, double* val,
+                     cudaStream_t st);
 
 // ---- reinversion (kernels_reinv.cu) -------------------------------------------
 void launch_reinv_classify(const DevState& s, cudaStream_t st);

@@ -50,6 +50,7 @@ struct lp_handle {
                                      // B^-1 and y are stale while it is
     bool s_force = true;             // rebuild the slot map and A_p on the next entry
     int32_t* s_relayout = nullptr;   // device flag: the entry rebuilt the slot map
+    int32_t* csc_cnt = nullptr;      // price_mode 2: per-column nonzero counts (scratch)
     double chain_s = 0.0, chain_b = 0.0;
     int chain_n = 0;
     double reinvert_seconds = 0.0;
@@ -425,6 +426,17 @@ static int upload_problem(lp_handle* h, const double* A, const double* b, const 
     CK(cudaMemsetAsync(flag, 0, sizeof(int32_t), h->stream));
     launch_validate(A_cm, bb, cc, m, n, ld, flag, h->stream);
     if (P.price_mode == 1) launch_to_bf16(A_cm, const_cast<uint16_t*>(s.A_lp), (size_t)n * ld, h->stream);
+    if (P.price_mode == 2) {
+        // sparse copy of A: counts and column starts, then the nonzeros
+        launch_csc_count(A_cm, m, n, ld, h->csc_cnt, const_cast<int64_t*>(s.csc_ptr), h->stream);
+        launch_csc_fill(A_cm, m, n, ld, s.csc_ptr, const_cast<int32_t*>(s.csc_row), const_cast<double*>(s.csc_val),
+                        h->stream);
+        int64_t nnz = 0;
+        CK(cudaMemcpyAsync(&nnz, s.csc_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        P.nnz = (double)nnz;
+        s.p = P;
+    }
     int32_t hflag = 0;
     CK(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -524,6 +536,19 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &s.y32, (size_t)ld));
     TRY(dalloc(h, &s.cand, (size_t)kMaxTopk + 1));
     TRY(dalloc(h, &s.cand_d, (size_t)kMaxTopk + 1));
+    if (P.price_mode == 2) {
+        // capacity for a fully dense A, so the captured graphs' pointers never change
+        int64_t* ptr = nullptr;
+        int32_t* row = nullptr;
+        double* val = nullptr;
+        TRY(dalloc(h, &ptr, (size_t)n + 1));
+        TRY(dalloc(h, &row, (size_t)m * n));
+        TRY(dalloc(h, &val, (size_t)m * n));
+        TRY(dalloc(h, &h->csc_cnt, (size_t)n));
+        s.csc_ptr = ptr;
+        s.csc_row = row;
+        s.csc_val = val;
+    }
     if (P.price_mode == 1) {
         uint16_t* lp = nullptr;
         TRY(dalloc(h, &lp, (size_t)n * ld));
@@ -560,21 +585,15 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(upload_problem(h, A, b, c, on_device));
     TRY(reset_state(h));
     TRY(capture_graph(h));
-    // persistent engine: price_mode 0 on a device that runs cooperative launches
-    // with one 1024-thread CTA on every SM
+    // Persistent engines.  The slack-structured one when asked for (the
+    // default) and it fits: price_mode 0, the tabu rule, a device that runs
+    // cooperative launches with one 1024-thread CTA on every SM.  Otherwise
+    // the dense one, unless captured graphs are asked for or the mode needs
+    // them (the BF16 screen, the lexicographic tie-break).
     {
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
-        // (k_iterate's ratio test holds one CTA partial per thread: at most 1024 CTAs)
-        if (h->opt.engine == 0 && h->opt.price_mode == 0 && !P.lex && coop && h->geo.sms <= 1024 &&
-            occupancy_iterate(h->ld) >= 1) {
-            h->persist = true;
-            h->persist_blocks = h->geo.sms;  // the partial arrays hold at least sms entries
-            if (h->opt.kernel_timing > 0) {
-                CK(cudaEventCreate(&h->evc0));
-                CK(cudaEventCreate(&h->evc1));
-            }
-        }
+        // (the ratio tests hold one CTA record per thread: at most 1024 CTAs)
         if (h->opt.engine == LP_ENGINE_STRUCTURED && h->opt.price_mode == 0 && !P.lex && coop && h->geo.sms <= 1024 &&
             struct_engine_fits(h->m, h->ld, h->geo.sms) && occupancy_iterate_s(h->ld) >= 1) {
             const int m = h->m, n = h->n, ld = h->ld;
@@ -594,10 +613,14 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
             h->structured = true;
             h->persist_blocks = h->geo.sms;
             h->s_force = true;
-            if (h->opt.kernel_timing > 0 && !h->evc0) {
-                CK(cudaEventCreate(&h->evc0));
-                CK(cudaEventCreate(&h->evc1));
-            }
+        } else if (h->opt.engine != LP_ENGINE_GRAPH && h->opt.price_mode != 1 && !P.lex && coop &&
+                   h->geo.sms <= 1024 && occupancy_iterate(h->ld) >= 1) {
+            h->persist = true;
+            h->persist_blocks = h->geo.sms;  // the partial arrays hold at least sms entries
+        }
+        if ((h->persist || h->structured) && h->opt.kernel_timing > 0) {
+            CK(cudaEventCreate(&h->evc0));
+            CK(cudaEventCreate(&h->evc1));
         }
     }
     CK(cudaStreamSynchronize(h->stream));
@@ -614,7 +637,7 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     lp_default_options(&o);
     if (opt) o = *opt;
     if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > LP_ENGINE_STRUCTURED || o.anticycling < 0 || o.anticycling > 1 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
-        o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 1 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
+        o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 2 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
         if (!finite_all(A, (size_t)m * n) || !finite_all(c, n) || !finite_all(b, m)) return LP_ERR_INVALID_ARG;

@@ -61,3 +61,15 @@ def test_perturbed_family():
     assert abs(np.mean(ratio) - 1) < 0.01 and abs(np.std(ratio) - 0.05) < 0.01
     A2, _, _ = lpgen.perturbed_lp(base, 99)
     assert np.array_equal(A, A2)
+
+
+def test_sparse_classes():
+    # the S20 / S60 classes: the dense real family with 20% / 60% zeros
+    for kind, frac in (("s20", 0.2), ("s60", 0.6)):
+        A, b, c = lpgen.make(kind, 300, 500, 3)
+        zeros = float(np.mean(A == 0.0))
+        assert abs(zeros - frac) < 0.01, (kind, zeros)
+        A10, b10, c10 = lpgen.dense_real_lp(300, 500, 3)
+        keep = A != 0.0
+        assert np.all(A[keep] == A10[keep])  # same values, a larger zero mask over the same draws
+        assert np.array_equal(b, b10) and np.array_equal(c, c10)
