@@ -306,7 +306,12 @@ __device__ Cand price_block(const DevState& s, int it, const double* ysh, const 
     if (threadIdx.x < kPriceCols) cand_init(csh[threadIdx.x]);
     const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
     const int nch = len_half >> 5;  // 32-double2 chunks priced per column
-    const int seg = warp % kSeg, gi = warp / kSeg;
+    // Warp w runs on scheduler w % 4.  When the column's chunks do not split
+    // evenly the two segments differ by one chunk, so the segments alternate
+    // between the warp pairs of consecutive groups: every scheduler gets the
+    // same FP64 work (the partial sums are combined in the same order).
+    static_assert(kSeg == 2, "segment interleave assumes two segments");
+    const int seg = (warp & 1) ^ ((warp >> 2) & 1), gi = warp / kSeg;
     const int k0 = 32 * (seg * nch / kSeg), k1 = 32 * ((seg + 1) * nch / kSeg);
     const double2* A2 = reinterpret_cast<const double2*>(Acol);
     for (int lb = 0; lb < owned; lb += kPriceThreads) {
@@ -435,6 +440,8 @@ __device__ Cand price_block_csc(const DevState& s, int it, const double* ysh, co
         for (int e = warp; e < cnt; e += nw) {
             const int j = jl[e];
             const long long p0 = __ldg(s.csc_ptr + j), p1 = __ldg(s.csc_ptr + j + 1);
+            // four independent nonzeros per lane per step (eight loads in flight;
+            // deeper unrolling spills in the persistent kernel)
             double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
             long long p = p0 + lane;
             for (; p + 96 < p1; p += 128) {

@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
     }
 }
 
-// ---- k_iterate: many pivots in one cooperative launch (price_mode 0) -----------------
+// ---- k_iterate: many pivots in one cooperative launch (price_mode 0 and 2) -----------
 //
 // The three kernels above, as phases of one persistent kernel with one CTA per
 // SM: (1) apply the chosen pivot (rho, y, bbar slices; the bookkeeping), (2)
@@ -445,6 +445,9 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_update(DevState s) {
 // variable of each row from the snapshot taken by the FTRAN (row_var), since
 // block 0 may already be exchanging the basis.
 
+// kCsc: PRICE over the sparse copy of A (price_mode 2), a separate instantiation so
+// that the dense PRICE keeps its registers.
+template <bool kCsc>
 __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int iters) {
     Ctrl* C = s.ctrl;
     const Params& P = s.p;
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
             }
             rh_staged = stage_rh;
             __syncthreads();
-            const Cand bc = (P.price_mode == 2 ? price_block_csc(s, S.it, sh, no_patch()) : price_block(s, S.it, sh, s.A_cm, P.ld >> 1, nullptr, P.m, no_patch()));
+            const Cand bc = kCsc ? price_block_csc(s, S.it, sh, no_patch()) : price_block(s, S.it, sh, s.A_cm, P.ld >> 1, nullptr, P.m, no_patch());
             if (threadIdx.x == 0) s.price_part[blockIdx.x] = to_price_cand(bc);
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             const Cand g = reduce_price_parts(s.price_part, G);
@@ -731,9 +734,10 @@ int occupancy_price(int ld) {
 size_t iterate_smem_bytes(int ld) { return 2 * (size_t)ld * sizeof(double); }
 
 int occupancy_iterate(int ld) {
-    cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iterate_smem_bytes(ld));
+    cudaFuncSetAttribute(k_iterate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iterate_smem_bytes(ld));
+    cudaFuncSetAttribute(k_iterate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iterate_smem_bytes(ld));
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iterate, kUpdateThreads, iterate_smem_bytes(ld));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iterate<false>, kUpdateThreads, iterate_smem_bytes(ld));
     return nb;
 }
 
@@ -750,7 +754,8 @@ cudaError_t launch_iterate(const DevState& s, int blocks, int iters, cudaStream_
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_iterate, s, iters);
+    return s.p.price_mode == 2 ? cudaLaunchKernelEx(&cfg, k_iterate<true>, s, iters)
+                               : cudaLaunchKernelEx(&cfg, k_iterate<false>, s, iters);
 }
 
 int barrier_selftest(int blocks, cudaStream_t st) {

@@ -112,11 +112,12 @@ constexpr int kMaxOwnedRows = 256;  // rows of B^-1 per CTA (ratio-test records 
 // memory (all m slots: the live ones for the dot product, the others for the
 // unit columns of the basic slacks), or nullptr for a slack, whose unit vector
 // sits at live slot aq_unit.  rh: rho / alpha_r in new slot order, zero past
-// kn.  Row l of the CTA leaves alpha', its ratio and its basic variable in
-// ral/rth/rvar[l] (and in global memory for the ratio test of other CTAs).
+// kn.  Row l of the CTA leaves alpha', bbar_i and its basic variable in
+// ral/rb/rvar[l] (alpha' and the variable also in global memory for the ratio
+// test of other CTAs); the ratios themselves are formed in row_record.
 __device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int q_new, bool do_upd, bool do_ftran,
                                const double* acur, double* anxt, const double* aqs, int aq_unit, const double* rh,
-                               double* ral, double* rth, int* rvar) {
+                               double* ral, double* rb, int* rvar) {
     const Params& P = s.p;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -187,57 +188,78 @@ __device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int
             const double al = warp_sum(a0 + a1);
             if (lane == 0) {
                 const double alf = al + (us >= 0 ? aqs[us] : 0.0);
-                double th = DBL_MAX;
-                if (alf > P.tol_piv) th = bb / alf;
                 anxt[i] = alf;
-                s.theta[i] = th;
                 s.row_var[i] = var;
                 ral[l] = alf;
-                rth[l] = th;
+                rb[l] = bb;
                 rvar[l] = var;
             }
         }
     }
 }
 
-// The CTA's ratio-test record from its rows' (alpha', ratio, variable): its
+// The CTA's ratio-test record from its rows' (alpha', bbar, variable): its
 // smallest ratio, and its best row and tie count under that ratio's tie
-// threshold (one warp; result written by lane 0).
-__device__ void row_record(const Params& P, int owned, bool bland, const double* ral, const double* rth,
+// threshold (one warp, one lane per row; result written by lane 0).  On this
+// chip every FP64 instruction holds a scheduler's FP64 pipe for 64 cycles
+// whatever the number of active lanes, so the ratios of 32 rows are formed by
+// one warp-wide division, and the minimum, the tie band and the largest pivot
+// are taken on integer keys.
+__device__ void row_record(const Params& P, int owned, bool bland, const double* ral, const double* rb,
                            const int* rvar, RowRec* out) {
     const int lane = threadIdx.x & 31;
     const int G = gridDim.x;
-    long long kmin = dkey(DBL_MAX);
-    for (int l = lane; l < owned; l += 32) kmin = min(kmin, dkey(rth[l]));
+    const long long kpiv = dkey(P.tol_piv), kbig = dkey(DBL_MAX);
+    // pass 1: ratios and their minimum
+    long long kmin = kbig;
+    double th0 = DBL_MAX;  // the first 32 rows' ratios, kept for pass 2
+    for (int l0 = 0; l0 < owned; l0 += 32) {
+        const int l = l0 + lane;
+        const double al = l < owned ? ral[l] : 0.0;
+        const bool ok = l < owned && dkey(al) > kpiv;
+        const double th = ok ? rb[l] / al : DBL_MAX;
+        if (l0 == 0) th0 = th;
+        kmin = min(kmin, dkey(th));
+    }
     for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
     const double tmin = kdouble(kmin);
-    RowCand best = {0.0, 0, -1, 0.0};
-    int cnt = 0;
-    double thr = DBL_MAX;
-    if (tmin != DBL_MAX) {
-        thr = tmin + P.tol_tie * fmax(1.0, fabs(tmin));
-        for (int l = lane; l < owned; l += 32) {
-            const double al = ral[l], th = rth[l];
-            if (al > P.tol_piv && th <= thr) {
+    const double thr = kmin == kbig ? DBL_MAX : tmin + P.tol_tie * fmax(1.0, fabs(tmin));
+    const long long kthr = dkey(thr);
+    // pass 2: tie band, its size and best row (largest pivot, then smallest basic index)
+    long long ka = LLONG_MIN;
+    int bvar = 0, bl = -1, cnt = 0;
+    double bth = 0.0;
+    if (kmin != kbig) {
+        for (int l0 = 0; l0 < owned; l0 += 32) {
+            const int l = l0 + lane;
+            const double al = l < owned ? ral[l] : 0.0;
+            const long long kal = dkey(al);
+            const bool ok = l < owned && kal > kpiv;
+            const double th = l0 == 0 ? th0 : (ok ? rb[l] / al : DBL_MAX);
+            if (ok && dkey(th) <= kthr) {
                 cnt++;
-                RowCand c = {al, rvar[l], (int)blockIdx.x + G * l, th};
-                if (row_beats(c, best, bland)) best = c;
+                const int v = rvar[l];
+                const bool better = bl < 0 || (bland ? v < bvar : (kal > ka || (kal == ka && v < bvar)));
+                if (better) { ka = kal; bvar = v; bl = l; bth = th; }
             }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        RowCand oc;
-        oc.a = __shfl_xor_sync(0xffffffffu, best.a, o);
-        oc.var = __shfl_xor_sync(0xffffffffu, best.var, o);
-        oc.row = __shfl_xor_sync(0xffffffffu, best.row, o);
-        oc.th = __shfl_xor_sync(0xffffffffu, best.th, o);
-        if (row_beats(oc, best, bland)) best = oc;
+        const long long oa = __shfl_xor_sync(0xffffffffu, ka, o);
+        const int ov = __shfl_xor_sync(0xffffffffu, bvar, o), ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        const double oth = __shfl_xor_sync(0xffffffffu, bth, o);
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (ol >= 0 && (bl < 0 || (bland ? ov < bvar : (oa > ka || (oa == ka && ov < bvar))))) {
+            ka = oa; bvar = ov; bl = ol; bth = oth;
+        }
     }
     if (lane == 0) {
         RowRec rp;
-        rp.tmin = kmin; rp.thr = dkey(thr); rp.a = best.a; rp.th = best.th;
-        rp.var = best.var; rp.row = best.row; rp.cnt = cnt; rp.pad_ = 0;
+        rp.tmin = kmin; rp.thr = kthr;
+        rp.a = bl >= 0 ? kdouble(ka) : 0.0;
+        rp.th = bth;
+        rp.var = bvar; rp.row = bl >= 0 ? (int)blockIdx.x + G * bl : -1;
+        rp.cnt = cnt; rp.pad_ = 0;
         *out = rp;
     }
 }
@@ -326,7 +348,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
     __shared__ long long wmin_sh[32], wthr_sh[32];
     __shared__ double rinv_sh;
     __shared__ int wcnt_sh[32];
-    __shared__ double ral[kMaxOwnedRows], rth[kMaxOwnedRows];
+    __shared__ double ral[kMaxOwnedRows], rb[kMaxOwnedRows];
     __shared__ int rvar[kMaxOwnedRows];
     unsigned epoch = 0;
     const bool lead = blockIdx.x == 0;
@@ -504,7 +526,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
         __syncthreads();
         const double* acur2 = s.alpha + (size_t)S.abuf * P.ld;
         double* anxt = s.alpha + (size_t)(S.abuf ^ 1) * P.ld;
-        update_block_s(s, mv, r, q, do_upd, do_ftran, acur2, anxt, aqp, aq_unit, rh, ral, rth, rvar);
+        update_block_s(s, mv, r, q, do_upd, do_ftran, acur2, anxt, aqp, aq_unit, rh, ral, rb, rvar);
         if (lead && threadIdx.x == 0) {
             S.bytes_update += (do_upd ? 16.0 : (do_ftran ? 8.0 : 0.0)) * P.m * (double)kn;
             S.n_update++;
@@ -514,7 +536,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
             break;
         }
         __syncthreads();
-        if (threadIdx.x < 32) row_record(P, owned, S.bland != 0, ral, rth, rvar, s.row_rec + blockIdx.x);
+        if (threadIdx.x < 32) row_record(P, owned, S.bland != 0, ral, rb, rvar, s.row_rec + blockIdx.x);
         if (!grid_barrier(s.gbar, epoch, &fail)) break;
         // ---- (C) CHUZR: minimum ratio, tie set, leaving row (every CTA), on
         // integer keys; the tie threshold comes with the record that holds
@@ -586,10 +608,10 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
         } else {
             // the tie set spans several CTAs: scan the rows of all CTAs
             for (int i = threadIdx.x; i < P.m; i += blockDim.x) {
-                const double al = __ldcg(anxt + i), th2 = __ldcg(s.theta + i);
-                if (al > P.tol_piv && th2 <= thr) {
+                const double al = __ldcg(anxt + i), bb = __ldcg(s.bbar + i);
+                if (al > P.tol_piv && bb <= thr * al) {
                     cnt++;
-                    RowCand c = {al, __ldcg(s.row_var + i), i, th2};
+                    RowCand c = {al, __ldcg(s.row_var + i), i, 0.0};
                     if (row_beats(c, b, bland)) b = c;
                 }
             }
@@ -602,7 +624,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
                 } else {
                     S.r = b.row;
                     S.leave = b.var;
-                    S.theta = b.th;
+                    S.theta = __ldcg(s.bbar + b.row) / b.a;
                     S.alpha_r = b.a;
                     S.tcount = cnt;
                     if (cnt > 1) S.flags |= kTfTieSet;
