@@ -336,6 +336,195 @@ __device__ PricePatch pivot_patch(const SlotMoves& v, int q, int leave, bool pus
 // the lead CTA writes them to memory (visible to all after the next barrier).
 // The y of the next step is written by the lead CTA to the other half of a
 // double buffer.
+// ---- exact PRICE through an FP32 screen ---------------------------------------------
+// FP32 runs at about 58x the FP64 rate on this chip.  Every listed column j is
+// first priced in FP32 -- s~_j = sum_t y32_t a32_tj with y32, a32 the FP32
+// roundings -- together with S~_j = sum_t |y32_t| |a32_tj|.  With u = 2^-24,
+// k summed rows and |y|, |a| within [2^-100, 2^40] or zero, the FP32 result
+// satisfies |s~_j - y^T a_j| <= gamma_{d+2} / ((1 - u)^2 (1 - gamma_d)) S~_j,
+// where gamma_n = n u / (1 - n u) and d = T + 5 bounds the roundings any term
+// goes through: the T fused multiply-adds of its lane's chain (T = 4 per 128
+// rows) and the five butterfly levels; the +2 are the roundings of y and a to
+// FP32, and the denominator turns the computed S~_j into an upper bound of
+// sum |y_t a_tj| (Higham, Accuracy and Stability of Numerical Algorithms,
+// ch. 3, for sums along any tree).  (d + 3) u 1.01 S~_j covers it for
+// d u < 1e-3 and (k + 8) 2^-100 covers underflow.  The interval
+// [c_j - s~_j - E_j, c_j - s~_j + E_j] is formed in FP32 with directed
+// rounding from c_j rounded down and up (kept per column), so it contains d_j
+// and costs no FP64 instruction.
+// A column can be the block's exact argmax of a category (all nonbasic,
+// non-tabu, non-tabu prioritised) only if its interval reaches the largest
+// lower end of the category; exactly those columns are re-priced in FP64 with
+// the arithmetic of the full PRICE (same segments, lanes and pairing order), so
+// the block's candidates -- and the pivots -- are bit-identical to it.  The
+// smallest-index rule of the safety net needs every improving column, so
+// under it the full FP64 PRICE runs.
+constexpr int kScreenMaxList = kPriceThreads;
+
+// order-preserving integer image of a float (no NaN; -0 and +0 share one key)
+__device__ __forceinline__ int fkey(float x) {
+    int b = __float_as_int(x);
+    if ((b & 0x7fffffff) == 0) b = 0;
+    return b >= 0 ? b : (b ^ 0x7fffffff);
+}
+
+__device__ __forceinline__ void dot2_f32(const float4* __restrict__ c0, const float4* __restrict__ c1,
+                                         const float4* y4, int n4, int lane, float& s0, float& a0, float& s1,
+                                         float& a1) {
+    s0 = a0 = s1 = a1 = 0.f;
+#pragma unroll 2
+    for (int k = lane; k < n4; k += 32) {
+        const float4 y = y4[k];
+        const float4 u = __ldcg(c0 + k), v = __ldcg(c1 + k);
+        s0 = fmaf(u.x, y.x, s0); s0 = fmaf(u.y, y.y, s0); s0 = fmaf(u.z, y.z, s0); s0 = fmaf(u.w, y.w, s0);
+        s1 = fmaf(v.x, y.x, s1); s1 = fmaf(v.y, y.y, s1); s1 = fmaf(v.z, y.z, s1); s1 = fmaf(v.w, y.w, s1);
+        a0 = fmaf(fabsf(u.x), fabsf(y.x), a0); a0 = fmaf(fabsf(u.y), fabsf(y.y), a0);
+        a0 = fmaf(fabsf(u.z), fabsf(y.z), a0); a0 = fmaf(fabsf(u.w), fabsf(y.w), a0);
+        a1 = fmaf(fabsf(v.x), fabsf(y.x), a1); a1 = fmaf(fabsf(v.y), fabsf(y.y), a1);
+        a1 = fmaf(fabsf(v.z), fabsf(y.z), a1); a1 = fmaf(fabsf(v.w), fabsf(y.w), a1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+}
+
+__device__ Cand price_block_screened(const DevState& s, int it, const double* ysh, const float* ysh32, int kk,
+                                     const int32_t* slack_rows, int nslack, const PricePatch& pp) {
+    const Params& P = s.p;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int G = gridDim.x;
+    const int half = P.ld >> 1;
+    const long long ktol = dkey(P.tol_d);
+    __shared__ int jl[kScreenMaxList];
+    __shared__ double jc[kScreenMaxList];
+    __shared__ int jt[kScreenMaxList], jr[kScreenMaxList];
+    __shared__ int wcnt[kPriceThreads / 32];
+    __shared__ int klo[kScreenMaxList], khi[kScreenMaxList];
+    __shared__ int bandsh[3][32];
+    __shared__ int rl[kScreenMaxList];
+    __shared__ int nrl;
+    __shared__ double part[2][kPriceThreads / 64];
+    Cand cand;
+    cand_init(cand);
+    // slack candidates: exact (d = -y), offered directly, loads issued first
+    int sj = -1;
+    const int si = blockIdx.x + G * threadIdx.x;
+    if (si < nslack) {
+        int row = -1;
+        for (int e = 0; e < pp.nsp && row < 0; ++e)
+            if (pp.sp_slot[e] == si) row = pp.sp_row[e];
+        if (row < 0) row = __ldcg(slack_rows + si);
+        sj = P.n + row;
+    }
+    const int n4 = kk >> 2;
+    const int depth = 4 * ((n4 + 31) >> 5) + 5;  // fused multiply-adds per lane + butterfly levels
+    const float umul = __fmul_ru((float)(depth + 3), 6.0200691e-8f);  // (d + 3) u 1.01, rounded up
+    const float uabs = __fmul_ru((float)(kk + 8), 7.8886091e-31f);     // (k + 8) 2^-100: underflow
+    const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
+    const float4* y4 = reinterpret_cast<const float4*>(ysh32);
+    for (int lb = 0; lb < owned; lb += kPriceThreads) {
+        const int cnt = list_nonbasic(s, pp, lb, owned, jl, jc, jt, jr, wcnt);
+        // (1) FP32 screen, two listed columns per warp
+        for (int e0 = 2 * warp; e0 < cnt; e0 += 2 * nw) {
+            const int e1 = min(e0 + 1, cnt - 1);
+            const int j0 = jl[e0], j1 = jl[e1];
+            const float4* c0 = reinterpret_cast<const float4*>(s.A_p32 + (size_t)j0 * P.ld);
+            const float4* c1 = reinterpret_cast<const float4*>(s.A_p32 + (size_t)j1 * P.ld);
+            float cl0 = 0.f, ch0 = 0.f, cl1 = 0.f, ch1 = 0.f;
+            if (lane == 0) {
+                cl0 = __ldg(s.c32lo + j0); ch0 = __ldg(s.c32hi + j0);
+                cl1 = __ldg(s.c32lo + j1); ch1 = __ldg(s.c32hi + j1);
+            }
+            float s0, a0, s1, a1;
+            dot2_f32(c0, c1, y4, n4, lane, s0, a0, s1, a1);
+            if (lane == 0) {
+                const float E0 = __fmaf_ru(umul, a0, uabs), E1 = __fmaf_ru(umul, a1, uabs);
+                klo[e0] = fkey(__fsub_rd(cl0, __fadd_ru(s0, E0)));
+                khi[e0] = fkey(__fadd_ru(__fsub_ru(ch0, s0), E0));
+                klo[e1] = fkey(__fsub_rd(cl1, __fadd_ru(s1, E1)));
+                khi[e1] = fkey(__fadd_ru(__fsub_ru(ch1, s1), E1));
+            }
+        }
+        __syncthreads();
+        // (2) the largest lower end of each category (slacks exact)
+        int b0 = INT_MIN, b1 = INT_MIN, b2 = INT_MIN;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const int lo = klo[e];
+            const bool nt = jt[e] <= it;
+            b0 = max(b0, lo);
+            if (nt) b1 = max(b1, lo);
+            if (nt && jr[e] != kNoRank) b2 = max(b2, lo);
+        }
+        if (lb == 0 && sj >= 0) {
+            const int kd = fkey(__double2float_rd(-ysh[si]));  // exact value, its lower FP32 bound
+            const bool nt = patched_tabu(s, pp, sj) <= it;
+            b0 = max(b0, kd);
+            if (nt) b1 = max(b1, kd);
+            if (nt && s.rank[sj] != kNoRank) b2 = max(b2, kd);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            b0 = max(b0, __shfl_xor_sync(0xffffffffu, b0, o));
+            b1 = max(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+            b2 = max(b2, __shfl_xor_sync(0xffffffffu, b2, o));
+        }
+        if (lane == 0) { bandsh[0][warp] = b0; bandsh[1][warp] = b1; bandsh[2][warp] = b2; }
+        if (threadIdx.x == 0) nrl = 0;
+        __syncthreads();
+        int L0 = INT_MIN, L1 = INT_MIN, L2 = INT_MIN;
+        for (int w = 0; w < nw; ++w) {
+            L0 = max(L0, bandsh[0][w]);
+            L1 = max(L1, bandsh[1][w]);
+            L2 = max(L2, bandsh[2][w]);
+        }
+        // (3) the columns whose interval reaches a category's lower end
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const int hi = khi[e];
+            const bool nt = jt[e] <= it;
+            if (hi >= L0 || (nt && hi >= L1) || (nt && jr[e] != kNoRank && hi >= L2)) rl[atomicAdd(&nrl, 1)] = e;
+        }
+        __syncthreads();
+        // (4) exact FP64 re-price, two warps (the two row segments) per column
+        const int nr = nrl;
+        const int nch = (kk >> 1) >> 5;
+        const int seg = warp & 1;
+        const int k0 = 32 * (seg * nch / 2), k1 = 32 * ((seg + 1) * nch / 2);
+        const double2* A2 = reinterpret_cast<const double2*>(s.A_p);
+        const double2* y2 = reinterpret_cast<const double2*>(ysh);
+        for (int r0 = 0; r0 < nr; r0 += nw / 2) {
+            const int slot = warp >> 1;
+            const int ri = r0 + slot;
+            if (ri < nr) {
+                const int col = jl[rl[ri]];
+                double acc[1];
+                dot_cols<1, true>(A2, &col, half, y2, k0, k1, lane, acc);
+                const double t = pair_sum(acc[0]);
+                if (lane == 0) part[seg][slot] = t;
+            }
+            __syncthreads();
+            if ((int)threadIdx.x < nw / 2 && r0 + (int)threadIdx.x < nr) {
+                const int e = rl[r0 + threadIdx.x];
+                const double sum = part[0][threadIdx.x] + part[1][threadIdx.x];
+                cand_offer(cand, jc[e] - sum, jl[e], jt[e] <= it, ktol, jr[e]);
+            }
+            __syncthreads();
+        }
+    }
+    if (sj >= 0) cand_offer(cand, -ysh[si], sj, patched_tabu(s, pp, sj) <= it, ktol, s.rank[sj]);
+    for (int i = si + G * blockDim.x; i < nslack; i += G * blockDim.x) {
+        int row = -1;
+        for (int e = 0; e < pp.nsp && row < 0; ++e)
+            if (pp.sp_slot[e] == i) row = pp.sp_row[e];
+        if (row < 0) row = __ldcg(slack_rows + i);
+        const int j = P.n + row;
+        cand_offer(cand, -ysh[i], j, patched_tabu(s, pp, j) <= it, ktol, s.rank[j]);
+    }
+    return cand_block_reduce(cand);
+}
+
 __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int iters) {
     Ctrl* C = s.ctrl;
     const Params& P = s.p;
@@ -347,6 +536,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
     __shared__ int nflag, flagged;
     __shared__ long long wmin_sh[32], wthr_sh[32];
     __shared__ double rinv_sh;
+    __shared__ int screen_sh;
     __shared__ int wcnt_sh[32];
     __shared__ double ral[kMaxOwnedRows], rb[kMaxOwnedRows];
     __shared__ int rvar[kMaxOwnedRows];
@@ -364,14 +554,17 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
         S.n_asp = C->n_asp; S.n_price = C->n_price; S.n_update = C->n_update;
         S.z = C->z; S.bytes_price = C->bytes_price; S.bytes_update = C->bytes_update;
         S.k = C->k_live; S.par = C->map_par;
+        screen_sh = P.screen && C->screen_off == 0;
     }
     if (!grid_barrier(s.gbar, epoch, &fail)) {
         if (lead && threadIdx.x == 0) C->err = kErrTimeout;
         return;
     }
+    const bool screen_ok = screen_sh != 0;
     double* ysh = sh;
     double* rh = sh + P.ld;
     double* aqs = sh + 2 * (size_t)P.ld;
+    float* ysh32 = reinterpret_cast<float*>(sh + 3 * (size_t)P.ld);  // y in FP32 for the screen
     for (int step = 0; step < iters; ++step) {
         // ---- (A) apply the pivot chosen by the last ratio test, then PRICE
         const bool piv = S.status == kRunning && S.r >= 0 && S.r < P.m && S.q >= 0;
@@ -408,6 +601,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
                 S.par = par ^ 1;
             }
         }
+        int ybig = 0;
         {
             // y and rho / alpha_r in the new slot order (every CTA, into shared memory)
             const double* yold = s.yp + (size_t)par * P.ld;
@@ -436,6 +630,9 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
                     }
                     rh[t] = rn;
                     ysh[t] = yv;
+                    ysh32[t] = (float)yv;
+                    // screen range: |y| <= 2^40 (exponent field test, no FP64 instruction)
+                    ybig |= ((__double_as_longlong(yv) >> 52) & 0x7ff) > 1023 + 40;
                 }
             }
         }
@@ -467,9 +664,11 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
                 }
                 for (int j = blockIdx.x + G * threadIdx.x; j < P.n && nm > 0; j += G * blockDim.x) {
                     double* col = s.A_p + (size_t)j * P.ld;
+                    float* col32 = s.A_p32 + (size_t)j * P.ld;
                     double val[3];
-                    for (int e = 0; e < nm; ++e) val[e] = __ldcg(col + src[e]);
-                    for (int e = 0; e < nm; ++e) col[dst[e]] = val[e];
+                    float v32[3];
+                    for (int e = 0; e < nm; ++e) { val[e] = __ldcg(col + src[e]); v32[e] = __ldcg(col32 + src[e]); }
+                    for (int e = 0; e < nm; ++e) { col[dst[e]] = val[e]; col32[dst[e]] = v32[e]; }
                 }
             }
             // bbar on the rows this CTA owns (their ratios are computed here too)
@@ -479,11 +678,15 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
                 s.bbar[i] = (i == r) ? th : __dsub_rn(bb, __dmul_rn(ak, th));
             }
         }
-        __syncthreads();  // y, rho, the A_p moves and thread 0's bookkeeping are done
+        const bool yrange = __syncthreads_or(ybig) == 0;  // y, rho, the A_p moves and thread 0's bookkeeping are done
         if (S.status == kReinvert) break;  // the slot moves are complete; B^-1 is rebuilt
         if (S.status == kRunning) {
             const int32_t* sr = s.slot_row + (size_t)par * P.m;  // + the patch: the map after the moves
-            const Cand bc = price_block<true>(s, S.it, ysh, s.A_p, kk >> 1, sr, kn, ppat);
+            // the FP32 screen unless the safety net needs every improving column
+            // or y leaves the screen's range (then the full FP64 PRICE)
+            const Cand bc = (screen_ok && yrange && !S.bland)
+                                ? price_block_screened(s, S.it, ysh, ysh32, kk, sr, kn, ppat)
+                                : price_block<true>(s, S.it, ysh, s.A_p, kk >> 1, sr, kn, ppat);
             if (threadIdx.x == 0) s.price_rec[blockIdx.x] = to_price_rec(bc);
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             // ---- (B) CHUZC (every CTA), then UPDATE + FTRAN + ratios
@@ -714,17 +917,31 @@ __global__ void __launch_bounds__(1024) k_struct_layout(DevState s, int force, i
     }
 }
 
-// A_p = A_cm with its rows in slot order (only after a rebuilt map)
+// A_p = A_cm with its rows in slot order and its FP32 copy (only after a
+// rebuilt map); the screen is switched off when a nonzero of A lies outside
+// [2^-100, 2^40] in magnitude.
 __global__ void k_struct_gather_A(DevState s, const int32_t* relayout) {
     if (*relayout == 0) return;
     const Params& P = s.p;
     const int32_t* sr = s.slot_row + (size_t)s.ctrl->map_par * P.m;
     const size_t total = (size_t)P.n * P.ld;
+    int off = 0;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         const size_t j = e / P.ld;
         const int t = (int)(e % P.ld);
-        s.A_p[e] = t < P.m ? s.A_cm[j * P.ld + sr[t]] : 0.0;
+        const double a = t < P.m ? s.A_cm[j * P.ld + sr[t]] : 0.0;
+        s.A_p[e] = a;
+        s.A_p32[e] = (float)a;
+        const int ex = (int)((__double_as_longlong(a) >> 52) & 0x7ff);
+        off |= a != 0.0 && (ex > 1023 + 40 || ex < 1023 - 100);
     }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.n; j += gridDim.x * blockDim.x) {
+        s.c32lo[j] = __double2float_rd(s.c[j]);
+        s.c32hi[j] = __double2float_ru(s.c[j]);
+        const int ex = (int)((__double_as_longlong(s.c[j]) >> 52) & 0x7ff);
+        off |= ex > 1023 + 100;  // c within FP32 range
+    }
+    if (__syncthreads_or(off) && threadIdx.x == 0) atomicOr(&s.ctrl->screen_off, 1);
 }
 
 // the live columns of the dense B^-1 and the live entries of y
@@ -772,10 +989,15 @@ __global__ void k_struct_init_maps(DevState s) {
 
 }  // namespace
 
-size_t iterate_s_smem_bytes(int ld) { return 3 * (size_t)ld * sizeof(double); }
+size_t iterate_s_smem_bytes(int ld) { return 3 * (size_t)ld * sizeof(double) + (size_t)ld * sizeof(float); }
 
 bool struct_engine_fits(int m, int ld, int ctas) {
-    return iterate_s_smem_bytes(ld) <= 200 * 1024 && (m + ctas - 1) / ctas <= kMaxOwnedRows;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_iterate_s) != cudaSuccess) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return fa.sharedSizeBytes + iterate_s_smem_bytes(ld) <= (size_t)optin && (m + ctas - 1) / ctas <= kMaxOwnedRows;
 }
 
 int occupancy_iterate_s(int ld) {

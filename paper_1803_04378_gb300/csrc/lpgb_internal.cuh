@@ -54,6 +54,7 @@ struct Params {
     int32_t topk;          // candidates re-priced in FP64 (price_mode 1), <= kMaxTopk
     int32_t lex;           // 1: lexicographic leaving rule (no tabu list, no safety net)
     double nnz;            // price_mode 2: nonzeros of A
+    int32_t screen;        // slack-structured engine: PRICE through the exact FP32 screen
 };
 
 constexpr int kMaxTopk = 32;
@@ -87,7 +88,7 @@ struct Ctrl {
     int32_t n_price;       // PRICE launches that did work
     int32_t n_update;      // UPDATE launches that did work
     int32_t map_par;       // slack-structured engine: which slot map is current
-    int32_t pad2_;
+    int32_t screen_off;    // slack-structured engine: A outside the FP32 screen's range
     double bytes_price;    // algorithmic HBM bytes moved by PRICE
     double bytes_update;   // algorithmic HBM bytes moved by UPDATE/FTRAN
     double dq;             // d_q of the pending pivot
@@ -177,6 +178,9 @@ struct DevState {
     // slack-structured engine (k_iterate_s): the constraint rows in slot order,
     // the rows whose slack is nonbasic in slots [0, k_live)
     double* A_p;        // n columns of ld doubles: A with its rows in slot order
+    float* A_p32;       // its FP32 copy (the PRICE screen)
+    float* c32lo;       // c rounded down and up to FP32 (the PRICE screen)
+    float* c32hi;
     double* bp;         // m rows of ld doubles: B^-1 columns of the live slots
     double* yp;         // 2*ld: y in slot order (zero outside the live slots), two copies by map_par
     int32_t* slot_row;  // 2*m: slot -> row, two copies (current, next) by map_par

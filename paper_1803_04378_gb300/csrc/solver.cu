@@ -598,6 +598,11 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
             struct_engine_fits(h->m, h->ld, h->geo.sms) && occupancy_iterate_s(h->ld) >= 1) {
             const int m = h->m, n = h->n, ld = h->ld;
             TRY(dalloc(h, &s.A_p, (size_t)n * ld));
+            TRY(dalloc(h, &s.A_p32, (size_t)n * ld));
+            TRY(dalloc(h, &s.c32lo, (size_t)n));
+            TRY(dalloc(h, &s.c32hi, (size_t)n));
+            h->p.screen = 1;
+            s.p.screen = 1;
             TRY(dalloc(h, &s.bp, (size_t)m * ld));
             TRY(dalloc(h, &s.yp, 2 * (size_t)ld));
             TRY(dalloc(h, &s.slot_row, 2 * (size_t)m));
