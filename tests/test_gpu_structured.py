@@ -220,3 +220,27 @@ def test_device_inputs():
     with lpgb.LP(At, bt, ct, engine=S) as lp:
         r2 = lp.solve(); z2 = lp.solution()[2]
     assert r1.iterations == r2.iterations and z1 == z2
+
+
+def test_screen_fallbacks():
+    """The FP32 screen of PRICE steps aside where its bound does not hold: an
+    entry of A beyond 2^40 switches it off for the problem (the full FP64
+    PRICE runs), and the pivots stay the method's."""
+    A, b, c = lpgen.dense_real_lp(150, 240, 21)
+    A[3, 7] = 3.0e13          # beyond 2^40: no FP32 screen for this problem
+    b[3] = 5.0e13
+    lp, res, x, y, z, tr = gpu_solve(A, b, c, engine=S)
+    assert res.status == 1 and res.persistent == 2
+    ref = oracle.solve(A, b, c)
+    assert abs(z - ref.objective) <= 1e-9 * max(1.0, abs(ref.objective))
+    assert_certificate(A, b, c, x, y)
+    follow_check(A, b, c, res, tr)
+    lp.close()
+    # tiny entries (below 2^-100) also switch it off
+    A2, b2, c2 = lpgen.dense_real_lp(120, 200, 22)
+    A2[5, 9] = 1e-40
+    lp, res, x, y, z, tr = gpu_solve(A2, b2, c2, engine=S)
+    ref = oracle.solve(A2, b2, c2)
+    assert res.status == 1 and abs(z - ref.objective) <= 1e-9 * max(1.0, abs(ref.objective))
+    follow_check(A2, b2, c2, res, tr)
+    lp.close()
