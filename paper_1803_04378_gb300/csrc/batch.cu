@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -74,9 +75,11 @@ constexpr int kSlotsPerSm = 8;  // scratch slots per SM and bucket (CTAs per SM 
 namespace {
 
 // ---------------------------------------------------------------- reductions
-struct BCand { double d; int j; };
+// Values are ordered through their integer images (dkey): every FP64 compare
+// or min would hold the FP64 pipe as long as an FMA on this chip.
+struct BCand { long long d; int j; };  // d: dkey image
 
-__device__ __forceinline__ bool bc_beats(double da, int ja, double db, int jb) {
+__device__ __forceinline__ bool bc_beats(long long da, int ja, long long db, int jb) {
     if (ja < 0) return false;
     if (jb < 0) return true;
     return da > db || (da == db && ja < jb);
@@ -115,15 +118,21 @@ __device__ int block_sum_int(int v, int* sh) {
     return r;
 }
 
+// Block minimum of dkey images; thread 0 also forms the ratio test's tie
+// threshold of the minimum (one FP64 evaluation per block), broadcast in *thr.
 template <int T>
-__device__ double block_min(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+__device__ long long block_min_key(long long v, long long* sh, double tol_tie, long long* thr) {
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) sh[w] = v;
     __syncthreads();
-    double r = sh[0];
-    for (int i = 1; i < T / 32; ++i) r = fmin(r, sh[i]);
+    long long r = sh[0];
+    for (int i = 1; i < T / 32; ++i) r = min(r, sh[i]);
+    if (threadIdx.x == 0) {
+        const double t = kdouble(r);
+        *thr = t == DBL_MAX ? r : dkey(t + tol_tie * fmax(1.0, fabs(t)));
+    }
     __syncthreads();
     return r;
 }
@@ -143,7 +152,7 @@ __device__ double block_sum(double v, double* sh) {
 
 // Leaving-row candidate: largest alpha, ties to the smallest basic variable
 // (Bland: smallest basic variable).
-struct RCand { double a; int var; int row; };
+struct RCand { long long a; int var; int row; };  // a: dkey image of alpha
 
 __device__ __forceinline__ bool rc_beats(const RCand& x, const RCand& y, bool bland) {
     if (x.row < 0) return false;
@@ -189,6 +198,7 @@ struct Red {
     BCand bc[32];
     RCand rc[32];
     double dv[32];
+    long long kv[33];  // keys; kv[32]: the tie threshold
     int iv[32];
     int kj[16 * kBatchTopk];   // top-K selection: each warp's kept columns
     float kd[16 * kBatchTopk];
@@ -367,20 +377,21 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
                 if (lane == 0) cand_d[t] = c[j] - acc;
             }
             // best exact slack (non-tabu)
-            BCand bs = {-DBL_MAX, -1};
+            BCand bs = {LLONG_MIN, -1};
             for (int i = tid; i < m; i += T) {
                 const int j = n + i;
-                if (pos[j] < 0 && tabu[j] <= it && bc_beats(-y[i], j, bs.d, bs.j)) bs = {-y[i], j};
+                const long long kd = dkey(-y[i]);
+                if (pos[j] < 0 && tabu[j] <= it && bc_beats(kd, j, bs.d, bs.j)) bs = {kd, j};
             }
             __syncthreads();
             bs = block_best<T>(bs, R.bc);
             if (tid == 0) {
                 BCand best = bs;
                 for (int t = 0; t < K; ++t)
-                    if (cand[t] >= 0 && bc_beats(cand_d[t], cand[t], best.d, best.j)) best = {cand_d[t], cand[t]};
-                if (best.j >= 0 && best.d > P.tol_d) {
+                    if (cand[t] >= 0 && bc_beats(dkey(cand_d[t]), cand[t], best.d, best.j)) best = {dkey(cand_d[t]), cand[t]};
+                if (best.j >= 0 && best.d > dkey(P.tol_d)) {
                     S.q = best.j;
-                    S.dq = best.d;
+                    S.dq = kdouble(best.d);
                     R.iv[0] = 1;
                 } else {
                     R.iv[0] = 0;
@@ -392,13 +403,14 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
         }
         if (!have_q) {
             // full FP64 PRICE (the oracle's rule, tabu and aspiration included)
-            BCand ball = {-DBL_MAX, -1}, bnt = {-DBL_MAX, -1};
+            BCand ball = {LLONG_MIN, -1}, bnt = {LLONG_MIN, -1};
             int jmin = -1;
-            double dmin = 0.0;
-            auto offer = [&](double d, int j) {
+            const long long ktol = dkey(P.tol_d);
+            auto offer = [&](double dv, int j) {
+                const long long d = dkey(dv);
                 if (bc_beats(d, j, ball.d, ball.j)) ball = {d, j};
                 if (tabu[j] <= it && bc_beats(d, j, bnt.d, bnt.j)) bnt = {d, j};
-                if (d > P.tol_d && (jmin < 0 || j < jmin)) { jmin = j; dmin = d; }
+                if (d > ktol && (jmin < 0 || j < jmin)) jmin = j;
             };
             // structural columns: four lanes per column
             for (int base = 0; base < n; base += T / 4) {
@@ -423,21 +435,21 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
             ball = block_best<T>(ball, R.bc);
             bnt = block_best<T>(bnt, R.bc);
             // smallest improving index: reduce as argmax of (-j)
-            BCand bm = {jmin >= 0 ? -(double)jmin : -DBL_MAX, jmin};
+            BCand bm = {jmin >= 0 ? -(long long)jmin : LLONG_MIN, jmin};
             bm = block_best<T>(bm, R.bc);
             if (tid == 0) {
-                if (ball.j < 0 || !(ball.d > P.tol_d)) {
+                if (ball.j < 0 || !(ball.d > ktol)) {
                     S.status = kOptimal;
                 } else if (bland) {
                     // d of the smallest improving index: recompute exactly below
                     S.q = bm.j;
                     S.flags |= kTfBland;
-                } else if (bnt.j >= 0 && bnt.d > P.tol_d) {
+                } else if (bnt.j >= 0 && bnt.d > ktol) {
                     S.q = bnt.j;
-                    S.dq = bnt.d;
+                    S.dq = kdouble(bnt.d);
                 } else {
                     S.q = ball.j;
-                    S.dq = ball.d;
+                    S.dq = kdouble(ball.d);
                     S.flags |= kTfAspiration;
                 }
             }
@@ -457,7 +469,6 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
                 }
                 __syncthreads();
             }
-            (void)dmin;
         }
         const int q = S.q;
         // ---- Step 5: FTRAN alpha = B^-1 a_q
@@ -479,35 +490,36 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
                 double acc = a0 + a1;
                 acc += __shfl_xor_sync(0xffffffffu, acc, 1);
                 acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                if (g == 0 && i < m) {
-                    al[i] = acc;
-                    th[i] = acc > P.tol_piv ? bbar[i] / acc : DBL_MAX;
-                }
+                if (g == 0 && i < m) al[i] = acc;
             }
         } else {
-            for (int i = tid; i < m; i += T) {
-                const double acc = Binv[(size_t)(q - n) * m + i];
-                al[i] = acc;
-                th[i] = acc > P.tol_piv ? bbar[i] / acc : DBL_MAX;
-            }
+            for (int i = tid; i < m; i += T) al[i] = Binv[(size_t)(q - n) * m + i];
         }
         __syncthreads();
-        // ---- Step 6: CHUZR with the tie set
-        double tl = DBL_MAX;
-        for (int i = tid; i < m; i += T) tl = fmin(tl, th[i]);
-        const double tmin = block_min<T>(tl, R.dv);
-        if (tmin == DBL_MAX) {
+        // ratios one row per lane: a warp-wide division covers 32 rows
+        const long long kpiv = dkey(P.tol_piv);
+        long long tl = dkey(DBL_MAX);
+        for (int i = tid; i < m; i += T) {
+            const double a = al[i];
+            const double t = dkey(a) > kpiv ? bbar[i] / a : DBL_MAX;
+            th[i] = t;
+            tl = min(tl, dkey(t));
+        }
+        // ---- Step 6: CHUZR with the tie set (on integer keys)
+        const long long kmin = block_min_key<T>(tl, R.kv, P.tol_tie, &R.kv[32]);
+        if (kmin == dkey(DBL_MAX)) {
             if (tid == 0) S.status = kUnbounded;
             __syncthreads();
             break;
         }
-        const double thr = tmin + P.tol_tie * fmax(1.0, fabs(tmin));
-        RCand rc = {0.0, 0, -1};
+        const long long kthr = R.kv[32];
+        RCand rc = {0, 0, -1};
         int cnt = 0;
         for (int i = tid; i < m; i += T) {
-            if (al[i] > P.tol_piv && th[i] <= thr) {
+            const long long ka = dkey(al[i]);
+            if (ka > kpiv && dkey(th[i]) <= kthr) {
                 cnt++;
-                RCand x = {al[i], basis[i], i};
+                RCand x = {ka, basis[i], i};
                 if (rc_beats(x, rc, bland)) rc = x;
             }
         }
@@ -583,14 +595,14 @@ __device__ void solve_one(const BatchState& s, int lp, unsigned char* smem, doub
             for (int a = tid; a < k; a += T) { pinv[a] = 0; pivrow[a] = -1; }  // pinv doubles as "row used"
             __syncthreads();
             for (int j = 0; j < k; ++j) {
-                BCand pc = {-DBL_MAX, -1};
+                BCand pc = {LLONG_MIN, -1};
                 for (int a = tid; a < k; a += T)
                     if (!pinv[a]) {
-                        const double v = fabs(W[(size_t)j * k + a]);
+                        const long long v = dkey(fabs(W[(size_t)j * k + a]));
                         if (bc_beats(v, a, pc.d, pc.j)) pc = {v, a};
                     }
                 pc = block_best<T>(pc, R.bc);
-                if (pc.j < 0 || !(pc.d > 0.0)) {
+                if (pc.j < 0 || !(pc.d > 0)) {
                     if (tid == 0) S.err = 2;
                     __syncthreads();
                     break;

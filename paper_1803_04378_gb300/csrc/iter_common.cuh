@@ -82,19 +82,8 @@ __device__ __forceinline__ void dot_cols(const double2* __restrict__ A2, const i
 }
 
 // ---- CHUZC candidate ---------------------------------------------------------
-// Reduced costs are compared through an order-preserving integer image: on
-// this chip every FP64 instruction (compares and min/max included) shares the
-// slow FP64 pipe with the FMAs, while the integer compares below do not.
-// dkey(a) > dkey(b) exactly when a > b, and -0 and +0 share one key (no NaN
-// reaches a candidate).
-__device__ __forceinline__ long long dkey(double d) {
-    long long b = __double_as_longlong(d);
-    if ((b & 0x7fffffffffffffffLL) == 0) b = 0;
-    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double kdouble(long long k) {
-    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
-}
+// Reduced costs are compared through their order-preserving integer images
+// (dkey, kdouble in lpgb_internal.cuh).
 
 // d_* fields hold dkey images of reduced costs.
 struct Cand {

@@ -205,6 +205,19 @@ struct DevState {
     double* rv_f;            // 2*k published pivot columns
 };
 
+// Order-preserving integer image of a double: on GB300 every FP64 instruction
+// (compares and min/max included) holds the slow FP64 pipe as long as an FMA,
+// while integer compares do not.  dkey(a) > dkey(b) exactly when a > b, and
+// -0 and +0 share one key (no NaN is ever compared).
+__device__ __forceinline__ long long dkey(double d) {
+    long long b = __double_as_longlong(d);
+    if ((b & 0x7fffffffffffffffLL) == 0) b = 0;
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double kdouble(long long k) {
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+
 // ---- launch geometry -----------------------------------------------------
 // Programmatic dependent launch: wait for the previous kernel of the stream
 // (its completion and memory), then let the next kernel's CTAs be scheduled.
