@@ -182,13 +182,19 @@ __global__ void __launch_bounds__(kStepThreads) k_gj_step(DevState s, int k, int
 // panel column has received every earlier transform before its pivot is
 // searched, so the pivots are those of the unblocked elimination.
 //
-// Inside a panel one hardware cluster barrier per step is the only
-// synchronisation: each CTA publishes its best candidate (|value| as an
-// ordered integer key, smaller row on equal keys) in its own shared memory;
-// after the barrier every CTA reads all candidates and the pivot row through
-// distributed shared memory.  The owner of the pivot row leaves it untouched
-// during the step (others are reading it) and folds the scaling into its
-// update of the next step, after the next barrier.
+// Inside a panel the steps are pipelined around one hardware cluster barrier
+// per step, split into arrive and wait.  Each CTA publishes its best
+// candidate for the next pivot (|value| as an ordered integer key, smaller row
+// on equal keys) in its own shared memory; after the barrier every CTA reads
+// all candidates and the pivot row through distributed shared memory.  Only
+// the next column and the candidate row are needed before the barrier, so
+// warp 0 updates those two first (lookahead), publishes and arrives; the
+// other warps arrive at once and eliminate the rest of the panel while the
+// barrier completes.  No row but a CTA's own candidate is ever read by another
+// CTA, and the owner of the pivot row leaves it untouched during the step
+// (others are reading it) and folds the scaling into its update of the next
+// step.  The arithmetic of every entry is the same as in the unpipelined
+// order, so the result does not depend on the schedule.
 constexpr int kPCS = 16;
 constexpr int kNB = 32;
 constexpr int kPLD = kNB + 1;  // padded row stride of the panel in shared memory
@@ -204,14 +210,23 @@ __device__ __forceinline__ bool cand_better(unsigned long long ka, int ra, unsig
     return ka > kb || (ka == kb && ra < rb);
 }
 
+// Warp-wide best candidate (largest key, then smallest row) with three
+// reductions: the high half of the key, the low half among the lanes that
+// hold the largest high half, the row among the lanes that hold the largest
+// key.  The result is in every lane.
 __device__ __forceinline__ void warp_best(unsigned long long& bk, int& br) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-        const int orow = __shfl_xor_sync(0xffffffffu, br, o);
-        if (cand_better(ok, orow, bk, br)) { bk = ok; br = orow; }
-    }
+    const unsigned hi = (unsigned)(bk >> 32), lo = (unsigned)bk;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    br = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? br : 0x7fffffff);
+    bk = ((unsigned long long)mh << 32) | ml;
 }
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory"); }
+// warp 0 hands the next column and the candidate row to the other warps
+__device__ __forceinline__ void handoff_arrive() { asm volatile("bar.arrive 1, %0;\n" ::"n"(kPanelThreads) : "memory"); }
+__device__ __forceinline__ void handoff_wait() { asm volatile("bar.sync 1, %0;\n" ::"n"(kPanelThreads) : "memory"); }
 
 size_t gj_panel_smem(int k) {
     const size_t rpc = (size_t)((k + kPCS - 1) / kPCS);
@@ -228,15 +243,17 @@ __global__ void __launch_bounds__(kPanelThreads) k_gj_panel(DevState s, int k, i
     const int rpc = (k + kPCS - 1) / kPCS;
     const int a0 = rank * rpc;
     const int nr = max(0, min(rpc, k - a0));
+    const int lane = threadIdx.x & 31;
+    const bool w0 = threadIdx.x < 32;
     extern __shared__ double psm[];
     double* pan = psm;                                          // rpc x kPLD, row-major
-    double* fcol = pan + (size_t)rpc * kPLD;                    // column t of the local rows
+    double* fcol = pan + (size_t)rpc * kPLD;                    // column t of the local rows before step t
     int* done = reinterpret_cast<int*>(fcol + rpc);             // row already a pivot
-    __shared__ double g[2][kNB];                                // scaled pivot row, by step parity
-    __shared__ unsigned long long ckey[2];
+    __shared__ double g[3][kNB];                                // scaled pivot row of step t in g[t % 3]
+    __shared__ unsigned long long ckey[2];                      // published candidate of step t in [t & 1]
     __shared__ int crow[2];
     __shared__ int piv[kNB];
-    __shared__ double rinv_sh;
+    __shared__ int cand_sh;                                     // local row of the published candidate, or -1
     __shared__ int fail_sh;
     for (int e = threadIdx.x; e < nr * w; e += blockDim.x) {
         const int r = e % nr, t = e / nr;
@@ -245,64 +262,108 @@ __global__ void __launch_bounds__(kPanelThreads) k_gj_panel(DevState s, int k, i
     for (int r = threadIdx.x; r < nr; r += blockDim.x) done[r] = s.rv_rowdone[a0 + r];
     if (threadIdx.x == 0) fail_sh = 0;
     __syncthreads();
-    int prev_local = -1;  // local row of the previous step's pivot, if owned here
-    for (int t = 0; t < w; ++t) {
-        const int par = t & 1;
-        if (threadIdx.x < 32) {
-            unsigned long long bk = 0ull;
-            int br = 0x7fffffff;
-            for (int r = threadIdx.x; r < nr; r += 32) {
-                if (done[r]) continue;
-                const unsigned long long kk = mag_key(pan[r * kPLD + t]);
-                if (cand_better(kk, a0 + r, bk, br)) { bk = kk; br = a0 + r; }
-            }
-            warp_best(bk, br);
-            if (threadIdx.x == 0) { ckey[par] = bk; crow[par] = br; }
+    if (w0) {  // candidate of step 0: column c0 is up to date
+        unsigned long long bk = 0ull;
+        int br = 0x7fffffff;
+        for (int r = lane; r < nr; r += 32) {
+            if (done[r]) continue;
+            const unsigned long long kk = mag_key(pan[r * kPLD]);
+            if (cand_better(kk, a0 + r, bk, br)) { bk = kk; br = a0 + r; }
         }
-        cl.sync();
-        if (threadIdx.x < 32) {
+        warp_best(bk, br);
+        if (lane == 0) { ckey[0] = bk; crow[0] = br; }
+    }
+    cluster_arrive();
+    int prev_local = -1;  // local row of the previous step's pivot, if owned here
+    bool fail = false;
+    for (int t = 0; t < w; ++t) {
+        const int gb = t % 3, gp = (t + 2) % 3;  // g of this step and of the previous one
+        cluster_wait();
+        if (w0) {
             unsigned long long bk = 0ull;
             int br = 0x7fffffff;
-            if (threadIdx.x < kPCS) {
-                bk = *cl.map_shared_rank(&ckey[par], threadIdx.x);
-                br = *cl.map_shared_rank(&crow[par], threadIdx.x);
+            if (lane < kPCS) {
+                bk = *cl.map_shared_rank(&ckey[t & 1], lane);
+                br = *cl.map_shared_rank(&crow[t & 1], lane);
             }
             warp_best(bk, br);
             if (bk == 0ull || br < 0 || br >= k) {
-                if (threadIdx.x == 0) fail_sh = 1;
+                if (lane == 0) fail_sh = 1;
             } else {
                 const int owner = br / rpc;
                 const double* src = cl.map_shared_rank(pan, owner) + (size_t)(br - owner * rpc) * kPLD;
-                const double pr = threadIdx.x < w ? src[threadIdx.x] : 0.0;
+                const double pr = lane < w ? src[lane] : 0.0;
                 const double pv = __shfl_sync(0xffffffffu, pr, t);
                 const double ri = 1.0 / pv;
-                if (threadIdx.x < w) g[par][threadIdx.x] = (threadIdx.x == t) ? ri : pr * ri;
-                if (threadIdx.x == 0) { piv[t] = br; rinv_sh = ri; }
+                if (lane < w) g[gb][lane] = (lane == t) ? ri : pr * ri;
+                if (lane == 0) piv[t] = br;
             }
-        } else {
-            for (int r = threadIdx.x - 32; r < nr; r += blockDim.x - 32)
-                fcol[r] = (r == prev_local) ? g[par ^ 1][t] : pan[r * kPLD + t];
         }
-        __syncthreads();
-        if (fail_sh) break;
+        __syncthreads();  // g, piv; the other warps are done with step t-1
+        if (fail_sh) {
+            fail = true;
+            break;
+        }
         const int p = piv[t];
         const int lp = (p >= a0 && p < a0 + nr) ? p - a0 : -1;
-        const double ri = rinv_sh;
-        for (int e = threadIdx.x; e < nr * w; e += blockDim.x) {
-            const int r = e / w, j = e - r * w;
-            if (r == lp) continue;  // read by the other CTAs during this step
-            const double f = fcol[r];
-            const double old = (r == prev_local) ? g[par ^ 1][j] : pan[r * kPLD + j];
-            pan[r * kPLD + j] = (j == t) ? -f * ri : fma(-f, g[par][j], old);
+        const bool next = t + 1 < w;
+        if (w0) {
+            // column t of every local row before the step, then column t+1
+            // after it (not the pivot row) and the candidate for step t+1
+            unsigned long long bk = 0ull;
+            int br = 0x7fffffff;
+            for (int r = lane; r < nr; r += 32) {
+                const bool pr_row = r == prev_local;
+                const double f = pr_row ? g[gp][t] : pan[r * kPLD + t];
+                fcol[r] = f;
+                if (next && r != lp) {
+                    const double old = pr_row ? g[gp][t + 1] : pan[r * kPLD + t + 1];
+                    const double v = fma(-f, g[gb][t + 1], old);
+                    pan[r * kPLD + t + 1] = v;
+                    if (!done[r]) {
+                        const unsigned long long kk = mag_key(v);
+                        if (cand_better(kk, a0 + r, bk, br)) { bk = kk; br = a0 + r; }
+                    }
+                }
+            }
+            int cand = -1;
+            if (next) {
+                warp_best(bk, br);
+                if (bk != 0ull) cand = br - a0;
+                __syncwarp();
+                if (cand >= 0 && lane < w && lane != t + 1) {  // the candidate row, complete
+                    const double f = fcol[cand];
+                    double* e = pan + cand * kPLD + lane;
+                    *e = (lane == t) ? -f * g[gb][t] : fma(-f, g[gb][lane], *e);
+                }
+                if (lane == 0) { ckey[(t + 1) & 1] = bk; crow[(t + 1) & 1] = br; }
+            }
+            if (lane == 0) {
+                cand_sh = cand;
+                if (lp >= 0) done[lp] = 1;
+            }
+            handoff_arrive();
+            cluster_arrive();
+        } else {
+            handoff_wait();
+            cluster_arrive();
+            const int cand = cand_sh;
+            const double ri = g[gb][t];
+            for (int e = threadIdx.x - 32; e < nr * w; e += blockDim.x - 32) {
+                const int r = e / w, j = e - r * w;
+                if (r == lp || r == cand || j == t + 1) continue;  // pivot row: read by the other CTAs
+                const double f = fcol[r];
+                const double old = (r == prev_local) ? g[gp][j] : pan[r * kPLD + j];
+                pan[r * kPLD + j] = (j == t) ? -f * ri : fma(-f, g[gb][j], old);
+            }
         }
-        if (lp >= 0 && threadIdx.x == 0) done[lp] = 1;
         prev_local = lp;
-        __syncthreads();
     }
-    cl.sync();  // every CTA has read the last pivot row
-    const int fail = fail_sh;
+    if (fail) cluster_arrive();
+    cluster_wait();  // every CTA has read the last pivot row
+    __syncthreads();
     if (!fail && prev_local >= 0) {
-        const int lw = (w - 1) & 1;
+        const int lw = (w - 1) % 3;
         for (int j = threadIdx.x; j < w; j += blockDim.x) pan[prev_local * kPLD + j] = g[lw][j];
     }
     __syncthreads();
@@ -370,6 +431,120 @@ __global__ void __launch_bounds__(kTrailThreads) k_gj_trail(DevState s, int k, i
     }
 }
 
+// ---- Reinversion by refinement ---------------------------------------------
+// A periodic reinversion starts from the updated inverse of the same basis
+// (the engines apply the last pivot's update before they stop for it), which
+// after at most reinvert_every rank-1 updates is close to B^-1.  One step of
+// the Newton-Schulz iteration for the matrix inverse (G. Schulz, 1933),
+//     Y1 = Y0 + Y0 (I - B11 Y0),   I - B11 Y1 = (I - B11 Y0)^2,
+// squares the residual of B11^-1: from ||I - B11 Y0||_inf <= kRefineTol the
+// new residual is below the rounding of the products, as after a fresh
+// elimination, for two k x k x k FP64 products instead of k sequential pivot
+// steps.  The slack rows -A[S, J] B11^-1 then follow from Y1 as after an
+// elimination.  A larger residual (or a NaN) falls back to Gauss-Jordan.
+//
+// Scratch: B11 (column-major, from k_gather), Y0 and R = I - B11 Y0
+// (row-major) in rv_M, which needs 3 k^2 <= m^2; per-tile partial row sums of
+// |R| after the first k^2 entries of rv_W; Y1 into rv_W, where the
+// elimination leaves B11^-1.
+
+// Y0[b][a] = stored B^-1[P_b][R_a]: the dense inverse, or the live column of
+// row R_a in the slack-structured state (slot map `par`, `k_live` live slots).
+__global__ void k_refine_extract(DevState s, int k, int from_struct, int k_live, int par) {
+    if (s.ctrl->err != kErrNone) return;
+    const size_t total = (size_t)k * k;
+    double* Y = s.rv_M + total;
+    const int32_t* rs = s.row_slot + (size_t)par * s.p.m;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / k), a = (int)(e % k);
+        const size_t prow = (size_t)s.rv_struct_pos[b] * s.p.ld;
+        const int i = s.rv_rows[a];
+        double v = 0.0;
+        if (from_struct) {
+            const int sl = rs[i];
+            if (sl >= 0 && sl < k_live) v = s.bp[prow + sl];
+        } else {
+            v = s.binv[prow + i];
+        }
+        Y[e] = v;
+    }
+}
+
+// kMode 0: R[i][c] = [i == c] - sum_l B11[i][l] Y0[l][c], and the sum of |R|
+//          over the tile's columns (in column order) per row into the partials;
+// kMode 1: Y1[i][c] = Y0[i][c] + sum_l Y0[i][l] R[l][c], into rv_W.
+// Each output is one fused multiply-add chain in increasing l, so the result
+// does not depend on the launch shape.  kRT x kRT tiles keep the SMs' shares
+// within one small tile of each other at k of a few hundred.
+constexpr int kRT = 8;
+template <int kMode>
+__global__ void __launch_bounds__(kRT * kRT) k_refine_gemm(DevState s, int k) {
+    if (s.ctrl->err != kErrNone) return;
+    const size_t kk = (size_t)k * k;
+    const double* B11 = s.rv_M;
+    const double* Y0 = s.rv_M + kk;
+    double* R = s.rv_M + 2 * kk;
+    const int tx = threadIdx.x % kRT, ty = threadIdx.x / kRT;
+    const int i = blockIdx.y * kRT + ty, c = blockIdx.x * kRT + tx;
+    const bool in = i < k && c < k;
+    double acc = 0.0;
+    if (in) {
+        if (kMode == 0) {
+            const double* x = B11 + i;  // B11[i][l] at l*k + i
+            const double* z = Y0 + c;   // Y0[l][c] at l*k + c
+#pragma unroll 8
+            for (int l = 0; l < k; ++l) acc = fma(x[(size_t)l * k], z[(size_t)l * k], acc);
+        } else {
+            const double* x = Y0 + (size_t)i * k;  // Y0[i][l]
+            const double* z = R + c;               // R[l][c] at l*k + c
+#pragma unroll 8
+            for (int l = 0; l < k; ++l) acc = fma(x[l], z[(size_t)l * k], acc);
+        }
+    }
+    if (kMode == 0) {
+        __shared__ double rabs[kRT][kRT];
+        double v = 0.0;
+        if (in) {
+            v = (i == c ? 1.0 : 0.0) - acc;
+            R[(size_t)i * k + c] = v;
+        }
+        rabs[ty][tx] = fabs(v);
+        __syncthreads();
+        if (tx == 0 && i < k) {
+            double t = 0.0;
+#pragma unroll
+            for (int u = 0; u < kRT; ++u) t += rabs[ty][u];
+            s.rv_W[kk + (size_t)i * gridDim.x + blockIdx.x] = t;
+        }
+    } else if (in) {
+        s.rv_W[(size_t)i * k + c] = Y0[(size_t)i * k + c] + acc;
+    }
+}
+
+// ||R||_inf from the partial row sums (each row summed in tile order) into
+// ctrl->refine_res; a NaN row counts as infinite.
+__global__ void __launch_bounds__(1024) k_refine_norm(DevState s, int k, int ntc) {
+    __shared__ double wmax[32];
+    const double* part = s.rv_W + (size_t)k * k;
+    double mx = 0.0;
+    if (s.ctrl->err == kErrNone)
+        for (int a = threadIdx.x; a < k; a += blockDim.x) {
+            double r = 0.0;
+            for (int t = 0; t < ntc; ++t) r += part[(size_t)a * ntc + t];
+            if (!(r >= 0.0)) r = DBL_MAX;  // NaN
+            mx = fmax(mx, r);
+        }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
+        s.ctrl->refine_res = s.ctrl->err == kErrNone ? m : DBL_MAX;
+    }
+}
+
 // pinv[pivrow[t]] = t (stored over rv_rowdone, no longer needed)
 __global__ void k_pivinv(DevState s, int k) {
     if (s.ctrl->err != kErrNone) return;
@@ -379,10 +554,11 @@ __global__ void k_pivinv(DevState s, int k) {
     }
 }
 
-// J[b], c_J[b] and the dense B11^-1 (row b, column a) = M[pinv[a]*k + pivrow[b]]
-__global__ void k_b11i(DevState s, int k) {
+// J[b], c_J[b] and, after an elimination, the dense B11^-1 (row b, column a)
+// = M[pinv[a]*k + pivrow[b]] (a refinement writes it directly)
+__global__ void k_b11i(DevState s, int k, int from_gj) {
     if (s.ctrl->err != kErrNone) return;
-    const size_t total = (size_t)k * k;
+    const size_t total = from_gj ? (size_t)k * k : 0;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(e / k), a = (int)(e % k);
@@ -619,13 +795,31 @@ void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t s
     k_pivinv<<<(k + 255) / 256, 256, 0, st>>>(s, k);
 }
 
-void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st) {
+bool refine_fits(int k, int m) { return k > 0 && 3 * (size_t)k * k <= (size_t)m * m; }
+
+void launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st) {
+    const size_t kk = (size_t)k * k;
+    int blocks = (int)((kk + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_gather<<<blocks, 256, 0, st>>>(s, k);
+    k_refine_extract<<<blocks, 256, 0, st>>>(s, k, from_struct, k_live, par);
+    const int nt = (k + kRT - 1) / kRT;
+    k_refine_gemm<0><<<dim3(nt, nt), kRT * kRT, 0, st>>>(s, k);
+    k_refine_norm<<<1, 1024, 0, st>>>(s, k, nt);
+}
+
+void launch_refine_apply(const DevState& s, int k, cudaStream_t st) {
+    const int nt = (k + kRT - 1) / kRT;
+    k_refine_gemm<1><<<dim3(nt, nt), kRT * kRT, 0, st>>>(s, k);
+}
+
+void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj) {
     const int nslack = s.p.m - k;
     if (k > 0) {
         const size_t kk = (size_t)k * k;
         int blocks = (int)((kk + 255) / 256);
         if (blocks > 4096) blocks = 4096;
-        k_b11i<<<blocks, 256, 0, st>>>(s, k);
+        k_b11i<<<blocks, 256, 0, st>>>(s, k, from_gj);
         if (nslack > 0) {
             dim3 grid((k + kGN - 1) / kGN, (nslack + kGM - 1) / kGM);
             k_slack_gemm<<<grid, 256, 0, st>>>(s, k, nslack);
