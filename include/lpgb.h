@@ -107,6 +107,10 @@ typedef struct lp_options {
                                CUDA graphs wherever the device refuses a cooperative launch) */
     int32_t anticycling;    /* LP_ANTICYCLING_*: the tabu rule of Sections 2.2/3.4 (default) or
                                the lexicographic rule it is compared with */
+    int32_t reinvert_refine; /* 1 (default): a periodic reinversion refines the updated inverse
+                               by one Newton-Schulz step, Y + Y (I - B11 Y), when
+                               ||I - B11 Y||_inf <= 2^-26 (else, and with 0, B11 is
+                               eliminated afresh by Gauss-Jordan); needs 3 k^2 <= m^2 */
     double tol_d;           /* optimality tolerance on the reduced costs */
     double tol_piv;         /* smallest admissible pivot alpha_r */
     double tol_tie;         /* relative width of the ratio-test tie set */
@@ -147,6 +151,8 @@ typedef struct lp_result {
                                 slack-structured one, 0: in captured graphs */
     int32_t phase1_iterations; /* b with negative entries: pivots of the Phase I problem */
     int32_t phase1_exchanged;  /* 1: the artificial ended basic at zero and was exchanged */
+    int32_t refined_reinversions; /* reinversions done by refinement (reinvert_refine) */
+    int32_t reserved2;
 } lp_result;
 
 /*

@@ -633,12 +633,11 @@ __device__ void pivot_bookkeeping(const DevState& s, IterState& S, bool lead) {
         if (lead) S.n_bland++;
     }
     S.flags = 0;
+    S.pending = 1;  // at a reinversion too: the update is applied before the launch stops
     if (P.reinvert_every > 0 && it1 % P.reinvert_every == 0) {
         S.status = kReinvert;
-        S.pending = 0;
-    } else {
-        S.pending = 1;
-        if (it1 >= P.max_iters) S.status = kIterLimit;
+    } else if (it1 >= P.max_iters) {
+        S.status = kIterLimit;
     }
 }
 

@@ -125,13 +125,9 @@ __global__ void __launch_bounds__(kPivotThreads) k_pivot(DevState s) {
         C->n_bland++;
     }
     C->flags = 0;
-    if (P.reinvert_every > 0 && it1 % P.reinvert_every == 0) {
-        C->status = kReinvert;
-        C->pending = 0;
-    } else {
-        C->pending = 1;
-        if (it1 >= P.max_iters) C->status = kIterLimit;
-    }
+    C->pending = 1;  // at a reinversion too: the next k_update applies it (B^-1 stays that of the basis)
+    if (P.reinvert_every > 0 && it1 % P.reinvert_every == 0) C->status = kReinvert;
+    else if (it1 >= P.max_iters) C->status = kIterLimit;
     __threadfence();
 }
 
@@ -503,7 +499,6 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
                 if (k < P.m) s.bbar[k] = (k == r) ? th : __dsub_rn(bb, __dmul_rn(ak, th));
             }
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
-            if (S.status == kReinvert) break;
         }
         double* rh = sh + P.ld;  // rho for UPDATE, staged with y
         // ---- (2) PRICE + CHUZC
@@ -587,7 +582,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate(DevState s, int i
             }
         }
         if (!do_ftran) {
-            // the pending update of the last pivot was applied (optimal or iteration limit)
+            // the pending update of the last pivot was applied (optimal, iteration limit or reinversion)
             if (threadIdx.x == 0) S.pending = 0;
             break;
         }

@@ -679,7 +679,6 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
             }
         }
         const bool yrange = __syncthreads_or(ybig) == 0;  // y, rho, the A_p moves and thread 0's bookkeeping are done
-        if (S.status == kReinvert) break;  // the slot moves are complete; B^-1 is rebuilt
         if (S.status == kRunning) {
             const int32_t* sr = s.slot_row + (size_t)par * P.m;  // + the patch: the map after the moves
             // the FP32 screen unless the safety net needs every improving column

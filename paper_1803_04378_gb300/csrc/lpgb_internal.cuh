@@ -95,6 +95,7 @@ struct Ctrl {
     double theta;          // step length bbar_r / alpha_r
     double alpha_r;        // pivot element
     double z;              // objective c_B^T bbar
+    double refine_res;     // reinversion by refinement: ||I - B11 Y0||_inf of the stored inverse
 };
 
 // Per-CTA ratio-test record of k_iterate: the CTA's smallest ratio, and its
@@ -290,7 +291,10 @@ void launch_csc_fill(const double* A_cm, int m, int n, int ld, const int64_t* pt
 void launch_reinv_classify(const DevState& s, cudaStream_t st);
 void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t st);
 int reinv_gj_launches(int k);
-void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st);
+void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj);
+bool refine_fits(int k, int m);
+void launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st);
+void launch_refine_apply(const DevState& s, int k, cudaStream_t st);
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible);
 int occupancy_price(int ld);
 int occupancy_price_lp(int ld);

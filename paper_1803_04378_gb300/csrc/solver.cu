@@ -41,6 +41,7 @@ struct lp_handle {
     std::vector<int32_t> warm_basis;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr, erg = nullptr, era = nullptr;
     double reinv_gj_s = 0.0, reinv_asm_s = 0.0;
+    int32_t reinv_refined = 0;       // reinversions of this solve done by refinement
     std::vector<cudaEvent_t> tev;    // kernel_timing: 3 events per timed iteration of the graph
     bool persist = false;            // pivots run in k_iterate (cooperative, one CTA per SM)
     int persist_blocks = 0;
@@ -204,18 +205,43 @@ int capture_graph(lp_handle* h) {
     return capture_graph_once(h, false);
 }
 
-// Rebuild B^-1, bbar, y, z from the current basis.
-int reinvert(lp_handle* h, int check_feasible) {
+// Largest ||I - B11 Y0||_inf of the stored inverse that a reinversion refines
+// (one Newton-Schulz step then leaves a residual at the rounding level);
+// above it the basis is eliminated afresh.
+constexpr double kRefineTol = 1.0 / 67108864.0;  // 2^-26
+
+// Rebuild B^-1, bbar, y, z from the current basis.  `refine`: the stored
+// inverse is that of the current basis (a periodic reinversion, the last
+// update applied), so B11^-1 may come from one refinement step of it.
+int reinvert(lp_handle* h, int check_feasible, bool refine) {
     CK(cudaEventRecord(h->er0, h->stream));
     launch_reinv_classify(h->ds, h->stream);
     TRY(read_ctrl(h));
     if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
     const int k = h->h_ctrl->k_struct;
-    h->launches += 1 + reinv_gj_launches(k) + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 3;
     CK(cudaEventRecord(h->erg, h->stream));
-    launch_reinv_gj(h->ds, k, h->geo, h->stream);
+    bool refined = false;
+    if (refine && h->opt.reinvert_refine && h->h_ctrl->pending == 0 && refine_fits(k, h->m)) {
+        const bool from_struct = h->structured && h->s_ready;
+        launch_refine_residual(h->ds, k, from_struct ? 1 : 0, h->h_ctrl->k_live, h->h_ctrl->map_par, h->stream);
+        CK(cudaGetLastError());
+        h->launches += 4;
+        TRY(read_ctrl(h));
+        if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
+        if (h->h_ctrl->refine_res <= kRefineTol) {
+            launch_refine_apply(h->ds, k, h->stream);
+            h->launches += 1;
+            h->reinv_refined++;
+            refined = true;
+        }
+    }
+    if (!refined) {
+        launch_reinv_gj(h->ds, k, h->geo, h->stream);
+        h->launches += reinv_gj_launches(k);
+    }
+    h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 3;
     CK(cudaEventRecord(h->era, h->stream));
-    launch_reinv_assemble(h->ds, k, h->geo, h->stream);
+    launch_reinv_assemble(h->ds, k, h->geo, h->stream, refined ? 0 : 1);
     launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible);
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->er1, h->stream));
@@ -380,6 +406,7 @@ void lp_default_options(lp_options* o) {
     o->kernel_timing = 0;
     o->engine = LP_ENGINE_STRUCTURED;
     o->anticycling = LP_ANTICYCLING_TABU;
+    o->reinvert_refine = 1;
     o->tol_d = 1e-9;
     o->tol_piv = 1e-9;
     o->tol_tie = 1e-12;
@@ -641,7 +668,7 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     lp_options o;
     lp_default_options(&o);
     if (opt) o = *opt;
-    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > LP_ENGINE_STRUCTURED || o.anticycling < 0 || o.anticycling > 1 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
+    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > LP_ENGINE_STRUCTURED || o.anticycling < 0 || o.anticycling > 1 || o.reinvert_refine < 0 || o.reinvert_refine > 1 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
         o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 2 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
@@ -724,6 +751,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
     CK(cudaEventRecord(h->ev0, h->stream));
     h->reinvert_seconds = 0.0;
     h->reinv_gj_s = h->reinv_asm_s = 0.0;
+    h->reinv_refined = 0;
     h->price_s = h->update_s = h->price_b = h->update_b = 0.0;
     h->price_n = h->update_n = 0;
     h->chain_s = h->chain_b = 0.0;
@@ -760,9 +788,9 @@ int lp_solve(lp_handle* h, lp_result* out) {
         CK(cudaGetLastError());
         h->warm_pending = false;
         if (h->warm_repair_max < 0) {
-            TRY(reinvert(h, 1));
+            TRY(reinvert(h, 1, false));
         } else {
-            int rc = reinvert(h, 0);
+            int rc = reinvert(h, 0, false);
             bool ok = rc == LP_OK;
             if (rc != LP_OK && rc != LP_ERR_SINGULAR) return rc;
             while (ok) {
@@ -777,7 +805,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
                 h->launches += 4;
                 warm_repairs++;
                 TRY(read_ctrl(h));
-                if (h->h_ctrl->status == kReinvert) TRY(reinvert(h, 0));
+                if (h->h_ctrl->status == kReinvert) TRY(reinvert(h, 0, true));
                 else if (h->h_ctrl->status != kRunning) break;
             }
             if (!ok) {
@@ -792,7 +820,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
         const Ctrl& C = *h->h_ctrl;
         if (C.err != kErrNone) return device_err_code(C.err);
         if (C.status == kReinvert) {
-            TRY(reinvert(h, 0));
+            TRY(reinvert(h, 0, true));
             continue;
         }
         if (C.status != kRunning) break;
@@ -828,7 +856,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
             // continue on the dense engines
             (void)cudaGetLastError();
             h->structured = false;
-            TRY(reinvert(h, 0));
+            TRY(reinvert(h, 0, false));
             continue;
         }
         if (!h->primed) {
@@ -933,6 +961,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->persistent = h->structured ? 2 : (h->persist ? 1 : 0);
         out->phase1_iterations = phase1_iters;
         out->phase1_exchanged = phase1_exch;
+        out->refined_reinversions = h->reinv_refined;
     }
     return LP_OK;
 }

@@ -38,7 +38,7 @@ class lp_options(ctypes.Structure):
                 ("price_mode", ctypes.c_int32), ("topk", ctypes.c_int32),
                 ("trace_cap", ctypes.c_int32), ("graph_iters", ctypes.c_int32),
                 ("kernel_timing", ctypes.c_int32), ("engine", ctypes.c_int32),
-                ("anticycling", ctypes.c_int32),
+                ("anticycling", ctypes.c_int32), ("reinvert_refine", ctypes.c_int32),
                 ("tol_d", ctypes.c_double), ("tol_piv", ctypes.c_double),
                 ("tol_tie", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
 
@@ -59,7 +59,8 @@ class lp_result(ctypes.Structure):
                 ("reinvert_assemble_seconds", ctypes.c_double), ("chain_seconds", ctypes.c_double),
                 ("chain_bytes", ctypes.c_double), ("chain_launches", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("phase1_iterations", ctypes.c_int32),
-                ("phase1_exchanged", ctypes.c_int32)]
+                ("phase1_exchanged", ctypes.c_int32), ("refined_reinversions", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
 
 
 class lp_batch_result(ctypes.Structure):
@@ -209,6 +210,7 @@ class Result:
     persistent: int = 0
     phase1_iterations: int = 0
     phase1_exchanged: int = 0
+    refined_reinversions: int = 0
 
     @property
     def status_name(self) -> str:
@@ -270,7 +272,7 @@ class LP:
                       r.kernel_launches, r.warm_repairs, r.warm_fallback, r.screen_passes,
                       r.full_passes, r.reinvert_gj_seconds, r.reinvert_assemble_seconds,
                       r.chain_seconds, r.chain_bytes, r.chain_launches, r.persistent,
-                      r.phase1_iterations, r.phase1_exchanged)
+                      r.phase1_iterations, r.phase1_exchanged, r.refined_reinversions)
 
     def reset(self):
         _check(_lib.lp_reset(self._h), "lp_reset")
