@@ -520,6 +520,11 @@ def main():
             "time_to_optimum_s": elapsed / args.steps,
             "pivots_per_solve": results[0].iterations,
             "reinversions_per_solve": results[0].reinversions,
+            "refined_reinversions_per_solve": results[0].refined_reinversions,
+            "refine_residual_max": max(r.refine_residual_max for r in results),
+            "reinversion_parts_s": {"refinement_or_elimination": sum(r.reinvert_gj_seconds for r in results) / len(results),
+                                    "slack_rows_assembly_bbar_y": sum(r.reinvert_assemble_seconds for r in results) / len(results),
+                                    "total": reinv_s / len(results)},
             "objective": z,
             "certificate": _certificate(A, b, c, x, y),
             "us_per_pivot_excl_reinversion": 1e6 * iter_s / iters,

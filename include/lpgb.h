@@ -153,6 +153,8 @@ typedef struct lp_result {
     int32_t phase1_exchanged;  /* 1: the artificial ended basic at zero and was exchanged */
     int32_t refined_reinversions; /* reinversions done by refinement (reinvert_refine) */
     int32_t reserved2;
+    double refine_residual_max;   /* largest ||I - B11 Y||_inf of the updated inverse found by the
+                                     refinement checks of this solve (drift of the updates) */
 } lp_result;
 
 /*

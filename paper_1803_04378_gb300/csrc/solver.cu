@@ -42,6 +42,7 @@ struct lp_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr, erg = nullptr, era = nullptr;
     double reinv_gj_s = 0.0, reinv_asm_s = 0.0;
     int32_t reinv_refined = 0;       // reinversions of this solve done by refinement
+    double refine_res_max = 0.0;     // largest residual the refinement checks of this solve found
     std::vector<cudaEvent_t> tev;    // kernel_timing: 3 events per timed iteration of the graph
     bool persist = false;            // pivots run in k_iterate (cooperative, one CTA per SM)
     int persist_blocks = 0;
@@ -228,6 +229,7 @@ int reinvert(lp_handle* h, int check_feasible, bool refine) {
         h->launches += 4;
         TRY(read_ctrl(h));
         if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
+        h->refine_res_max = std::max(h->refine_res_max, h->h_ctrl->refine_res);
         if (h->h_ctrl->refine_res <= kRefineTol) {
             launch_refine_apply(h->ds, k, h->stream);
             h->launches += 1;
@@ -752,6 +754,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
     h->reinvert_seconds = 0.0;
     h->reinv_gj_s = h->reinv_asm_s = 0.0;
     h->reinv_refined = 0;
+    h->refine_res_max = 0.0;
     h->price_s = h->update_s = h->price_b = h->update_b = 0.0;
     h->price_n = h->update_n = 0;
     h->chain_s = h->chain_b = 0.0;
@@ -962,6 +965,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->phase1_iterations = phase1_iters;
         out->phase1_exchanged = phase1_exch;
         out->refined_reinversions = h->reinv_refined;
+        out->refine_residual_max = h->refine_res_max;
     }
     return LP_OK;
 }

@@ -60,7 +60,7 @@ class lp_result(ctypes.Structure):
                 ("chain_bytes", ctypes.c_double), ("chain_launches", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("phase1_iterations", ctypes.c_int32),
                 ("phase1_exchanged", ctypes.c_int32), ("refined_reinversions", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("reserved2", ctypes.c_int32), ("refine_residual_max", ctypes.c_double)]
 
 
 class lp_batch_result(ctypes.Structure):
@@ -211,6 +211,7 @@ class Result:
     phase1_iterations: int = 0
     phase1_exchanged: int = 0
     refined_reinversions: int = 0
+    refine_residual_max: float = 0.0
 
     @property
     def status_name(self) -> str:
@@ -272,7 +273,8 @@ class LP:
                       r.kernel_launches, r.warm_repairs, r.warm_fallback, r.screen_passes,
                       r.full_passes, r.reinvert_gj_seconds, r.reinvert_assemble_seconds,
                       r.chain_seconds, r.chain_bytes, r.chain_launches, r.persistent,
-                      r.phase1_iterations, r.phase1_exchanged, r.refined_reinversions)
+                      r.phase1_iterations, r.phase1_exchanged, r.refined_reinversions,
+                      r.refine_residual_max)
 
     def reset(self):
         _check(_lib.lp_reset(self._h), "lp_reset")
