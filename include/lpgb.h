@@ -109,11 +109,14 @@ typedef struct lp_options {
                                the lexicographic rule it is compared with */
     int32_t reinvert_refine; /* 1 (default): a periodic reinversion refines the updated inverse
                                by one Newton-Schulz step, Y + Y (I - B11 Y), when
-                               ||I - B11 Y||_inf <= 2^-26 (else, and with 0, B11 is
+                               ||I - B11 Y||_inf <= refine_tol (else, and with 0, B11 is
                                eliminated afresh by Gauss-Jordan); needs 3 k^2 <= m^2 */
     double tol_d;           /* optimality tolerance on the reduced costs */
     double tol_piv;         /* smallest admissible pivot alpha_r */
     double tol_tie;         /* relative width of the ratio-test tie set */
+    double refine_tol;      /* reinvert_refine: largest ||I - B11 Y||_inf that is refined (default
+                               and maximum 2^-26, so that one step leaves the residual below
+                               2^-52; 0 refines only an exact inverse) */
     void* cuda_stream;      /* cudaStream_t to run on; NULL: the handle's own stream */
 } lp_options;
 

@@ -206,10 +206,10 @@ int capture_graph(lp_handle* h) {
     return capture_graph_once(h, false);
 }
 
-// Largest ||I - B11 Y0||_inf of the stored inverse that a reinversion refines
-// (one Newton-Schulz step then leaves a residual at the rounding level);
-// above it the basis is eliminated afresh.
-constexpr double kRefineTol = 1.0 / 67108864.0;  // 2^-26
+// Largest admissible refine_tol, ||I - B11 Y0||_inf of the stored inverse that
+// a reinversion refines (one Newton-Schulz step then leaves a residual below
+// 2^-52, at the rounding level); above it the basis is eliminated afresh.
+constexpr double kRefineTolMax = 1.0 / 67108864.0;  // 2^-26
 
 // Rebuild B^-1, bbar, y, z from the current basis.  `refine`: the stored
 // inverse is that of the current basis (a periodic reinversion, the last
@@ -230,7 +230,7 @@ int reinvert(lp_handle* h, int check_feasible, bool refine) {
         TRY(read_ctrl(h));
         if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
         h->refine_res_max = std::max(h->refine_res_max, h->h_ctrl->refine_res);
-        if (h->h_ctrl->refine_res <= kRefineTol) {
+        if (h->h_ctrl->refine_res <= h->opt.refine_tol) {
             launch_refine_apply(h->ds, k, h->stream);
             h->launches += 1;
             h->reinv_refined++;
@@ -412,6 +412,7 @@ void lp_default_options(lp_options* o) {
     o->tol_d = 1e-9;
     o->tol_piv = 1e-9;
     o->tol_tie = 1e-12;
+    o->refine_tol = kRefineTolMax;
     o->cuda_stream = nullptr;
 }
 
@@ -671,7 +672,7 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     lp_default_options(&o);
     if (opt) o = *opt;
     if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > LP_ENGINE_STRUCTURED || o.anticycling < 0 || o.anticycling > 1 || o.reinvert_refine < 0 || o.reinvert_refine > 1 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
-        o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 2 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0))
+        o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 2 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0) || !(o.refine_tol >= 0 && o.refine_tol <= kRefineTolMax))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
         if (!finite_all(A, (size_t)m * n) || !finite_all(c, n) || !finite_all(b, m)) return LP_ERR_INVALID_ARG;

@@ -40,7 +40,8 @@ class lp_options(ctypes.Structure):
                 ("kernel_timing", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("anticycling", ctypes.c_int32), ("reinvert_refine", ctypes.c_int32),
                 ("tol_d", ctypes.c_double), ("tol_piv", ctypes.c_double),
-                ("tol_tie", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+                ("tol_tie", ctypes.c_double), ("refine_tol", ctypes.c_double),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class lp_result(ctypes.Structure):

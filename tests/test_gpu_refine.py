@@ -12,6 +12,9 @@ elimination of B11 (needs a GB300).
 * B^-1 right after a refined reinversion agrees with the oracle's fresh
   inverse of the same basis element by element, and B^-1 B = I.
 * With set_basis (no updated inverse to refine) the elimination runs.
+* refine_tol = 0: every residual is computed and rejected, and the
+  elimination that follows gives a run identical, bit for bit, to one without
+  refinement (the fallback path leaves nothing behind).
 """
 import numpy as np
 import pytest
@@ -82,8 +85,26 @@ def test_set_basis_eliminates():
         assert res.reinversions == 1 and res.refined_reinversions == 0
 
 
+@pytest.mark.parametrize("engine", [0, 1, 2])
+def test_rejected_refinement_falls_back(engine):
+    A, b, c = lpgen.dense_real_lp(300, 500, 31)
+    lp1, r1, x1, y1, z1, t1 = gpu_solve(A, b, c, engine=engine, reinvert_every=16, refine_tol=0.0)
+    lp0, r0, x0, y0, z0, t0 = gpu_solve(A, b, c, engine=engine, reinvert_every=16, reinvert_refine=0)
+    assert r1.status == r0.status == 1 and r1.reinversions >= 3
+    assert r1.refined_reinversions == 0 and r1.refine_residual_max > 0.0
+    assert r0.refine_residual_max == 0.0
+    assert np.array_equal(t1["q"], t0["q"]) and np.array_equal(t1["r"], t0["r"])
+    assert z1 == z0 and np.array_equal(x1, x0) and np.array_equal(y1, y0)
+    lp1.close()
+    lp0.close()
+
+
 def test_option_validated():
     from paper_1803_04378_gb300 import lpgb
     A, b, c = lpgen.dense_int_lp(20, 30, 0)
     with pytest.raises(lpgb.LPError):
         lpgb.LP(A, b, c, reinvert_refine=2)
+    with pytest.raises(lpgb.LPError):
+        lpgb.LP(A, b, c, refine_tol=1e-6)
+    with pytest.raises(lpgb.LPError):
+        lpgb.LP(A, b, c, refine_tol=-1.0)
