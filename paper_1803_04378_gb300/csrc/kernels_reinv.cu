@@ -11,7 +11,9 @@
 // positions (slack of row s) = [ -A[s, J] B11^-1 | e_s ].  Only B11 is
 // inverted (2k^3 flops) plus one (m-k) x k x k product, instead of 2m^3.
 //
-// B11^-1 comes from in-place Gauss-Jordan elimination with partial pivoting
+// At a periodic reinversion B11^-1 comes from one Newton-Schulz refinement
+// step of the updated inverse when that is close enough (k_refine_* below);
+// otherwise from in-place Gauss-Jordan elimination with partial pivoting
 // (row pivots chosen among rows not yet used, no physical swaps), blocked in
 // panels of columns (k_gj_panel + k_gj_trail below); per-step kernels remain
 // for a device that refuses the cluster launch.  The matrix lives
