@@ -221,6 +221,21 @@ def run_batched(lpgb, args, with_cpu: bool):
     return out
 
 
+def aggregate_ranks(elapsed: float, iters: int, ws: int, device):
+    """Whole-job figures of N replicas: the slowest rank's time and the pivots
+    of all ranks (value = their ratio).  Needs an initialised process group
+    when ws > 1 (NCCL on the GPUs, gloo in the CPU tests)."""
+    if ws <= 1:
+        return elapsed, iters
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    it_t = torch.tensor([iters], dtype=torch.int64, device=device)
+    dist.all_reduce(it_t)
+    return float(tt.item()), int(it_t.item())
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -359,15 +374,7 @@ def main():
     elapsed = e0.elapsed_time(e1) * 1e-3
     iters = sum(r.iterations for r in results)
     x, y, z = lp.solution()
-    if ws > 1:
-        tt = torch.tensor([elapsed], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(tt.item())
-        it_t = torch.tensor([float(iters)], device="cuda")
-        torch.distributed.all_reduce(it_t)
-        iters_all = int(it_t.item())
-    else:
-        iters_all = iters
+    elapsed, iters_all = aggregate_ranks(elapsed, iters, ws, "cuda")
 
     # dominant kernel and its live roofline
     ps = sum(r.price_seconds for r in results)
