@@ -16,7 +16,9 @@ def main():
     dist.init_process_group("gloo")
     # rank r took 1 + r seconds for 100 (r + 1) pivots
     elapsed, iters = bench.aggregate_ranks(1.0 + rank, 100 * (rank + 1), ws, "cpu")
-    print(json.dumps({"rank": rank, "elapsed": elapsed, "iters": iters}), flush=True)
+    # one file per rank: lines printed by two ranks into one pipe can interleave
+    with open(os.path.join(sys.argv[1], f"rank{rank}.json"), "w") as f:
+        json.dump({"rank": rank, "elapsed": elapsed, "iters": iters}, f)
     dist.barrier()
     dist.destroy_process_group()
 

@@ -23,11 +23,11 @@ def _torchrun(args, timeout):
     return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=timeout)
 
 
-def test_replica_aggregation_gloo():
-    p = _torchrun([os.path.join("tests", "rank_worker.py")], 300)
+def test_replica_aggregation_gloo(tmp_path):
+    p = _torchrun([os.path.join("tests", "rank_worker.py"), str(tmp_path)], 300)
     assert p.returncode == 0, p.stderr[-2000:]
-    lines = [json.loads(x) for x in p.stdout.splitlines() if x.startswith("{")]
-    assert sorted(x["rank"] for x in lines) == [0, 1]
+    lines = [json.load(open(tmp_path / f"rank{r}.json")) for r in (0, 1)]
+    assert [x["rank"] for x in lines] == [0, 1]
     for x in lines:
         assert x["elapsed"] == 2.0 and x["iters"] == 300
 
