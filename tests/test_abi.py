@@ -39,3 +39,30 @@ def test_binding_imports_without_gpu():
     assert o.reinvert_every == 64 and o.tabu_tenure == 7 and o.bland_after == 50
     assert abs(o.tol_d - 1e-9) < 1e-24 and abs(o.tol_tie - 1e-12) < 1e-27
     assert lpgb.lib().lp_strerror(-4) == b"singular basis during reinversion"
+
+
+def test_option_defaults_and_validation_on_host():
+    """lp_default_options and lp_create's argument checks are host code: they
+    run (and reject bad options before any device call) without a GPU."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_1803_04378_gb300 import lpgb
+    o = lpgb.default_options()
+    assert o.engine == lpgb.LP_ENGINE_STRUCTURED and o.anticycling == lpgb.LP_ANTICYCLING_TABU
+    assert o.reinvert_refine == 1 and o.refine_tol == 2.0 ** -26
+    A = np.ones((3, 4))
+    b = np.ones(3)
+    c = np.ones(4)
+    for bad in (dict(reinvert_refine=2), dict(refine_tol=1e-6), dict(refine_tol=-1.0), dict(refine_tol=float("nan")),
+                dict(engine=3), dict(anticycling=2), dict(price_mode=3), dict(graph_iters=0), dict(tol_piv=0.0)):
+        h = ctypes.c_void_p()
+        rc = lpgb.lib().lp_create(ctypes.byref(h), 3, 4, lpgb._ptr(A), lpgb._ptr(b), lpgb._ptr(c), 0,
+                                  ctypes.byref(lpgb.default_options(**bad)))
+        assert rc == lpgb.LP_ERR_INVALID_ARG, bad
+        assert not h.value
+    A[0, 0] = float("inf")
+    h = ctypes.c_void_p()
+    assert lpgb.lib().lp_create(ctypes.byref(h), 3, 4, lpgb._ptr(A), lpgb._ptr(b), lpgb._ptr(c), 0,
+                                ctypes.byref(lpgb.default_options())) == lpgb.LP_ERR_INVALID_ARG
