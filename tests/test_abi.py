@@ -66,3 +66,37 @@ def test_option_defaults_and_validation_on_host():
     h = ctypes.c_void_p()
     assert lpgb.lib().lp_create(ctypes.byref(h), 3, 4, lpgb._ptr(A), lpgb._ptr(b), lpgb._ptr(c), 0,
                                 ctypes.byref(lpgb.default_options())) == lpgb.LP_ERR_INVALID_ARG
+
+
+def test_struct_layout_matches_the_binding(tmp_path):
+    """The ctypes mirrors of the ABI's structs have the C layout: a C
+    program compiled against the header prints every field's offset and the
+    structs' sizes."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_1803_04378_gb300 import lpgb
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lpgb.h"', "int main(void) {"]
+    structs = ((lpgb.lp_options, "lp_options"), (lpgb.lp_result, "lp_result"),
+               (lpgb.lp_batch_result, "lp_batch_result"))
+    for st, cname in structs:
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for name, _ in st._fields_:
+            lines.append(f'printf("{cname} {name} %zu\\n", offsetof({cname}, {name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I", include, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (x.split() for x in out if x)}
+    for st, cname in structs:
+        assert got[(cname, "sizeof")] == ctypes.sizeof(st)
+        for name, _ in st._fields_:
+            assert got[(cname, name)] == getattr(st, name).offset, (cname, name)
