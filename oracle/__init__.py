@@ -34,8 +34,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "simplex_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 OPTIMAL, UNBOUNDED, ITER_LIMIT, SINGULAR, MISMATCH = 1, 2, 3, 4, 5
 INFEASIBLE = 7  # two-phase only: the auxiliary optimum is below -tol (no feasible x)
@@ -45,18 +47,23 @@ TF_DEGENERATE, TF_TABU_PUSH, TF_ASPIRATION, TF_BLAND = 1, 2, 4, 8
 TF_ADOPT_Q, TF_ADOPT_R, TF_TIE_SET = 16, 32, 64
 
 
-def build(force: bool = False) -> str:
-    """Compiles the oracle with gcc (no FP contraction, same bits on x86/Arm)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compiles the oracle with gcc (no FP contraction, same bits on x86/Arm).
+    ``openmp`` builds the parallel variant (same source, -fopenmp), whose
+    results are bit-identical to the serial build."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    path = _LIB_OMP_PATH if openmp else _LIB_PATH
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    if openmp:
+        cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class _Opts(ctypes.Structure):
@@ -83,22 +90,40 @@ class _Trace(ctypes.Structure):
                 ("cap", ctypes.c_int32)]
 
 
-def _load():
-    global _lib
+def _load(threads: int = 1):
+    """The serial library, or the OpenMP one when ``threads`` != 1 (0 = every
+    host core)."""
+    global _lib, _lib_omp
     with _lock:
+        if threads != 1:
+            if _lib_omp is None:
+                _lib_omp = _bind(ctypes.CDLL(build(openmp=True)))
+            _lib_omp.oracle_threads(threads if threads > 0 else (os.cpu_count() or 1))
+            return _lib_omp
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            vp, i32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
-            lib.oracle_solve.restype = i32
-            lib.oracle_solve.argtypes = [i32, i32, vp, vp, vp, ctypes.POINTER(_Opts), vp,
-                                         vp, vp, i32, i32, ctypes.POINTER(_Trace),
-                                         vp, vp, vp, vp, vp, ctypes.POINTER(_Result)]
-            lib.oracle_gj_inverse.restype = i32
-            lib.oracle_gj_inverse.argtypes = [i32, vp, vp]
-            lib.oracle_reduced_costs.restype = None
-            lib.oracle_reduced_costs.argtypes = [i32, i32, vp, vp, vp, vp]
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def threads_used(threads: int) -> int:
+    """Threads the library selected by ``threads`` runs with."""
+    return int(_load(threads).oracle_threads(0))
+
+
+def _bind(lib):
+    """Declares the exported functions' signatures."""
+    vp, i32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    lib.oracle_solve.restype = i32
+    lib.oracle_solve.argtypes = [i32, i32, vp, vp, vp, ctypes.POINTER(_Opts), vp,
+                                 vp, vp, i32, i32, ctypes.POINTER(_Trace),
+                                 vp, vp, vp, vp, vp, ctypes.POINTER(_Result)]
+    lib.oracle_gj_inverse.restype = i32
+    lib.oracle_gj_inverse.argtypes = [i32, vp, vp]
+    lib.oracle_reduced_costs.restype = None
+    lib.oracle_reduced_costs.argtypes = [i32, i32, vp, vp, vp, vp]
+    lib.oracle_threads.restype = i32
+    lib.oracle_threads.argtypes = [i32]
+    return lib
 
 
 def _p(a):
@@ -162,13 +187,16 @@ class Solution:
 
 
 def solve(A, b, c, opts: Options | None = None, start_basis=None, follow=None,
-          follow_status: int = OPTIMAL, want_binv: bool = False, trace_cap: int = 0) -> Solution:
+          follow_status: int = OPTIMAL, want_binv: bool = False, trace_cap: int = 0,
+          threads: int = 1) -> Solution:
     """Runs the oracle on ``max c^T x, A x <= b, x >= 0``.
 
     ``follow=(q_seq, r_seq)`` checks another solver's pivot sequence pivot by
     pivot (see the C file); ``q_seq[t] = -1`` marks where it stopped.
+    ``threads`` != 1 runs the OpenMP build (0 = every host core); its results
+    are bit-identical to the serial build.
     """
-    lib = _load()
+    lib = _load(threads)
     o = opts or Options()
     A = np.ascontiguousarray(A, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -210,9 +238,9 @@ def solve(A, b, c, opts: Options | None = None, start_basis=None, follow=None,
                     res.aspirations, res.adopted, res.mismatch_at, res.mismatch_kind, arrays)
 
 
-def gj_inverse(M) -> np.ndarray:
+def gj_inverse(M, threads: int = 1) -> np.ndarray:
     """Gauss-Jordan inverse with partial pivoting (raises on a zero pivot column)."""
-    lib = _load()
+    lib = _load(threads)
     M = np.ascontiguousarray(M, dtype=np.float64)
     k = M.shape[0]
     out = np.zeros_like(M)
@@ -222,9 +250,9 @@ def gj_inverse(M) -> np.ndarray:
     return out
 
 
-def reduced_costs(A, c, y) -> np.ndarray:
+def reduced_costs(A, c, y, threads: int = 1) -> np.ndarray:
     """d_j = c_j - y^T a_j for j < n and d_{n+i} = -y_i."""
-    lib = _load()
+    lib = _load(threads)
     A = np.ascontiguousarray(A, dtype=np.float64)
     c = np.ascontiguousarray(c, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)

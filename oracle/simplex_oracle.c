@@ -7,6 +7,13 @@
  * plain loops, sums in increasing index order, no BLAS.  It is compiled with
  * -ffp-contract=off so that x86 and Arm hosts produce the same bits.
  *
+ * Parallel build (-fopenmp, liboracle_omp.so): the loops over independent
+ * output elements -- PRICE over columns j, FTRAN and the Step 8 update over
+ * rows i, the Gauss-Jordan elimination over rows, bbar and y after a
+ * reinversion -- are shared among threads.  Every element is still summed by
+ * one thread in the same increasing index order, so both builds give the
+ * same bits; every decision (CHUZC, CHUZR, tabu, follow mode) stays serial.
+ *
  * Problem: max c^T x  s.t.  A x <= b, x >= 0, b >= 0 (A is m x n, row-major).
  * Section 2.1 states the method for min C^T X, AX = b with A = (A', I_m);
  * the max form is the same problem with C' = -c.  Variables 0..n-1 are the
@@ -72,6 +79,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_RUNNING 0
 #define OR_OPTIMAL 1
@@ -122,6 +132,17 @@ typedef struct {
 
 static double dmax(double a, double b) { return a > b ? a : b; }
 
+/* Threads of the parallel build (nt > 0 sets them); 1 in the serial build. */
+int oracle_threads(int nt) {
+#ifdef _OPENMP
+    if (nt > 0) omp_set_num_threads(nt);
+    return omp_get_max_threads();
+#else
+    (void)nt;
+    return 1;
+#endif
+}
+
 /* Column j of [A | I_m] as a dense m-vector. */
 static void column(int m, int n, const double* A, int j, double* out) {
     if (j < n) {
@@ -161,6 +182,7 @@ int oracle_gj_inverse(int k, const double* M, double* inv) {
         }
         double piv = G[j * w + j];
         for (size_t t = 0; t < w; ++t) G[j * w + t] /= piv;
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < k; ++i) {
             if (i == j) continue;
             double f = G[i * w + j];
@@ -178,11 +200,24 @@ int oracle_gj_inverse(int k, const double* M, double* inv) {
    d_{n+i} = -y_i for the slacks; basic variables are reported as well. */
 void oracle_reduced_costs(int m, int n, const double* A, const double* c, const double* y, double* d) {
     double* dot = (double*)calloc((size_t)n, sizeof(double));
+#ifdef _OPENMP
+    /* each thread owns a block of columns and adds its rows in increasing i */
+#pragma omp parallel for schedule(static)
+    for (int j0 = 0; j0 < n; j0 += 512) {
+        const int j1 = j0 + 512 < n ? j0 + 512 : n;
+        for (int i = 0; i < m; ++i) {
+            const double* Ai = A + (size_t)i * n;
+            double yi = y[i];
+            for (int j = j0; j < j1; ++j) dot[j] += yi * Ai[j];
+        }
+    }
+#else
     for (int i = 0; i < m; ++i) {
         const double* Ai = A + (size_t)i * n;
         double yi = y[i];
         for (int j = 0; j < n; ++j) dot[j] += yi * Ai[j];
     }
+#endif
     for (int j = 0; j < n; ++j) d[j] = c[j] - dot[j];
     for (int i = 0; i < m; ++i) d[n + i] = -y[i];
     free(dot);
@@ -219,11 +254,13 @@ static int reinvert(int m, int n, const double* A, const double* b, const double
     free(B);
     free(col);
     if (rc) return rc;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < m; ++i) {
         double s = 0.0;
         for (int k = 0; k < m; ++k) s += Binv[(size_t)i * m + k] * b[k];
         bbar[i] = s;
     }
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < m; ++k) {
         double s = 0.0;
         for (int p = 0; p < m; ++p) s += cost(n, c, basis[p]) * Binv[(size_t)p * m + k];
@@ -378,6 +415,7 @@ int oracle_solve(int m, int n, const double* A, const double* b, const double* c
 
         /* Step 5: FTRAN alpha = B^-1 a_q. */
         column(m, n, A, q, aq);
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < m; ++i) {
             double s = 0.0;
             const double* Bi = Binv + (size_t)i * m;
@@ -507,6 +545,7 @@ int oracle_solve(int m, int n, const double* A, const double* b, const double* c
         for (int k = 0; k < m; ++k) rho[k] = Br[k] / ar; /* new row r */
         for (int k = 0; k < m; ++k) Br[k] = rho[k];
         double bnew_r = bbar[r] / ar;
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < m; ++i) {
             if (i == r) continue;
             double ai = alpha[i];
