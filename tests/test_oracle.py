@@ -322,3 +322,32 @@ def test_follow_relaxed_accepts_any_improving_column_only():
     bad = oracle.solve(A, b, c3, oracle.Options(max_iters=1, follow_relaxed=1),
                        follow=(q3, np.array([0], np.int32)))
     assert bad.status == oracle.MISMATCH and bad.mismatch_kind == 1
+
+
+def test_certificate_flags_infeasible_and_suboptimal_points():
+    """Negative pins of ``certificate``: it must flag a primal-infeasible x, a
+    dual-infeasible y (a violated A^T y >= c, or a negative y_i) and a
+    feasible but suboptimal pair, each by the residual that names it."""
+    A, b, c = lpgen.dense_real_lp(40, 70, 21)
+    s = oracle.solve(A, b, c)
+    assert s.status == oracle.OPTIMAL
+    ok = oracle.certificate(A, b, c, s.x, s.y)
+    assert ok["primal"] <= 1e-12 and ok["dual"] <= 1e-12 and ok["gap"] <= 1e-12
+    # primal: push a basic x_j past its row's bound (A x <= b violated)
+    j = int(np.argmax(s.x))
+    x_bad = s.x.copy()
+    x_bad[j] += 2.0 * np.max(b) / max(1e-3, float(np.min(A[A[:, j] > 0, j])))
+    assert oracle.certificate(A, b, c, x_bad, s.y)["primal"] > 1e-3
+    x_neg = s.x.copy()
+    x_neg[j] = -1.0
+    assert oracle.certificate(A, b, c, x_neg, s.y)["primal"] >= 1.0 / max(1.0, np.max(b))
+    # dual: y = 0 leaves A^T y >= c violated by max c
+    d0 = oracle.certificate(A, b, c, s.x, np.zeros_like(s.y))
+    assert d0["dual"] >= 0.99 * np.max(c) / max(1.0, np.max(c))
+    y_neg = s.y.copy()
+    i = int(np.argmax(s.y))
+    y_neg[i] = -0.5
+    assert oracle.certificate(A, b, c, s.x, y_neg)["dual"] >= 0.5 / max(1.0, np.max(c))
+    # gap: x = 0 is feasible but not optimal against the optimal y
+    g = oracle.certificate(A, b, c, np.zeros_like(s.x), s.y)
+    assert g["primal"] == 0.0 and g["dual"] <= 1e-12 and g["gap"] > 1.0
