@@ -110,9 +110,10 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-# FP64 FMA peak of the GB300 (1.25 TFLOP/s nominal: 152 SMs x 2 FP64 FMA/clk
-# x ~2.06 GHz); the probe in profiles/fp64_probe.md measured 1.20 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.20
+# FP64 peak of the GB300: 1.25 TFLOP/s nominal, i.e. 2 FP64 FMA per clock per
+# SM x 152 SMs x 2.07 GHz x 2 flops (no FP64 figure is among the measured
+# peaks; a standalone FMA-chain probe reached 1.20 TFLOP/s, 96% of it).
+FP64_PEAK_TFLOPS = 1.25
 # Kernel durations come from CUDA events around the PRICE and UPDATE launches
 # of one pivot (the first) of each 64-pivot captured graph, inside the timed
 # solves; the other pivots keep their launch overlap.
@@ -154,16 +155,32 @@ def _certificate(A, b, c, x, y):
             "gap_rel": abs(pz - dz) / max(1.0, abs(pz))}
 
 
-def cpu_baseline(A, b, c, iters: int):
-    """The oracle (single-threaded C, unmodified) on the first `iters` pivots
-    of the same workload (no reinversion inside the sample)."""
+def oracle_sample(A, b, c, iters: int, threads: int):
+    """One timed oracle run over the first `iters` pivots from the slack basis
+    (with iters >= 64 the reinversion after pivot 64 is included); returns
+    (pivots, seconds)."""
     import oracle
     t0 = time.perf_counter()
-    s = oracle.solve(A, b, c, oracle.Options(max_iters=iters))
-    dt = time.perf_counter() - t0
-    return {"value": s.iterations / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {s.iterations} pivots of {WORKLOAD['name']} from the slack basis "
-                      f"(single-threaded plain C FP64 revised simplex), {dt:.1f} s"}
+    s = oracle.solve(A, b, c, oracle.Options(max_iters=iters), threads=threads)
+    return s.iterations, time.perf_counter() - t0
+
+
+def cpu_baseline(A, b, c, iters: int):
+    """The oracle (plain C, unmodified) on the first `iters` pivots of the
+    same workload, the reinversion after pivot 64 included: the serial build
+    (the paper's sequential version) and the OpenMP build on every host core
+    (bit-identical results; PRICE columns, FTRAN and update rows and the
+    elimination rows shared among threads)."""
+    import oracle
+    its, dt = oracle_sample(A, b, c, iters, 1)
+    out = {"value": its / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {its} pivots of {WORKLOAD['name']} from the slack basis, the reinversion after "
+                     f"pivot 64 included (single-threaded plain C FP64 revised simplex), {dt:.1f} s"}
+    nt = oracle.threads_used(0)
+    its_p, dt_p = oracle_sample(A, b, c, iters, 0)
+    out["all_cores"] = {"value": its_p / dt_p, "unit": "iters/s", "cores": nt, "kind": "oracle (OpenMP build)",
+                        "sample": f"the same {its_p} pivots, {dt_p:.1f} s"}
+    return out
 
 
 def run_batched(lpgb, args, with_cpu: bool):
@@ -244,24 +261,29 @@ def run_reference(args):
     import oracle
     A, b, c = lpgen.make(WORKLOAD["kind"], WORKLOAD["m"], WORKLOAD["n"], WORKLOAD["seed"])
     oracle.build()
-    sample = 16
+    # the same sample as cpu_baseline (first 64 pivots, the reinversion after
+    # pivot 64 included); each timed step is one run of it.  Warm-up runs are
+    # capped at one: the oracle has no caches to warm beyond the first run.
+    sample = args.cpu_iters
     times = []
-    for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        s = oracle.solve(A, b, c, oracle.Options(max_iters=sample))
-        dt = time.perf_counter() - t0
-        if step >= args.warmup:
+    for step in range(min(1, args.warmup) + args.steps):
+        its, dt = oracle_sample(A, b, c, sample, 1)
+        if step >= min(1, args.warmup):
             times.append(dt)
     total = sum(times)
-    value = sample * len(times) / total
+    value = its * len(times) / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "m": WORKLOAD["m"], "n": WORKLOAD["n"],
-                       "seed": WORKLOAD["seed"], "step": f"first {sample} pivots from the slack basis"},
+                       "seed": WORKLOAD["seed"], "A": "U[0,1) with 10% zeros", "reinvert_every": 64,
+                       "tabu_tenure": 7,
+                       "step": f"first {its} pivots from the slack basis"
+                               + (" (the reinversion after pivot 64 included)" if its >= 64 else "")},
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {sample} pivots of {WORKLOAD['name']} per step"},
+                             "sample": f"first {its} pivots of {WORKLOAD['name']} per step, "
+                                       f"the same sample as the GPU line's cpu_baseline"},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -273,7 +295,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-iters", type=int, default=128, help="pivots of the CPU baseline sample")
+    ap.add_argument("--cpu-iters", type=int, default=64,
+                    help="pivots of the CPU baseline sample (64: the reinversion after pivot 64 included)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-variants", action="store_true")
