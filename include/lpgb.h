@@ -76,6 +76,20 @@ extern "C" {
                                    k columns of B^-1 (exactly the same pivots up to the
                                    order of summation; extra device memory: 8 ld (n + m) bytes) */
 
+/* lp_result.engine_reason: the first condition, checked in this order, that kept
+   lp_create from running the engine lp_options.engine asked for. */
+#define LP_ENGINE_REASON_NONE 0            /* the asked engine runs */
+#define LP_ENGINE_REASON_PRICE_MODE 1      /* price_mode 1 runs on captured graphs; price_mode 2
+                                              on the dense persistent engine */
+#define LP_ENGINE_REASON_LEXICOGRAPHIC 2   /* the lexicographic rule runs on captured graphs */
+#define LP_ENGINE_REASON_NO_COOPERATIVE 3  /* the device refuses cooperative launches, or has
+                                              more than 1024 SMs */
+#define LP_ENGINE_REASON_SIZE 4            /* LP_ENGINE_STRUCTURED: more than 256 rows per SM,
+                                              or its 28 ld bytes of shared memory exceed the
+                                              device's per-block limit (m above about 5600 on
+                                              152 SMs) */
+#define LP_ENGINE_REASON_OCCUPANCY 5       /* the persistent kernel does not fit one CTA per SM */
+
 typedef struct lp_handle lp_handle;
 
 /*
@@ -155,7 +169,8 @@ typedef struct lp_result {
     int32_t phase1_iterations; /* b with negative entries: pivots of the Phase I problem */
     int32_t phase1_exchanged;  /* 1: the artificial ended basic at zero and was exchanged */
     int32_t refined_reinversions; /* reinversions done by refinement (reinvert_refine) */
-    int32_t reserved2;
+    int32_t engine_reason;   /* LP_ENGINE_REASON_*: why `persistent` is not the engine that
+                                lp_options.engine asked for (0: it is) */
     double refine_residual_max;   /* largest ||I - B11 Y||_inf of the updated inverse found by the
                                      refinement checks of this solve (drift of the updates) */
 } lp_result;
@@ -316,7 +331,9 @@ int lp_get_trace(const lp_handle* h, int32_t* q, int32_t* r, double* theta,
  * at zero is cleared by every call), so calls whose kernels overlap on the GPU
  * race with each other: serialise them, e.g. on one stream.  The first call
  * on a device looks up the array's device address and sets the kernel's
- * shared-memory limit; make that first call before any stream capture.
+ * shared-memory limit; make that first call before any stream capture.  The
+ * address is kept per device context: the first call after the device's
+ * context was replaced (cudaDeviceReset) repeats that set-up.
  */
 #define LP_PRICE_STATIC_MAX_M 12288
 int lp_price_static(int32_t m, int32_t n, const double* A_colmajor, int32_t lda,

@@ -48,6 +48,7 @@ struct lp_handle {
     int persist_blocks = 0;
     cudaEvent_t evc0 = nullptr, evc1 = nullptr;  // kernel_timing around k_iterate launches
     bool structured = false;         // pivots run in k_iterate_s (LP_ENGINE_STRUCTURED)
+    int engine_reason = LP_ENGINE_REASON_NONE;  // why the engine that runs is not the one asked for
     bool s_ready = false;            // the structured state (bp, yp, slot maps) is current; the dense
                                      // B^-1 and y are stale while it is
     bool s_force = true;             // rebuild the slot map and A_p on the next entry
@@ -624,8 +625,20 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
         // (the ratio tests hold one CTA record per thread: at most 1024 CTAs)
-        if (h->opt.engine == LP_ENGINE_STRUCTURED && h->opt.price_mode == 0 && !P.lex && coop && h->geo.sms <= 1024 &&
-            struct_engine_fits(h->m, h->ld, h->geo.sms) && occupancy_iterate_s(h->ld) >= 1) {
+        const bool want_s = h->opt.engine == LP_ENGINE_STRUCTURED;
+        const bool fits_s = want_s && h->opt.price_mode == 0 && !P.lex && coop && h->geo.sms <= 1024 &&
+                            struct_engine_fits(h->m, h->ld, h->geo.sms);
+        const bool occ_s = fits_s && occupancy_iterate_s(h->ld) >= 1;
+        // the first condition that keeps the asked engine from running
+        if (h->opt.engine != LP_ENGINE_GRAPH) {
+            if (h->opt.price_mode == 1) h->engine_reason = LP_ENGINE_REASON_PRICE_MODE;
+            else if (P.lex) h->engine_reason = LP_ENGINE_REASON_LEXICOGRAPHIC;
+            else if (!coop || h->geo.sms > 1024) h->engine_reason = LP_ENGINE_REASON_NO_COOPERATIVE;
+            else if (want_s && h->opt.price_mode != 0) h->engine_reason = LP_ENGINE_REASON_PRICE_MODE;
+            else if (want_s && !fits_s) h->engine_reason = LP_ENGINE_REASON_SIZE;
+            else if (want_s && !occ_s) h->engine_reason = LP_ENGINE_REASON_OCCUPANCY;
+        }
+        if (occ_s) {
             const int m = h->m, n = h->n, ld = h->ld;
             TRY(dalloc(h, &s.A_p, (size_t)n * ld));
             TRY(dalloc(h, &s.A_p32, (size_t)n * ld));
@@ -652,6 +665,8 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
                    h->geo.sms <= 1024 && occupancy_iterate(h->ld) >= 1) {
             h->persist = true;
             h->persist_blocks = h->geo.sms;  // the partial arrays hold at least sms entries
+        } else if (h->opt.engine != LP_ENGINE_GRAPH && h->engine_reason == LP_ENGINE_REASON_NONE) {
+            h->engine_reason = LP_ENGINE_REASON_OCCUPANCY;
         }
         if ((h->persist || h->structured) && h->opt.kernel_timing > 0) {
             CK(cudaEventCreate(&h->evc0));
@@ -780,6 +795,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
                 out->seconds = ms1 * 1e-3;
                 out->phase1_iterations = phase1_iters;
                 out->persistent = h->structured ? 2 : (h->persist ? 1 : 0);
+                out->engine_reason = h->engine_reason;
             }
             return LP_OK;
         }
@@ -963,6 +979,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->chain_bytes = h->chain_b;
         out->chain_launches = h->chain_n;
         out->persistent = h->structured ? 2 : (h->persist ? 1 : 0);
+                out->engine_reason = h->engine_reason;
         out->phase1_iterations = phase1_iters;
         out->phase1_exchanged = phase1_exch;
         out->refined_reinversions = h->reinv_refined;

@@ -29,6 +29,8 @@ STATUS_NAMES = {0: "running", 1: "optimal", 2: "unbounded", 3: "iter_limit", 4: 
 LP_TF_DEGENERATE, LP_TF_TABU_PUSH, LP_TF_ASPIRATION, LP_TF_BLAND, LP_TF_TIE_SET = 1, 2, 4, 8, 64
 LP_TF_GUIDED = 128
 LP_ENGINE_DENSE, LP_ENGINE_GRAPH, LP_ENGINE_STRUCTURED = 0, 1, 2
+ENGINE_REASONS = {0: "none", 1: "price_mode", 2: "lexicographic", 3: "no_cooperative", 4: "size",
+                  5: "occupancy"}
 LP_ANTICYCLING_TABU, LP_ANTICYCLING_LEXICOGRAPHIC = 0, 1
 
 
@@ -61,7 +63,7 @@ class lp_result(ctypes.Structure):
                 ("chain_bytes", ctypes.c_double), ("chain_launches", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("phase1_iterations", ctypes.c_int32),
                 ("phase1_exchanged", ctypes.c_int32), ("refined_reinversions", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32), ("refine_residual_max", ctypes.c_double)]
+                ("engine_reason", ctypes.c_int32), ("refine_residual_max", ctypes.c_double)]
 
 
 class lp_batch_result(ctypes.Structure):
@@ -213,6 +215,7 @@ class Result:
     phase1_exchanged: int = 0
     refined_reinversions: int = 0
     refine_residual_max: float = 0.0
+    engine_reason: int = 0
 
     @property
     def status_name(self) -> str:
@@ -275,7 +278,7 @@ class LP:
                       r.full_passes, r.reinvert_gj_seconds, r.reinvert_assemble_seconds,
                       r.chain_seconds, r.chain_bytes, r.chain_launches, r.persistent,
                       r.phase1_iterations, r.phase1_exchanged, r.refined_reinversions,
-                      r.refine_residual_max)
+                      r.refine_residual_max, r.engine_reason)
 
     def reset(self):
         _check(_lib.lp_reset(self._h), "lp_reset")
