@@ -11,9 +11,12 @@
 //
 // Host code must not hand the array's name to a kernel: in host code the name
 // is only a host-side stand-in.  The device address is fetched once per
-// device with cudaGetSymbolAddress (with that device current) and passed in.
+// device context with cudaGetSymbolAddress (with that device current) and
+// passed in; a call that finds a different context on its device than the
+// one the address was fetched in (after cudaDeviceReset, say) fetches it again.
 #include "../../include/lpgb.h"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -42,7 +45,8 @@ static __device__ __align__(256) Scratch g_price_scratch;
 
 struct DeviceSetup {
     bool ready = false;
-    Scratch* scratch = nullptr;  // device address of g_price_scratch
+    unsigned long long ctx_id = 0;  // the context the address below belongs to
+    Scratch* scratch = nullptr;     // device address of g_price_scratch
     int sms = 0;
 };
 DeviceSetup g_setup[kMaxDevices];
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_price_static(int m, int n, const d
                                                            const double* __restrict__ y,
                                                            const int32_t* __restrict__ pos, double tol_d,
                                                            int32_t* q_out, double* dq_out, Scratch* sc) {
-    extern __shared__ double ysh[];
+    extern __shared__ __align__(16) double ysh[];  // read as double2 below
     const int me = (m + 1) & ~1;
     for (int k = threadIdx.x; k < me; k += blockDim.x) ysh[k] = k < m ? y[k] : 0.0;
     __syncthreads();
@@ -145,11 +149,40 @@ __global__ void __launch_bounds__(kThreads) k_price_static(int m, int n, const d
     }
 }
 
-// Once per device, with that device current: the scratch's device address,
-// the shared-memory opt-in and the SM count.
+// Identity of the calling thread's current context (driver entry points
+// looked up through the runtime, so the library needs no libcuda at link
+// time).  Host-only queries: they enqueue nothing and allocate nothing.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+int current_ctx_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return LP_ERR_CUDA;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+        get_id = reinterpret_cast<CtxGetIdFn>(f1);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return LP_ERR_CUDA;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return LP_ERR_CUDA;
+    return LP_OK;
+}
+
+// Once per device context, with that device current: the scratch's device
+// address, the shared-memory opt-in and the SM count.
 int setup_device(int dev, DeviceSetup** out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSetup& s = g_setup[dev];
+    unsigned long long ctx_id = 0;
+    if (current_ctx_id(&ctx_id) != LP_OK) return LP_ERR_CUDA;
+    if (s.ready && s.ctx_id != ctx_id) s.ready = false;  // a new context: the old address is void
     if (!s.ready) {
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_price_scratch) != cudaSuccess || ptr == nullptr) return LP_ERR_CUDA;
@@ -161,6 +194,7 @@ int setup_device(int dev, DeviceSetup** out) {
             return LP_ERR_CUDA;
         s.scratch = static_cast<Scratch*>(ptr);
         s.sms = sms;
+        s.ctx_id = ctx_id;
         s.ready = true;
     }
     *out = &s;

@@ -8,27 +8,40 @@ performs the same PRICE and Dantzig choice is the solver itself (lp_create +
 lp_solve, which records every pivot's entering variable and reduced cost in
 lp_get_trace).  This test stops a solve after K pivots, hands its duals and
 basis to lp_price_static, and checks the answer against the entering variable
-and reduced cost that the solver records at pivot K.  The calls come one after
-another, because the static scratch keeps the previous call's contents.
+and reduced cost that the solver records at pivot K, and against the CPU
+oracle's reduced costs at the same duals.  The reference solves run without
+the tabu list (tenure 0), so their entering choice is the plain Dantzig
+argmax that lp_price_static computes.  The calls come one after another,
+because the static scratch keeps the previous call's contents.
 """
 import numpy as np
 import pytest
 
 import lpgen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
 
 def _solver_state(A, b, c, K):
     from paper_1803_04378_gb300 import lpgb
-    with lpgb.LP(A, b, c, max_iters=K) as lp:
+    with lpgb.LP(A, b, c, max_iters=K, tabu_tenure=0) as lp:
         res = lp.solve()
         _, y, _ = lp.solution()
         basis = lp.basis()
-    with lpgb.LP(A, b, c, max_iters=K + 1, trace_cap=K + 1) as lp:
+    with lpgb.LP(A, b, c, max_iters=K + 1, trace_cap=K + 1, tabu_tenure=0) as lp:
         lp.solve()
         tr = lp.trace()
     return res, y, basis, tr
+
+
+def _oracle_choice(A, c, y, pos, tol_d=1e-9):
+    """Dantzig's choice from the oracle's reduced costs at the same duals
+    (largest d_j > tol_d over nonbasic j, exact ties to the smallest j)."""
+    d = oracle.reduced_costs(A, c, y)
+    d = np.where(pos < 0, d, -np.inf)
+    j = int(np.argmax(d))
+    return (j if d[j] > tol_d else -1), float(d[j])
 
 
 def test_price_static_matches_solver_pricing():
@@ -61,6 +74,10 @@ def test_price_static_matches_solver_pricing():
         assert int(q_out.item()) == int(tr["q"][K])
         want = float(tr["dq"][K])
         assert abs(float(dq_out.item()) - want) <= 1e-12 * max(1.0, abs(want))
+        # the oracle at the same y: the same column, d_q to 1e-12 (summation order only)
+        oq, od = _oracle_choice(A, c, y, pos)
+        assert int(q_out.item()) == oq
+        assert abs(float(dq_out.item()) - od) <= 1e-12 * max(1.0, abs(od))
 
     # at the optimal basis there is no entering variable
     with lpgb.LP(A, b, c) as lp:
