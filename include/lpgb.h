@@ -340,6 +340,26 @@ int lp_price_static(int32_t m, int32_t n, const double* A_colmajor, int32_t lda,
                     const double* c, const double* y, const int32_t* pos, double tol_d,
                     int32_t* q_out, double* dq_out, void* cuda_stream);
 
+/*
+ * lp_tc_gemm -- D = A B^T on the tensor cores (tcgen05.mma, FP32 accumulation
+ * in tensor memory; operand tiles staged by TMA).  The building block of the
+ * reinversion's FP64 products, which are formed from exact 7-bit slices of
+ * their operands (no counterpart in the paper, whose reinversion-free method
+ * needs no such product), and of the warm-start network.  Exposed so that the
+ * primitive can be checked on its own.
+ *
+ * All pointers are DEVICE pointers owned by the caller:
+ *  A  M x K, row-major with row stride lda elements (lda >= K, lda % 8 == 0)
+ *  B  N x K, row-major with row stride ldb elements (ldb >= K, ldb % 8 == 0)
+ *     (16-bit elements: bf16 != 0 selects BF16, else FP16; 16-byte aligned)
+ *  D  M x N FP32, row stride ldd >= N
+ * Runs on cuda_stream (NULL: legacy default stream) and waits for it.
+ * Returns LP_OK, LP_ERR_INVALID_ARG (shape, stride or alignment), LP_ERR_CUDA,
+ * or LP_ERR_TIMEOUT (a bounded wait inside the kernel gave up).
+ */
+int lp_tc_gemm(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, const void* B, int32_t ldb,
+               float* D, int32_t ldd, int32_t bf16, void* cuda_stream);
+
 /* ---- batches of small LPs ------------------------------------------------ */
 
 /*

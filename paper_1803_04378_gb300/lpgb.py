@@ -110,6 +110,8 @@ def _load():
     lib.lp_strerror.restype = ctypes.c_char_p
     lib.lp_price_static.argtypes = [i32, i32, vp, i32, vp, vp, vp, ctypes.c_double, vp, vp, vp]
     lib.lp_price_static.restype = ctypes.c_int
+    lib.lp_tc_gemm.argtypes = [i32, i32, i32, vp, i32, vp, i32, vp, i32, i32, vp]
+    lib.lp_tc_gemm.restype = ctypes.c_int
     lib.lp_set_basis_repair.argtypes = [vp, vp, i32]
     lib.lp_set_basis_repair.restype = ctypes.c_int
     lib.lp_update_problem.argtypes = [vp, vp, vp, vp, i32]
@@ -357,6 +359,18 @@ def price_static(m: int, n: int, A_colmajor, lda: int, c, y, pos, tol_d: float, 
     st = None if stream is None else ctypes.c_void_p(stream)
     return _lib.lp_price_static(int(m), int(n), _ptr(A_colmajor), int(lda), _ptr(c), _ptr(y), _ptr(pos),
                                 float(tol_d), _ptr(q_out), _ptr(dq_out), st)
+
+
+def tc_gemm(A, B, D, bf16: bool, stream=None) -> int:
+    """lp_tc_gemm: D = A B^T on the tensor cores for torch CUDA tensors (A:
+    M x K and B: N x K, 16-bit, row strides multiples of 8 elements; D: M x N
+    float32); returns the C return code.  Only the first K columns of A and B
+    are read (their strides may be larger)."""
+    st = None if stream is None else ctypes.c_void_p(stream)
+    M, K = int(A.shape[0]), int(A.shape[1])
+    N = int(B.shape[0])
+    return _lib.lp_tc_gemm(M, N, K, _ptr(A), int(A.stride(0)), _ptr(B), int(B.stride(0)), _ptr(D),
+                           int(D.stride(0)), 1 if bf16 else 0, st)
 
 
 LP_BATCH_MAX_M = 256
