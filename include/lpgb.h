@@ -97,7 +97,7 @@ typedef struct lp_handle lp_handle;
  * reinvert_every 64, tabu_tenure 7, bland_after 50, max_iters 50,000,000,
  * price_mode 0, topk 16, trace_cap 0, graph_iters 64, kernel_timing 0,
  * engine LP_ENGINE_STRUCTURED (LP_ENGINE_DENSE where it does not fit),
- * anticycling LP_ANTICYCLING_TABU,
+ * anticycling LP_ANTICYCLING_TABU, reinvert_refine 1, reinvert_tc 1,
  * tol_d 1e-9, tol_piv 1e-9, tol_tie 1e-12, cuda_stream NULL.
  */
 typedef struct lp_options {
@@ -125,6 +125,10 @@ typedef struct lp_options {
                                by one Newton-Schulz step, Y + Y (I - B11 Y), when
                                ||I - B11 Y||_inf <= refine_tol (else, and with 0, B11 is
                                eliminated afresh by Gauss-Jordan); needs 3 k^2 <= m^2 */
+    int32_t reinvert_tc;    /* 1 (default): the reinversion's slack-row product -A[S, J] B11^-1
+                               runs on the BF16 tensor cores from exact 7-bit slices of its
+                               FP64 operands, combined in 64-bit fixed point (k <= 1024;
+                               extra device memory about 16 m min(m, 1024) bytes); 0: FP64 FMAs */
     double tol_d;           /* optimality tolerance on the reduced costs */
     double tol_piv;         /* smallest admissible pivot alpha_r */
     double tol_tie;         /* relative width of the ratio-test tie set */
@@ -143,7 +147,7 @@ typedef struct lp_result {
     int32_t tabu_pushes;     /* times the tabu rule fired */
     int32_t bland_fallbacks; /* times the Bland safety net switched on */
     int32_t aspirations;     /* iterations where every improving candidate was tabu */
-    int32_t reserved;
+    int32_t tc_reinversions; /* reinversions whose slack-row product ran on the tensor cores */
     double objective;        /* c^T x at the final basis */
     double seconds;          /* device time of the solve (CUDA events) */
     double reinvert_seconds; /* device time spent in reinversion */

@@ -815,19 +815,29 @@ void launch_refine_apply(const DevState& s, int k, cudaStream_t st) {
     k_refine_gemm<1><<<dim3(nt, nt), kRT * kRT, 0, st>>>(s, k);
 }
 
-void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj) {
+// Returns 1 when the slack-row product ran on the tensor cores.
+int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj) {
     const int nslack = s.p.m - k;
+    int tc = 0;
     if (k > 0) {
         const size_t kk = (size_t)k * k;
         int blocks = (int)((kk + 255) / 256);
         if (blocks > 4096) blocks = 4096;
         k_b11i<<<blocks, 256, 0, st>>>(s, k, from_gj);
         if (nslack > 0) {
-            dim3 grid((k + kGN - 1) / kGN, (nslack + kGM - 1) / kGM);
-            k_slack_gemm<<<grid, 256, 0, st>>>(s, k, nslack);
+            if (s.p.reinvert_tc && s.oz_xs && oz_fits(k) &&
+                oz_slack_product(s.A_cm, s.p.ld, s.rv_J, s.rv_slack_pos, s.rv_W, k, nslack, s.rv_W + kk, s.oz_xs,
+                                 s.oz_ys, s.oz_ex, s.oz_ey, &s.ctrl->err, st) == cudaSuccess) {
+                tc = 1;
+            } else {
+                (void)cudaGetLastError();
+                dim3 grid((k + kGN - 1) / kGN, (nslack + kGM - 1) / kGM);
+                k_slack_gemm<<<grid, 256, 0, st>>>(s, k, nslack);
+            }
         }
     }
     k_assemble_rows<<<g.sms * 4, 256, 0, st>>>(s, k);
+    return tc;
 }
 
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible) {

@@ -55,6 +55,7 @@ struct Params {
     int32_t lex;           // 1: lexicographic leaving rule (no tabu list, no safety net)
     double nnz;            // price_mode 2: nonzeros of A
     int32_t screen;        // slack-structured engine: PRICE through the exact FP32 screen
+    int32_t reinvert_tc;   // slack-row product of the reinversion on the tensor cores
 };
 
 constexpr int kMaxTopk = 32;
@@ -202,6 +203,10 @@ struct DevState {
     double* rv_W;            // m*m: dense B11^-1 (k x k) then -A[S,J] B11^-1 ((m-k) x k)
     int32_t* rv_pivrow;      // k: pivot row chosen for column t (GJ)
     int32_t* rv_rowdone;     // k: row already used as pivot
+    __nv_bfloat16* oz_xs;    // reinvert_tc: 7-bit slices of A[S, J] (8 rows per slack row), or null
+    __nv_bfloat16* oz_ys;    // reinvert_tc: slices of B11^-1 (8 rows per column)
+    int32_t* oz_ex;          // reinvert_tc: row exponents of A[S, J] (m)
+    int32_t* oz_ey;          // reinvert_tc: column exponents of B11^-1 (m)
     double* rv_M;            // k*k column-major workspace (B11 then its GJ form)
     double* rv_f;            // 2*k published pivot columns
 };
@@ -291,8 +296,15 @@ void launch_csc_fill(const double* A_cm, int m, int n, int ld, const int64_t* pt
 void launch_reinv_classify(const DevState& s, cudaStream_t st);
 void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t st);
 int reinv_gj_launches(int k);
-void launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj);
+int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj);
 bool refine_fits(int k, int m);
+// sliced FP64 products on the tensor cores (ozaki.cu)
+bool oz_fits(int k);
+size_t oz_scratch_x_elems(int m);
+size_t oz_scratch_y_elems(int m);
+cudaError_t oz_slack_product(const double* A_cm, int ld, const int32_t* J, const int32_t* S, const double* W,
+                             int k, int nslack, double* C, __nv_bfloat16* xs, __nv_bfloat16* ys, int32_t* ex,
+                             int32_t* ey, int32_t* err, cudaStream_t st);
 void launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st);
 void launch_refine_apply(const DevState& s, int k, cudaStream_t st);
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible);

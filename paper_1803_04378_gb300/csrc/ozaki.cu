@@ -1,0 +1,214 @@
+// ozaki.cu -- FP64 matrix products on the BF16 tensor cores, from exact
+// 7-bit slices of the operands (the error-free splitting of Ozaki, Ogita,
+// Oishi and Rump, "Error-free transformations of matrix multiplication by
+// using fast routines of matrix multiplication and its applicability",
+// Numer. Algorithms 59, 2012), used for the slack rows of the reinversion,
+// C = -A[S, J] B11^-1 (kernels_reinv.cu).  On this chip FP64 FMAs run at
+// 1/58 of the FP32 rate and FP64 tensor instructions at the FMA rate, while
+// BF16 tensor instructions run three orders of magnitude faster.
+//
+// Splitting.  Row i of X (M x K) gets the exponent e_i with max_l |X_il| <
+// 2^e_i; then X_il = 2^e_i sum_{p<8} d_p(X_il) 2^{-7(p+1)} + r_il with integer
+// digits |d_p| <= 127 (sign-magnitude, taken from the bits of the double:
+// no FP64 instruction) and |r_il| < 2^{e_i - 56}.  Column c of Y (K x N)
+// likewise with exponents f_c.  A digit is exact in BF16.
+//
+// Products.  S_pq[i][c] = sum_l d_p(X_il) d_q(Y_lc) has |terms| < 2^14, so for
+// K <= 1024 every partial sum is an integer below 2^24 and the tensor cores'
+// FP32 accumulation is exact (checked bit for bit by the GPU tests of
+// lp_tc_gemm).  One GEMM computes all 64 digit pairs: the A operand stacks
+// the slices of X with row 8 i + p, the B operand those of Y with row 8 c + q.
+//
+// Combination (GEMM epilogue).  X Y = 2^{e_i + f_c} sum_{p,q} S_pq 2^{-7(p+q+2)};
+// the pairs with p + q <= 8 are added as 64-bit integers in fixed point with
+// 51 fraction bits relative to 2^{e_i + f_c} (exact left shifts; the right
+// shifts of the 22 pairs with p + q >= 6 round to nearest), the 8 lanes that
+// hold p = 0..7 of one row combine by shuffles, and the sum is converted to
+// FP64 once.  Relative to 2^{e_i + f_c}, the error is below K 2^-55 (the
+// remainders r), K 2^-60 (the pairs left out) and 2^-47 (the fixed-point
+// roundings), plus the final rounding to FP64: of the order of an FP64
+// product's own rounding (bound K 2^-53 sum_l |X_il||Y_lc|) unless a row or
+// column mixes entries of very different size.
+#include "tc_gemm.cuh"
+
+#include <cuda_bf16.h>
+
+#include <climits>
+
+namespace lpgb {
+namespace {
+
+constexpr int kSlices = 8;   // 7-bit digits per operand (56 bits)
+constexpr int kLevels = 8;   // digit pairs with p + q <= kLevels are combined
+constexpr int kFrac = 51;    // fraction bits of the fixed-point combination
+constexpr int kNoDigits = INT_MIN / 4;  // exponent of an all-zero row or column
+
+// binary exponent E of x = 1.f 2^E; zero and subnormals (below 2^-1022) give kNoDigits
+__device__ __forceinline__ int dexp(double x) {
+    const int ef = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+    return ef == 0 ? kNoDigits : ef - 1023;
+}
+
+// the 8 signed 7-bit digits of x / 2^e (|x| < 2^e), as BF16
+__device__ __forceinline__ void digits(double x, int e, __nv_bfloat16 (&d)[kSlices]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((b >> 52) & 0x7ff);
+    unsigned long long fix = 0;  // |x| 2^{56 - e}, truncated
+    if (ef != 0 && e != kNoDigits) {
+        const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = (ef - 1023) + 4 - e;  // <= 3
+        if (sh >= 0) fix = mant << sh;
+        else if (sh > -64) fix = mant >> (-sh);
+    }
+    const bool neg = (b >> 63) != 0;
+#pragma unroll
+    for (int p = 0; p < kSlices; ++p) {
+        const int dg = (int)((fix >> (49 - 7 * p)) & 127u);
+        d[p] = __float2bfloat16_rn((float)(neg ? -dg : dg));
+    }
+}
+
+// X rows of the slack-row product: X[i][l] = A[S_i, J_l] (A column-major)
+struct SrcAsj {
+    const double* A;
+    const int32_t* J;
+    const int32_t* S;
+    int ld;
+    __device__ double operator()(int i, int l) const { return A[(size_t)J[l] * ld + S[i]]; }
+};
+// Y columns: Y[l][c] = W[l * k + c] (row-major k x k)
+struct SrcRowMajor {
+    const double* W;
+    int k;
+    __device__ double operator()(int c, int l) const { return W[(size_t)l * k + c]; }
+};
+
+// exp[o] = 1 + max_l E(src(o, l)) over l < K (kNoDigits when all zero);
+// 32 outer indices per block (consecutive, for coalescing) x 8 inner groups.
+template <class Src>
+__global__ void __launch_bounds__(256) k_oz_exp(Src src, int nout, int K, int32_t* exps, const int32_t* err) {
+    if (*err != kErrNone) return;
+    __shared__ int red[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int o = blockIdx.x * 32 + tx;
+    int e = kNoDigits;
+    if (o < nout)
+        for (int l = ty; l < K; l += 8) e = max(e, dexp(src(o, l)));
+    red[ty][tx] = e;
+    __syncthreads();
+    if (ty == 0 && o < nout) {
+        int m = red[0][tx];
+#pragma unroll
+        for (int t = 1; t < 8; ++t) m = max(m, red[t][tx]);
+        exps[o] = m == kNoDigits ? kNoDigits : m + 1;
+    }
+}
+
+// out[(8 o + p) * ldk + l] = digit p of src(o, l) / 2^exp[o]; 32 x 32 tiles
+// read along o and written along l through shared memory.
+template <class Src>
+__global__ void __launch_bounds__(256) k_oz_slice(Src src, int nout, int K, const int32_t* exps,
+                                                  __nv_bfloat16* out, int ldk, const int32_t* err) {
+    if (*err != kErrNone) return;
+    __shared__ __nv_bfloat16 t[kSlices][32][34];  // [p][o][l]
+    const int o0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int o = o0 + tx;
+    const int e = o < nout ? exps[o] : kNoDigits;
+    for (int ll = ty; ll < 32; ll += 8) {
+        const int l = l0 + ll;
+        __nv_bfloat16 d[kSlices];
+        digits((o < nout && l < K) ? src(o, l) : 0.0, e, d);
+#pragma unroll
+        for (int p = 0; p < kSlices; ++p) t[p][tx][ll] = d[p];
+    }
+    __syncthreads();
+    // each warp writes rows (o, p) with l along the lanes
+    for (int r = ty; r < 32 * kSlices; r += 8) {
+        const int oo = r / kSlices, p = r % kSlices;
+        const int orow = o0 + oo, l = l0 + tx;
+        if (orow < nout && l < K) out[(size_t)(kSlices * orow + p) * ldk + l] = t[p][oo][tx];
+    }
+}
+
+// GEMM epilogue: combines the 64 digit pairs of each output (see the file
+// comment) and writes sign * (X Y)[i][c] into out (row stride ldo).
+struct OzEpi {
+    double* out;
+    int ldo, M, N;
+    const int32_t* ex;
+    const int32_t* ey;
+    int negate;
+    __device__ void operator()(int trow, int m0, int n0, int c0, const float (&v)[32]) const {
+        const int grow = m0 + trow;
+        const int i = grow >> 3, p = grow & 7;
+        const int cb = (n0 + c0) >> 3;  // n0 + c0 is a multiple of 32
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            long long t = 0;
+#pragma unroll
+            for (int q = 0; q < kSlices; ++q) {
+                const int L = p + q;
+                if (L <= kLevels) {
+                    const long long sv = __float2ll_rn(v[cc * 8 + q]);  // an exact integer below 2^24
+                    const int sh = kFrac - 14 - 7 * L;
+                    t += sh >= 0 ? sv * (1ll << sh) : ((sv + (1ll << (-sh - 1))) >> (-sh));
+                }
+            }
+            t += __shfl_xor_sync(0xffffffffu, t, 1);
+            t += __shfl_xor_sync(0xffffffffu, t, 2);
+            t += __shfl_xor_sync(0xffffffffu, t, 4);
+            const int c = cb + cc;
+            if (p == cc && i < M && c < N) {
+                double val = 0.0;
+                const int ei = ex[i], fc = ey[c];
+                if (t != 0 && ei != kNoDigits && fc != kNoDigits)
+                    val = scalbn(__ll2double_rn(negate ? -t : t), ei + fc - kFrac);
+                out[(size_t)i * ldo + c] = val;
+            }
+        }
+    }
+};
+
+}  // namespace
+
+bool oz_fits(int k) { return k >= 1 && k <= 1024; }
+
+size_t oz_scratch_x_elems(int m) {
+    // 8 (m - k) ldk over 1 <= k <= min(m, 1024), ldk = k rounded up to 8
+    size_t best = 0;
+    const int kmax = m < 1024 ? m : 1024;
+    for (int k = 1; k <= kmax; ++k) {
+        const size_t v = (size_t)kSlices * (size_t)(m - k) * (size_t)((k + 7) & ~7);
+        if (v > best) best = v;
+    }
+    return best;
+}
+size_t oz_scratch_y_elems(int m) {
+    const int kmax = m < 1024 ? m : 1024;
+    return (size_t)kSlices * kmax * (size_t)((kmax + 7) & ~7);
+}
+
+// C (nslack x k, row stride k) = -A[S, J] W, W = B11^-1 row-major k x k.
+// xs / ys: BF16 slice scratch (oz_scratch_*_elems), ex / ey: nslack and k ints.
+cudaError_t oz_slack_product(const double* A_cm, int ld, const int32_t* J, const int32_t* S, const double* W,
+                             int k, int nslack, double* C, __nv_bfloat16* xs, __nv_bfloat16* ys, int32_t* ex,
+                             int32_t* ey, int32_t* err, cudaStream_t st) {
+    if (!oz_fits(k) || nslack < 1) return cudaErrorInvalidValue;
+    const int ldk = (k + 7) & ~7;
+    const SrcAsj sx{A_cm, J, S, ld};
+    const SrcRowMajor sy{W, k};
+    k_oz_exp<<<(nslack + 31) / 32, 256, 0, st>>>(sx, nslack, k, ex, err);
+    k_oz_exp<<<(k + 31) / 32, 256, 0, st>>>(sy, k, k, ey, err);
+    k_oz_slice<<<dim3((nslack + 31) / 32, (k + 31) / 32), 256, 0, st>>>(sx, nslack, k, ex, xs, ldk, err);
+    k_oz_slice<<<dim3((k + 31) / 32, (k + 31) / 32), 256, 0, st>>>(sy, k, k, ey, ys, ldk, err);
+    CUtensorMap ma, mb;
+    constexpr int BN = 128;
+    if (!tc_make_map_16bit(&ma, xs, kSlices * nslack, k, ldk, tcg::kTM, true) ||
+        !tc_make_map_16bit(&mb, ys, kSlices * k, k, ldk, BN, true))
+        return cudaErrorInvalidValue;
+    const OzEpi epi{C, k, nslack, k, ex, ey, 1};
+    return tcg::launch_tc_gemm<BN, true>(ma, mb, epi, kSlices * nslack, kSlices * k, k, err, st);
+}
+
+}  // namespace lpgb

@@ -42,6 +42,7 @@ struct lp_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr, erg = nullptr, era = nullptr;
     double reinv_gj_s = 0.0, reinv_asm_s = 0.0;
     int32_t reinv_refined = 0;       // reinversions of this solve done by refinement
+    int32_t reinv_tc = 0;            // reinversions of this solve whose slack rows ran on the tensor cores
     double refine_res_max = 0.0;     // largest residual the refinement checks of this solve found
     std::vector<cudaEvent_t> tev;    // kernel_timing: 3 events per timed iteration of the graph
     bool persist = false;            // pivots run in k_iterate (cooperative, one CTA per SM)
@@ -244,7 +245,10 @@ int reinvert(lp_handle* h, int check_feasible, bool refine) {
     }
     h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 3;
     CK(cudaEventRecord(h->era, h->stream));
-    launch_reinv_assemble(h->ds, k, h->geo, h->stream, refined ? 0 : 1);
+    if (launch_reinv_assemble(h->ds, k, h->geo, h->stream, refined ? 0 : 1)) {
+        h->reinv_tc++;
+        h->launches += 4;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
+    }
     launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible);
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->er1, h->stream));
@@ -410,6 +414,7 @@ void lp_default_options(lp_options* o) {
     o->engine = LP_ENGINE_STRUCTURED;
     o->anticycling = LP_ANTICYCLING_TABU;
     o->reinvert_refine = 1;
+    o->reinvert_tc = 1;
     o->tol_d = 1e-9;
     o->tol_piv = 1e-9;
     o->tol_tie = 1e-12;
@@ -523,6 +528,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     P.price_mode = h->opt.price_mode;
     P.topk = h->opt.topk;
     P.lex = h->opt.anticycling == LP_ANTICYCLING_LEXICOGRAPHIC ? 1 : 0;
+    P.reinvert_tc = h->opt.reinvert_tc;
     if (P.lex) {
         // the lexicographic rule needs neither the tabu list nor the safety net
         P.tabu_tenure = 0;
@@ -567,6 +573,13 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &s.y32, (size_t)ld));
     TRY(dalloc(h, &s.cand, (size_t)kMaxTopk + 1));
     TRY(dalloc(h, &s.cand_d, (size_t)kMaxTopk + 1));
+    if (P.reinvert_tc && m > 1) {
+        // digit slices of the slack-row product (k <= 1024 structural columns)
+        TRY(dalloc(h, &s.oz_xs, oz_scratch_x_elems(m)));
+        TRY(dalloc(h, &s.oz_ys, oz_scratch_y_elems(m)));
+        TRY(dalloc(h, &s.oz_ex, (size_t)m));
+        TRY(dalloc(h, &s.oz_ey, (size_t)m));
+    }
     if (P.price_mode == 2) {
         // capacity for a fully dense A, so the captured graphs' pointers never change
         int64_t* ptr = nullptr;
@@ -686,7 +699,7 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
     lp_options o;
     lp_default_options(&o);
     if (opt) o = *opt;
-    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > LP_ENGINE_STRUCTURED || o.anticycling < 0 || o.anticycling > 1 || o.reinvert_refine < 0 || o.reinvert_refine > 1 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
+    if (o.graph_iters < 1 || o.graph_iters > 4096 || o.engine < 0 || o.engine > LP_ENGINE_STRUCTURED || o.anticycling < 0 || o.anticycling > 1 || o.reinvert_refine < 0 || o.reinvert_refine > 1 || o.reinvert_tc < 0 || o.reinvert_tc > 1 || o.max_iters < 0 || o.reinvert_every < 0 || o.tabu_tenure < 0 || o.kernel_timing < 0 ||
         o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 2 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0) || !(o.refine_tol >= 0 && o.refine_tol <= kRefineTolMax))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
@@ -770,6 +783,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
     h->reinvert_seconds = 0.0;
     h->reinv_gj_s = h->reinv_asm_s = 0.0;
     h->reinv_refined = 0;
+    h->reinv_tc = 0;
     h->refine_res_max = 0.0;
     h->price_s = h->update_s = h->price_b = h->update_b = 0.0;
     h->price_n = h->update_n = 0;
@@ -983,6 +997,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->phase1_iterations = phase1_iters;
         out->phase1_exchanged = phase1_exch;
         out->refined_reinversions = h->reinv_refined;
+        out->tc_reinversions = h->reinv_tc;
         out->refine_residual_max = h->refine_res_max;
     }
     return LP_OK;

@@ -41,6 +41,7 @@ class lp_options(ctypes.Structure):
                 ("trace_cap", ctypes.c_int32), ("graph_iters", ctypes.c_int32),
                 ("kernel_timing", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("anticycling", ctypes.c_int32), ("reinvert_refine", ctypes.c_int32),
+                ("reinvert_tc", ctypes.c_int32),
                 ("tol_d", ctypes.c_double), ("tol_piv", ctypes.c_double),
                 ("tol_tie", ctypes.c_double), ("refine_tol", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p)]
@@ -50,7 +51,7 @@ class lp_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("reinversions", ctypes.c_int32), ("degenerate", ctypes.c_int32),
                 ("tabu_pushes", ctypes.c_int32), ("bland_fallbacks", ctypes.c_int32),
-                ("aspirations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("aspirations", ctypes.c_int32), ("tc_reinversions", ctypes.c_int32),
                 ("objective", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("reinvert_seconds", ctypes.c_double), ("bytes_moved", ctypes.c_double),
                 ("price_seconds", ctypes.c_double), ("update_seconds", ctypes.c_double),
@@ -218,6 +219,7 @@ class Result:
     refined_reinversions: int = 0
     refine_residual_max: float = 0.0
     engine_reason: int = 0
+    tc_reinversions: int = 0
 
     @property
     def status_name(self) -> str:
@@ -280,7 +282,7 @@ class LP:
                       r.full_passes, r.reinvert_gj_seconds, r.reinvert_assemble_seconds,
                       r.chain_seconds, r.chain_bytes, r.chain_launches, r.persistent,
                       r.phase1_iterations, r.phase1_exchanged, r.refined_reinversions,
-                      r.refine_residual_max, r.engine_reason)
+                      r.refine_residual_max, r.engine_reason, r.tc_reinversions)
 
     def reset(self):
         _check(_lib.lp_reset(self._h), "lp_reset")
