@@ -679,18 +679,30 @@ __global__ void k_bbar_struct(DevState s, int k) {
     }
 }
 
-// y[R[a]] = sum_b c_J[b] B11^-1[b][a]; y = 0 on rows with a basic slack
+// y[R[a]] = sum_b c_J[b] B11^-1[b][a] (one warp per a: lane-strided partial
+// sums in increasing b, combined in a fixed shuffle order); y = 0 on rows with
+// a basic slack
 __global__ void k_duals_struct(DevState s, int k) {
     if (s.ctrl->err != kErrNone) return;
     const int m = s.p.m;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.p.ld; i += gridDim.x * blockDim.x) {
-        const int a = i < m ? s.rv_row_index[i] : -1;
-        double acc = 0.0;
-        if (a >= 0) {
-            for (int b = 0; b < k; ++b) acc = fma(s.rv_cJ[b], s.rv_W[(size_t)b * k + a], acc);
+        if (i >= m || s.rv_row_index[i] < 0) {
+            s.y[i] = 0.0;
+            s.y32[i] = 0.f;
         }
-        s.y[i] = acc;
-        s.y32[i] = (float)acc;
+    }
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int a = gw; a < k; a += nw) {
+        double acc = 0.0;
+        for (int b = lane; b < k; b += 32) acc = fma(s.rv_cJ[b], s.rv_W[(size_t)b * k + a], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const int i = s.rv_rows[a];
+            s.y[i] = acc;
+            s.y32[i] = (float)acc;
+        }
     }
 }
 
@@ -815,8 +827,11 @@ void launch_refine_apply(const DevState& s, int k, cudaStream_t st) {
     k_refine_gemm<1><<<dim3(nt, nt), kRT * kRT, 0, st>>>(s, k);
 }
 
-// Returns 1 when the slack-row product ran on the tensor cores.
-int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj) {
+// Returns 1 when the slack-row product ran on the tensor cores.  dense_rows:
+// write the dense B^-1 (the slack-structured engine gathers its live columns
+// from W and C instead).
+int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj,
+                          bool dense_rows) {
     const int nslack = s.p.m - k;
     int tc = 0;
     if (k > 0) {
@@ -836,13 +851,13 @@ int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStrea
             }
         }
     }
-    k_assemble_rows<<<g.sms * 4, 256, 0, st>>>(s, k);
+    if (dense_rows) k_assemble_rows<<<g.sms * 4, 256, 0, st>>>(s, k);
     return tc;
 }
 
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible) {
     k_bbar_struct<<<g.sms * 2, 256, 0, st>>>(s, k);
-    k_duals_struct<<<(s.p.ld + 255) / 256, 256, 0, st>>>(s, k);
+    k_duals_struct<<<g.sms * 2, 256, 0, st>>>(s, k);
     k_reinv_close<<<1, 1024, 0, st>>>(s, check_feasible);
 }
 

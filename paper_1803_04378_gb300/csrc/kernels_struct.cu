@@ -200,18 +200,18 @@ __device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int
 
 // The CTA's ratio-test record from its rows' (alpha', bbar, variable): its
 // smallest ratio, and its best row and tie count under that ratio's tie
-// threshold (one warp, one lane per row; result written by lane 0).  On this
-// chip every FP64 instruction holds a scheduler's FP64 pipe for 64 cycles
-// whatever the number of active lanes, so the ratios of 32 rows are formed by
-// one warp-wide division, and the minimum, the tie band and the largest pivot
-// are taken on integer keys.
+// threshold (one warp, one lane per row).  On this chip every FP64
+// instruction holds a scheduler's FP64 pipe for 64 cycles whatever the number
+// of active lanes, so the ratios of 32 rows are formed by one warp-wide
+// division; the minimum, the tie band and the largest pivot are taken on
+// integer keys, across the warp by redux (a dependent shuffle costs more).
 __device__ void row_record(const Params& P, int owned, bool bland, const double* ral, const double* rb,
                            const int* rvar, RowRec* out) {
     const int lane = threadIdx.x & 31;
     const int G = gridDim.x;
     const long long kpiv = dkey(P.tol_piv), kbig = dkey(DBL_MAX);
     // pass 1: ratios and their minimum
-    long long kmin = kbig;
+    long long kmin_l = kbig;
     double th0 = DBL_MAX;  // the first 32 rows' ratios, kept for pass 2
     for (int l0 = 0; l0 < owned; l0 += 32) {
         const int l = l0 + lane;
@@ -219,15 +219,16 @@ __device__ void row_record(const Params& P, int owned, bool bland, const double*
         const bool ok = l < owned && dkey(al) > kpiv;
         const double th = ok ? rb[l] / al : DBL_MAX;
         if (l0 == 0) th0 = th;
-        kmin = min(kmin, dkey(th));
+        kmin_l = min(kmin_l, dkey(th));
     }
-    for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    const long long kmin = warp_min_key(kmin_l);
     const double tmin = kdouble(kmin);
     const double thr = kmin == kbig ? DBL_MAX : tmin + P.tol_tie * fmax(1.0, fabs(tmin));
     const long long kthr = dkey(thr);
-    // pass 2: tie band, its size and best row (largest pivot, then smallest basic index)
+    // pass 2: the tie band, its size and best row (largest pivot, then smallest
+    // basic index; Bland: smallest basic index), lane by lane
     long long ka = LLONG_MIN;
-    int bvar = 0, bl = -1, cnt = 0;
+    int bvar = INT_MAX, bl = -1, cnt = 0;
     double bth = 0.0;
     if (kmin != kbig) {
         for (int l0 = 0; l0 < owned; l0 += 32) {
@@ -244,22 +245,17 @@ __device__ void row_record(const Params& P, int owned, bool bland, const double*
             }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        const long long oa = __shfl_xor_sync(0xffffffffu, ka, o);
-        const int ov = __shfl_xor_sync(0xffffffffu, bvar, o), ol = __shfl_xor_sync(0xffffffffu, bl, o);
-        const double oth = __shfl_xor_sync(0xffffffffu, bth, o);
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (ol >= 0 && (bl < 0 || (bland ? ov < bvar : (oa > ka || (oa == ka && ov < bvar))))) {
-            ka = oa; bvar = ov; bl = ol; bth = oth;
-        }
-    }
-    if (lane == 0) {
+    const int tot = __reduce_add_sync(0xffffffffu, cnt);
+    long long kbest;
+    const int win = bland ? warp_argmin_index(bvar, bl >= 0)
+                          : warp_argmax_key(ka, bvar, bl >= 0, kbest);
+    if (win < 0 ? lane == 0 : lane == win) {
         RowRec rp;
         rp.tmin = kmin; rp.thr = kthr;
-        rp.a = bl >= 0 ? kdouble(ka) : 0.0;
-        rp.th = bth;
-        rp.var = bvar; rp.row = bl >= 0 ? (int)blockIdx.x + G * bl : -1;
-        rp.cnt = cnt; rp.pad_ = 0;
+        rp.a = win >= 0 ? kdouble(ka) : 0.0;
+        rp.th = win >= 0 ? bth : 0.0;
+        rp.var = win >= 0 ? bvar : 0; rp.row = win >= 0 ? (int)blockIdx.x + G * bl : -1;
+        rp.cnt = tot; rp.pad_ = 0;
         *out = rp;
     }
 }
@@ -273,8 +269,9 @@ __device__ __forceinline__ PriceRec to_price_rec(const Cand& c) {
     return r;
 }
 
-// CHUZC over the per-CTA partials with the warps that hold them (result in
-// thread 0); each record arrives in four 16-byte loads.
+// CHUZC over the per-CTA partials (result in thread 0): the warps that hold
+// them take one record per lane (four 16-byte loads), reduce it across the
+// warp by redux, and warp 0 reduces the warps' results the same way.
 __device__ Cand reduce_price_parts_s(const PriceRec* part, int nparts) {
     __shared__ Cand wsh[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -296,18 +293,18 @@ __device__ Cand reduce_price_parts_s(const PriceRec* part, int nparts) {
             o.k_pr = w3.x;
             cand_merge(g, o);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cand_merge(g, cand_shfl(g, o));
+        g = cand_warp_reduce(g);
         if (lane == 0) wsh[warp] = g;
     }
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (int w = 1; w < nwu; ++w) cand_merge(g, wsh[w]);
+    if (warp == 0) {
+        if (lane < nwu) g = wsh[lane];
+        else cand_init(g);
+        g = cand_warp_reduce(g);
+    }
     return g;
 }
 
-// The pivot's changes to the data PRICE reads, for a CTA that may not see
-// the lead CTA's bookkeeping stores yet.
 __device__ PricePatch pivot_patch(const SlotMoves& v, int q, int leave, bool push, int tabu_until) {
     PricePatch p = no_patch();
     p.basic_j = q;
@@ -756,13 +753,11 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
             rec.var = w2.x; rec.row = w2.y; rec.cnt = w2.z;
         }
         const int nwu = (G + 31) >> 5;
-        long long wm = rec.tmin, wt = rec.thr;
         if (warp < nwu) {
-            for (int o = 16; o > 0; o >>= 1) {
-                const long long om = __shfl_xor_sync(0xffffffffu, wm, o), ot = __shfl_xor_sync(0xffffffffu, wt, o);
-                if (om < wm) { wm = om; wt = ot; }
-            }
-            if (lane == 0) { wmin_sh[warp] = wm; wthr_sh[warp] = wt; }
+            // (the threshold is a function of the minimum: any lane holding it has it)
+            const long long wm = warp_min_key(rec.tmin);
+            const unsigned hold = __ballot_sync(0xffffffffu, rec.tmin == wm);
+            if (lane == __ffs(hold) - 1) { wmin_sh[warp] = wm; wthr_sh[warp] = rec.thr; }
         }
         __syncthreads();
         long long gmin = wmin_sh[0], gthr = wthr_sh[0];
@@ -959,6 +954,29 @@ __global__ void k_struct_gather_B(DevState s) {
         yp[t] = t < k ? s.y[sr[t]] : 0.0;
 }
 
+// The live columns straight from a reinversion's compact result, without the
+// dense B^-1: column t is row R_a = slot_row[t] of B^-1, which is W[b][a] on
+// the structural position of index b and C[g][a] on the position of the slack
+// of the g-th row with a basic slack (the same values k_assemble_rows writes).
+__global__ void k_struct_gather_B_compact(DevState s) {
+    const Params& P = s.p;
+    const int k = s.ctrl->k_live;
+    const int32_t* sr = s.slot_row + (size_t)s.ctrl->map_par * P.m;
+    const double* W = s.rv_W;
+    const double* Cs = s.rv_W + (size_t)k * k;
+    const size_t total = (size_t)P.m * k;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / k), t = (int)(e % k);
+        const int a = s.rv_row_index[sr[t]];
+        const int v = s.basis[i];
+        s.bp[(size_t)i * P.ld + t] = v < P.n ? W[(size_t)s.rv_b_of_pos[i] * k + a]
+                                             : Cs[(size_t)s.rv_g_of_row[v - P.n] * k + a];
+    }
+    double* yp = s.yp + (size_t)s.ctrl->map_par * P.ld;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P.ld; t += gridDim.x * blockDim.x)
+        yp[t] = t < k ? s.y[sr[t]] : 0.0;
+}
+
 // dense y (and its FP32 copy) from the slot-order y, for the solution and every
 // dense consumer
 __global__ void k_struct_scatter_y(DevState s) {
@@ -1022,10 +1040,13 @@ cudaError_t launch_iterate_s(const DevState& s, int blocks, int iters, cudaStrea
     return cudaLaunchKernelEx(&cfg, k_iterate_s, s, iters);
 }
 
-void launch_struct_enter(const DevState& s, int force, int32_t* relayout, cudaStream_t st) {
+void launch_struct_enter(const DevState& s, int force, int32_t* relayout, cudaStream_t st, bool compact) {
     k_struct_layout<<<1, 1024, 0, st>>>(s, force, relayout);
     k_struct_gather_A<<<1024, 256, 0, st>>>(s, relayout);
-    k_struct_gather_B<<<1024, 256, 0, st>>>(s);
+    if (compact)
+        k_struct_gather_B_compact<<<1024, 256, 0, st>>>(s);
+    else
+        k_struct_gather_B<<<1024, 256, 0, st>>>(s);
 }
 
 void launch_struct_scatter_y(const DevState& s, cudaStream_t st) {

@@ -277,7 +277,7 @@ int occupancy_iterate_s(int ld);
 bool struct_engine_fits(int m, int ld, int ctas);  // shared-memory and per-CTA row limits
 // Dense state -> structured state: slot map check (rebuilt when force or
 // inconsistent, then A_p regathered), live B^-1 columns and y, start at PRICE.
-void launch_struct_enter(const DevState& s, int force, int32_t* relayout, cudaStream_t st);
+void launch_struct_enter(const DevState& s, int force, int32_t* relayout, cudaStream_t st, bool compact);
 void launch_struct_scatter_y(const DevState& s, cudaStream_t st);  // yp -> y (row order)
 void launch_struct_init_maps(const DevState& s, cudaStream_t st);
 // Bounded-wait self-test: a grid barrier that cannot complete (lp_selftest_barrier_timeout).
@@ -296,7 +296,7 @@ void launch_csc_fill(const double* A_cm, int m, int n, int ld, const int64_t* pt
 void launch_reinv_classify(const DevState& s, cudaStream_t st);
 void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t st);
 int reinv_gj_launches(int k);
-int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj);
+int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj, bool dense_rows);
 bool refine_fits(int k, int m);
 // sliced FP64 products on the tensor cores (ozaki.cu)
 bool oz_fits(int k);

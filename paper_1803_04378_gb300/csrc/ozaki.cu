@@ -131,8 +131,36 @@ __global__ void __launch_bounds__(256) k_oz_slice(Src src, int nout, int K, cons
     }
 }
 
+// t 2^s as the nearest binary64 (ties to even), t != 0, built from the
+// IEEE-754 binary64 format with integer instructions only (on this chip every
+// FP64 instruction holds a scheduler's FP64 pipe for ~64 cycles); results
+// below 2^-1022 flush to zero, above the range become infinite.
+__device__ __forceinline__ double ll_scaled(long long t, int s) {
+    const unsigned long long sign = t < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long u = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+    const int msb = 63 - __clzll((long long)u);
+    int e = msb + s;  // weight of the leading bit
+    unsigned long long mant;
+    if (msb > 52) {
+        const int sh = msb - 52;
+        const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        mant = u >> sh;
+        if (rem > half || (rem == half && (mant & 1ull))) {
+            ++mant;
+            if (mant == (1ull << 53)) { mant >>= 1; ++e; }
+        }
+    } else {
+        mant = u << (52 - msb);
+    }
+    const int be = e + 1023;
+    if (be >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+    if (be <= 0) return __longlong_as_double((long long)sign);
+    return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 // GEMM epilogue: combines the 64 digit pairs of each output (see the file
-// comment) and writes sign * (X Y)[i][c] into out (row stride ldo).
+// comment) and writes sign * (X Y)[i][c] into out (row stride ldo); integer
+// instructions only.
 struct OzEpi {
     double* out;
     int ldo, M, N;
@@ -150,9 +178,9 @@ struct OzEpi {
             for (int q = 0; q < kSlices; ++q) {
                 const int L = p + q;
                 if (L <= kLevels) {
-                    const long long sv = __float2ll_rn(v[cc * 8 + q]);  // an exact integer below 2^24
+                    const long long sv = __float2int_rz(v[cc * 8 + q]);  // an exact integer below 2^24
                     const int sh = kFrac - 14 - 7 * L;
-                    t += sh >= 0 ? sv * (1ll << sh) : ((sv + (1ll << (-sh - 1))) >> (-sh));
+                    t += sh >= 0 ? (long long)((unsigned long long)sv << sh) : ((sv + (1ll << (-sh - 1))) >> (-sh));
                 }
             }
             t += __shfl_xor_sync(0xffffffffu, t, 1);
@@ -162,8 +190,7 @@ struct OzEpi {
             if (p == cc && i < M && c < N) {
                 double val = 0.0;
                 const int ei = ex[i], fc = ey[c];
-                if (t != 0 && ei != kNoDigits && fc != kNoDigits)
-                    val = scalbn(__ll2double_rn(negate ? -t : t), ei + fc - kFrac);
+                if (t != 0 && ei != kNoDigits && fc != kNoDigits) val = ll_scaled(negate ? -t : t, ei + fc - kFrac);
                 out[(size_t)i * ldo + c] = val;
             }
         }
@@ -208,7 +235,7 @@ cudaError_t oz_slack_product(const double* A_cm, int ld, const int32_t* J, const
         !tc_make_map_16bit(&mb, ys, kSlices * k, k, ldk, BN, true))
         return cudaErrorInvalidValue;
     const OzEpi epi{C, k, nslack, k, ex, ey, 1};
-    return tcg::launch_tc_gemm<BN, true>(ma, mb, epi, kSlices * nslack, kSlices * k, k, err, st);
+    return tcg::launch_tc_gemm<BN, 3, 2, true>(ma, mb, epi, kSlices * nslack, kSlices * k, k, err, st);
 }
 
 }  // namespace lpgb

@@ -216,7 +216,11 @@ constexpr double kRefineTolMax = 1.0 / 67108864.0;  // 2^-26
 // Rebuild B^-1, bbar, y, z from the current basis.  `refine`: the stored
 // inverse is that of the current basis (a periodic reinversion, the last
 // update applied), so B11^-1 may come from one refinement step of it.
-int reinvert(lp_handle* h, int check_feasible, bool refine) {
+// `to_struct`: the next consumer is the slack-structured engine, which then
+// receives its live columns straight from B11^-1 and the slack rows (the
+// dense B^-1 is not written).
+int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = false) {
+    const bool compact = to_struct && h->structured;
     CK(cudaEventRecord(h->er0, h->stream));
     launch_reinv_classify(h->ds, h->stream);
     TRY(read_ctrl(h));
@@ -243,9 +247,9 @@ int reinvert(lp_handle* h, int check_feasible, bool refine) {
         launch_reinv_gj(h->ds, k, h->geo, h->stream);
         h->launches += reinv_gj_launches(k);
     }
-    h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 3;
+    h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 3 - (compact ? 1 : 0);
     CK(cudaEventRecord(h->era, h->stream));
-    if (launch_reinv_assemble(h->ds, k, h->geo, h->stream, refined ? 0 : 1)) {
+    if (launch_reinv_assemble(h->ds, k, h->geo, h->stream, refined ? 0 : 1, !compact)) {
         h->reinv_tc++;
         h->launches += 4;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
     }
@@ -263,6 +267,13 @@ int reinvert(lp_handle* h, int check_feasible, bool refine) {
     h->primed = false;
     h->s_ready = false;
     if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
+    if (compact) {
+        launch_struct_enter(h->ds, h->s_force ? 1 : 0, h->s_relayout, h->stream, true);
+        CK(cudaGetLastError());
+        h->launches += 3;
+        h->s_force = false;
+        h->s_ready = true;
+    }
     return LP_OK;
 }
 
@@ -854,14 +865,14 @@ int lp_solve(lp_handle* h, lp_result* out) {
         const Ctrl& C = *h->h_ctrl;
         if (C.err != kErrNone) return device_err_code(C.err);
         if (C.status == kReinvert) {
-            TRY(reinvert(h, 0, true));
+            TRY(reinvert(h, 0, true, true));
             continue;
         }
         if (C.status != kRunning) break;
         if (h->structured) {
             if (!h->s_ready) {
                 // enter the structured form from the dense state (rebuilt B^-1 or slack basis)
-                launch_struct_enter(h->ds, h->s_force ? 1 : 0, h->s_relayout, h->stream);
+                launch_struct_enter(h->ds, h->s_force ? 1 : 0, h->s_relayout, h->stream, false);
                 CK(cudaGetLastError());
                 h->launches += 3;
                 h->s_force = false;

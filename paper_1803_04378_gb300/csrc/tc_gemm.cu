@@ -80,8 +80,8 @@ cudaError_t tc_gemm(const void* A, int lda, const void* B, int ldb, float* D, in
     if (!tc_make_map_16bit(&ma, A, M, K, lda, tcg::kTM, bf16) || !tc_make_map_16bit(&mb, B, N, K, ldb, BN, bf16))
         return cudaErrorInvalidValue;
     const StoreF32 epi{D, ldd, M, N};
-    return bf16 ? tcg::launch_tc_gemm<BN, true>(ma, mb, epi, M, N, K, err, st)
-                : tcg::launch_tc_gemm<BN, false>(ma, mb, epi, M, N, K, err, st);
+    return bf16 ? tcg::launch_tc_gemm<BN, 4, 1, true>(ma, mb, epi, M, N, K, err, st)
+                : tcg::launch_tc_gemm<BN, 4, 1, false>(ma, mb, epi, M, N, K, err, st);
 }
 
 }  // namespace lpgb

@@ -26,10 +26,9 @@ namespace tcg {
 
 constexpr int kTM = 128;      // tile rows (MMA M)
 constexpr int kTK = 64;       // elements of K per stage (one 128-byte swizzle row)
-constexpr int kStages = 4;
 constexpr int kGemmThreads = 192;
 
-template <int BN>
+template <int BN, int kStages>
 struct GemmSmem {
     static constexpr int kA = kTM * kTK * 2;
     static constexpr int kB = BN * kTK * 2;
@@ -41,11 +40,14 @@ struct GemmSmem {
 // Epi: a functor called by every lane of an epilogue warp (warp-collective)
 // with the tile row of the lane (0..127, the TMEM lane), the tile's first row
 // and column in the output, the first of the 32 columns, and their values.
-template <int BN, bool kBF16, class Epi>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+// kStages shared-memory stages; kMinBlocks CTAs share an SM (their TMEM
+// allocations, BN columns each, must fit the SM's 512).
+template <int BN, int kStages, int kMinBlocks, bool kBF16, class Epi>
+__global__ void __launch_bounds__(kGemmThreads, kMinBlocks)
     k_tc_gemm(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb, Epi epi, int K,
               int32_t* err) {
-    using L = GemmSmem<BN>;
+    static_assert(kMinBlocks * BN <= 512, "TMEM columns of the co-resident CTAs");
+    using L = GemmSmem<BN, kStages>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * L::kStage);
@@ -132,15 +134,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 }
 
 // Tensor maps of the two operands and the launch (grid = N/BN x M/128 tiles).
-template <int BN, bool kBF16, class Epi>
+template <int BN, int kStages, int kMinBlocks, bool kBF16, class Epi>
 cudaError_t launch_tc_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const Epi& epi, int M, int N, int K,
                            int32_t* err, cudaStream_t st) {
-    using L = GemmSmem<BN>;
-    static cudaError_t attr_rc = cudaFuncSetAttribute(k_tc_gemm<BN, kBF16, Epi>,
+    using L = GemmSmem<BN, kStages>;
+    static cudaError_t attr_rc = cudaFuncSetAttribute(k_tc_gemm<BN, kStages, kMinBlocks, kBF16, Epi>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
     if (attr_rc != cudaSuccess) return attr_rc;
     const dim3 grid((N + BN - 1) / BN, (M + kTM - 1) / kTM);
-    k_tc_gemm<BN, kBF16, Epi><<<grid, kGemmThreads, L::kBytes, st>>>(ma, mb, epi, K, err);
+    k_tc_gemm<BN, kStages, kMinBlocks, kBF16, Epi><<<grid, kGemmThreads, L::kBytes, st>>>(ma, mb, epi, K, err);
     return cudaGetLastError();
 }
 
