@@ -81,6 +81,44 @@ __device__ __forceinline__ void dot_cols(const double2* __restrict__ A2, const i
     }
 }
 
+// ---- warp reductions on 64-bit keys by 32-bit redux ------------------------------
+// On this chip a dependent warp shuffle costs about 110 cycles and a redux
+// about 90: a five-level butterfly of a 64-bit key takes ten shuffles in
+// sequence, these take two or three reduxes (the high half, then the low
+// half among the lanes that hold the extreme high half).  Keys are the
+// order-preserving integer images of doubles (dkey); every lane gets the result.
+__device__ __forceinline__ long long key_join(int hi, unsigned lo) {
+    return (long long)(((unsigned long long)(unsigned)hi << 32) | lo);
+}
+__device__ __forceinline__ long long warp_min_key(long long k) {
+    const int hi = (int)(k >> 32);
+    const int h = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned lo = __reduce_min_sync(0xffffffffu, hi == h ? (unsigned)k : 0xffffffffu);
+    return key_join(h, lo);
+}
+// maximum over the lanes with `valid` (LLONG_MIN when there is none)
+__device__ __forceinline__ long long warp_max_key(long long k, bool valid) {
+    const int hi = valid ? (int)(k >> 32) : INT_MIN;
+    const int h = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned lo = __reduce_max_sync(0xffffffffu, (valid && hi == h) ? (unsigned)k : 0u);
+    return key_join(h, lo);
+}
+// The lane holding the largest key, exact ties to the smallest index, among
+// the lanes with `valid` (-1 when there is none); kbest gets the key.
+__device__ __forceinline__ int warp_argmax_key(long long k, int idx, bool valid, long long& kbest) {
+    kbest = warp_max_key(k, valid);
+    const bool top = valid && k == kbest;
+    const int imin = __reduce_min_sync(0xffffffffu, top ? idx : INT_MAX);
+    const unsigned b = __ballot_sync(0xffffffffu, top && idx == imin);
+    return b ? __ffs(b) - 1 : -1;
+}
+// The lane holding the smallest index among the lanes with `valid` (-1: none).
+__device__ __forceinline__ int warp_argmin_index(int idx, bool valid) {
+    const int imin = __reduce_min_sync(0xffffffffu, valid ? idx : INT_MAX);
+    const unsigned b = __ballot_sync(0xffffffffu, valid && idx == imin);
+    return b ? __ffs(b) - 1 : -1;
+}
+
 // ---- CHUZC candidate ---------------------------------------------------------
 // Reduced costs are compared through their order-preserving integer images
 // (dkey, kdouble in lpgb_internal.cuh).
@@ -138,11 +176,33 @@ __device__ __forceinline__ Cand cand_shfl(const Cand& c, int off) {
     return o;
 }
 
+// Warp-wide cand_merge of every lane's candidate, by redux (see the warp
+// reductions above): the four categories reduce independently, each to its
+// largest key with exact ties to the smallest index (j_min: the smallest
+// index); the payloads come from the winning lanes.  Every lane gets the result.
+__device__ Cand cand_warp_reduce(const Cand& c) {
+    Cand g;
+    cand_init(g);
+    long long kb;
+    int w = warp_argmax_key(c.d_all, c.j_all, c.j_all >= 0, kb);
+    if (w >= 0) { g.d_all = kb; g.j_all = __shfl_sync(0xffffffffu, c.j_all, w); }
+    w = warp_argmax_key(c.d_nt, c.j_nt, c.j_nt >= 0, kb);
+    if (w >= 0) { g.d_nt = kb; g.j_nt = __shfl_sync(0xffffffffu, c.j_nt, w); }
+    w = warp_argmin_index(c.j_min, c.j_min >= 0);
+    if (w >= 0) { g.j_min = __shfl_sync(0xffffffffu, c.j_min, w); g.d_min = __shfl_sync(0xffffffffu, c.d_min, w); }
+    w = warp_argmax_key(c.d_pr, c.j_pr, c.j_pr >= 0, kb);
+    if (w >= 0) {
+        g.d_pr = kb;
+        g.j_pr = __shfl_sync(0xffffffffu, c.j_pr, w);
+        g.k_pr = __shfl_sync(0xffffffffu, c.k_pr, w);
+    }
+    return g;
+}
+
 // Block-wide reduction; the result is valid in thread 0.
 __device__ Cand cand_block_reduce(Cand c) {
     __shared__ Cand sh[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cand_merge(c, cand_shfl(c, o));
+    c = cand_warp_reduce(c);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) sh[wid] = c;
@@ -150,8 +210,7 @@ __device__ Cand cand_block_reduce(Cand c) {
     if (wid == 0) {
         const int nw = blockDim.x >> 5;
         if (lane < nw) c = sh[lane]; else cand_init(c);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cand_merge(c, cand_shfl(c, o));
+        c = cand_warp_reduce(c);
     }
     return c;
 }
