@@ -139,6 +139,20 @@ def _traffic(kernel: str):
     return ent.get("dram_bytes_per_launch_full_size")
 
 
+def _oracle_golden():
+    """The oracle's full solve of the timed workload (objective, pivot count),
+    stored by tests/golden/make_fullsize.py, which calls only the oracle."""
+    p = os.path.join(ROOT, "tests", "golden", f"{WORKLOAD['name']}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f)
+
+
+def _rel_err(z, ref):
+    return None if ref is None else abs(z - ref) / max(1.0, abs(ref))
+
+
 def _certificate(A, b, c, x, y):
     """Optimality residuals of the returned solution (host, numpy): primal
     infeasibility of Ax <= b, x >= 0 and dual infeasibility of A^T y >= c,
@@ -230,11 +244,14 @@ def run_batched(lpgb, args, with_cpu: bool):
         import oracle
         sample = 32
         t0 = time.perf_counter()
-        for k in range(sample):
-            oracle.solve(*probs[k])
+        sols = [oracle.solve(*probs[k]) for k in range(sample)]
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": sample / dt, "unit": "LPs/s", "cores": 1, "kind": "oracle",
                                "sample": f"first {sample} LPs of the batch, single-threaded oracle, {dt:.1f} s"}
+        out["max_objective_rel_err_vs_oracle"] = max(
+            abs(float(obj[k]) - s_.objective) / max(1.0, abs(s_.objective)) for k, s_ in enumerate(sols))
+        out["status_equal_oracle"] = all(int(st[k]) == s_.status for k, s_ in enumerate(sols))
+        out["oracle_checked_lps"] = sample
     return out
 
 
@@ -464,6 +481,9 @@ def main():
                "h2d_bytes_per_step": 8 * (m * n + m + n), "d2h_bytes_per_step": 8 * (n + m) + 8,
                "seconds_per_step": t_e2e / args.e2e_steps}
 
+    golden = _oracle_golden()
+    z_oracle = golden["objective"] if golden else None
+
     # variant: BF16-screened PRICE, each screening block's best two columns
     # re-priced in FP64 (same FP64 UPDATE/FTRAN/ratio test/reinversion;
     # optimality certified in FP64)
@@ -491,6 +511,7 @@ def main():
             "value": rs_.iterations / ts_, "unit": "iters/s", "time_to_optimum_s": ts_,
             "pivots_per_solve": rs_.iterations, "reinversions_per_solve": rs_.reinversions,
             "objective": zs_, "objective_rel_err_vs_timed_engine": abs(zs_ - z) / max(1.0, abs(z)),
+            "objective_rel_err_vs_oracle": _rel_err(zs_, z_oracle),
             "reinversion_seconds": rs_.reinvert_seconds,
             "us_per_pivot_excl_reinversion": 1e6 * (ts_ - rs_.reinvert_seconds) / max(1, rs_.iterations),
             "chain_seconds": rs_.chain_seconds, "chain_launches": rs_.chain_launches,
@@ -516,6 +537,7 @@ def main():
             "value": rv.iterations / tv, "unit": "iters/s", "time_to_optimum_s": tv,
             "pivots_per_solve": rv.iterations, "objective": zv,
             "objective_rel_err_vs_fp64_path": abs(zv - z) / max(1.0, abs(z)),
+            "objective_rel_err_vs_oracle": _rel_err(zv, z_oracle),
             "us_per_price": 1e6 * rv.price_seconds / max(1, rv.price_launches),
             "price_hbm_gbs": rv.price_bytes / rv.price_seconds / 1e9 if rv.price_seconds else None,
             "screen_passes": rv.screen_passes, "full_fp64_passes": rv.full_passes,
@@ -546,6 +568,7 @@ def main():
                               "no flush: A (268 MB) + B^-1 (134 MB) streamed every pivot exceed L2"),
                        "engine": {2: "slack-structured persistent", 1: "dense persistent",
                                   0: "captured graphs"}[results[0].persistent],
+                       "engine_reason": lpgb.ENGINE_REASONS.get(results[0].engine_reason),
                        "parallelism": f"replicas x{ws}"},
             "time_to_optimum_s": elapsed / args.steps,
             "pivots_per_solve": results[0].iterations,
@@ -556,6 +579,12 @@ def main():
                                     "slack_rows_assembly_bbar_y": sum(r.reinvert_assemble_seconds for r in results) / len(results),
                                     "total": reinv_s / len(results)},
             "objective": z,
+            "objective_rel_err_vs_oracle": _rel_err(z, z_oracle),
+            "oracle_golden": ({"objective": golden["objective"], "pivots": golden["iterations"],
+                               "reinversions": golden["reinversions"],
+                               "pivots_equal": results[0].iterations == golden["iterations"],
+                               "source": "tests/golden/dense_real_4096x8192.json (the oracle's full solve)"}
+                              if golden else None),
             "certificate": _certificate(A, b, c, x, y),
             "us_per_pivot_excl_reinversion": 1e6 * iter_s / iters,
             "reinversion_share": reinv_s / sum(r.seconds for r in results),
