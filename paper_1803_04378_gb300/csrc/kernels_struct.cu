@@ -417,6 +417,9 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
         if (row < 0) row = __ldcg(slack_rows + si);
         sj = P.n + row;
     }
+    // its tabu expiry and priority, loaded now and used twice below
+    const int sj_tabu = sj >= 0 ? patched_tabu(s, pp, sj) : 0;
+    const int sj_rank = sj >= 0 ? s.rank[sj] : kNoRank;
     const int n4 = kk >> 2;
     const int depth = 4 * ((n4 + 31) >> 5) + 5;  // fused multiply-adds per lane + butterfly levels
     const float umul = __fmul_ru((float)(depth + 3), 6.0200691e-8f);  // (d + 3) u 1.01, rounded up
@@ -458,25 +461,21 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
         }
         if (lb == 0 && sj >= 0) {
             const int kd = fkey(__double2float_rd(-ysh[si]));  // exact value, its lower FP32 bound
-            const bool nt = patched_tabu(s, pp, sj) <= it;
+            const bool nt = sj_tabu <= it;
             b0 = max(b0, kd);
             if (nt) b1 = max(b1, kd);
-            if (nt && s.rank[sj] != kNoRank) b2 = max(b2, kd);
+            if (nt && sj_rank != kNoRank) b2 = max(b2, kd);
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            b0 = max(b0, __shfl_xor_sync(0xffffffffu, b0, o));
-            b1 = max(b1, __shfl_xor_sync(0xffffffffu, b1, o));
-            b2 = max(b2, __shfl_xor_sync(0xffffffffu, b2, o));
-        }
+        // across the warp, then across the 32 warps, by redux
+        b0 = __reduce_max_sync(0xffffffffu, b0);
+        b1 = __reduce_max_sync(0xffffffffu, b1);
+        b2 = __reduce_max_sync(0xffffffffu, b2);
         if (lane == 0) { bandsh[0][warp] = b0; bandsh[1][warp] = b1; bandsh[2][warp] = b2; }
         if (threadIdx.x == 0) nrl = 0;
         __syncthreads();
-        int L0 = INT_MIN, L1 = INT_MIN, L2 = INT_MIN;
-        for (int w = 0; w < nw; ++w) {
-            L0 = max(L0, bandsh[0][w]);
-            L1 = max(L1, bandsh[1][w]);
-            L2 = max(L2, bandsh[2][w]);
-        }
+        const int L0 = __reduce_max_sync(0xffffffffu, lane < nw ? bandsh[0][lane] : INT_MIN);
+        const int L1 = __reduce_max_sync(0xffffffffu, lane < nw ? bandsh[1][lane] : INT_MIN);
+        const int L2 = __reduce_max_sync(0xffffffffu, lane < nw ? bandsh[2][lane] : INT_MIN);
         // (3) the columns whose interval reaches a category's lower end
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
             const int hi = khi[e];
@@ -510,7 +509,7 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
             __syncthreads();
         }
     }
-    if (sj >= 0) cand_offer(cand, -ysh[si], sj, patched_tabu(s, pp, sj) <= it, ktol, s.rank[sj]);
+    if (sj >= 0) cand_offer(cand, -ysh[si], sj, sj_tabu <= it, ktol, sj_rank);
     for (int i = si + G * blockDim.x; i < nslack; i += G * blockDim.x) {
         int row = -1;
         for (int e = 0; e < pp.nsp && row < 0; ++e)
@@ -568,6 +567,14 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
         const int r = S.r, q = S.q, par = S.par;
         const double* acur = s.alpha + (size_t)S.abuf * P.ld;
         const double ar = S.alpha_r, th = S.theta, dq = S.dq;
+        // this thread's first pair of the pivot row of B^-1 and of the old y,
+        // loaded before the slot moves are known (k grows by one at most)
+        const int kpre = min(P.ld, (S.k + 1 + 63) & ~63);
+        double2 pre_rb = make_double2(0.0, 0.0), pre_yb = make_double2(0.0, 0.0);
+        if (2 * (int)threadIdx.x < kpre) {
+            if (piv) pre_rb = __ldcg(reinterpret_cast<const double2*>(s.bp + (size_t)r * P.ld) + threadIdx.x);
+            pre_yb = __ldcg(reinterpret_cast<const double2*>(s.yp + (size_t)par * P.ld) + threadIdx.x);
+        }
         if (threadIdx.x == 0) {
             if (piv) {
                 mv = slot_moves(s, S.leave, S.q, S.k, par);
@@ -606,8 +613,10 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
             const double* brow = s.bp + (size_t)(piv ? r : 0) * P.ld;
             // slot pairs in 16-byte loads; a moved slot reads its source itself
             for (int p = threadIdx.x; 2 * p < kk; p += blockDim.x) {
-                const double2 rb = piv ? __ldcg(reinterpret_cast<const double2*>(brow) + p) : make_double2(0.0, 0.0);
-                const double2 yb = __ldcg(reinterpret_cast<const double2*>(yold) + p);
+                const bool first = p == (int)threadIdx.x;  // kk <= kpre: prefetched above
+                const double2 rb = first ? pre_rb
+                                         : (piv ? __ldcg(reinterpret_cast<const double2*>(brow) + p) : make_double2(0.0, 0.0));
+                const double2 yb = first ? pre_yb : __ldcg(reinterpret_cast<const double2*>(yold) + p);
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int t = 2 * p + e;
