@@ -89,6 +89,8 @@ extern "C" {
                                               device's per-block limit (m above about 5600 on
                                               152 SMs) */
 #define LP_ENGINE_REASON_OCCUPANCY 5       /* the persistent kernel does not fit one CTA per SM */
+#define LP_ENGINE_REASON_OUT_OF_CORE 6     /* tableau_budget_mb: B^-1 streams through the device in row
+                                              blocks (Case 2), on the captured-graph engine's kernels */
 
 typedef struct lp_handle lp_handle;
 
@@ -135,6 +137,15 @@ typedef struct lp_options {
     double refine_tol;      /* reinvert_refine: largest ||I - B11 Y||_inf that is refined (default
                                and maximum 2^-26, so that one step leaves the residual below
                                2^-52; 0 refines only an exact inverse) */
+    double tableau_budget_mb; /* device memory granted to the explicit inverse (the tableau of
+                               Step 8), in MB (1e6 bytes); 0 (default): no limit.  When the
+                               m x ld FP64 inverse exceeds it (Case 2 of Section 3), B^-1
+                               lives in pinned host memory and streams through two device
+                               buffers of budget/2 each in blocks of consecutive rows, every
+                               pivot (the captured-graph engine's kernels; the block updated
+                               last stays on the device for the next pivot, row r is fetched
+                               once).  The reinversion's scratch is not counted.  Not with
+                               LP_ANTICYCLING_LEXICOGRAPHIC. */
     void* cuda_stream;      /* cudaStream_t to run on; NULL: the handle's own stream */
 } lp_options;
 
@@ -177,6 +188,9 @@ typedef struct lp_result {
                                 lp_options.engine asked for (0: it is) */
     double refine_residual_max;   /* largest ||I - B11 Y||_inf of the updated inverse found by the
                                      refinement checks of this solve (drift of the updates) */
+    int32_t ooc_blocks;      /* tableau_budget_mb: row blocks B^-1 streams in (0: resident) */
+    int32_t ooc_block_rows;  /* rows per block */
+    double ooc_bytes;        /* host <-> device bytes of the streamed blocks in this solve */
 } lp_result;
 
 /*

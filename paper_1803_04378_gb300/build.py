@@ -14,7 +14,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(BUILD, "liblpgb.so")
 SOURCES = ["kernels_iter.cu", "kernels_struct.cu", "kernels_sparse.cu", "kernels_reinv.cu", "kernels_setup.cu", "kernels_price_lp.cu", "solver.cu",
            "price_static.cu", "batch.cu", "mlp.cu",
-           "family.cu", "tc_gemm.cu", "ozaki.cu"]
+           "family.cu", "tc_gemm.cu", "ozaki.cu", "ooc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

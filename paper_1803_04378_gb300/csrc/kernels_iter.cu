@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kPivotThreads) k_pivot(DevState s) {
     const double ar = acur[r];
     const double th = C->theta;  // bbar_r / alpha_r, computed by the ratio test
     const double dq = C->dq;
-    const double* brow = s.binv + (size_t)r * P.ld;
+    const double* brow = s.prow ? s.prow : s.binv + (size_t)r * P.ld;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     // new row r of the tableau and the row-0 (dual) update

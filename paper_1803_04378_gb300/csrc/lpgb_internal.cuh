@@ -160,7 +160,9 @@ struct DevState {
     double* cand_d;          // their exact reduced costs
     const double* c;
     const double* b;
-    double* binv;
+    double* binv;            // out of core (Case 2): pinned host memory, read and written by
+                             // kernels over the host link only outside the per-pivot blocks
+    const double* prow;      // out of core: row r of the updated B^-1 for k_pivot (else null)
     double* bbar;
     double* y;
     double* rho;
@@ -298,6 +300,12 @@ void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t s
 int reinv_gj_launches(int k);
 int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj, bool dense_rows);
 bool refine_fits(int k, int m);
+// Case 2 out-of-core blocks of B^-1 (ooc.cu)
+void launch_ooc_update(const DevState& s, const Geometry& g, double* win, int i0, int i1, cudaStream_t st);
+void launch_ooc_chuzr(const DevState& s, cudaStream_t st);
+void launch_ooc_fetch_row(const DevState& s, const double* host_binv, const double* win, int w0, int w1,
+                          double* prow, cudaStream_t st);
+int configure_ooc_kernels(int ld);
 // sliced FP64 products on the tensor cores (ozaki.cu)
 bool oz_fits(int k);
 size_t oz_scratch_x_elems(int m);

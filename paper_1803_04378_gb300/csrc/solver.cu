@@ -50,6 +50,17 @@ struct lp_handle {
     cudaEvent_t evc0 = nullptr, evc1 = nullptr;  // kernel_timing around k_iterate launches
     bool structured = false;         // pivots run in k_iterate_s (LP_ENGINE_STRUCTURED)
     int engine_reason = LP_ENGINE_REASON_NONE;  // why the engine that runs is not the one asked for
+    // Case 2 (tableau_budget_mb exceeded): B^-1 in pinned host memory, streamed in row blocks
+    bool ooc = false;
+    int ooc_rows = 0, ooc_w = 0;        // rows per block, blocks
+    double* ooc_host = nullptr;         // B^-1 (m x ld), pinned host memory
+    double* ooc_buf[2] = {};            // device block buffers (ooc_rows x ld)
+    double* ooc_prow = nullptr;         // device copy of row r for the next pivot
+    int ooc_res = -1, ooc_res_buf = 0;  // block left on the device by the last pass (-1: none), its buffer
+    bool ooc_primed = false;
+    double ooc_bytes = 0.0;             // host <-> device block bytes of this solve
+    cudaStream_t ooc_h2d = nullptr, ooc_d2h = nullptr;
+    cudaEvent_t ooc_ev_h2d[2] = {}, ooc_ev_upd[2] = {}, ooc_ev_d2h[2] = {};
     bool s_ready = false;            // the structured state (bp, yp, slot maps) is current; the dense
                                      // B^-1 and y are stale while it is
     bool s_force = true;             // rebuild the slot map and A_p on the next entry
@@ -125,6 +136,15 @@ void free_all(lp_handle* h) {
     if (h->evc0) cudaEventDestroy(h->evc0);
     if (h->evc1) cudaEventDestroy(h->evc1);
     h->evc0 = h->evc1 = nullptr;
+    if (h->ooc_host) cudaFreeHost(h->ooc_host);
+    h->ooc_host = nullptr;
+    for (int b = 0; b < 2; ++b) {
+        if (h->ooc_ev_h2d[b]) cudaEventDestroy(h->ooc_ev_h2d[b]);
+        if (h->ooc_ev_upd[b]) cudaEventDestroy(h->ooc_ev_upd[b]);
+        if (h->ooc_ev_d2h[b]) cudaEventDestroy(h->ooc_ev_d2h[b]);
+    }
+    if (h->ooc_h2d) cudaStreamDestroy(h->ooc_h2d);
+    if (h->ooc_d2h) cudaStreamDestroy(h->ooc_d2h);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -208,6 +228,96 @@ int capture_graph(lp_handle* h) {
     return capture_graph_once(h, false);
 }
 
+// ---- Case 2: B^-1 in host memory, streamed through the device in row blocks ----
+// The block left on the device by the last pass goes back to host memory (on
+// the solve's stream, after every block copy of the pass).
+int ooc_flush(lp_handle* h) {
+    if (!h->ooc || h->ooc_res < 0) return LP_OK;
+    const int i0 = h->ooc_res * h->ooc_rows, i1 = std::min(h->m, i0 + h->ooc_rows);
+    CK(cudaStreamWaitEvent(h->stream, h->ooc_ev_d2h[0], 0));
+    CK(cudaStreamWaitEvent(h->stream, h->ooc_ev_d2h[1], 0));
+    CK(cudaMemcpyAsync(h->ooc_host + (size_t)i0 * h->ld, h->ooc_buf[h->ooc_res_buf],
+                       sizeof(double) * (size_t)(i1 - i0) * h->ld, cudaMemcpyDeviceToHost, h->stream));
+    h->ooc_bytes += 8.0 * (double)(i1 - i0) * h->ld;
+    h->ooc_res = -1;
+    return LP_OK;
+}
+
+// One pass over every block: copy in (one cudaMemcpyAsync per block, except the
+// block the last pass left on the device), Step 8 of the pending pivot fused
+// with the next FTRAN and the ratios, copy out (except the block visited last,
+// which stays); then the ratio test over all rows and the fetch of row r.
+// Blocks are visited from the end where the resident block is, so the order
+// alternates between passes.
+int ooc_pass(lp_handle* h) {
+    const int W = h->ooc_w, R = h->ooc_rows, m = h->m, ld = h->ld;
+    const bool desc = h->ooc_res == W - 1 && W > 1;
+    int prev = -1;
+    for (int t = 0; t < W; ++t) {
+        const int w = desc ? W - 1 - t : t;
+        const int i0 = w * R, i1 = std::min(m, i0 + R);
+        const size_t bytes = sizeof(double) * (size_t)(i1 - i0) * ld;
+        int bi;
+        if (t == 0 && h->ooc_res == w) {
+            bi = h->ooc_res_buf;
+        } else {
+            bi = prev < 0 ? 0 : prev ^ 1;
+            // every earlier copy-out is complete (the host rows of this block
+            // are current) and so is the last use of this buffer
+            CK(cudaStreamWaitEvent(h->ooc_h2d, h->ooc_ev_d2h[0], 0));
+            CK(cudaStreamWaitEvent(h->ooc_h2d, h->ooc_ev_d2h[1], 0));
+            CK(cudaStreamWaitEvent(h->ooc_h2d, h->ooc_ev_upd[bi], 0));
+            CK(cudaMemcpyAsync(h->ooc_buf[bi], h->ooc_host + (size_t)i0 * ld, bytes, cudaMemcpyHostToDevice,
+                               h->ooc_h2d));
+            CK(cudaEventRecord(h->ooc_ev_h2d[bi], h->ooc_h2d));
+            CK(cudaStreamWaitEvent(h->stream, h->ooc_ev_h2d[bi], 0));
+            h->ooc_bytes += (double)bytes;
+        }
+        launch_ooc_update(h->ds, h->geo, h->ooc_buf[bi], i0, i1, h->stream);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(h->ooc_ev_upd[bi], h->stream));
+        h->launches += 1;
+        if (t < W - 1) {
+            CK(cudaStreamWaitEvent(h->ooc_d2h, h->ooc_ev_upd[bi], 0));
+            CK(cudaMemcpyAsync(h->ooc_host + (size_t)i0 * ld, h->ooc_buf[bi], bytes, cudaMemcpyDeviceToHost,
+                               h->ooc_d2h));
+            CK(cudaEventRecord(h->ooc_ev_d2h[bi], h->ooc_d2h));
+            h->ooc_bytes += (double)bytes;
+        } else {
+            h->ooc_res = w;
+            h->ooc_res_buf = bi;
+        }
+        prev = bi;
+    }
+    // the host copy is current before row r is read from it
+    CK(cudaStreamWaitEvent(h->stream, h->ooc_ev_d2h[0], 0));
+    CK(cudaStreamWaitEvent(h->stream, h->ooc_ev_d2h[1], 0));
+    launch_ooc_chuzr(h->ds, h->stream);
+    const int r0 = h->ooc_res * R, r1 = std::min(m, r0 + R);
+    launch_ooc_fetch_row(h->ds, h->ooc_host, h->ooc_buf[h->ooc_res_buf], r0, r1, h->ooc_prow, h->stream);
+    CK(cudaGetLastError());
+    h->launches += 2;
+    return LP_OK;
+}
+
+// One iteration of Case 2: the pending pivot's bookkeeping (row r from the
+// device copy), PRICE + CHUZC, and a pass over the blocks.  The first
+// iteration after a reset or a reinversion only prices and passes.
+int ooc_iteration(lp_handle* h) {
+    if (h->ooc_primed) {
+        DevState so = h->ds;
+        so.prow = h->ooc_prow;
+        launch_pivot(so, h->geo, h->stream, false);
+        h->launches += 1;
+    }
+    launch_price(h->ds, h->geo, h->stream, false);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    TRY(ooc_pass(h));
+    h->ooc_primed = true;
+    return LP_OK;
+}
+
 // Largest admissible refine_tol, ||I - B11 Y0||_inf of the stored inverse that
 // a reinversion refines (one Newton-Schulz step then leaves a residual below
 // 2^-52, at the rounding level); above it the basis is eliminated afresh.
@@ -221,6 +331,8 @@ constexpr double kRefineTolMax = 1.0 / 67108864.0;  // 2^-26
 // dense B^-1 is not written).
 int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = false) {
     const bool compact = to_struct && h->structured;
+    TRY(ooc_flush(h));  // the rebuild reads and writes B^-1 in host memory
+    h->ooc_primed = false;
     CK(cudaEventRecord(h->er0, h->stream));
     launch_reinv_classify(h->ds, h->stream);
     TRY(read_ctrl(h));
@@ -278,6 +390,8 @@ int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = fal
 }
 
 int reset_state(lp_handle* h) {
+    h->ooc_res = -1;  // B^-1 = I is written to host memory; no block is on the device
+    h->ooc_primed = false;
     launch_init_slack(h->ds, h->stream);
     CK(cudaGetLastError());
     h->primed = false;
@@ -301,7 +415,7 @@ int binv_rows(const lp_handle* h, int p0, int np, double* out) {
     const int m = h->m;
     if (!(h->structured && h->s_ready)) {
         CK(cudaMemcpy2D(out, sizeof(double) * m, h->ds.binv + (size_t)p0 * h->ld, sizeof(double) * h->ld,
-                        sizeof(double) * m, np, cudaMemcpyDeviceToHost));
+                        sizeof(double) * m, np, h->ooc ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost));
         return LP_OK;
     }
     Ctrl c;
@@ -554,7 +668,31 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &A_cm, (size_t)n * ld));
     TRY(dalloc(h, &cc, (size_t)n));
     TRY(dalloc(h, &bb, (size_t)ld));
-    TRY(dalloc(h, &binv, (size_t)m * ld));
+    // Case 2 of Section 3: the explicit inverse does not fit the memory granted to it
+    const double tab_bytes = 8.0 * (double)m * (double)ld;
+    if (h->opt.tableau_budget_mb > 0.0 && tab_bytes > 1e6 * h->opt.tableau_budget_mb) {
+        const double row_bytes = 8.0 * (double)ld;
+        h->ooc = true;
+        h->ooc_rows = (int)std::max(1.0, std::floor(0.5e6 * h->opt.tableau_budget_mb / row_bytes));
+        h->ooc_rows = std::min(h->ooc_rows, m);
+        h->ooc_w = (m + h->ooc_rows - 1) / h->ooc_rows;
+        if (P.lex) return LP_ERR_INVALID_ARG;  // its tie-break reads rows of B^-1 that are not on the device
+        CK(cudaMallocHost(&h->ooc_host, sizeof(double) * (size_t)m * ld));
+        binv = h->ooc_host;  // device-accessible (unified addressing): init and reinversion write it directly
+        TRY(dalloc(h, &h->ooc_buf[0], (size_t)h->ooc_rows * ld));
+        TRY(dalloc(h, &h->ooc_buf[1], (size_t)h->ooc_rows * ld));
+        TRY(dalloc(h, &h->ooc_prow, (size_t)ld));
+        CK(cudaStreamCreateWithFlags(&h->ooc_h2d, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->ooc_d2h, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            CK(cudaEventCreateWithFlags(&h->ooc_ev_h2d[b], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->ooc_ev_upd[b], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->ooc_ev_d2h[b], cudaEventDisableTiming));
+        }
+        if (configure_ooc_kernels(ld) != 0) return LP_ERR_CUDA;
+    } else {
+        TRY(dalloc(h, &binv, (size_t)m * ld));
+    }
     TRY(dalloc(h, &bbar, (size_t)m));
     TRY(dalloc(h, &y, (size_t)ld));
     TRY(dalloc(h, &rho, (size_t)ld));
@@ -654,7 +792,9 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
                             struct_engine_fits(h->m, h->ld, h->geo.sms);
         const bool occ_s = fits_s && occupancy_iterate_s(h->ld) >= 1;
         // the first condition that keeps the asked engine from running
-        if (h->opt.engine != LP_ENGINE_GRAPH) {
+        if (h->ooc) {
+            h->engine_reason = LP_ENGINE_REASON_OUT_OF_CORE;
+        } else if (h->opt.engine != LP_ENGINE_GRAPH) {
             if (h->opt.price_mode == 1) h->engine_reason = LP_ENGINE_REASON_PRICE_MODE;
             else if (P.lex) h->engine_reason = LP_ENGINE_REASON_LEXICOGRAPHIC;
             else if (!coop || h->geo.sms > 1024) h->engine_reason = LP_ENGINE_REASON_NO_COOPERATIVE;
@@ -662,7 +802,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
             else if (want_s && !fits_s) h->engine_reason = LP_ENGINE_REASON_SIZE;
             else if (want_s && !occ_s) h->engine_reason = LP_ENGINE_REASON_OCCUPANCY;
         }
-        if (occ_s) {
+        if (occ_s && !h->ooc) {
             const int m = h->m, n = h->n, ld = h->ld;
             TRY(dalloc(h, &s.A_p, (size_t)n * ld));
             TRY(dalloc(h, &s.A_p32, (size_t)n * ld));
@@ -685,11 +825,11 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
             h->structured = true;
             h->persist_blocks = h->geo.sms;
             h->s_force = true;
-        } else if (h->opt.engine != LP_ENGINE_GRAPH && h->opt.price_mode != 1 && !P.lex && coop &&
+        } else if (!h->ooc && h->opt.engine != LP_ENGINE_GRAPH && h->opt.price_mode != 1 && !P.lex && coop &&
                    h->geo.sms <= 1024 && occupancy_iterate(h->ld) >= 1) {
             h->persist = true;
             h->persist_blocks = h->geo.sms;  // the partial arrays hold at least sms entries
-        } else if (h->opt.engine != LP_ENGINE_GRAPH && h->engine_reason == LP_ENGINE_REASON_NONE) {
+        } else if (!h->ooc && h->opt.engine != LP_ENGINE_GRAPH && h->engine_reason == LP_ENGINE_REASON_NONE) {
             h->engine_reason = LP_ENGINE_REASON_OCCUPANCY;
         }
         if ((h->persist || h->structured) && h->opt.kernel_timing > 0) {
@@ -796,6 +936,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
     h->reinv_refined = 0;
     h->reinv_tc = 0;
     h->refine_res_max = 0.0;
+    h->ooc_bytes = 0.0;
     h->price_s = h->update_s = h->price_b = h->update_b = 0.0;
     h->price_n = h->update_n = 0;
     h->chain_s = h->chain_b = 0.0;
@@ -869,6 +1010,11 @@ int lp_solve(lp_handle* h, lp_result* out) {
             continue;
         }
         if (C.status != kRunning) break;
+        if (h->ooc) {
+            TRY(ooc_iteration(h));
+            TRY(read_ctrl(h));
+            continue;
+        }
         if (h->structured) {
             if (!h->s_ready) {
                 // enter the structured form from the dense state (rebuilt B^-1 or slack basis)
@@ -968,6 +1114,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
         CK(cudaGetLastError());
         h->launches += 1;
     }
+    TRY(ooc_flush(h));  // B^-1 whole in host memory for lp_get_state and the next solve
     CK(cudaEventRecord(h->ev1, h->stream));
     CK(cudaEventSynchronize(h->ev1));
     float ms = 0.f;
@@ -1009,6 +1156,9 @@ int lp_solve(lp_handle* h, lp_result* out) {
         out->phase1_exchanged = phase1_exch;
         out->refined_reinversions = h->reinv_refined;
         out->tc_reinversions = h->reinv_tc;
+        out->ooc_blocks = h->ooc ? h->ooc_w : 0;
+        out->ooc_block_rows = h->ooc ? h->ooc_rows : 0;
+        out->ooc_bytes = h->ooc_bytes;
         out->refine_residual_max = h->refine_res_max;
     }
     return LP_OK;

@@ -29,8 +29,10 @@ STATUS_NAMES = {0: "running", 1: "optimal", 2: "unbounded", 3: "iter_limit", 4: 
 LP_TF_DEGENERATE, LP_TF_TABU_PUSH, LP_TF_ASPIRATION, LP_TF_BLAND, LP_TF_TIE_SET = 1, 2, 4, 8, 64
 LP_TF_GUIDED = 128
 LP_ENGINE_DENSE, LP_ENGINE_GRAPH, LP_ENGINE_STRUCTURED = 0, 1, 2
+(LP_ENGINE_REASON_NONE, LP_ENGINE_REASON_PRICE_MODE, LP_ENGINE_REASON_LEXICOGRAPHIC, LP_ENGINE_REASON_NO_COOPERATIVE,
+ LP_ENGINE_REASON_SIZE, LP_ENGINE_REASON_OCCUPANCY, LP_ENGINE_REASON_OUT_OF_CORE) = range(7)
 ENGINE_REASONS = {0: "none", 1: "price_mode", 2: "lexicographic", 3: "no_cooperative", 4: "size",
-                  5: "occupancy"}
+                  5: "occupancy", 6: "out_of_core"}
 LP_ANTICYCLING_TABU, LP_ANTICYCLING_LEXICOGRAPHIC = 0, 1
 
 
@@ -44,6 +46,7 @@ class lp_options(ctypes.Structure):
                 ("reinvert_tc", ctypes.c_int32),
                 ("tol_d", ctypes.c_double), ("tol_piv", ctypes.c_double),
                 ("tol_tie", ctypes.c_double), ("refine_tol", ctypes.c_double),
+                ("tableau_budget_mb", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p)]
 
 
@@ -64,7 +67,9 @@ class lp_result(ctypes.Structure):
                 ("chain_bytes", ctypes.c_double), ("chain_launches", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("phase1_iterations", ctypes.c_int32),
                 ("phase1_exchanged", ctypes.c_int32), ("refined_reinversions", ctypes.c_int32),
-                ("engine_reason", ctypes.c_int32), ("refine_residual_max", ctypes.c_double)]
+                ("engine_reason", ctypes.c_int32), ("refine_residual_max", ctypes.c_double),
+                ("ooc_blocks", ctypes.c_int32), ("ooc_block_rows", ctypes.c_int32),
+                ("ooc_bytes", ctypes.c_double)]
 
 
 class lp_batch_result(ctypes.Structure):
@@ -220,6 +225,9 @@ class Result:
     refine_residual_max: float = 0.0
     engine_reason: int = 0
     tc_reinversions: int = 0
+    ooc_blocks: int = 0
+    ooc_block_rows: int = 0
+    ooc_bytes: float = 0.0
 
     @property
     def status_name(self) -> str:
@@ -282,7 +290,8 @@ class LP:
                       r.full_passes, r.reinvert_gj_seconds, r.reinvert_assemble_seconds,
                       r.chain_seconds, r.chain_bytes, r.chain_launches, r.persistent,
                       r.phase1_iterations, r.phase1_exchanged, r.refined_reinversions,
-                      r.refine_residual_max, r.engine_reason, r.tc_reinversions)
+                      r.refine_residual_max, r.engine_reason, r.tc_reinversions, r.ooc_blocks,
+                      r.ooc_block_rows, r.ooc_bytes)
 
     def reset(self):
         _check(_lib.lp_reset(self._h), "lp_reset")
