@@ -225,7 +225,11 @@ void lp_default_options(lp_options* opt);
  *                   slack s with the largest |B^-1[p][s]| if it is still basic
  *                   at zero in row p) is the Phase II start.
  *  inputs_on_device 0: A, b, c are host pointers; 1: device pointers, which
- *                   must stay valid until lp_create returns
+ *                   must stay valid until lp_create returns.  Device inputs
+ *                   are read on the handle's stream (lp_options.cuda_stream,
+ *                   else a non-blocking stream of the handle's own), which
+ *                   does not wait for other streams: the caller finishes
+ *                   (or orders before that stream) the work that writes them
  *  opt              options, or NULL for the defaults
  * Errors: LP_ERR_INVALID_ARG (sizes, NULL, NaN/Inf), LP_ERR_OOM,
  * LP_ERR_CUDA.  The handle is on the current CUDA device.
@@ -249,6 +253,7 @@ int lp_set_basis(lp_handle* h, const int32_t* basis_m);
  * same m and n (same conventions as lp_create) and returns to the slack basis,
  * reusing every device buffer and the captured graph.  For families of LPs
  * (for example the perturbed instances a learned warm start is trained on).
+ * Device inputs are read on the handle's stream, as for lp_create.
  */
 int lp_update_problem(lp_handle* h, const double* A_rowmajor, const double* b, const double* c,
                       int32_t inputs_on_device);
@@ -496,6 +501,22 @@ int lp_family_perturb(int32_t m, int32_t n, const double* A0, const double* b0, 
 int lp_family_features(int32_t m, int32_t n, const double* A0, const double* b0, const double* c0,
                        const double* A, const double* b, const double* c, double sigma,
                        float* features, void* cuda_stream);
+
+/*
+ * lp_family_propose -- the network's proposed basis from its n+m scores
+ * (DEVICE float32 `scores`, higher = more likely basic; structurals first,
+ * then slacks).  The structurals with score > 0, in the order (score
+ * descending, index ascending), at most m of them, are J_0 .. J_{k-1}; the k
+ * slack rows of lowest score (ties: lower row) give up their positions, the
+ * t-th of them to J_t; every other row keeps its slack.  Outputs (DEVICE
+ * int32): basis (m entries, a valid proposal for lp_set_basis_repair) and
+ * work (m + 1 entries: J in its first min(k, m) entries, the number of
+ * structurals with score > 0, before the cap at m, in work[m]).  Nothing is
+ * allocated; enqueued on cuda_stream.  Errors: LP_ERR_INVALID_ARG (sizes,
+ * NULL), LP_ERR_CUDA.
+ */
+int lp_family_propose(int32_t m, int32_t n, const float* scores, int32_t* basis, int32_t* work,
+                      void* cuda_stream);
 
 /* lp_destroy -- frees the handle and its device memory (NULL is ignored). */
 void lp_destroy(lp_handle* h);

@@ -100,9 +100,81 @@ __global__ void k_feat_cols(int m, int n, const double* __restrict__ A0, const d
     if (j < m) out[j] = b0[j] != 0.0 ? (float)((b[j] / b0[j] - 1.0) / sigma) : 0.f;
 }
 
+// ---- the proposed basis from the network's scores ------------------------------
+// Structural j is proposed when its score z_j > 0; the proposed structurals in
+// the order (z_j descending, j ascending), at most m of them, are J_0, J_1, ...
+// Slack rows in the order (z_{n+i} ascending, i ascending) give up their
+// positions: the t-th of them holds J_t.  Orders are computed as ranks (the
+// number of elements that come first), which needs no sort and is exact for
+// ties.  Scores are read through shared-memory tiles.
+
+constexpr int kTile = 1024;
+
+// rank of every proposed structural; J[rank] = j for rank < m; work[m] counts them
+__global__ void __launch_bounds__(256) k_rank_structurals(int m, int n, const float* __restrict__ z,
+                                                          int32_t* __restrict__ work) {
+    __shared__ float zt[kTile];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const float zj = j < n ? z[j] : 0.f;
+    const bool cand = j < n && zj > 0.f;
+    int rank = 0;
+    for (int t0 = 0; t0 < n; t0 += kTile) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < kTile && t0 + k < n; k += blockDim.x) zt[k] = z[t0 + k];
+        __syncthreads();
+        const int tn = n - t0 < kTile ? n - t0 : kTile;
+        if (cand)
+            for (int k = 0; k < tn; ++k) {
+                const float v = zt[k];
+                rank += (v > zj || (v == zj && t0 + k < j)) ? 1 : 0;  // v > zj > 0: proposed too
+            }
+    }
+    if (cand) {
+        if (rank < m) work[rank] = j;
+        atomicAdd(work + m, 1);
+    }
+}
+
+// basis[i]: J_t when slack row i is the t-th to give up its position (t < k =
+// min(m, count)), else the slack n + i
+__global__ void __launch_bounds__(256) k_place_structurals(int m, int n, const float* __restrict__ z,
+                                                           const int32_t* __restrict__ work,
+                                                           int32_t* __restrict__ basis) {
+    __shared__ float zt[kTile];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float zi = i < m ? z[n + i] : 0.f;
+    int rank = 0;
+    for (int t0 = 0; t0 < m; t0 += kTile) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < kTile && t0 + k < m; k += blockDim.x) zt[k] = z[n + t0 + k];
+        __syncthreads();
+        const int tn = m - t0 < kTile ? m - t0 : kTile;
+        if (i < m)
+            for (int k = 0; k < tn; ++k) {
+                const float v = zt[k];
+                rank += (v < zi || (v == zi && t0 + k < i)) ? 1 : 0;
+            }
+    }
+    if (i < m) {
+        const int cnt = work[m];
+        const int kk = cnt < m ? cnt : m;
+        basis[i] = rank < kk ? work[rank] : n + i;
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+int lp_family_propose(int32_t m, int32_t n, const float* scores, int32_t* basis, int32_t* work,
+                      void* cuda_stream) {
+    if (m < 1 || n < 1 || !scores || !basis || !work) return LP_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaMemsetAsync(work + m, 0, sizeof(int32_t), st) != cudaSuccess) return LP_ERR_CUDA;
+    k_rank_structurals<<<(n + 255) / 256, 256, 0, st>>>(m, n, scores, work);
+    k_place_structurals<<<(m + 255) / 256, 256, 0, st>>>(m, n, scores, work, basis);
+    return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
 
 int lp_family_perturb(int32_t m, int32_t n, const double* A0, const double* b0, const double* c0, uint64_t key,
                       double sigma, double* A, double* b, double* c, void* cuda_stream) {

@@ -115,16 +115,25 @@ namespace {
 // Warm-start repair (one block): if some basic value is below -tol, pick the
 // most negative position p and, among nonbasic slacks s, the most negative
 // B^-1[p][s]; stage the pivot (q = n+s, r = p) for k_pivot / k_update.
-// Ctrl::repair becomes 2 when no value is negative, 3 when no slack can fix p.
-__global__ void __launch_bounds__(1024) k_repair_pick(DevState s, double tol) {
+// Ctrl::repair becomes 2 when no value is negative, 3 when no slack can fix p,
+// 4 when p exists but the iteration count has reached limit_it.  Nothing is
+// staged (q = -1, so k_pivot and k_update do nothing) when the repair has
+// ended or the solve is not running (a reinversion is due): repair steps can
+// be enqueued in batches and the host reads the outcome once per batch.
+__global__ void __launch_bounds__(1024) k_repair_pick(DevState s, double tol, int limit_it) {
     Ctrl* C = s.ctrl;
     const Params& P = s.p;
     __shared__ double sv[32];
     __shared__ int si[32];
     __shared__ int p_sh;
+    __shared__ int go_sh;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) C->repair = 1;
+    if (threadIdx.x == 0) {
+        go_sh = C->repair == 1 && C->status == kRunning;
+        C->q = -1;
+    }
     __syncthreads();
+    if (!go_sh) return;
     // most negative basic value (ties: smallest position)
     double v = 0.0;
     int pi = -1;
@@ -144,8 +153,9 @@ __global__ void __launch_bounds__(1024) k_repair_pick(DevState s, double tol) {
         int bp = -1;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
             if (si[i] >= 0 && (bp < 0 || sv[i] < bvv || (sv[i] == bvv && si[i] < bp))) { bvv = sv[i]; bp = si[i]; }
-        p_sh = bp;
         if (bp < 0) C->repair = 2;
+        else if (C->it >= limit_it) { C->repair = 4; bp = -1; }
+        p_sh = bp;
     }
     __syncthreads();
     const int p = p_sh;
@@ -198,12 +208,23 @@ __global__ void __launch_bounds__(1024) k_repair_pick(DevState s, double tol) {
 // after the repair pivot's bookkeeping: no FTRAN of a next column
 __global__ void k_repair_clear(DevState s) { s.ctrl->q = -1; }
 
+__global__ void k_repair_begin(DevState s) { s.ctrl->repair = 1; }
+
 }  // namespace
 
-void launch_repair_pick(const DevState& s, double tol, cudaStream_t st) {
-    k_repair_pick<<<1, 1024, 0, st>>>(s, tol);
-}
+void launch_repair_begin(const DevState& s, cudaStream_t st) { k_repair_begin<<<1, 1, 0, st>>>(s); }
 
-void launch_repair_clear(const DevState& s, cudaStream_t st) { k_repair_clear<<<1, 1, 0, st>>>(s); }
+// `steps` repair pivots (pick, the pivot's bookkeeping, no next column, the
+// B^-1 update) enqueued back to back; the steps after the repair ends, a
+// reinversion falls due or the iteration count reaches limit_it do nothing.
+void launch_repair_steps(const DevState& s, const Geometry& g, double tol, int steps, int limit_it,
+                         cudaStream_t st) {
+    for (int t = 0; t < steps; ++t) {
+        k_repair_pick<<<1, 1024, 0, st>>>(s, tol, limit_it);
+        launch_pivot(s, g, st);
+        k_repair_clear<<<1, 1, 0, st>>>(s);
+        launch_update(s, g, st);
+    }
+}
 
 }  // namespace lpgb

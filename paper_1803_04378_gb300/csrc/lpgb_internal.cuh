@@ -80,7 +80,7 @@ struct Ctrl {
     int32_t ticket_pivot;
     int32_t nsb;           // structural variables in the basis
     int32_t k_live;        // slack-structured engine: rows whose slack is nonbasic (live slots)
-    int32_t repair;        // warm-start repair: 1 pivot staged, 2 feasible, 3 cannot repair
+    int32_t repair;        // warm-start repair: 1 running, 2 feasible, 3 cannot repair, 4 limit reached
     int32_t need_full;     // price_mode 1: the screen found no improving candidate
     int32_t n_full;        // price_mode 1: full FP64 PRICE passes
     int32_t n_lp;          // price_mode 1: screen + re-price passes
@@ -327,7 +327,8 @@ void launch_build_aux(const double* A_cm, int ld, int m, int n, const double* b,
 void launch_validate(const double* A_cm, const double* b, const double* c, int m, int n, int ld,
                      int32_t* flag, cudaStream_t st);
 void launch_load_basis(const DevState& s, cudaStream_t st);
-void launch_repair_pick(const DevState& s, double tol, cudaStream_t st);
-void launch_repair_clear(const DevState& s, cudaStream_t st);
+void launch_repair_begin(const DevState& s, cudaStream_t st);
+void launch_repair_steps(const DevState& s, const Geometry& g, double tol, int steps, int limit_it,
+                         cudaStream_t st);
 
 }  // namespace lpgb

@@ -322,6 +322,7 @@ int ooc_iteration(lp_handle* h) {
 // a reinversion refines (one Newton-Schulz step then leaves a residual below
 // 2^-52, at the rounding level); above it the basis is eliminated afresh.
 constexpr double kRefineTolMax = 1.0 / 67108864.0;  // 2^-26
+constexpr int kRepairBatch = 16;  // warm-start repair pivots enqueued per read of the outcome
 
 // Rebuild B^-1, bbar, y, z from the current basis.  `refine`: the stored
 // inverse is that of the current basis (a periodic reinversion, the last
@@ -979,20 +980,27 @@ int lp_solve(lp_handle* h, lp_result* out) {
             int rc = reinvert(h, 0, false);
             bool ok = rc == LP_OK;
             if (rc != LP_OK && rc != LP_ERR_SINGULAR) return rc;
-            while (ok) {
-                launch_repair_pick(h->ds, 1e-9 * h->p.b_scale, h->stream);
+            if (ok) {
+                // repair pivots in batches, the outcome read once per batch
                 TRY(read_ctrl(h));
-                if (h->h_ctrl->repair == 2) break;                  // feasible
-                if (h->h_ctrl->repair == 3 || warm_repairs >= h->warm_repair_max) { ok = false; break; }
-                launch_pivot(h->ds, h->geo, h->stream);
-                launch_repair_clear(h->ds, h->stream);
-                launch_update(h->ds, h->geo, h->stream);
-                CK(cudaGetLastError());
-                h->launches += 4;
-                warm_repairs++;
-                TRY(read_ctrl(h));
-                if (h->h_ctrl->status == kReinvert) TRY(reinvert(h, 0, true));
-                else if (h->h_ctrl->status != kRunning) break;
+                const int it0 = h->h_ctrl->it;
+                const int limit = it0 + h->warm_repair_max;
+                launch_repair_begin(h->ds, h->stream);
+                h->launches += 1;
+                for (;;) {
+                    const int steps = std::min(kRepairBatch, std::max(1, limit - h->h_ctrl->it + 1));
+                    launch_repair_steps(h->ds, h->geo, 1e-9 * h->p.b_scale, steps, limit, h->stream);
+                    CK(cudaGetLastError());
+                    h->launches += 4 * steps;
+                    TRY(read_ctrl(h));
+                    const Ctrl& C = *h->h_ctrl;
+                    if (C.err != kErrNone) return device_err_code(C.err);
+                    if (C.repair == 2) break;                       // feasible
+                    if (C.repair >= 3) { ok = false; break; }       // no slack can repair, or the cap
+                    if (C.status == kReinvert) TRY(reinvert(h, 0, true));
+                    else if (C.status != kRunning) break;
+                }
+                warm_repairs = h->h_ctrl->it - it0;
             }
             if (!ok) {
                 warm_fallback = 1;

@@ -144,6 +144,8 @@ def _load():
     lib.lp_family_perturb.restype = ctypes.c_int
     lib.lp_family_features.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, ctypes.c_double, vp, vp]
     lib.lp_family_features.restype = ctypes.c_int
+    lib.lp_family_propose.argtypes = [i32, i32, vp, vp, vp, vp]
+    lib.lp_family_propose.restype = ctypes.c_int
     lib.lp_batch_create.argtypes = [P(vp), i32, vp, vp, vp, vp, vp, i32, P(lp_options)]
     lib.lp_batch_create.restype = ctypes.c_int
     lib.lp_batch_solve.argtypes = [vp, P(lp_batch_result)]
@@ -179,6 +181,14 @@ def default_options(**overrides) -> lp_options:
     for k, v in overrides.items():
         setattr(o, k, v)
     return o
+
+
+def _device_inputs_ready():
+    """The library reads device inputs on the handle's own stream, which does
+    not wait for work that torch (or another stream) still has queued on the
+    tensors: finish every stream of the device before passing their pointers."""
+    import torch
+    torch.cuda.synchronize()
 
 
 def _ptr(a):
@@ -250,6 +260,7 @@ class LP:
             b = b.to(torch.float64).contiguous()
             c = c.to(torch.float64).contiguous()
             m, n = A.shape
+            _device_inputs_ready()
         else:
             A = np.ascontiguousarray(A, dtype=np.float64)
             b = np.ascontiguousarray(b, dtype=np.float64)
@@ -298,7 +309,9 @@ class LP:
 
     def update_problem(self, A, b, c):
         on_dev = hasattr(A, "is_cuda") and A.is_cuda
-        if not on_dev:
+        if on_dev:
+            _device_inputs_ready()
+        else:
             A = np.ascontiguousarray(A, dtype=np.float64)
             b = np.ascontiguousarray(b, dtype=np.float64)
             c = np.ascontiguousarray(c, dtype=np.float64)
@@ -550,3 +563,10 @@ def family_features(A0, b0, c0, A, b, c, sigma: float, out, stream=None):
     st = None if stream is None else ctypes.c_void_p(stream)
     _check(_lib.lp_family_features(int(m), int(n), _ptr(A0), _ptr(b0), _ptr(c0), _ptr(A), _ptr(b), _ptr(c),
                                    float(sigma), _ptr(out), st), "lp_family_features")
+
+
+def family_propose(scores, m: int, n: int, basis, work, stream=None):
+    """lp_family_propose: scores (torch CUDA float32, n+m) -> basis (int32, m)
+    and work (int32, m+1: the proposed structurals, their count in work[m])."""
+    st = None if stream is None else ctypes.c_void_p(stream)
+    _check(_lib.lp_family_propose(int(m), int(n), _ptr(scores), _ptr(basis), _ptr(work), st), "lp_family_propose")

@@ -5,17 +5,15 @@ by an independent N(1, sigma^2) draw.  A small network (lp_mlp_*: 2(m+n)
 features -> 512 -> 512 -> n+m logits) learns, from (instance -> optimal basis)
 pairs that the solver itself produces, which variables are basic at the
 optimum.  A new instance starts from the basis the network proposes
-(lp_set_basis_repair: negative basic values are repaired by dual-style slack
-pivots, an unusable proposal falls back to the slack basis), and the predicted
-columns are priced first (lp_set_priority, Dantzig's rule restricted to them
-while any of them improves).  Every pivot is an ordinary simplex pivot and the
-plain method certifies the optimum.
+(lp_family_propose on the device; lp_set_basis_repair: negative basic values
+are repaired by slack pivots, and a proposal that needs more than a capped
+number of them falls back to the slack basis, which bounds what a poor
+proposal costs).  The plain method then runs to its certified optimum; the
+guided variants also price the predicted columns first (lp_set_priority).
 
 Everything here is orchestration: instances are drawn and featurised on the
-GPU (lp_family_*), solved by the CUDA solver, and the network is trained by
-the library's own kernels.  Training labels come from solves started from
-the base LP's optimal basis, which reach an optimum in a fraction of the cold
-pivots.
+GPU (lp_family_*), solved by the CUDA solver, and the network is trained and
+served by the library's own kernels.
 """
 from __future__ import annotations
 
@@ -64,20 +62,28 @@ class Family:
     def features(self, out):
         lpgb.family_features(self.A0, self.b0, self.c0, self.A, self.b, self.c, self.sigma, out, self.stream)
 
-    def solve(self, start=None, mode: str = "repair"):
+    def solve(self, start=None, mode: str = "repair", max_repairs: int | None = None):
         """Solve the current instance.  start = (basis, structural set):
-        mode "repair" starts from `basis` (repaired if infeasible) with the
-        guided rule on the structural set; mode "guided" starts from the slack
-        basis and only applies the guided rule.  None solves cold."""
+        mode "repair" starts from `basis` (repaired by at most max_repairs
+        slack pivots, default m, else the slack basis) with the plain rule;
+        "repair_guided" adds the guided rule on the structural set; "guided"
+        starts from the slack basis with the guided rule only.  None solves
+        cold."""
         self.lp.update_problem(self.A, self.b, self.c)
         if start is None:
             self.lp.set_priority([])
         else:
             basis, structurals = start
-            self.lp.set_priority(structurals)
+            cap = self.m if max_repairs is None else int(max_repairs)
             if mode == "repair":
-                self.lp.set_basis_repair(basis, self.m)
-            elif mode != "guided":
+                self.lp.set_priority([])
+                self.lp.set_basis_repair(basis, cap)
+            elif mode == "repair_guided":
+                self.lp.set_priority(structurals)
+                self.lp.set_basis_repair(basis, cap)
+            elif mode == "guided":
+                self.lp.set_priority(structurals)
+            else:
                 raise ValueError(mode)
         res = self.lp.solve()
         return res, self.lp.basis()
@@ -91,20 +97,6 @@ def base_hint(family: Family):
     family.lp.solve()
     basis = family.lp.basis()
     return basis, [int(v) for v in basis if v < family.n]
-
-
-def basis_from_scores(z, m: int, n: int):
-    """Proposed basis from per-variable scores z (n+m; higher = more likely
-    basic): the structurals with z > 0, best first, placed at the positions of
-    the rows whose slacks score lowest; every other row keeps its slack."""
-    zs = np.asarray(z[:n])
-    order = np.argsort(-zs, kind="stable")
-    J = [int(j) for j in order if zs[j] > 0.0][:m]
-    rows = np.argsort(np.asarray(z[n:n + m]), kind="stable")[:len(J)]
-    basis = np.arange(n, n + m, dtype=np.int32)
-    for j, r in zip(J, rows):
-        basis[r] = j
-    return basis, J
 
 
 def generate_labels(family: Family, seeds, hint=None, log_every: int = 0):
@@ -166,75 +158,99 @@ def train(X, Y, hidden: int = 512, epochs: int = 10, batch: int = 256, lr: float
     return net, losses
 
 
-def predicted_start(net, features, m: int, n: int):
-    """The network's proposal for one instance: (basis, structural set)."""
-    import torch
-    logits = torch.empty((1, net.out_dim), dtype=torch.float32, device="cuda")
-    net.forward(features.reshape(1, -1).contiguous(), logits)
-    torch.cuda.synchronize()
-    return basis_from_scores(logits[0].cpu().numpy(), m, n)
+class Proposer:
+    """Inference on the device: features -> logits (lp_mlp_forward) -> proposed
+    basis (lp_family_propose); only the m basis entries and the proposed
+    structurals come back to the host."""
+
+    def __init__(self, net, m: int, n: int):
+        import torch
+        self.net, self.m, self.n = net, m, n
+        self.logits = torch.empty((1, net.out_dim), dtype=torch.float32, device="cuda")
+        self.basis = torch.empty(m, dtype=torch.int32, device="cuda")
+        self.work = torch.empty(m + 1, dtype=torch.int32, device="cuda")
+
+    def __call__(self, features):
+        self.net.forward(features.reshape(1, -1).contiguous(), self.logits)
+        lpgb.family_propose(self.logits, self.m, self.n, self.basis, self.work)
+        basis = self.basis.cpu().numpy()
+        work = self.work.cpu().numpy()
+        k = min(int(work[self.m]), self.m)
+        return basis, [int(j) for j in work[:k]]
 
 
-def evaluate(family: Family, net, instances, guided: bool = False):
-    """Cold vs warm solves of host instances: pivots, device seconds, objectives
-    (guided: also the slack-basis start with the guided rule only)."""
+MODES = ("repair", "repair_guided", "guided")
+
+
+def evaluate(family: Family, net, instances, modes=("repair",), max_repairs: int | None = None):
+    """Cold vs warm solves of held-out instances (instance seeds drawn on the
+    device, or host (A, b, c) triples): pivots, device seconds (inference
+    included for the warm starts), objectives, and how far the proposal is
+    from the cold optimum's structural set (false positives / negatives)."""
     import torch
     feat = torch.empty(family.n_features, dtype=torch.float32, device="cuda")
+    prop = Proposer(net, family.m, family.n)
     rows = []
-    for (A, b, c) in instances:
-        family.load(A, b, c)
-        cold, _ = family.solve(None)
+    for inst in instances:
+        if isinstance(inst, (int, np.integer)):
+            family.draw(int(inst))
+        else:
+            family.load(*inst)
+        cold, basis_cold = family.solve(None)
         z_cold = family.lp.solution()[2]
+        opt = {int(v) for v in basis_cold if v < family.n}
         family.features(feat)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        start = predicted_start(net, feat, family.m, family.n)
+        start = prop(feat)
         t_pred = time.perf_counter() - t0
-        warm, _ = family.solve(start)
-        z_warm = family.lp.solution()[2]
-        row = dict(cold_pivots=cold.iterations, warm_pivots=warm.iterations,
-                   cold_s=cold.seconds, warm_s=warm.seconds + t_pred, predict_s=t_pred,
-                   z_cold=z_cold, z_warm=z_warm, predicted=len(start[1]),
-                   repairs=warm.warm_repairs, fallback=warm.warm_fallback,
-                   status=(cold.status, warm.status))
-        if guided:
-            gd, _ = family.solve(start, mode="guided")
-            row.update(guided_pivots=gd.iterations, guided_s=gd.seconds + t_pred,
-                       z_guided=family.lp.solution()[2], guided_status=gd.status)
+        J = set(start[1])
+        row = dict(cold_pivots=cold.iterations, cold_s=cold.seconds, z_cold=z_cold, cold_status=cold.status,
+                   cold_reinvert_s=cold.reinvert_seconds, cold_chain_s=cold.chain_seconds,
+                   predict_s=t_pred, predicted=len(J), optimal_structurals=len(opt),
+                   false_pos=len(J - opt), false_neg=len(opt - J))
+        for mode in modes:
+            res, _ = family.solve(start, mode=mode, max_repairs=max_repairs)
+            row[mode] = dict(pivots=res.iterations, s=res.seconds + t_pred, z=family.lp.solution()[2],
+                             status=res.status, repairs=res.warm_repairs, fallback=res.warm_fallback,
+                             reinvert_s=res.reinvert_seconds, chain_s=res.chain_seconds)
         rows.append(row)
     return rows
 
 
-def summarize(rows):
+def summarize(rows, modes=("repair",)):
+    """Per mode: mean pivots and time-to-optimum against cold, the speedup
+    (sum of cold over sum of warm device seconds), fallbacks and the largest
+    relative objective gap to the cold solve."""
     cp = np.array([r["cold_pivots"] for r in rows], float)
-    wp = np.array([r["warm_pivots"] for r in rows], float)
     cs = np.array([r["cold_s"] for r in rows])
-    wsec = np.array([r["warm_s"] for r in rows])
     zc = np.array([r["z_cold"] for r in rows])
-    zw = np.array([r["z_warm"] for r in rows])
-    fb = np.array([r.get("fallback", 0) for r in rows])
-    rp = np.array([r.get("repairs", 0) for r in rows])
-    out = dict(instances=len(rows), cold_pivots_mean=float(cp.mean()), warm_pivots_mean=float(wp.mean()),
-               fallbacks=int(fb.sum()), repairs_mean=float(rp.mean()),
-               pivot_ratio=float(wp.sum() / cp.sum()), cold_time_to_optimum_s=float(cs.mean()),
-               warm_time_to_optimum_s=float(wsec.mean()), speedup=float(cs.sum() / wsec.sum()),
-               max_rel_objective_gap=float(np.max(np.abs(zw - zc) / np.maximum(1.0, np.abs(zc)))))
-    if rows and "guided_pivots" in rows[0]:
-        gp = np.array([r["guided_pivots"] for r in rows], float)
-        gs = np.array([r["guided_s"] for r in rows])
-        zg = np.array([r["z_guided"] for r in rows])
-        out.update(guided_pivots_mean=float(gp.mean()), guided_pivot_ratio=float(gp.sum() / cp.sum()),
-                   guided_time_to_optimum_s=float(gs.mean()), guided_speedup=float(cs.sum() / gs.sum()),
-                   guided_max_rel_objective_gap=float(np.max(np.abs(zg - zc) / np.maximum(1.0, np.abs(zc)))))
+    out = dict(instances=len(rows), cold_pivots_mean=float(cp.mean()), cold_time_to_optimum_s=float(cs.mean()),
+               predicted_mean=float(np.mean([r["predicted"] for r in rows])),
+               optimal_structurals_mean=float(np.mean([r["optimal_structurals"] for r in rows])),
+               false_pos_mean=float(np.mean([r["false_pos"] for r in rows])),
+               false_neg_mean=float(np.mean([r["false_neg"] for r in rows])),
+               predict_s_mean=float(np.mean([r["predict_s"] for r in rows])))
+    for mode in modes:
+        wp = np.array([r[mode]["pivots"] for r in rows], float)
+        ws = np.array([r[mode]["s"] for r in rows])
+        zw = np.array([r[mode]["z"] for r in rows])
+        out[mode] = dict(pivots_mean=float(wp.mean()), pivot_ratio=float(wp.sum() / cp.sum()),
+                         time_to_optimum_s=float(ws.mean()), speedup=float(cs.sum() / ws.sum()),
+                         faster_fraction=float(np.mean(ws < cs)),
+                         fallbacks=int(sum(r[mode]["fallback"] for r in rows)),
+                         repairs_mean=float(np.mean([r[mode]["repairs"] for r in rows])),
+                         optimal=bool(all(r[mode]["status"] == lpgb.LP_OPTIMAL for r in rows)),
+                         max_rel_objective_gap=float(np.max(np.abs(zw - zc) / np.maximum(1.0, np.abs(zc)))))
     return out
 
 
 def main():
-    """Full experiment: 20000 training pairs, 1000 held-out instances, base
-    as the dense real workload at m=1024, n=2048 (seed 4)."""
+    """The configured experiment: 20000 training pairs, 1000 held-out
+    instances, base as the dense real workload at m=1024, n=2048 (seed 4)."""
     import argparse
     import json
 
-    import torch
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=20000)
     ap.add_argument("--heldout", type=int, default=1000)
@@ -242,11 +258,13 @@ def main():
     ap.add_argument("--m", type=int, default=1024)
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--out", default="")
-    ap.add_argument("--labels", default="hint", choices=["hint", "cold"],
-                    help="label solves start from the base LP's optimal basis (hint) or the slack basis")
-    ap.add_argument("--guided", action="store_true",
-                    help="also evaluate the slack-basis start with the guided rule only")
+    ap.add_argument("--labels", default="cold", choices=["hint", "cold"],
+                    help="label solves start from the slack basis (cold) or the base LP's optimal basis (hint)")
+    ap.add_argument("--modes", default="repair", help="comma-separated subset of " + ",".join(MODES))
+    ap.add_argument("--max-repairs", type=int, default=None,
+                    help="repair pivots before a proposal falls back to the slack basis (default m)")
     args = ap.parse_args()
+    modes = tuple(v for v in args.modes.split(",") if v)
     from . import build
     build.build()
     base = lpgen.dense_real_lp(args.m, args.n, 4)
@@ -258,14 +276,14 @@ def main():
     t0 = time.perf_counter()
     net, losses = train(X, Y, epochs=args.epochs, log=True)
     t_train = time.perf_counter() - t0
-    held = [lpgen.perturbed_lp(base, 10_000_000 + k) for k in range(args.heldout)]
-    rows = evaluate(fam, net, held, guided=args.guided)
-    out = dict(summarize(rows), train_pairs=args.train, label_seconds=t_labels, train_seconds=t_train,
-               label_pivots_mean=float(piv.mean()), losses=losses, m=args.m, n=args.n, labels=args.labels)
+    rows = evaluate(fam, net, range(10_000_000, 10_000_000 + args.heldout), modes, args.max_repairs)
+    out = dict(summarize(rows, modes), train_pairs=args.train, label_seconds=t_labels, train_seconds=t_train,
+               label_pivots_mean=float(piv.mean()), losses=losses, m=args.m, n=args.n, labels=args.labels,
+               max_repairs=args.max_repairs if args.max_repairs is not None else args.m)
     print(json.dumps(out))
     if args.out:
-        json.dump(out, open(args.out, "w"), indent=1)
-    del torch
+        with open(args.out, "w") as f:
+            json.dump(dict(out, rows=rows), f, indent=1)
 
 
 if __name__ == "__main__":

@@ -6,7 +6,7 @@ torch = pytest.importorskip("torch")
 
 
 def test_basis_from_scores_places_structurals_on_low_slack_rows():
-    from paper_1803_04378_gb300.warmstart import basis_from_scores
+    from proposal_ref import basis_from_scores
     m, n = 5, 4
     # structural scores: 2 and 0 positive (2 best); slack scores: rows 3 and 1 lowest
     z = np.array([0.5, -1.0, 2.0, -0.2,  0.3, -4.0, 1.0, -5.0, 0.1])
@@ -17,7 +17,7 @@ def test_basis_from_scores_places_structurals_on_low_slack_rows():
 
 
 def test_basis_from_scores_caps_at_m_and_handles_none():
-    from paper_1803_04378_gb300.warmstart import basis_from_scores
+    from proposal_ref import basis_from_scores
     m, n = 2, 5
     basis, J = basis_from_scores(np.ones(n + m), m, n)
     assert len(J) == 2 and sorted(basis.tolist()) == sorted(J)
