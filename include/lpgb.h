@@ -63,8 +63,9 @@ extern "C" {
                                            pivots (the method) */
 #define LP_ANTICYCLING_LEXICOGRAPHIC 1  /* no tabu list and no safety net; the tie set's row whose
                                            row of B^-1 / alpha_i is lexicographically smallest
-                                           leaves (entries within tol_tie relative count as equal);
-                                           runs on the captured-graph engine */
+                                           leaves (entries within tol_tie relative count as equal;
+                                           then the smaller basic index); runs on the
+                                           slack-structured and captured-graph engines */
 
 /* lp_options.engine: how the pivots of price_mode 0 run. */
 #define LP_ENGINE_DENSE 0       /* persistent cooperative kernel on the m x m B^-1, graph_iters
@@ -81,7 +82,8 @@ extern "C" {
 #define LP_ENGINE_REASON_NONE 0            /* the asked engine runs */
 #define LP_ENGINE_REASON_PRICE_MODE 1      /* price_mode 1 runs on captured graphs; price_mode 2
                                               on the dense persistent engine */
-#define LP_ENGINE_REASON_LEXICOGRAPHIC 2   /* the lexicographic rule runs on captured graphs */
+#define LP_ENGINE_REASON_LEXICOGRAPHIC 2   /* LP_ENGINE_DENSE: the lexicographic rule runs on
+                                              captured graphs there */
 #define LP_ENGINE_REASON_NO_COOPERATIVE 3  /* the device refuses cooperative launches, or has
                                               more than 1024 SMs */
 #define LP_ENGINE_REASON_SIZE 4            /* LP_ENGINE_STRUCTURED: more than 256 rows per SM,

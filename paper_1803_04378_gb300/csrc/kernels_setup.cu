@@ -115,25 +115,31 @@ namespace {
 // Warm-start repair (one block): if some basic value is below -tol, pick the
 // most negative position p and, among nonbasic slacks s, the most negative
 // B^-1[p][s]; stage the pivot (q = n+s, r = p) for k_pivot / k_update.
-// Ctrl::repair becomes 2 when no value is negative, 3 when no slack can fix p,
-// 4 when p exists but the iteration count has reached limit_it.  Nothing is
-// staged (q = -1, so k_pivot and k_update do nothing) when the repair has
-// ended or the solve is not running (a reinversion is due): repair steps can
-// be enqueued in batches and the host reads the outcome once per batch.
-__global__ void __launch_bounds__(1024) k_repair_pick(DevState s, double tol, int limit_it) {
+// tol = Ctrl::repair_tol.  Ctrl::repair becomes 2 when no value is negative,
+// 3 when no slack can fix p, 4 when p exists but the iteration count has
+// reached Ctrl::repair_limit.  Nothing is staged (q = -1, so k_pivot and
+// k_update do nothing) when the repair has ended or the solve is not running
+// (a reinversion is due): repair steps run in batches (a captured graph) and
+// the host reads the outcome once per batch.
+__global__ void __launch_bounds__(1024) k_repair_pick(DevState s) {
     Ctrl* C = s.ctrl;
     const Params& P = s.p;
     __shared__ double sv[32];
     __shared__ int si[32];
     __shared__ int p_sh;
-    __shared__ int go_sh;
+    __shared__ int go_sh, limit_sh;
+    __shared__ double tol_sh;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         go_sh = C->repair == 1 && C->status == kRunning;
+        tol_sh = C->repair_tol;
+        limit_sh = C->repair_limit;
         C->q = -1;
     }
     __syncthreads();
     if (!go_sh) return;
+    const double tol = tol_sh;
+    const int limit_it = limit_sh;
     // most negative basic value (ties: smallest position)
     double v = 0.0;
     int pi = -1;
@@ -208,19 +214,25 @@ __global__ void __launch_bounds__(1024) k_repair_pick(DevState s, double tol, in
 // after the repair pivot's bookkeeping: no FTRAN of a next column
 __global__ void k_repair_clear(DevState s) { s.ctrl->q = -1; }
 
-__global__ void k_repair_begin(DevState s) { s.ctrl->repair = 1; }
+__global__ void k_repair_begin(DevState s, double tol, int limit_it) {
+    Ctrl* C = s.ctrl;
+    C->repair = 1;
+    C->repair_tol = tol;
+    C->repair_limit = limit_it;
+}
 
 }  // namespace
 
-void launch_repair_begin(const DevState& s, cudaStream_t st) { k_repair_begin<<<1, 1, 0, st>>>(s); }
+void launch_repair_begin(const DevState& s, double tol, int limit_it, cudaStream_t st) {
+    k_repair_begin<<<1, 1, 0, st>>>(s, tol, limit_it);
+}
 
 // `steps` repair pivots (pick, the pivot's bookkeeping, no next column, the
 // B^-1 update) enqueued back to back; the steps after the repair ends, a
-// reinversion falls due or the iteration count reaches limit_it do nothing.
-void launch_repair_steps(const DevState& s, const Geometry& g, double tol, int steps, int limit_it,
-                         cudaStream_t st) {
+// reinversion falls due or the iteration count reaches the limit do nothing.
+void launch_repair_steps(const DevState& s, const Geometry& g, int steps, cudaStream_t st) {
     for (int t = 0; t < steps; ++t) {
-        k_repair_pick<<<1, 1024, 0, st>>>(s, tol, limit_it);
+        k_repair_pick<<<1, 1024, 0, st>>>(s);
         launch_pivot(s, g, st);
         k_repair_clear<<<1, 1, 0, st>>>(s);
         launch_update(s, g, st);

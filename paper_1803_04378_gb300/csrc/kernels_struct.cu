@@ -260,6 +260,99 @@ __device__ void row_record(const Params& P, int owned, bool bland, const double*
     }
 }
 
+// ---- lexicographic leaving rule on the slack-structured inverse ---------------------
+// Row i of B^-1 at constraint k is bp[i][slot(k)] when row k is live (slot <
+// kn), else the unit column of row k's basic slack: 1 where that slack is the
+// basic variable of position i, 0 elsewhere.  Rows i and r, each divided by its
+// alpha, are compared in constraint order by one warp, 32 constraints per round
+// trip, as x_i a_r against x_r a_i (both alphas are positive): -1 if row i comes
+// first, +1 if row r does, 0 if every entry agrees within tau relative (the
+// result in every lane).
+__device__ int lex_cmp_s(const DevState& s, const double* anxt, const int32_t* rs, int kn, int i, int r,
+                         double tau) {
+    const Params& P = s.p;
+    const int lane = threadIdx.x & 31;
+    const double ai = __ldcg(anxt + i), ar = __ldcg(anxt + r);
+    const int vi = __ldcg(s.row_var + i), vr = __ldcg(s.row_var + r);
+    const double* bi = s.bp + (size_t)i * P.ld;
+    const double* br = s.bp + (size_t)r * P.ld;
+    const double aa = ai * ar;
+    for (int k0 = 0; k0 < P.m; k0 += 32) {
+        const int k = k0 + lane;
+        int code = 0;  // 1 for a difference, sign in bit 2
+        if (k < P.m) {
+            const int slot = __ldcg(rs + k);
+            double x, y;
+            if (slot < kn) {
+                x = __ldcg(bi + slot);
+                y = __ldcg(br + slot);
+            } else {
+                x = vi == P.n + k ? 1.0 : 0.0;
+                y = vr == P.n + k ? 1.0 : 0.0;
+            }
+            if (((__double_as_longlong(x) | __double_as_longlong(y)) << 1) != 0) {
+                const double u = x * ar, v = y * ai;
+                if (fabs(u - v) > tau * fmax(aa, fmax(fabs(u), fabs(v)))) code = 1 | (u < v ? 4 : 0);
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, code != 0);
+        if (bal) {
+            const int cd = __shfl_sync(0xffffffffu, code, __ffs(bal) - 1);
+            return (cd & 4) ? -1 : 1;
+        }
+    }
+    return 0;
+}
+
+// row c leaves before row b: lexicographically smaller, exact ties to the smaller basic index
+__device__ __forceinline__ bool lex_before_s(const DevState& s, const double* anxt, const int32_t* rs, int kn,
+                                             int c, int b, double tau) {
+    const int cmp = lex_cmp_s(s, anxt, rs, kn, c, b, tau);
+    return cmp < 0 || (cmp == 0 && __ldcg(s.row_var + c) < __ldcg(s.row_var + b));
+}
+
+// The tie set's lexicographically smallest row (every thread of the CTA; the
+// result in every thread).  The tie set is that of the ratio test: alpha_i >
+// tol_piv and bbar_i <= thr alpha_i.  Warp w scans its contiguous range of
+// rows in order, keeping the row that leaves first; warp 0 then takes the
+// warps' rows in warp order.  The comparisons follow the same fixed schedule in
+// every CTA, so every CTA picks the same row.
+__device__ int lex_pick_s(const DevState& s, const double* anxt, const int32_t* rs, int kn, double thr) {
+    const Params& P = s.p;
+    __shared__ int wbest[32];
+    __shared__ int pick_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (P.m + nw - 1) / nw;
+    const int r0 = warp * per, r1 = min(P.m, r0 + per);
+    int best = -1;
+    for (int base = r0; base < r1; base += 32) {
+        const int i = base + lane;
+        bool tied = false;
+        if (i < r1) {
+            const double al = __ldcg(anxt + i), bb = __ldcg(s.bbar + i);
+            tied = al > P.tol_piv && bb <= thr * al;
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, tied);
+        while (bal) {
+            const int c = base + __ffs(bal) - 1;
+            bal &= bal - 1;
+            if (best < 0 || lex_before_s(s, anxt, rs, kn, c, best, P.tol_tie)) best = c;
+        }
+    }
+    if (lane == 0) wbest[warp] = best;
+    __syncthreads();
+    if (warp == 0) {
+        int b = -1;
+        for (int w = 0; w < nw; ++w) {
+            const int c = wbest[w];
+            if (c >= 0 && (b < 0 || lex_before_s(s, anxt, rs, kn, c, b, P.tol_tie))) b = c;
+        }
+        if (lane == 0) pick_sh = b;
+    }
+    __syncthreads();
+    return pick_sh;
+}
+
 __device__ __forceinline__ PriceRec to_price_rec(const Cand& c) {
     PriceRec r;
     r.d_all = c.d_all; r.d_nt = c.d_nt;  // keys
@@ -840,6 +933,19 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
         }
         __syncthreads();
         if (S.status != kRunning) break;
+        if (P.lex && S.tcount > 1) {
+            // lexicographic rule: the tie set's row of B^-1 / alpha_i that is
+            // lexicographically smallest leaves instead
+            const int rr = lex_pick_s(s, anxt, s.row_slot + (size_t)S.par * P.m, kn, thr);
+            if (threadIdx.x == 0 && rr >= 0) {
+                const double al = __ldcg(anxt + rr);
+                S.r = rr;
+                S.leave = __ldcg(s.row_var + rr);
+                S.theta = __ldcg(s.bbar + rr) / al;
+                S.alpha_r = al;
+            }
+            __syncthreads();
+        }
     }
     if (lead && threadIdx.x == 0) {
         iterate_flush(s, S);

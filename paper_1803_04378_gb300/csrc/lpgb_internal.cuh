@@ -97,6 +97,9 @@ struct Ctrl {
     double alpha_r;        // pivot element
     double z;              // objective c_B^T bbar
     double refine_res;     // reinversion by refinement: ||I - B11 Y0||_inf of the stored inverse
+    double repair_tol;     // warm-start repair: basic values below -repair_tol are repaired
+    int32_t repair_limit;  // warm-start repair: no repair pivot once it reaches this count
+    int32_t pad_;
 };
 
 // Per-CTA ratio-test record of k_iterate: the CTA's smallest ratio, and its
@@ -327,8 +330,7 @@ void launch_build_aux(const double* A_cm, int ld, int m, int n, const double* b,
 void launch_validate(const double* A_cm, const double* b, const double* c, int m, int n, int ld,
                      int32_t* flag, cudaStream_t st);
 void launch_load_basis(const DevState& s, cudaStream_t st);
-void launch_repair_begin(const DevState& s, cudaStream_t st);
-void launch_repair_steps(const DevState& s, const Geometry& g, double tol, int steps, int limit_it,
-                         cudaStream_t st);
+void launch_repair_begin(const DevState& s, double tol, int limit_it, cudaStream_t st);
+void launch_repair_steps(const DevState& s, const Geometry& g, int steps, cudaStream_t st);
 
 }  // namespace lpgb

@@ -29,6 +29,7 @@ struct lp_handle {
     Geometry geo{};
     Ctrl* h_ctrl = nullptr;          // pinned mirror of the control block
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t rgraph = nullptr;  // kRepairBatch warm-start repair steps (captured on first use)
     std::vector<void*> allocs;
     int32_t* flag = nullptr;         // device validation flag
     bool solved = false;
@@ -122,6 +123,7 @@ int read_ctrl(lp_handle* h) {
 
 void free_all(lp_handle* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->rgraph) cudaGraphExecDestroy(h->rgraph);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
@@ -208,6 +210,22 @@ int capture_graph_once(lp_handle* h, bool pdl) {
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return LP_OK;
+}
+
+constexpr int kRepairBatch = 16;  // warm-start repair pivots enqueued per read of the outcome
+
+// kRepairBatch warm-start repair steps; their limit and tolerance are read
+// from Ctrl, so one capture serves every solve of the handle.
+int capture_repair_graph(lp_handle* h) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    launch_repair_steps(h->ds, h->geo, kRepairBatch, h->stream);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&h->rgraph, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e);
     return LP_OK;
@@ -322,7 +340,6 @@ int ooc_iteration(lp_handle* h) {
 // a reinversion refines (one Newton-Schulz step then leaves a residual below
 // 2^-52, at the rounding level); above it the basis is eliminated afresh.
 constexpr double kRefineTolMax = 1.0 / 67108864.0;  // 2^-26
-constexpr int kRepairBatch = 16;  // warm-start repair pivots enqueued per read of the outcome
 
 // Rebuild B^-1, bbar, y, z from the current basis.  `refine`: the stored
 // inverse is that of the current basis (a periodic reinversion, the last
@@ -780,16 +797,16 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(reset_state(h));
     TRY(capture_graph(h));
     // Persistent engines.  The slack-structured one when asked for (the
-    // default) and it fits: price_mode 0, the tabu rule, a device that runs
-    // cooperative launches with one 1024-thread CTA on every SM.  Otherwise
-    // the dense one, unless captured graphs are asked for or the mode needs
-    // them (the BF16 screen, the lexicographic tie-break).
+    // default) and it fits: price_mode 0, a device that runs cooperative
+    // launches with one 1024-thread CTA on every SM.  Otherwise the dense one,
+    // unless captured graphs are asked for or the mode needs them (the BF16
+    // screen; the lexicographic tie-break, which the dense engine lacks).
     {
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
         // (the ratio tests hold one CTA record per thread: at most 1024 CTAs)
         const bool want_s = h->opt.engine == LP_ENGINE_STRUCTURED;
-        const bool fits_s = want_s && h->opt.price_mode == 0 && !P.lex && coop && h->geo.sms <= 1024 &&
+        const bool fits_s = want_s && h->opt.price_mode == 0 && coop && h->geo.sms <= 1024 &&
                             struct_engine_fits(h->m, h->ld, h->geo.sms);
         const bool occ_s = fits_s && occupancy_iterate_s(h->ld) >= 1;
         // the first condition that keeps the asked engine from running
@@ -797,7 +814,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
             h->engine_reason = LP_ENGINE_REASON_OUT_OF_CORE;
         } else if (h->opt.engine != LP_ENGINE_GRAPH) {
             if (h->opt.price_mode == 1) h->engine_reason = LP_ENGINE_REASON_PRICE_MODE;
-            else if (P.lex) h->engine_reason = LP_ENGINE_REASON_LEXICOGRAPHIC;
+            else if (P.lex && !want_s) h->engine_reason = LP_ENGINE_REASON_LEXICOGRAPHIC;
             else if (!coop || h->geo.sms > 1024) h->engine_reason = LP_ENGINE_REASON_NO_COOPERATIVE;
             else if (want_s && h->opt.price_mode != 0) h->engine_reason = LP_ENGINE_REASON_PRICE_MODE;
             else if (want_s && !fits_s) h->engine_reason = LP_ENGINE_REASON_SIZE;
@@ -981,17 +998,17 @@ int lp_solve(lp_handle* h, lp_result* out) {
             bool ok = rc == LP_OK;
             if (rc != LP_OK && rc != LP_ERR_SINGULAR) return rc;
             if (ok) {
-                // repair pivots in batches, the outcome read once per batch
+                // repair pivots in batches (a captured graph of kRepairBatch
+                // steps), the outcome read once per batch
                 TRY(read_ctrl(h));
                 const int it0 = h->h_ctrl->it;
                 const int limit = it0 + h->warm_repair_max;
-                launch_repair_begin(h->ds, h->stream);
+                launch_repair_begin(h->ds, 1e-9 * h->p.b_scale, limit, h->stream);
                 h->launches += 1;
+                if (!h->rgraph) TRY(capture_repair_graph(h));
                 for (;;) {
-                    const int steps = std::min(kRepairBatch, std::max(1, limit - h->h_ctrl->it + 1));
-                    launch_repair_steps(h->ds, h->geo, 1e-9 * h->p.b_scale, steps, limit, h->stream);
-                    CK(cudaGetLastError());
-                    h->launches += 4 * steps;
+                    CK(cudaGraphLaunch(h->rgraph, h->stream));
+                    h->launches += 4 * kRepairBatch;
                     TRY(read_ctrl(h));
                     const Ctrl& C = *h->h_ctrl;
                     if (C.err != kErrNone) return device_err_code(C.err);

@@ -29,19 +29,51 @@ def _lib():
     from paper_1803_04378_gb300 import lpgb  # noqa: F401
 
 
+ENGINES = {"structured": (2, 2), "graph": (1, 0)}  # lp_options.engine, lp_result.persistent
+
+
+@pytest.mark.parametrize("engine", ["structured", "graph"])
 @pytest.mark.parametrize("kind,m,n,seed", [("degenerate", 64, 128, 2), ("degenerate", 128, 256, 3),
                                           ("degenerate", 200, 300, 5), ("int", 37, 61, 5),
-                                          ("int", 200, 200, 0), ("real", 129, 257, 4)])
-def test_pivots_match_oracle(kind, m, n, seed):
+                                          ("int", 200, 200, 0), ("real", 129, 257, 4),
+                                          ("degenerate", 700, 900, 6)])
+def test_pivots_match_oracle(kind, m, n, seed, engine):
     A, b, c = lpgen.make(kind, m, n, seed)
-    lp, res, x, y, z, tr = gpu_solve(A, b, c, anticycling=LEX)
-    assert res.status == 1 and res.persistent == 0
+    eng, persistent = ENGINES[engine]
+    lp, res, x, y, z, tr = gpu_solve(A, b, c, anticycling=LEX, engine=eng, reinvert_every=32)
+    assert res.status == 1 and res.persistent == persistent and res.engine_reason == 0
     assert res.tabu_pushes == 0 and res.bland_fallbacks == 0
-    ref = oracle.solve(A, b, c, oracle.lexicographic_options())
+    opts = oracle.lexicographic_options()
+    opts.reinvert_every = 32
+    ref = oracle.solve(A, b, c, opts)
     assert abs(z - ref.objective) <= 1e-9 * max(1.0, abs(ref.objective))
     assert_certificate(A, b, c, x, y)
-    follow_check(A, b, c, res, tr, oracle.lexicographic_options())
+    follow_check(A, b, c, res, tr, opts)
     lp.close()
+
+
+def test_structured_engine_equals_graph_engine_on_the_degenerate_workload():
+    """2048 x 4096, integer A in -5..10, 30% of b_i = 0: every pivot is
+    degenerate.  Both engines make the same pivots under the lexicographic
+    rule; the oracle follows the structured engine's first 96 of them."""
+    from paper_1803_04378_gb300 import lpgb
+    A, b, c = lpgen.make("degenerate", 2048, 4096, 2)
+    out = {}
+    for engine in ("structured", "graph"):
+        eng, persistent = ENGINES[engine]
+        lp, res, x, y, z, tr = gpu_solve(A, b, c, anticycling=LEX, engine=eng)
+        assert res.status == lpgb.LP_OPTIMAL and res.persistent == persistent
+        assert res.tabu_pushes == 0 and res.bland_fallbacks == 0
+        out[engine] = (res, tr, z)
+        lp.close()
+    rs, ts, zs = out["structured"]
+    rg, tg, zg = out["graph"]
+    assert rs.iterations == rg.iterations and np.array_equal(ts["q"], tg["q"]) and np.array_equal(ts["r"], tg["r"])
+    assert abs(zs) <= 1e-9 and abs(zg) <= 1e-9
+    K = 96
+    chk = oracle.solve(A, b, c, oracle.lexicographic_options(max_iters=K), follow=(ts["q"][:K], ts["r"][:K]),
+                       follow_status=lpgb.LP_ITER_LIMIT, threads=0)
+    assert chk.mismatch_at < 0 and chk.iterations == min(K, rs.iterations), (chk.mismatch_at, chk.iterations)
 
 
 def test_beale_and_slack_basis_tie():
