@@ -245,6 +245,40 @@ def summarize(rows, modes=("repair",)):
     return out
 
 
+def proposal_sensitivity(family: Family, seeds, swaps=(0, 1, 2, 4, 8, 16), seed: int = 0):
+    """How good a proposal must be: each instance is solved cold, then started
+    (mode "repair") from its own optimal basis with k of its basic structurals
+    replaced by random nonbasic structurals.  Returns, per k, the mean pivots,
+    repair pivots and device seconds against cold, and the largest objective
+    gap."""
+    rng = np.random.default_rng(seed)
+    acc = {k: [] for k in swaps}
+    cold_p, cold_s = [], []
+    for inst in seeds:
+        family.draw(int(inst))
+        cold, basis = family.solve(None)
+        zc = family.lp.solution()[2]
+        cold_p.append(cold.iterations)
+        cold_s.append(cold.seconds)
+        spos = np.nonzero(basis < family.n)[0]
+        nonb = np.setdiff1d(np.arange(family.n), basis)
+        for k in swaps:
+            prop = basis.copy()
+            kk = min(k, len(spos))
+            if kk:
+                prop[rng.choice(spos, kk, replace=False)] = rng.choice(nonb, kk, replace=False)
+            res, _ = family.solve((prop, []), mode="repair")
+            acc[k].append((res.iterations, res.warm_repairs, res.seconds, res.warm_fallback,
+                           abs(family.lp.solution()[2] - zc) / max(1.0, abs(zc))))
+    out = dict(instances=len(cold_p), cold_pivots_mean=float(np.mean(cold_p)), cold_s_mean=float(np.mean(cold_s)))
+    for k in swaps:
+        a = np.array(acc[k])
+        out[f"swap{k}"] = dict(pivots_mean=float(a[:, 0].mean()), repairs_mean=float(a[:, 1].mean()),
+                               s_mean=float(a[:, 2].mean()), speedup=float(np.sum(cold_s) / a[:, 2].sum()),
+                               fallbacks=int(a[:, 3].sum()), max_rel_objective_gap=float(a[:, 4].max()))
+    return out
+
+
 def main():
     """The configured experiment: 20000 training pairs, 1000 held-out
     instances, base as the dense real workload at m=1024, n=2048 (seed 4)."""
@@ -263,12 +297,18 @@ def main():
     ap.add_argument("--modes", default="repair", help="comma-separated subset of " + ",".join(MODES))
     ap.add_argument("--max-repairs", type=int, default=None,
                     help="repair pivots before a proposal falls back to the slack basis (default m)")
+    ap.add_argument("--sensitivity", type=int, default=0,
+                    help="only measure starts from the optimal basis with k structurals swapped, on this many instances")
     args = ap.parse_args()
     modes = tuple(v for v in args.modes.split(",") if v)
     from . import build
     build.build()
     base = lpgen.dense_real_lp(args.m, args.n, 4)
     fam = Family(base)
+    if args.sensitivity:
+        out = dict(proposal_sensitivity(fam, range(20_000_000, 20_000_000 + args.sensitivity)), m=args.m, n=args.n)
+        print(json.dumps(out))
+        return
     hint = base_hint(fam) if args.labels == "hint" else None
     t0 = time.perf_counter()
     X, Y, piv = generate_labels(fam, range(1, args.train + 1), hint, log_every=1000)
