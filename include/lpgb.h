@@ -507,18 +507,18 @@ int lp_family_features(int32_t m, int32_t n, const double* A0, const double* b0,
 /*
  * lp_family_propose -- the network's proposed basis from its n+m scores
  * (DEVICE float32 `scores`, higher = more likely basic; structurals first,
- * then slacks).  The structurals with score > 0, in the order (score
+ * then slacks).  The structurals with score > threshold, in the order (score
  * descending, index ascending), at most m of them, are J_0 .. J_{k-1}; the k
  * slack rows of lowest score (ties: lower row) give up their positions, the
  * t-th of them to J_t; every other row keeps its slack.  Outputs (DEVICE
  * int32): basis (m entries, a valid proposal for lp_set_basis_repair) and
  * work (m + 1 entries: J in its first min(k, m) entries, the number of
- * structurals with score > 0, before the cap at m, in work[m]).  Nothing is
+ * structurals with score > threshold, before the cap at m, in work[m]).  Nothing is
  * allocated; enqueued on cuda_stream.  Errors: LP_ERR_INVALID_ARG (sizes,
  * NULL), LP_ERR_CUDA.
  */
-int lp_family_propose(int32_t m, int32_t n, const float* scores, int32_t* basis, int32_t* work,
-                      void* cuda_stream);
+int lp_family_propose(int32_t m, int32_t n, const float* scores, float threshold, int32_t* basis,
+                      int32_t* work, void* cuda_stream);
 
 /* lp_destroy -- frees the handle and its device memory (NULL is ignored). */
 void lp_destroy(lp_handle* h);

@@ -101,9 +101,9 @@ __global__ void k_feat_cols(int m, int n, const double* __restrict__ A0, const d
 }
 
 // ---- the proposed basis from the network's scores ------------------------------
-// Structural j is proposed when its score z_j > 0; the proposed structurals in
-// the order (z_j descending, j ascending), at most m of them, are J_0, J_1, ...
-// Slack rows in the order (z_{n+i} ascending, i ascending) give up their
+// Structural j is proposed when its score z_j exceeds the threshold; the
+// proposed structurals in the order (z_j descending, j ascending), at most m of
+// them, are J_0, J_1, ...  Slack rows in the order (z_{n+i} ascending, i ascending) give up their
 // positions: the t-th of them holds J_t.  Orders are computed as ranks (the
 // number of elements that come first), which needs no sort and is exact for
 // ties.  Scores are read through shared-memory tiles.
@@ -112,11 +112,11 @@ constexpr int kTile = 1024;
 
 // rank of every proposed structural; J[rank] = j for rank < m; work[m] counts them
 __global__ void __launch_bounds__(256) k_rank_structurals(int m, int n, const float* __restrict__ z,
-                                                          int32_t* __restrict__ work) {
+                                                          float thr, int32_t* __restrict__ work) {
     __shared__ float zt[kTile];
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const float zj = j < n ? z[j] : 0.f;
-    const bool cand = j < n && zj > 0.f;
+    const bool cand = j < n && zj > thr;
     int rank = 0;
     for (int t0 = 0; t0 < n; t0 += kTile) {
         __syncthreads();
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_rank_structurals(int m, int n, const fl
         if (cand)
             for (int k = 0; k < tn; ++k) {
                 const float v = zt[k];
-                rank += (v > zj || (v == zj && t0 + k < j)) ? 1 : 0;  // v > zj > 0: proposed too
+                rank += (v > zj || (v == zj && t0 + k < j)) ? 1 : 0;  // v >= zj > thr: proposed too
             }
     }
     if (cand) {
@@ -166,12 +166,12 @@ __global__ void __launch_bounds__(256) k_place_structurals(int m, int n, const f
 
 extern "C" {
 
-int lp_family_propose(int32_t m, int32_t n, const float* scores, int32_t* basis, int32_t* work,
+int lp_family_propose(int32_t m, int32_t n, const float* scores, float threshold, int32_t* basis, int32_t* work,
                       void* cuda_stream) {
-    if (m < 1 || n < 1 || !scores || !basis || !work) return LP_ERR_INVALID_ARG;
+    if (m < 1 || n < 1 || !scores || !basis || !work || !(threshold == threshold)) return LP_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (cudaMemsetAsync(work + m, 0, sizeof(int32_t), st) != cudaSuccess) return LP_ERR_CUDA;
-    k_rank_structurals<<<(n + 255) / 256, 256, 0, st>>>(m, n, scores, work);
+    k_rank_structurals<<<(n + 255) / 256, 256, 0, st>>>(m, n, scores, threshold, work);
     k_place_structurals<<<(m + 255) / 256, 256, 0, st>>>(m, n, scores, work, basis);
     return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
 }

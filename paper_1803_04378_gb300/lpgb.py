@@ -144,7 +144,7 @@ def _load():
     lib.lp_family_perturb.restype = ctypes.c_int
     lib.lp_family_features.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, ctypes.c_double, vp, vp]
     lib.lp_family_features.restype = ctypes.c_int
-    lib.lp_family_propose.argtypes = [i32, i32, vp, vp, vp, vp]
+    lib.lp_family_propose.argtypes = [i32, i32, vp, ctypes.c_float, vp, vp, vp]
     lib.lp_family_propose.restype = ctypes.c_int
     lib.lp_batch_create.argtypes = [P(vp), i32, vp, vp, vp, vp, vp, i32, P(lp_options)]
     lib.lp_batch_create.restype = ctypes.c_int
@@ -565,8 +565,9 @@ def family_features(A0, b0, c0, A, b, c, sigma: float, out, stream=None):
                                    float(sigma), _ptr(out), st), "lp_family_features")
 
 
-def family_propose(scores, m: int, n: int, basis, work, stream=None):
+def family_propose(scores, m: int, n: int, basis, work, threshold: float = 0.0, stream=None):
     """lp_family_propose: scores (torch CUDA float32, n+m) -> basis (int32, m)
     and work (int32, m+1: the proposed structurals, their count in work[m])."""
     st = None if stream is None else ctypes.c_void_p(stream)
-    _check(_lib.lp_family_propose(int(m), int(n), _ptr(scores), _ptr(basis), _ptr(work), st), "lp_family_propose")
+    _check(_lib.lp_family_propose(int(m), int(n), _ptr(scores), float(threshold), _ptr(basis), _ptr(work), st),
+           "lp_family_propose")

@@ -163,16 +163,16 @@ class Proposer:
     basis (lp_family_propose); only the m basis entries and the proposed
     structurals come back to the host."""
 
-    def __init__(self, net, m: int, n: int):
+    def __init__(self, net, m: int, n: int, threshold: float = 0.0):
         import torch
-        self.net, self.m, self.n = net, m, n
+        self.net, self.m, self.n, self.threshold = net, m, n, threshold
         self.logits = torch.empty((1, net.out_dim), dtype=torch.float32, device="cuda")
         self.basis = torch.empty(m, dtype=torch.int32, device="cuda")
         self.work = torch.empty(m + 1, dtype=torch.int32, device="cuda")
 
     def __call__(self, features):
         self.net.forward(features.reshape(1, -1).contiguous(), self.logits)
-        lpgb.family_propose(self.logits, self.m, self.n, self.basis, self.work)
+        lpgb.family_propose(self.logits, self.m, self.n, self.basis, self.work, self.threshold)
         basis = self.basis.cpu().numpy()
         work = self.work.cpu().numpy()
         k = min(int(work[self.m]), self.m)
@@ -182,14 +182,15 @@ class Proposer:
 MODES = ("repair", "repair_guided", "guided")
 
 
-def evaluate(family: Family, net, instances, modes=("repair",), max_repairs: int | None = None):
+def evaluate(family: Family, net, instances, modes=("repair",), max_repairs: int | None = None,
+             threshold: float = 0.0):
     """Cold vs warm solves of held-out instances (instance seeds drawn on the
     device, or host (A, b, c) triples): pivots, device seconds (inference
     included for the warm starts), objectives, and how far the proposal is
     from the cold optimum's structural set (false positives / negatives)."""
     import torch
     feat = torch.empty(family.n_features, dtype=torch.float32, device="cuda")
-    prop = Proposer(net, family.m, family.n)
+    prop = Proposer(net, family.m, family.n, threshold)
     rows = []
     for inst in instances:
         if isinstance(inst, (int, np.integer)):
@@ -245,12 +246,14 @@ def summarize(rows, modes=("repair",)):
     return out
 
 
-def proposal_sensitivity(family: Family, seeds, swaps=(0, 1, 2, 4, 8, 16), seed: int = 0):
+def proposal_sensitivity(family: Family, seeds, swaps=(0, 1, 2, 4, 8, 16), seed: int = 0, kind: str = "swap"):
     """How good a proposal must be: each instance is solved cold, then started
-    (mode "repair") from its own optimal basis with k of its basic structurals
-    replaced by random nonbasic structurals.  Returns, per k, the mean pivots,
-    repair pivots and device seconds against cold, and the largest objective
-    gap."""
+    (mode "repair") from its own optimal basis with k errors: "swap" replaces
+    k basic structurals by random nonbasic structurals, "drop" replaces them
+    by the slacks of k random tight rows (a proposal that misses structurals),
+    "add" replaces k basic slacks by random nonbasic structurals (a proposal
+    with extra ones).  Returns, per k, the mean pivots, repair pivots and
+    device seconds against cold, and the largest objective gap."""
     rng = np.random.default_rng(seed)
     acc = {k: [] for k in swaps}
     cold_p, cold_s = [], []
@@ -260,13 +263,20 @@ def proposal_sensitivity(family: Family, seeds, swaps=(0, 1, 2, 4, 8, 16), seed:
         zc = family.lp.solution()[2]
         cold_p.append(cold.iterations)
         cold_s.append(cold.seconds)
-        spos = np.nonzero(basis < family.n)[0]
-        nonb = np.setdiff1d(np.arange(family.n), basis)
+        spos = np.nonzero(basis < family.n)[0]                       # positions of basic structurals
+        lpos = np.nonzero(basis >= family.n)[0]                      # positions of basic slacks
+        nonb = np.setdiff1d(np.arange(family.n), basis)              # nonbasic structurals
+        tight = np.setdiff1d(np.arange(family.n, family.n + family.m), basis)  # nonbasic slacks
         for k in swaps:
             prop = basis.copy()
-            kk = min(k, len(spos))
+            if kind == "add":
+                kk = min(k, len(lpos), len(nonb))
+                at, new = lpos, nonb
+            else:
+                kk = min(k, len(spos), len(nonb) if kind == "swap" else len(tight))
+                at, new = spos, (nonb if kind == "swap" else tight)
             if kk:
-                prop[rng.choice(spos, kk, replace=False)] = rng.choice(nonb, kk, replace=False)
+                prop[rng.choice(at, kk, replace=False)] = rng.choice(new, kk, replace=False)
             res, _ = family.solve((prop, []), mode="repair")
             acc[k].append((res.iterations, res.warm_repairs, res.seconds, res.warm_fallback,
                            abs(family.lp.solution()[2] - zc) / max(1.0, abs(zc))))
@@ -288,7 +298,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=20000)
     ap.add_argument("--heldout", type=int, default=1000)
-    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--m", type=int, default=1024)
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--out", default="")
@@ -297,8 +307,13 @@ def main():
     ap.add_argument("--modes", default="repair", help="comma-separated subset of " + ",".join(MODES))
     ap.add_argument("--max-repairs", type=int, default=None,
                     help="repair pivots before a proposal falls back to the slack basis (default m)")
+    ap.add_argument("--thresholds", default="0,1,2,3",
+                    help="proposal thresholds on the structural scores, the best one picked on the validation instances")
+    ap.add_argument("--validation", type=int, default=200, help="validation instances for the threshold")
+    ap.add_argument("--save-params", default="", help="write the trained parameters (float32 .npy) here")
     ap.add_argument("--sensitivity", type=int, default=0,
-                    help="only measure starts from the optimal basis with k structurals swapped, on this many instances")
+                    help="only measure starts from the optimal basis with k errors, on this many instances")
+    ap.add_argument("--kind", default="swap", choices=["swap", "drop", "add"], help="error kind of --sensitivity")
     args = ap.parse_args()
     modes = tuple(v for v in args.modes.split(",") if v)
     from . import build
@@ -306,7 +321,8 @@ def main():
     base = lpgen.dense_real_lp(args.m, args.n, 4)
     fam = Family(base)
     if args.sensitivity:
-        out = dict(proposal_sensitivity(fam, range(20_000_000, 20_000_000 + args.sensitivity)), m=args.m, n=args.n)
+        out = dict(proposal_sensitivity(fam, range(20_000_000, 20_000_000 + args.sensitivity), kind=args.kind),
+                   m=args.m, n=args.n, kind=args.kind)
         print(json.dumps(out))
         return
     hint = base_hint(fam) if args.labels == "hint" else None
@@ -316,10 +332,23 @@ def main():
     t0 = time.perf_counter()
     net, losses = train(X, Y, epochs=args.epochs, log=True)
     t_train = time.perf_counter() - t0
-    rows = evaluate(fam, net, range(10_000_000, 10_000_000 + args.heldout), modes, args.max_repairs)
+    if args.save_params:
+        np.save(args.save_params, net.get_params())
+    # the proposal threshold: the best time-to-optimum on validation instances
+    # (seeds disjoint from the training and held-out ones)
+    val = range(30_000_000, 30_000_000 + args.validation)
+    sel = {}
+    for t in (float(v) for v in args.thresholds.split(",") if v):
+        sv = summarize(evaluate(fam, net, val, ("repair",), args.max_repairs, t), ("repair",))
+        sel[t] = sv["repair"]["speedup"]
+        print(f"validation threshold {t}: speedup {sel[t]:.3f}, pivot ratio {sv['repair']['pivot_ratio']:.3f}",
+              flush=True)
+    thr = max(sel, key=sel.get) if sel else 0.0
+    rows = evaluate(fam, net, range(10_000_000, 10_000_000 + args.heldout), modes, args.max_repairs, thr)
     out = dict(summarize(rows, modes), train_pairs=args.train, label_seconds=t_labels, train_seconds=t_train,
                label_pivots_mean=float(piv.mean()), losses=losses, m=args.m, n=args.n, labels=args.labels,
-               max_repairs=args.max_repairs if args.max_repairs is not None else args.m)
+               max_repairs=args.max_repairs if args.max_repairs is not None else args.m, epochs=args.epochs,
+               threshold=thr, validation_speedups=sel, validation_instances=args.validation)
     print(json.dumps(out))
     if args.out:
         with open(args.out, "w") as f:

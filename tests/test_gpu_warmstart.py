@@ -125,9 +125,10 @@ def test_propose_kernel_matches_definition():
     from paper_1803_04378_gb300 import lpgb
     from proposal_ref import basis_from_scores
     rng = np.random.default_rng(7)
-    cases = [(5, 4, None), (2, 5, "all"), (7, 9, "none"), (300, 600, None), (1300, 2500, None),
-             (1024, 2048, "ties"), (64, 3000, "many")]
-    for m, n, kind in cases:
+    cases = [(5, 4, None, 0.0), (2, 5, "all", 0.0), (7, 9, "none", 0.0), (300, 600, None, 0.0),
+             (1300, 2500, None, 0.0), (1024, 2048, "ties", 0.0), (64, 3000, "many", 0.0),
+             (300, 600, None, 1.25), (1024, 2048, "ties", -0.5)]
+    for m, n, kind, thr in cases:
         z = rng.standard_normal(n + m).astype(np.float32)
         if kind == "all":
             z[:] = 1.0
@@ -140,11 +141,11 @@ def test_propose_kernel_matches_definition():
         zt = torch.from_numpy(z).cuda()
         basis = torch.full((m,), -1, dtype=torch.int32, device="cuda")
         work = torch.full((m + 1,), -1, dtype=torch.int32, device="cuda")
-        lpgb.family_propose(zt, m, n, basis, work)
+        lpgb.family_propose(zt, m, n, basis, work, thr)
         torch.cuda.synchronize()
-        want_basis, want_J = basis_from_scores(z, m, n)
+        want_basis, want_J = basis_from_scores(z, m, n, thr)
         got_basis, got_work = basis.cpu().numpy(), work.cpu().numpy()
-        assert got_work[m] == int(np.sum(z[:n] > 0)), (m, n, kind)
+        assert got_work[m] == int(np.sum(z[:n] > np.float32(thr))), (m, n, kind)
         k = min(int(got_work[m]), m)
         assert got_work[:k].tolist() == want_J, (m, n, kind)
         assert np.array_equal(got_basis, want_basis), (m, n, kind)
