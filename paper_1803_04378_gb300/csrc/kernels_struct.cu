@@ -264,10 +264,13 @@ __device__ void row_record(const Params& P, int owned, bool bland, const double*
 // Row i of B^-1 at constraint k is bp[i][slot(k)] when row k is live (slot <
 // kn), else the unit column of row k's basic slack: 1 where that slack is the
 // basic variable of position i, 0 elsewhere.  Rows i and r, each divided by its
-// alpha, are compared in constraint order by one warp, 32 constraints per round
-// trip, as x_i a_r against x_r a_i (both alphas are positive): -1 if row i comes
-// first, +1 if row r does, 0 if every entry agrees within tau relative (the
-// result in every lane).
+// alpha, are compared in constraint order by one warp, kLexPer x 32 constraints
+// per round trip (all loads of a round issued before any test), as x_i a_r
+// against x_r a_i (both alphas are positive): -1 if row i comes first, +1 if
+// row r does, 0 if every entry agrees within tau relative (the result in every
+// lane).
+constexpr int kLexPer = 8;
+
 __device__ int lex_cmp_s(const DevState& s, const double* anxt, const int32_t* rs, int kn, int i, int r,
                          double tau) {
     const Params& P = s.p;
@@ -277,28 +280,37 @@ __device__ int lex_cmp_s(const DevState& s, const double* anxt, const int32_t* r
     const double* bi = s.bp + (size_t)i * P.ld;
     const double* br = s.bp + (size_t)r * P.ld;
     const double aa = ai * ar;
-    for (int k0 = 0; k0 < P.m; k0 += 32) {
-        const int k = k0 + lane;
-        int code = 0;  // 1 for a difference, sign in bit 2
-        if (k < P.m) {
-            const int slot = __ldcg(rs + k);
-            double x, y;
-            if (slot < kn) {
-                x = __ldcg(bi + slot);
-                y = __ldcg(br + slot);
+    for (int k0 = 0; k0 < P.m; k0 += 32 * kLexPer) {
+        int slot[kLexPer];
+#pragma unroll
+        for (int u = 0; u < kLexPer; ++u) {
+            const int k = k0 + 32 * u + lane;
+            slot[u] = k < P.m ? __ldcg(rs + k) : -1;
+        }
+        double x[kLexPer], y[kLexPer];
+#pragma unroll
+        for (int u = 0; u < kLexPer; ++u) {
+            const int k = k0 + 32 * u + lane;
+            if (slot[u] >= 0 && slot[u] < kn) {
+                x[u] = __ldcg(bi + slot[u]);
+                y[u] = __ldcg(br + slot[u]);
             } else {
-                x = vi == P.n + k ? 1.0 : 0.0;
-                y = vr == P.n + k ? 1.0 : 0.0;
-            }
-            if (((__double_as_longlong(x) | __double_as_longlong(y)) << 1) != 0) {
-                const double u = x * ar, v = y * ai;
-                if (fabs(u - v) > tau * fmax(aa, fmax(fabs(u), fabs(v)))) code = 1 | (u < v ? 4 : 0);
+                x[u] = vi == P.n + k ? 1.0 : 0.0;
+                y[u] = vr == P.n + k ? 1.0 : 0.0;
             }
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, code != 0);
-        if (bal) {
-            const int cd = __shfl_sync(0xffffffffu, code, __ffs(bal) - 1);
-            return (cd & 4) ? -1 : 1;
+#pragma unroll
+        for (int u = 0; u < kLexPer; ++u) {
+            int code = 0;  // 1 for a difference, sign in bit 2
+            if (slot[u] >= 0 && ((__double_as_longlong(x[u]) | __double_as_longlong(y[u])) << 1) != 0) {
+                const double a = x[u] * ar, b = y[u] * ai;
+                if (fabs(a - b) > tau * fmax(aa, fmax(fabs(a), fabs(b)))) code = 1 | (a < b ? 4 : 0);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, code != 0);
+            if (bal) {
+                const int cd = __shfl_sync(0xffffffffu, code, __ffs(bal) - 1);
+                return (cd & 4) ? -1 : 1;
+            }
         }
     }
     return 0;
@@ -314,13 +326,12 @@ __device__ __forceinline__ bool lex_before_s(const DevState& s, const double* an
 // The tie set's lexicographically smallest row (every thread of the CTA; the
 // result in every thread).  The tie set is that of the ratio test: alpha_i >
 // tol_piv and bbar_i <= thr alpha_i.  Warp w scans its contiguous range of
-// rows in order, keeping the row that leaves first; warp 0 then takes the
-// warps' rows in warp order.  The comparisons follow the same fixed schedule in
-// every CTA, so every CTA picks the same row.
+// rows in order, keeping the row that leaves first; the warps' rows then meet
+// in a binary tree in warp order.  The comparisons follow the same fixed
+// schedule in every CTA, so every CTA picks the same row.
 __device__ int lex_pick_s(const DevState& s, const double* anxt, const int32_t* rs, int kn, double thr) {
     const Params& P = s.p;
     __shared__ int wbest[32];
-    __shared__ int pick_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int per = (P.m + nw - 1) / nw;
     const int r0 = warp * per, r1 = min(P.m, r0 + per);
@@ -341,16 +352,18 @@ __device__ int lex_pick_s(const DevState& s, const double* anxt, const int32_t* 
     }
     if (lane == 0) wbest[warp] = best;
     __syncthreads();
-    if (warp == 0) {
-        int b = -1;
-        for (int w = 0; w < nw; ++w) {
-            const int c = wbest[w];
-            if (c >= 0 && (b < 0 || lex_before_s(s, anxt, rs, kn, c, b, P.tol_tie))) b = c;
+    for (int h = 1; h < nw; h *= 2) {
+        // round h: warp w (a multiple of 2h) meets warp w + h
+        if (warp % (2 * h) == 0 && warp + h < nw) {
+            const int a = wbest[warp], c = wbest[warp + h];
+            int win = a;
+            if (c >= 0 && (a < 0 || lex_before_s(s, anxt, rs, kn, c, a, P.tol_tie))) win = c;
+            __syncwarp();
+            if (lane == 0) wbest[warp] = win;
         }
-        if (lane == 0) pick_sh = b;
+        __syncthreads();
     }
-    __syncthreads();
-    return pick_sh;
+    return wbest[0];
 }
 
 __device__ __forceinline__ PriceRec to_price_rec(const Cand& c) {
@@ -482,8 +495,47 @@ __device__ __forceinline__ void dot2_f32(const float4* __restrict__ c0, const fl
     }
 }
 
+// The block's list of nonbasic owned columns kept from the last step (jl, jc,
+// jt, jr, count): the pivot made column basic_j basic and free_j nonbasic (each
+// only if it is a structural this block owns), and free_j carries its patched
+// tabu expiry; no other listed entry changes.  Entry order is immaterial to the
+// screened PRICE (every candidate comparison breaks ties by column index).
+__device__ int list_patch(const DevState& s, const PricePatch& pp, int* jl, double* jc, int* jt, int* jr,
+                          int* cnt_sh) {
+    __shared__ int rm_sh;
+    const int G = gridDim.x;
+    const int bj = pp.basic_j, fj = pp.free_j;
+    const bool rm = bj >= 0 && bj < s.p.n && bj % G == (int)blockIdx.x;
+    const bool add = fj >= 0 && fj < s.p.n && fj % G == (int)blockIdx.x;
+    const int cnt = *cnt_sh;
+    if (threadIdx.x == 0) rm_sh = -1;
+    __syncthreads();
+    if (rm)
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x)
+            if (jl[e] == bj) rm_sh = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = cnt;
+        const int e = rm_sh;
+        if (e >= 0) {
+            --c;
+            jl[e] = jl[c]; jc[e] = jc[c]; jt[e] = jt[c]; jr[e] = jr[c];
+        }
+        if (add) {
+            jl[c] = fj; jc[c] = s.c[fj]; jt[c] = patched_tabu(s, pp, fj); jr[c] = s.rank[fj];
+            ++c;
+        }
+        *cnt_sh = c;
+    }
+    __syncthreads();
+    return *cnt_sh;
+}
+
+// list_ok (shared, in the calling kernel): the list of the last step is
+// current up to this step's pivot (set here after a one-chunk list; the caller
+// clears it when a step prices by the full FP64 path or a launch begins).
 __device__ Cand price_block_screened(const DevState& s, int it, const double* ysh, const float* ysh32, int kk,
-                                     const int32_t* slack_rows, int nslack, const PricePatch& pp) {
+                                     const int32_t* slack_rows, int nslack, const PricePatch& pp, int* list_ok) {
     const Params& P = s.p;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int G = gridDim.x;
@@ -498,6 +550,7 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
     __shared__ int rl[kScreenMaxList];
     __shared__ int nrl;
     __shared__ double part[2][kPriceThreads / 64];
+    __shared__ int list_cnt;  // entries of the kept list
     Cand cand;
     cand_init(cand);
     // slack candidates: exact (d = -y), offered directly, loads issued first
@@ -518,9 +571,12 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
     const float umul = __fmul_ru((float)(depth + 3), 6.0200691e-8f);  // (d + 3) u 1.01, rounded up
     const float uabs = __fmul_ru((float)(kk + 8), 7.8886091e-31f);     // (k + 8) 2^-100: underflow
     const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
+    const bool keep = owned <= kScreenMaxList;  // one chunk: the list is kept from step to step
     const float4* y4 = reinterpret_cast<const float4*>(ysh32);
     for (int lb = 0; lb < owned; lb += kPriceThreads) {
-        const int cnt = list_nonbasic(s, pp, lb, owned, jl, jc, jt, jr, wcnt);
+        const int cnt = (keep && *list_ok) ? list_patch(s, pp, jl, jc, jt, jr, &list_cnt)
+                                           : list_nonbasic(s, pp, lb, owned, jl, jc, jt, jr, wcnt);
+        if (keep && threadIdx.x == 0) list_cnt = cnt;
         // (1) FP32 screen, two listed columns per warp
         for (int e0 = 2 * warp; e0 < cnt; e0 += 2 * nw) {
             const int e1 = min(e0 + 1, cnt - 1);
@@ -602,6 +658,7 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
             __syncthreads();
         }
     }
+    if (threadIdx.x == 0) *list_ok = keep ? 1 : 0;  // every thread read it before the loop's barriers
     if (sj >= 0) cand_offer(cand, -ysh[si], sj, sj_tabu <= it, ktol, sj_rank);
     for (int i = si + G * blockDim.x; i < nslack; i += G * blockDim.x) {
         int row = -1;
@@ -626,6 +683,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
     __shared__ long long wmin_sh[32], wthr_sh[32];
     __shared__ double rinv_sh;
     __shared__ int screen_sh;
+    __shared__ int list_ok;  // the screened PRICE's list of nonbasic columns is current
     __shared__ int wcnt_sh[32];
     __shared__ double ral[kMaxOwnedRows], rb[kMaxOwnedRows];
     __shared__ int rvar[kMaxOwnedRows];
@@ -644,6 +702,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
         S.z = C->z; S.bytes_price = C->bytes_price; S.bytes_update = C->bytes_update;
         S.k = C->k_live; S.par = C->map_par;
         screen_sh = P.screen && C->screen_off == 0;
+        list_ok = 0;
     }
     if (!grid_barrier(s.gbar, epoch, &fail)) {
         if (lead && threadIdx.x == 0) C->err = kErrTimeout;
@@ -782,9 +841,10 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
             const int32_t* sr = s.slot_row + (size_t)par * P.m;  // + the patch: the map after the moves
             // the FP32 screen unless the safety net needs every improving column
             // or y leaves the screen's range (then the full FP64 PRICE)
-            const Cand bc = (screen_ok && yrange && !S.bland)
-                                ? price_block_screened(s, S.it, ysh, ysh32, kk, sr, kn, ppat)
+            const bool scr = screen_ok && yrange && !S.bland;
+            const Cand bc = scr ? price_block_screened(s, S.it, ysh, ysh32, kk, sr, kn, ppat, &list_ok)
                                 : price_block<true>(s, S.it, ysh, s.A_p, kk >> 1, sr, kn, ppat);
+            if (!scr && threadIdx.x == 0) list_ok = 0;  // this step's pivot is not in the kept list
             if (threadIdx.x == 0) s.price_rec[blockIdx.x] = to_price_rec(bc);
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             // ---- (B) CHUZC (every CTA), then UPDATE + FTRAN + ratios
