@@ -524,6 +524,40 @@ __global__ void __launch_bounds__(kRT * kRT) k_refine_gemm(DevState s, int k) {
     }
 }
 
+// Tensor-core form of the two products (reinvert_tc, k <= 1024): the exact
+// 7-bit-sliced products of ozaki.cu give P = -(B11 Y0) into R's place and
+// P = Y0 R into rv_W; these kernels finish them.
+// R = I - B11 Y0 = I + P in place, and each row's sum of |R| (columns in order,
+// one warp per row) as its single partial for k_refine_norm.
+__global__ void __launch_bounds__(256) k_refine_finish_residual(DevState s, int k) {
+    if (s.ctrl->err != kErrNone) return;
+    const size_t kk = (size_t)k * k;
+    double* R = s.rv_M + 2 * kk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = blockIdx.x * nw + warp; i < k; i += gridDim.x * nw) {
+        double t = 0.0;
+        for (int c = lane; c < k; c += 32) {
+            double v = R[(size_t)i * k + c];
+            if (c == i) {
+                v = 1.0 + v;
+                R[(size_t)i * k + c] = v;
+            }
+            t += fabs(v);
+        }
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s.rv_W[kk + i] = t;
+    }
+}
+
+// Y1 = Y0 + P, P = Y0 R in rv_W
+__global__ void k_refine_add(DevState s, int k) {
+    if (s.ctrl->err != kErrNone) return;
+    const size_t kk = (size_t)k * k;
+    const double* Y0 = s.rv_M + kk;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < kk; e += (size_t)gridDim.x * blockDim.x)
+        s.rv_W[e] = Y0[e] + s.rv_W[e];
+}
+
 // ||R||_inf from the partial row sums (each row summed in tile order) into
 // ctrl->refine_res; a NaN row counts as infinite.
 __global__ void __launch_bounds__(1024) k_refine_norm(DevState s, int k, int ntc) {
@@ -811,20 +845,43 @@ void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t s
 
 bool refine_fits(int k, int m) { return k > 0 && 3 * (size_t)k * k <= (size_t)m * m; }
 
-void launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st) {
+static bool refine_on_tc(const DevState& s, int k) { return s.p.reinvert_tc && s.oz_xs && oz_fits(k); }
+
+// Returns the number of kernels launched.
+int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st) {
     const size_t kk = (size_t)k * k;
     int blocks = (int)((kk + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     k_gather<<<blocks, 256, 0, st>>>(s, k);
     k_refine_extract<<<blocks, 256, 0, st>>>(s, k, from_struct, k_live, par);
+    if (refine_on_tc(s, k) &&
+        oz_refine_residual_product(s.rv_M, s.rv_M + kk, k, s.rv_M + 2 * kk, s.oz_xs, s.oz_ys, s.oz_ex, s.oz_ey,
+                                   &s.ctrl->err, st) == cudaSuccess) {
+        k_refine_finish_residual<<<(k + 7) / 8, 256, 0, st>>>(s, k);
+        k_refine_norm<<<1, 1024, 0, st>>>(s, k, 1);
+        return 9;
+    }
+    (void)cudaGetLastError();
     const int nt = (k + kRT - 1) / kRT;
     k_refine_gemm<0><<<dim3(nt, nt), kRT * kRT, 0, st>>>(s, k);
     k_refine_norm<<<1, 1024, 0, st>>>(s, k, nt);
+    return 4;
 }
 
-void launch_refine_apply(const DevState& s, int k, cudaStream_t st) {
+int launch_refine_apply(const DevState& s, int k, cudaStream_t st) {
+    const size_t kk = (size_t)k * k;
+    if (refine_on_tc(s, k) &&
+        oz_refine_update_product(s.rv_M + kk, s.rv_M + 2 * kk, k, s.rv_W, s.oz_xs, s.oz_ys, s.oz_ex, s.oz_ey,
+                                 &s.ctrl->err, st) == cudaSuccess) {
+        int blocks = (int)((kk + 255) / 256);
+        if (blocks > 4096) blocks = 4096;
+        k_refine_add<<<blocks, 256, 0, st>>>(s, k);
+        return 6;
+    }
+    (void)cudaGetLastError();
     const int nt = (k + kRT - 1) / kRT;
     k_refine_gemm<1><<<dim3(nt, nt), kRT * kRT, 0, st>>>(s, k);
+    return 1;
 }
 
 // Returns 1 when the slack-row product ran on the tensor cores.  dense_rows:

@@ -316,8 +316,13 @@ size_t oz_scratch_y_elems(int m);
 cudaError_t oz_slack_product(const double* A_cm, int ld, const int32_t* J, const int32_t* S, const double* W,
                              int k, int nslack, double* C, __nv_bfloat16* xs, __nv_bfloat16* ys, int32_t* ex,
                              int32_t* ey, int32_t* err, cudaStream_t st);
-void launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st);
-void launch_refine_apply(const DevState& s, int k, cudaStream_t st);
+cudaError_t oz_refine_residual_product(const double* B11_cm, const double* Y0, int k, double* P,
+                                       __nv_bfloat16* xs, __nv_bfloat16* ys, int32_t* ex, int32_t* ey,
+                                       int32_t* err, cudaStream_t st);
+cudaError_t oz_refine_update_product(const double* Y0, const double* R, int k, double* P, __nv_bfloat16* xs,
+                                     __nv_bfloat16* ys, int32_t* ex, int32_t* ey, int32_t* err, cudaStream_t st);
+int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st);
+int launch_refine_apply(const DevState& s, int k, cudaStream_t st);
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible);
 int occupancy_price(int ld);
 int occupancy_price_lp(int ld);

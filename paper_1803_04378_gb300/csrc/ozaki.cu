@@ -82,6 +82,18 @@ struct SrcRowMajor {
     int k;
     __device__ double operator()(int c, int l) const { return W[(size_t)l * k + c]; }
 };
+// X rows of a row-major k x k matrix: X[i][l] = W[i * k + l]
+struct SrcRowsOf {
+    const double* W;
+    int k;
+    __device__ double operator()(int i, int l) const { return W[(size_t)i * k + l]; }
+};
+// X rows of a column-major k x k matrix: X[i][l] = W[l * k + i]
+struct SrcColsOf {
+    const double* W;
+    int k;
+    __device__ double operator()(int i, int l) const { return W[(size_t)l * k + i]; }
+};
 
 // exp[o] = 1 + max_l E(src(o, l)) over l < K (kNoDigits when all zero);
 // 32 outer indices per block (consecutive, for coalescing) x 8 inner groups.
@@ -202,11 +214,13 @@ struct OzEpi {
 bool oz_fits(int k) { return k >= 1 && k <= 1024; }
 
 size_t oz_scratch_x_elems(int m) {
-    // 8 (m - k) ldk over 1 <= k <= min(m, 1024), ldk = k rounded up to 8
+    // 8 max(m - k, k) ldk over 1 <= k <= min(m, 1024), ldk = k rounded up to 8
+    // (the slack rows, m - k of them, or the k rows of a refinement product)
     size_t best = 0;
     const int kmax = m < 1024 ? m : 1024;
     for (int k = 1; k <= kmax; ++k) {
-        const size_t v = (size_t)kSlices * (size_t)(m - k) * (size_t)((k + 7) & ~7);
+        const int rows = m - k > k ? m - k : k;
+        const size_t v = (size_t)kSlices * (size_t)rows * (size_t)((k + 7) & ~7);
         if (v > best) best = v;
     }
     return best;
@@ -216,26 +230,51 @@ size_t oz_scratch_y_elems(int m) {
     return (size_t)kSlices * kmax * (size_t)((kmax + 7) & ~7);
 }
 
+namespace {
+
+// out (M x N, row stride ldo) = sign (X Y), X = sx (M x K), Y = sy (K x N),
+// K <= 1024: exponents, slices of both operands, then one stacked GEMM whose
+// epilogue combines the digit pairs.
+template <class SX, class SY>
+cudaError_t oz_product(SX sx, SY sy, int M, int N, int K, double* out, int ldo, int negate, __nv_bfloat16* xs,
+                       __nv_bfloat16* ys, int32_t* ex, int32_t* ey, int32_t* err, cudaStream_t st) {
+    if (!oz_fits(K) || M < 1 || N < 1) return cudaErrorInvalidValue;
+    const int ldk = (K + 7) & ~7;
+    k_oz_exp<<<(M + 31) / 32, 256, 0, st>>>(sx, M, K, ex, err);
+    k_oz_exp<<<(N + 31) / 32, 256, 0, st>>>(sy, N, K, ey, err);
+    k_oz_slice<<<dim3((M + 31) / 32, (K + 31) / 32), 256, 0, st>>>(sx, M, K, ex, xs, ldk, err);
+    k_oz_slice<<<dim3((N + 31) / 32, (K + 31) / 32), 256, 0, st>>>(sy, N, K, ey, ys, ldk, err);
+    CUtensorMap ma, mb;
+    constexpr int BN = 128;
+    if (!tc_make_map_16bit(&ma, xs, kSlices * M, K, ldk, tcg::kTM, true) ||
+        !tc_make_map_16bit(&mb, ys, kSlices * N, K, ldk, BN, true))
+        return cudaErrorInvalidValue;
+    const OzEpi epi{out, ldo, M, N, ex, ey, negate};
+    return tcg::launch_tc_gemm<BN, 3, 2, true>(ma, mb, epi, kSlices * M, kSlices * N, K, err, st);
+}
+
+}  // namespace
+
 // C (nslack x k, row stride k) = -A[S, J] W, W = B11^-1 row-major k x k.
 // xs / ys: BF16 slice scratch (oz_scratch_*_elems), ex / ey: nslack and k ints.
 cudaError_t oz_slack_product(const double* A_cm, int ld, const int32_t* J, const int32_t* S, const double* W,
                              int k, int nslack, double* C, __nv_bfloat16* xs, __nv_bfloat16* ys, int32_t* ex,
                              int32_t* ey, int32_t* err, cudaStream_t st) {
-    if (!oz_fits(k) || nslack < 1) return cudaErrorInvalidValue;
-    const int ldk = (k + 7) & ~7;
-    const SrcAsj sx{A_cm, J, S, ld};
-    const SrcRowMajor sy{W, k};
-    k_oz_exp<<<(nslack + 31) / 32, 256, 0, st>>>(sx, nslack, k, ex, err);
-    k_oz_exp<<<(k + 31) / 32, 256, 0, st>>>(sy, k, k, ey, err);
-    k_oz_slice<<<dim3((nslack + 31) / 32, (k + 31) / 32), 256, 0, st>>>(sx, nslack, k, ex, xs, ldk, err);
-    k_oz_slice<<<dim3((k + 31) / 32, (k + 31) / 32), 256, 0, st>>>(sy, k, k, ey, ys, ldk, err);
-    CUtensorMap ma, mb;
-    constexpr int BN = 128;
-    if (!tc_make_map_16bit(&ma, xs, kSlices * nslack, k, ldk, tcg::kTM, true) ||
-        !tc_make_map_16bit(&mb, ys, kSlices * k, k, ldk, BN, true))
-        return cudaErrorInvalidValue;
-    const OzEpi epi{C, k, nslack, k, ex, ey, 1};
-    return tcg::launch_tc_gemm<BN, 3, 2, true>(ma, mb, epi, kSlices * nslack, kSlices * k, k, err, st);
+    return oz_product(SrcAsj{A_cm, J, S, ld}, SrcRowMajor{W, k}, nslack, k, k, C, k, 1, xs, ys, ex, ey, err, st);
+}
+
+// The two products of a Newton-Schulz refinement step (kernels_reinv.cu), k x k:
+// P = -(B11 Y0) with B11 column-major and Y0 row-major, and P = Y0 R with both
+// row-major; P row-major.
+cudaError_t oz_refine_residual_product(const double* B11_cm, const double* Y0, int k, double* P,
+                                       __nv_bfloat16* xs, __nv_bfloat16* ys, int32_t* ex, int32_t* ey,
+                                       int32_t* err, cudaStream_t st) {
+    return oz_product(SrcColsOf{B11_cm, k}, SrcRowMajor{Y0, k}, k, k, k, P, k, 1, xs, ys, ex, ey, err, st);
+}
+
+cudaError_t oz_refine_update_product(const double* Y0, const double* R, int k, double* P, __nv_bfloat16* xs,
+                                     __nv_bfloat16* ys, int32_t* ex, int32_t* ey, int32_t* err, cudaStream_t st) {
+    return oz_product(SrcRowsOf{Y0, k}, SrcRowMajor{R, k}, k, k, k, P, k, 0, xs, ys, ex, ey, err, st);
 }
 
 }  // namespace lpgb

@@ -360,15 +360,14 @@ int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = fal
     bool refined = false;
     if (refine && h->opt.reinvert_refine && h->h_ctrl->pending == 0 && refine_fits(k, h->m)) {
         const bool from_struct = h->structured && h->s_ready;
-        launch_refine_residual(h->ds, k, from_struct ? 1 : 0, h->h_ctrl->k_live, h->h_ctrl->map_par, h->stream);
+        h->launches += launch_refine_residual(h->ds, k, from_struct ? 1 : 0, h->h_ctrl->k_live, h->h_ctrl->map_par,
+                                              h->stream);
         CK(cudaGetLastError());
-        h->launches += 4;
         TRY(read_ctrl(h));
         if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
         h->refine_res_max = std::max(h->refine_res_max, h->h_ctrl->refine_res);
         if (h->h_ctrl->refine_res <= h->opt.refine_tol) {
-            launch_refine_apply(h->ds, k, h->stream);
-            h->launches += 1;
+            h->launches += launch_refine_apply(h->ds, k, h->stream);
             h->reinv_refined++;
             refined = true;
         }

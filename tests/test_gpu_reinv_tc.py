@@ -1,6 +1,7 @@
-"""The reinversion's slack-row product -A[S, J] B11^-1 on the tensor cores
-(exact 7-bit slices of the FP64 operands, combined in 64-bit fixed point)
-against the same product in FP64 FMAs and against the oracle.
+"""The reinversion's products on the tensor cores (exact 7-bit slices of the
+FP64 operands, combined in 64-bit fixed point) -- the slack-row product
+-A[S, J] B11^-1 and the two Newton-Schulz refinement products B11 Y0 and
+Y0 R -- against the same products in FP64 FMAs and against the oracle.
 
 * B^-1 of a basis with k structural columns: with the tensor cores and
   without, within 1e-12 of the largest entry of each other, and both within
@@ -13,6 +14,9 @@ against the same product in FP64 FMAs and against the oracle.
 * Whole solves with reinversions every 16 pivots: the oracle follows every
   pivot, the objective equals that of FP64 products to 1e-12, and on the real
   family (no ties) the pivots are those of FP64 products.
+* A refined reinversion (the updated inverse refined by one Newton-Schulz
+  step): B^-1, bbar and y with the tensor cores and without within 1e-12 of
+  the largest entry of each other, and within 1e-9 of the oracle's.
 * k > 1024 (beyond the exact FP32 accumulation of the digit products) falls
   back to FP64 products.
 """
@@ -89,11 +93,39 @@ def test_solves_with_tensor_core_reinversions(kind, m, n, seed):
     (r1, t1, z1), (r0, t0, z0) = runs
     assert r1.status == r0.status == lpgb.LP_OPTIMAL
     assert r1.reinversions >= 1 and r1.tc_reinversions >= 1 and r0.tc_reinversions == 0
+    assert r1.refined_reinversions >= 1 and r0.refined_reinversions >= 1
     if kind == "real":
         # no ties: the last-bit differences of the two products cannot change a choice
         assert np.array_equal(t1["q"], t0["q"]) and np.array_equal(t1["r"], t0["r"])
     assert z1 == pytest.approx(z0, rel=1e-12, abs=1e-12)
     follow_check(A, b, c, r1, t1, oracle.Options(reinvert_every=16))
+
+
+@pytest.mark.parametrize("kind,m,n,seed,K", [("real", 600, 1000, 7, 80), ("real", 1100, 1600, 8, 192)])
+def test_refined_reinversion_on_tensor_cores(kind, m, n, seed, K):
+    """State right after the refined reinversion at pivot K (reinversions every
+    K/2 pivots), with and without the tensor cores, against the oracle
+    following the same pivots."""
+    from paper_1803_04378_gb300 import lpgb
+    A, b, c = lpgen.make(kind, m, n, seed)
+    out = []
+    for tc in (1, 0):
+        with lpgb.LP(A, b, c, reinvert_every=K // 2, reinvert_tc=tc, max_iters=K, trace_cap=K) as lp:
+            res = lp.solve()
+            binv, bbar = lp.state()
+            y = lp.solution()[1]
+            tr = lp.trace()
+        assert res.iterations == K and res.refined_reinversions == 2, (res.iterations, res.refined_reinversions)
+        out.append((binv, bbar, y, tr))
+    (B1, b1, y1, t1), (B0, b0, y0, t0) = out
+    assert np.array_equal(t1["q"], t0["q"]) and np.array_equal(t1["r"], t0["r"])
+    for u, v in ((B1, B0), (b1, b0), (y1, y0)):
+        assert np.max(np.abs(u - v)) <= 1e-12 * max(1.0, np.max(np.abs(v)))
+    ref = oracle.solve(A, b, c, oracle.Options(max_iters=K, reinvert_every=K // 2),
+                       follow=(t1["q"], t1["r"]), follow_status=lpgb.LP_ITER_LIMIT, want_binv=True)
+    assert ref.mismatch_at < 0
+    assert np.max(np.abs(B1 - ref.binv)) <= 1e-9 * max(1.0, np.max(np.abs(ref.binv)))
+    assert np.max(np.abs(b1 - ref.bbar)) <= 1e-9 * max(1.0, np.max(np.abs(ref.bbar)))
 
 
 def test_more_than_1024_structurals_use_fp64_products():
