@@ -115,12 +115,18 @@ constexpr int kMaxOwnedRows = 256;  // rows of B^-1 per CTA (ratio-test records 
 // kn.  Row l of the CTA leaves alpha', bbar_i and its basic variable in
 // ral/rb/rvar[l] (alpha' and the variable also in global memory for the ratio
 // test of other CTAs); the ratios themselves are formed in row_record.
-__device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int q_new, bool do_upd, bool do_ftran,
+// upd: which rows take the pending rank-1 update here -- kUpdAll, kUpdRowR
+// (only row r: the others were updated by the update warps while the rest of
+// the CTA priced), kUpdButR (every row but r, no FTRAN: the update warps), or
+// kUpdNone.  Warps w0 .. w0 + nwarps - 1 share the CTA's rows.
+enum { kUpdNone = 0, kUpdAll = 1, kUpdRowR = 2, kUpdButR = 3 };
+
+__device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int q_new, int upd, bool do_ftran,
                                const double* acur, double* anxt, const double* aqs, int aq_unit, const double* rh,
-                               double* ral, double* rb, int* rvar) {
+                               double* ral, double* rb, int* rvar, int w0, int nwarps) {
     const Params& P = s.p;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int warp = (int)(threadIdx.x >> 5) - w0, nw = nwarps;
     const int kn = v.kn;
     const int kh = (kn + 1) >> 1;  // double2 units covering the live slots
     const double2* aq2 = reinterpret_cast<const double2*>(aqs);
@@ -129,6 +135,8 @@ __device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int
     const int owned = (P.m - (int)blockIdx.x + G - 1) / G;
     for (int l = warp; l < owned; l += nw) {
         const int i = blockIdx.x + G * l;
+        const bool do_upd = upd == kUpdAll || (upd == kUpdRowR && i == r) || (upd == kUpdButR && i != r);
+        if (!do_upd && !do_ftran) continue;
         double* rowd = s.bp + (size_t)i * P.ld;
         double2* row = reinterpret_cast<double2*>(rowd);
         // per-row scalars, all issued before the row streams in
@@ -136,7 +144,7 @@ __device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int
         const double na = (do_upd && i != r) ? -__ldcg(acur + i) : 0.0;
         const double bte = (do_upd && i != r && v.src_te >= 0) ? __ldcg(rowd + v.src_te) : 0.0;
         const double bb = do_ftran ? __ldcg(s.bbar + i) : 0.0;
-        const int var = do_ftran ? (i == r && do_upd ? q_new : __ldcg(s.basis + i)) : 0;
+        const int var = do_ftran ? (i == r && upd != kUpdNone ? q_new : __ldcg(s.basis + i)) : 0;
         double a0 = 0.0, a1 = 0.0;
         if (do_upd && i == r) {
             // row r becomes rho / alpha_r (every slot, the moved ones included)
@@ -169,7 +177,10 @@ __device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int
                         const double b1 = t1 == v.J ? 0.0 : (t1 == v.te && v.src_te >= 0 ? bte : o[t].y);
                         nv.x = fma(na, p.x, b0);
                         nv.y = fma(na, p.y, b1);
-                        if (st) __stcs(row + k, nv);
+                        if (st) {
+                            if (do_ftran) __stcs(row + k, nv);
+                            else __stcg(row + k, nv);  // read again by the next FTRAN
+                        }
                     }
                     if (do_ftran) {
                         const double2 w = aqs ? aq2[k] : make_double2(t0 == aq_unit ? 1.0 : 0.0, t1 == aq_unit ? 1.0 : 0.0);
@@ -495,11 +506,24 @@ __device__ __forceinline__ void dot2_f32(const float4* __restrict__ c0, const fl
     }
 }
 
+// k_iterate_s prices with warps 0 .. kPriceWarpsS-1 while the others apply the
+// pending rank-1 update to the CTA's rows; the pricing warps synchronise on
+// named barrier 1 (kPT threads), never on the block barrier.
+constexpr int kPriceWarpsS = 20;
+constexpr int kPriceGroupS = 32 * kPriceWarpsS;
+
+template <int kPT>
+__device__ __forceinline__ void group_sync() {
+    if (kPT == kUpdateThreads) __syncthreads();
+    else asm volatile("bar.sync 1, %0;\n" ::"n"(kPT) : "memory");
+}
+
 // The block's list of nonbasic owned columns kept from the last step (jl, jc,
 // jt, jr, count): the pivot made column basic_j basic and free_j nonbasic (each
 // only if it is a structural this block owns), and free_j carries its patched
 // tabu expiry; no other listed entry changes.  Entry order is immaterial to the
 // screened PRICE (every candidate comparison breaks ties by column index).
+template <int kPT>
 __device__ int list_patch(const DevState& s, const PricePatch& pp, int* jl, double* jc, int* jt, int* jr,
                           int* cnt_sh) {
     __shared__ int rm_sh;
@@ -509,11 +533,11 @@ __device__ int list_patch(const DevState& s, const PricePatch& pp, int* jl, doub
     const bool add = fj >= 0 && fj < s.p.n && fj % G == (int)blockIdx.x;
     const int cnt = *cnt_sh;
     if (threadIdx.x == 0) rm_sh = -1;
-    __syncthreads();
+    group_sync<kPT>();
     if (rm)
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x)
+        for (int e = threadIdx.x; e < cnt; e += kPT)
             if (jl[e] == bj) rm_sh = e;
-    __syncthreads();
+    group_sync<kPT>();
     if (threadIdx.x == 0) {
         int c = cnt;
         const int e = rm_sh;
@@ -527,17 +551,76 @@ __device__ int list_patch(const DevState& s, const PricePatch& pp, int* jl, doub
         }
         *cnt_sh = c;
     }
-    __syncthreads();
+    group_sync<kPT>();
     return *cnt_sh;
+}
+
+// Lists, in order, the nonbasic columns among the block's owned columns
+// lb .. lb+kPT-1 (block b owns j = b, b+G, ...), with their cost, tabu
+// expiry and priority, all loaded in the same round trip, by the kPT pricing
+// threads.  Returns the count.
+template <int kPT>
+__device__ int list_nonbasic_g(const DevState& s, const PricePatch& pp, int lb, int owned, int* jl, double* jc,
+                               int* jt, int* jr, int* wcnt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int G = gridDim.x;
+    const int l = lb + (int)threadIdx.x;
+    const int jj = (int)blockIdx.x + G * l;
+    bool nb = false;
+    double cj = 0.0;
+    int tj = 0, rj = kNoRank;
+    if (l < owned) {
+        const int pj = __ldcg(s.pos + jj);
+        cj = s.c[jj];
+        tj = patched_tabu(s, pp, jj);
+        rj = s.rank[jj];
+        nb = jj == pp.basic_j ? false : (jj == pp.free_j ? true : pj < 0);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, nb);
+    if (lane == 0) wcnt[warp] = __popc(bal);
+    group_sync<kPT>();
+    int before = 0, cnt = 0;
+    for (int w = 0; w < kPT / 32; ++w) {
+        const int cw = wcnt[w];
+        if (w < warp) before += cw;
+        cnt += cw;
+    }
+    if (nb) {
+        const int e = before + __popc(bal & ((1u << lane) - 1u));
+        jl[e] = jj;
+        jc[e] = cj;
+        jt[e] = tj;
+        jr[e] = rj;
+    }
+    group_sync<kPT>();
+    return cnt;
+}
+
+// cand_block_reduce over the kPT pricing threads (the result in thread 0)
+template <int kPT>
+__device__ Cand cand_group_reduce(Cand c) {
+    __shared__ Cand csh[32];
+    c = cand_warp_reduce(c);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    group_sync<kPT>();
+    if (lane == 0) csh[wid] = c;
+    group_sync<kPT>();
+    if (wid == 0) {
+        if (lane < kPT / 32) c = csh[lane];
+        else cand_init(c);
+        c = cand_warp_reduce(c);
+    }
+    return c;
 }
 
 // list_ok (shared, in the calling kernel): the list of the last step is
 // current up to this step's pivot (set here after a one-chunk list; the caller
 // clears it when a step prices by the full FP64 path or a launch begins).
+template <int kPT>
 __device__ Cand price_block_screened(const DevState& s, int it, const double* ysh, const float* ysh32, int kk,
                                      const int32_t* slack_rows, int nslack, const PricePatch& pp, int* list_ok) {
     const Params& P = s.p;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kPT >> 5;
     const int G = gridDim.x;
     const int half = P.ld >> 1;
     const long long ktol = dkey(P.tol_d);
@@ -571,11 +654,11 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
     const float umul = __fmul_ru((float)(depth + 3), 6.0200691e-8f);  // (d + 3) u 1.01, rounded up
     const float uabs = __fmul_ru((float)(kk + 8), 7.8886091e-31f);     // (k + 8) 2^-100: underflow
     const int owned = (P.n - (int)blockIdx.x + G - 1) / G;
-    const bool keep = owned <= kScreenMaxList;  // one chunk: the list is kept from step to step
+    const bool keep = owned <= kPT;  // one chunk: the list is kept from step to step
     const float4* y4 = reinterpret_cast<const float4*>(ysh32);
-    for (int lb = 0; lb < owned; lb += kPriceThreads) {
-        const int cnt = (keep && *list_ok) ? list_patch(s, pp, jl, jc, jt, jr, &list_cnt)
-                                           : list_nonbasic(s, pp, lb, owned, jl, jc, jt, jr, wcnt);
+    for (int lb = 0; lb < owned; lb += kPT) {
+        const int cnt = (keep && *list_ok) ? list_patch<kPT>(s, pp, jl, jc, jt, jr, &list_cnt)
+                                           : list_nonbasic_g<kPT>(s, pp, lb, owned, jl, jc, jt, jr, wcnt);
         if (keep && threadIdx.x == 0) list_cnt = cnt;
         // (1) FP32 screen, two listed columns per warp
         for (int e0 = 2 * warp; e0 < cnt; e0 += 2 * nw) {
@@ -598,10 +681,10 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
                 khi[e1] = fkey(__fadd_ru(__fsub_ru(ch1, s1), E1));
             }
         }
-        __syncthreads();
+        group_sync<kPT>();
         // (2) the largest lower end of each category (slacks exact)
         int b0 = INT_MIN, b1 = INT_MIN, b2 = INT_MIN;
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        for (int e = threadIdx.x; e < cnt; e += kPT) {
             const int lo = klo[e];
             const bool nt = jt[e] <= it;
             b0 = max(b0, lo);
@@ -621,17 +704,17 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
         b2 = __reduce_max_sync(0xffffffffu, b2);
         if (lane == 0) { bandsh[0][warp] = b0; bandsh[1][warp] = b1; bandsh[2][warp] = b2; }
         if (threadIdx.x == 0) nrl = 0;
-        __syncthreads();
+        group_sync<kPT>();
         const int L0 = __reduce_max_sync(0xffffffffu, lane < nw ? bandsh[0][lane] : INT_MIN);
         const int L1 = __reduce_max_sync(0xffffffffu, lane < nw ? bandsh[1][lane] : INT_MIN);
         const int L2 = __reduce_max_sync(0xffffffffu, lane < nw ? bandsh[2][lane] : INT_MIN);
         // (3) the columns whose interval reaches a category's lower end
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        for (int e = threadIdx.x; e < cnt; e += kPT) {
             const int hi = khi[e];
             const bool nt = jt[e] <= it;
             if (hi >= L0 || (nt && hi >= L1) || (nt && jr[e] != kNoRank && hi >= L2)) rl[atomicAdd(&nrl, 1)] = e;
         }
-        __syncthreads();
+        group_sync<kPT>();
         // (4) exact FP64 re-price, two warps (the two row segments) per column
         const int nr = nrl;
         const int nch = (kk >> 1) >> 5;
@@ -649,18 +732,18 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
                 const double t = pair_sum(acc[0]);
                 if (lane == 0) part[seg][slot] = t;
             }
-            __syncthreads();
+            group_sync<kPT>();
             if ((int)threadIdx.x < nw / 2 && r0 + (int)threadIdx.x < nr) {
                 const int e = rl[r0 + threadIdx.x];
                 const double sum = part[0][threadIdx.x] + part[1][threadIdx.x];
                 cand_offer(cand, jc[e] - sum, jl[e], jt[e] <= it, ktol, jr[e]);
             }
-            __syncthreads();
+            group_sync<kPT>();
         }
     }
     if (threadIdx.x == 0) *list_ok = keep ? 1 : 0;  // every thread read it before the loop's barriers
     if (sj >= 0) cand_offer(cand, -ysh[si], sj, sj_tabu <= it, ktol, sj_rank);
-    for (int i = si + G * blockDim.x; i < nslack; i += G * blockDim.x) {
+    for (int i = si + G * kPT; i < nslack; i += G * kPT) {
         int row = -1;
         for (int e = 0; e < pp.nsp && row < 0; ++e)
             if (pp.sp_slot[e] == i) row = pp.sp_row[e];
@@ -668,7 +751,7 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
         const int j = P.n + row;
         cand_offer(cand, -ysh[i], j, patched_tabu(s, pp, j) <= it, ktol, s.rank[j]);
     }
-    return cand_block_reduce(cand);
+    return cand_group_reduce<kPT>(cand);
 }
 
 __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int iters) {
@@ -837,15 +920,32 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
             }
         }
         const bool yrange = __syncthreads_or(ybig) == 0;  // y, rho, the A_p moves and thread 0's bookkeeping are done
+        bool upd_early = false;  // the rows but r took the pivot's update while the others priced
         if (S.status == kRunning) {
             const int32_t* sr = s.slot_row + (size_t)par * P.m;  // + the patch: the map after the moves
             // the FP32 screen unless the safety net needs every improving column
             // or y leaves the screen's range (then the full FP64 PRICE)
             const bool scr = screen_ok && yrange && !S.bland;
-            const Cand bc = scr ? price_block_screened(s, S.it, ysh, ysh32, kk, sr, kn, ppat, &list_ok)
-                                : price_block<true>(s, S.it, ysh, s.A_p, kk >> 1, sr, kn, ppat);
-            if (!scr && threadIdx.x == 0) list_ok = 0;  // this step's pivot is not in the kept list
-            if (threadIdx.x == 0) s.price_rec[blockIdx.x] = to_price_rec(bc);
+            if (scr) {
+                // warps 0 .. kPriceWarpsS-1 price; the others apply the pivot's
+                // rank-1 update to the CTA's rows but r (row r is read by every
+                // CTA for its rho in this step, so it changes after the barrier)
+                if ((int)(threadIdx.x >> 5) < kPriceWarpsS) {
+                    const Cand bc =
+                        price_block_screened<kPriceGroupS>(s, S.it, ysh, ysh32, kk, sr, kn, ppat, &list_ok);
+                    if (threadIdx.x == 0) s.price_rec[blockIdx.x] = to_price_rec(bc);
+                } else if (piv) {
+                    update_block_s(s, mv, r, q, kUpdButR, false, acur, nullptr, nullptr, -1, rh, nullptr, nullptr,
+                                   nullptr, kPriceWarpsS, kUpdateThreads / 32 - kPriceWarpsS);
+                }
+                upd_early = piv;
+            } else {
+                const Cand bc = price_block<true>(s, S.it, ysh, s.A_p, kk >> 1, sr, kn, ppat);
+                if (threadIdx.x == 0) {
+                    list_ok = 0;  // this step's pivot is not in the kept list
+                    s.price_rec[blockIdx.x] = to_price_rec(bc);
+                }
+            }
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             // ---- (B) CHUZC (every CTA), then UPDATE + FTRAN + ratios
             const Cand g = reduce_price_parts_s(s.price_rec, G);
@@ -870,6 +970,13 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
         const bool do_upd = piv;
         const bool do_ftran = S.status == kRunning && S.q >= 0 && S.q < P.n + P.m;
         if (!do_upd && !do_ftran) break;
+        if (do_upd && S.status != kRunning) {
+            // no PRICE barrier in this step (the pivot's bookkeeping stopped the
+            // run: a reinversion is due or the iteration limit is reached), yet
+            // the owner of row r overwrites it below: every CTA must have read
+            // it for its rho first (the status is the same in every CTA)
+            if (!grid_barrier(s.gbar, epoch, &fail)) break;
+        }
         const double* aqp = nullptr;
         int aq_unit = -1;
         if (do_ftran) {
@@ -887,7 +994,8 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
         __syncthreads();
         const double* acur2 = s.alpha + (size_t)S.abuf * P.ld;
         double* anxt = s.alpha + (size_t)(S.abuf ^ 1) * P.ld;
-        update_block_s(s, mv, r, q, do_upd, do_ftran, acur2, anxt, aqp, aq_unit, rh, ral, rb, rvar);
+        update_block_s(s, mv, r, q, do_upd ? (upd_early ? kUpdRowR : kUpdAll) : kUpdNone, do_ftran, acur2, anxt, aqp,
+                       aq_unit, rh, ral, rb, rvar, 0, kUpdateThreads / 32);
         if (lead && threadIdx.x == 0) {
             S.bytes_update += (do_upd ? 16.0 : (do_ftran ? 8.0 : 0.0)) * P.m * (double)kn;
             S.n_update++;
