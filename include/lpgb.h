@@ -172,7 +172,8 @@ typedef struct lp_result {
     int32_t price_launches;  /* kernel_timing: PRICE launches timed */
     int32_t update_launches; /* kernel_timing: UPDATE launches timed */
     int64_t kernel_launches; /* all kernels this call launched (graph nodes included) */
-    int32_t warm_repairs;    /* lp_set_basis_repair: repair pivots performed */
+    int32_t warm_repairs;    /* lp_set_basis_repair: repair pivots performed; lp_set_crash: crash
+                                pivots performed */
     int32_t warm_fallback;   /* 1: the proposal was unusable, the solve started from the slack basis */
     int32_t screen_passes;   /* price_mode 1: BF16 screen + re-price passes (cumulative) */
     int32_t full_passes;     /* price_mode 1: full FP64 PRICE passes (cumulative) */
@@ -287,6 +288,23 @@ int lp_set_priority(lp_handle* h, const int32_t* vars, int32_t count);
  * the optimum as usual.
  */
 int lp_set_basis_repair(lp_handle* h, const int32_t* basis_m, int32_t max_repairs);
+
+/*
+ * lp_set_crash -- warm start by a crash from the slack basis (the paper has no
+ * warm start; the learned warm start's use of a predicted set).  When the next
+ * lp_solve starts, the `count` structurals in vars (host; distinct, in [0, n),
+ * count <= m) enter one by one in the order given, each by an ordinary pivot:
+ * FTRAN of its column and the ratio test of Step 6 with the method's tie rule,
+ * so the basis stays primal feasible.  A variable is passed over when it is
+ * basic already, when its column has no alpha_i > tol_piv, or when the ratio
+ * test would make a structural leave (the crash replaces slacks only).  The
+ * plain method then runs to the optimum; lp_result.warm_repairs counts the
+ * crash pivots (they are iterations).  One solve consumes the list; lp_set_basis,
+ * lp_set_basis_repair and lp_reset clear it, and it clears a pending
+ * lp_set_basis.  LP_ERR_STATE when b has a negative entry (Phase I) or B^-1 is
+ * out of core (tableau_budget_mb).
+ */
+int lp_set_crash(lp_handle* h, const int32_t* vars, int32_t count);
 
 /* lp_reset -- return to the slack basis and clear all counters. */
 int lp_reset(lp_handle* h);

@@ -221,7 +221,95 @@ __global__ void k_repair_begin(DevState s, double tol, int limit_it) {
     C->repair_limit = limit_it;
 }
 
+// ---- warm-start crash from the slack basis ---------------------------------------
+// The proposed structurals enter one by one, in the order given, each by an
+// ordinary pivot of the method: FTRAN of the column and the ratio test of
+// Step 6 (k_update), so the basis stays primal feasible.  A candidate is
+// passed over when it is basic already, when no alpha_i exceeds tol_piv, or
+// when the ratio test would make a structural leave (a crash only replaces
+// slacks).  Ctrl::crash: 1 running, 2 done; Ctrl::crash_t: the next list
+// position.  Every kernel does nothing unless a crash is running and the
+// solve is running (a reinversion may fall due between crash pivots).
+
+__global__ void k_crash_begin(DevState s, int count) {
+    Ctrl* C = s.ctrl;
+    C->crash = count > 0 ? 1 : 2;
+    C->crash_t = 0;
+    C->crash_n = count;
+    C->q = -1;
+}
+
+// next candidate into q with d_q = c_q - y^T a_q (one block); q = -1 and
+// crash = 2 once the list is exhausted
+__global__ void __launch_bounds__(256) k_crash_next(DevState s) {
+    Ctrl* C = s.ctrl;
+    const Params& P = s.p;
+    __shared__ int q_sh;
+    __shared__ double part[8];
+    if (threadIdx.x == 0) {
+        int q = -1;
+        if (C->crash == 1 && C->status == kRunning) {
+            int t = C->crash_t;
+            while (t < C->crash_n && s.pos[s.crash_list[t]] >= 0) ++t;
+            if (t < C->crash_n) {
+                q = s.crash_list[t];
+                C->crash_t = t + 1;
+            } else {
+                C->crash = 2;
+                C->crash_t = t;
+                C->q = -1;
+            }
+        }
+        q_sh = q;
+    }
+    __syncthreads();
+    const int q = q_sh;
+    if (q < 0) return;
+    const double* col = s.A_cm + (size_t)q * P.ld;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < P.m; i += blockDim.x) acc = fma(s.y[i], col[i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        C->q = q;
+        C->dq = s.c[q] - t;
+        C->flags = 0;
+    }
+}
+
+// after k_update's FTRAN and ratio test: pass the candidate over (q = -1)
+// when its column has no alpha_i > tol_piv (k_update then reported the
+// problem unbounded along it) or a structural would leave
+__global__ void k_crash_check(DevState s) {
+    Ctrl* C = s.ctrl;
+    if (C->crash != 1 || C->q < 0) return;
+    if (C->status == kUnbounded) {
+        C->status = kRunning;
+        C->q = -1;
+        return;
+    }
+    if (C->status != kRunning) return;
+    const int r = C->r;
+    if (r < 0 || r >= s.p.m || s.basis[r] < s.p.n) C->q = -1;
+}
+
 }  // namespace
+
+void launch_crash_begin(const DevState& s, int count, cudaStream_t st) { k_crash_begin<<<1, 1, 0, st>>>(s, count); }
+
+// `steps` crash steps: the next candidate, the pending update with the
+// candidate's FTRAN and ratio test, the check, the pivot's bookkeeping
+void launch_crash_steps(const DevState& s, const Geometry& g, int steps, cudaStream_t st) {
+    for (int t = 0; t < steps; ++t) {
+        k_crash_next<<<1, 256, 0, st>>>(s);
+        launch_update(s, g, st);
+        k_crash_check<<<1, 1, 0, st>>>(s);
+        launch_pivot(s, g, st);
+    }
+}
 
 void launch_repair_begin(const DevState& s, double tol, int limit_it, cudaStream_t st) {
     k_repair_begin<<<1, 1, 0, st>>>(s, tol, limit_it);

@@ -99,7 +99,9 @@ struct Ctrl {
     double refine_res;     // reinversion by refinement: ||I - B11 Y0||_inf of the stored inverse
     double repair_tol;     // warm-start repair: basic values below -repair_tol are repaired
     int32_t repair_limit;  // warm-start repair: no repair pivot once it reaches this count
-    int32_t pad_;
+    int32_t crash;         // warm-start crash: 1 running, 2 done
+    int32_t crash_t;       // next position in the crash list
+    int32_t crash_n;       // entries of the crash list
 };
 
 // Per-CTA ratio-test record of k_iterate: the CTA's smallest ratio, and its
@@ -181,6 +183,7 @@ struct DevState {
     RowPart* row_part;  // k_iterate: per-CTA ratio-test record
     int32_t* row_var;   // m: basic variable of each row as seen by the last FTRAN (k_iterate)
     int32_t* lex_rows;  // m: rows of the ratio-test tie set (lexicographic rule)
+    int32_t* crash_list;  // m: the structurals a warm-start crash enters, in order (lp_set_crash)
     uint32_t* gbar;     // k_iterate grid barrier: arrivals, released epoch
     // slack-structured engine (k_iterate_s): the constraint rows in slot order,
     // the rows whose slack is nonbasic in slots [0, k_live)
@@ -335,6 +338,8 @@ void launch_build_aux(const double* A_cm, int ld, int m, int n, const double* b,
 void launch_validate(const double* A_cm, const double* b, const double* c, int m, int n, int ld,
                      int32_t* flag, cudaStream_t st);
 void launch_load_basis(const DevState& s, cudaStream_t st);
+void launch_crash_begin(const DevState& s, int count, cudaStream_t st);
+void launch_crash_steps(const DevState& s, const Geometry& g, int steps, cudaStream_t st);
 void launch_repair_begin(const DevState& s, double tol, int limit_it, cudaStream_t st);
 void launch_repair_steps(const DevState& s, const Geometry& g, int steps, cudaStream_t st);
 

@@ -30,6 +30,7 @@ struct lp_handle {
     Ctrl* h_ctrl = nullptr;          // pinned mirror of the control block
     cudaGraphExec_t graph = nullptr;
     cudaGraphExec_t rgraph = nullptr;  // kRepairBatch warm-start repair steps (captured on first use)
+    cudaGraphExec_t cgraph = nullptr;  // kRepairBatch warm-start crash steps (captured on first use)
     std::vector<void*> allocs;
     int32_t* flag = nullptr;         // device validation flag
     bool solved = false;
@@ -40,6 +41,7 @@ struct lp_handle {
     bool warm_pending = false;
     int warm_repair_max = -1;         // >= 0: lp_set_basis_repair
     std::vector<int32_t> warm_basis;
+    std::vector<int32_t> crash;       // lp_set_crash: structurals to enter first (consumed by the next solve)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, er0 = nullptr, er1 = nullptr, erg = nullptr, era = nullptr;
     double reinv_gj_s = 0.0, reinv_asm_s = 0.0;
     int32_t reinv_refined = 0;       // reinversions of this solve done by refinement
@@ -124,6 +126,7 @@ int read_ctrl(lp_handle* h) {
 void free_all(lp_handle* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->rgraph) cudaGraphExecDestroy(h->rgraph);
+    if (h->cgraph) cudaGraphExecDestroy(h->cgraph);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
@@ -226,6 +229,20 @@ int capture_repair_graph(lp_handle* h) {
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaGraphInstantiate(&h->rgraph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return LP_OK;
+}
+
+// kRepairBatch warm-start crash steps (kernels_setup.cu); they read their
+// state from Ctrl and the crash list, so one capture serves every solve.
+int capture_crash_graph(lp_handle* h) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    launch_crash_steps(h->ds, h->geo, kRepairBatch, h->stream);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&h->cgraph, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e);
     return LP_OK;
@@ -773,6 +790,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     TRY(dalloc(h, &upd_part, (size_t)parts));
     TRY(dalloc(h, &s.row_var, (size_t)m));
     TRY(dalloc(h, &s.lex_rows, (size_t)m));
+    TRY(dalloc(h, &s.crash_list, (size_t)m));
     TRY(dalloc(h, &s.row_part, (size_t)parts));
     TRY(dalloc(h, &s.gbar, 2));
     if (P.trace_cap > 0) {
@@ -893,9 +911,24 @@ int lp_set_basis_repair(lp_handle* h, const int32_t* basis, int32_t max_repairs)
     return rc;
 }
 
+int lp_set_crash(lp_handle* h, const int32_t* vars, int32_t count) {
+    if (!h || count < 0 || count > h->m || (count > 0 && !vars)) return LP_ERR_INVALID_ARG;
+    if (h->neg_b || h->ooc) return LP_ERR_STATE;  // needs a feasible slack basis and B^-1 on the device
+    std::vector<char> seen((size_t)h->n, 0);
+    for (int t = 0; t < count; ++t) {
+        const int v = vars[t];
+        if (v < 0 || v >= h->n || seen[v]) return LP_ERR_INVALID_ARG;
+        seen[v] = 1;
+    }
+    h->crash.assign(vars, vars + count);
+    h->warm_pending = false;
+    return LP_OK;
+}
+
 int lp_set_basis(lp_handle* h, const int32_t* basis) {
     if (!h || !basis) return LP_ERR_INVALID_ARG;
     h->warm_repair_max = -1;
+    h->crash.clear();
     std::vector<char> seen((size_t)h->n + h->m, 0);
     for (int p = 0; p < h->m; ++p) {
         const int v = basis[p];
@@ -940,6 +973,7 @@ int lp_set_priority(lp_handle* h, const int32_t* vars, int32_t count) {
 int lp_reset(lp_handle* h) {
     if (!h) return LP_ERR_INVALID_ARG;
     h->warm_pending = false;
+    h->crash.clear();
     TRY(reset_state(h));
     CK(cudaStreamSynchronize(h->stream));
     return LP_OK;
@@ -1024,6 +1058,34 @@ int lp_solve(lp_handle* h, lp_result* out) {
             }
             h->primed = false;
         }
+    }
+    if (h->neg_b || h->ooc) h->crash.clear();  // (lp_update_problem may have brought a negative b)
+    if (!h->crash.empty()) {
+        // crash from the slack basis: the listed structurals enter by ordinary
+        // ratio-test pivots, in batches of a captured graph, the outcome read
+        // once per batch
+        const int cn = (int)h->crash.size();
+        TRY(reset_state(h));
+        CK(cudaMemcpyAsync(h->ds.crash_list, h->crash.data(), sizeof(int32_t) * cn, cudaMemcpyHostToDevice,
+                           h->stream));
+        h->crash.clear();
+        TRY(read_ctrl(h));
+        const int it0 = h->h_ctrl->it;
+        launch_crash_begin(h->ds, cn, h->stream);
+        h->launches += 1;
+        if (!h->cgraph) TRY(capture_crash_graph(h));
+        for (;;) {
+            CK(cudaGraphLaunch(h->cgraph, h->stream));
+            h->launches += 4 * kRepairBatch;
+            TRY(read_ctrl(h));
+            const Ctrl& C = *h->h_ctrl;
+            if (C.err != kErrNone) return device_err_code(C.err);
+            if (C.crash == 2 && C.pending == 0) break;
+            if (C.status == kReinvert) TRY(reinvert(h, 0, true));
+            else if (C.status != kRunning) break;
+        }
+        warm_repairs = h->h_ctrl->it - it0;
+        h->primed = false;
     }
     TRY(read_ctrl(h));
     for (;;) {

@@ -120,6 +120,8 @@ def _load():
     lib.lp_tc_gemm.restype = ctypes.c_int
     lib.lp_set_basis_repair.argtypes = [vp, vp, i32]
     lib.lp_set_basis_repair.restype = ctypes.c_int
+    lib.lp_set_crash.argtypes = [vp, vp, i32]
+    lib.lp_set_crash.restype = ctypes.c_int
     lib.lp_update_problem.argtypes = [vp, vp, vp, vp, i32]
     lib.lp_update_problem.restype = ctypes.c_int
     lib.lp_set_priority.argtypes = [vp, vp, i32]
@@ -333,6 +335,10 @@ class LP:
         if bb.shape != (self.m,):
             raise ValueError("basis must have m entries")
         _check(_lib.lp_set_basis_repair(self._h, _ptr(bb), int(max_repairs)), "lp_set_basis_repair")
+
+    def set_crash(self, vars_in_order):
+        v = np.ascontiguousarray(vars_in_order, dtype=np.int32)
+        _check(_lib.lp_set_crash(self._h, _ptr(v) if len(v) else None, len(v)), "lp_set_crash")
 
     def solution(self):
         x = np.zeros(self.n)

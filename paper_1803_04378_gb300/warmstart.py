@@ -66,9 +66,11 @@ class Family:
         """Solve the current instance.  start = (basis, structural set):
         mode "repair" starts from `basis` (repaired by at most max_repairs
         slack pivots, default m, else the slack basis) with the plain rule;
-        "repair_guided" adds the guided rule on the structural set; "guided"
-        starts from the slack basis with the guided rule only.  None solves
-        cold."""
+        "repair_guided" adds the guided rule on the structural set; "crash"
+        starts from the slack basis and first enters the structural set in its
+        order by ratio-test pivots (lp_set_crash), then the plain rule;
+        "guided" starts from the slack basis with the guided rule only.  None
+        solves cold."""
         self.lp.update_problem(self.A, self.b, self.c)
         if start is None:
             self.lp.set_priority([])
@@ -81,6 +83,9 @@ class Family:
             elif mode == "repair_guided":
                 self.lp.set_priority(structurals)
                 self.lp.set_basis_repair(basis, cap)
+            elif mode == "crash":
+                self.lp.set_priority([])
+                self.lp.set_crash(list(structurals)[:self.m])
             elif mode == "guided":
                 self.lp.set_priority(structurals)
             else:
@@ -179,7 +184,7 @@ class Proposer:
         return basis, [int(j) for j in work[:k]]
 
 
-MODES = ("repair", "repair_guided", "guided")
+MODES = ("repair", "repair_guided", "crash", "guided")
 
 
 def evaluate(family: Family, net, instances, modes=("repair",), max_repairs: int | None = None,
