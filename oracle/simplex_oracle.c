@@ -278,6 +278,134 @@ static int reinvert(int m, int n, const double* A, const double* b, const double
  * stopped at iteration t with status follow_status).  Optional outputs may be
  * NULL: x (n), y_out (m), basis_out (m), binv_out (m*m), bbar_out (m), trace.
  */
+/* ---- checking another solver's pivots (follow mode) and the separation
+ * margins of the trace.  None of this changes the method's own decisions. */
+
+/* How far the entering choice q stands from the best other candidate of the
+   same rule: (d_q - second) / max(1, |d_q|). */
+static double entering_margin(int N, const double* d, const int32_t* pos, const int32_t* tabu_until, int it,
+                              int aspiration, int q) {
+    double second = -INFINITY;
+    for (int j = 0; j < N; ++j)
+        if (j != q && pos[j] < 0 && (aspiration || tabu_until[j] <= it) && d[j] > second) second = d[j];
+    return (d[q] - second) / dmax(1.0, fabs(d[q]));
+}
+
+/* The smallest relative separation of the leaving row r from every other row
+   with alpha_i > tol_piv: by alpha within the tie set (none under the
+   lexicographic rule), by ratio outside it. */
+static double leaving_margin(int m, const oracle_opts* o, const double* alpha, const double* theta, double tmin,
+                             double thr, int r) {
+    double margin = INFINITY;
+    for (int i = 0; i < m; ++i) {
+        if (i == r || !(alpha[i] > o->tol_piv)) continue;
+        double sep;
+        if (theta[i] <= thr && o->ratio_rule == 2) sep = INFINITY;
+        else if (theta[i] <= thr) sep = (alpha[r] - alpha[i]) / dmax(1.0, alpha[r]);
+        else sep = (theta[i] - thr) / dmax(1.0, fabs(tmin));
+        if (sep < margin) margin = sep;
+    }
+    return margin;
+}
+
+/* The other solver's entering choice fq at this iteration (fq < 0: it
+   stopped), against the oracle's own (*opt, *q).  A different choice is
+   accepted when, in the oracle's arithmetic, it is tied with the oracle's
+   within tie_cmp (or, with follow_relaxed, is any improving eligible column);
+   it is then adopted (*opt, *q, *flags |= TF_ADOPT_Q).  Returns 0 on a
+   mismatch. */
+static int follow_entering(const oracle_opts* o, int N, const double* d, const int32_t* pos,
+                           const int32_t* tabu_until, int it, int bland, double dmax_all, int fq,
+                           int follow_status, int* opt, int* q, int* flags, int32_t* adopted) {
+    const double eps = o->tie_cmp;
+    if (fq < 0 || *opt) {
+        if (fq < 0 && *opt && follow_status == OR_OPTIMAL) return 1;
+        /* borderline optimality: max d within the tie window of tol_d */
+        int border = fabs(dmax_all - o->tol_d) <= eps * dmax(1.0, fabs(o->tol_d));
+        if (fq < 0 && follow_status == OR_OPTIMAL && border) {
+            *opt = 1;
+            (*adopted)++;
+            return 1;
+        }
+        if (fq >= 0 && *opt && border && fq < N && pos[fq] < 0) {
+            *opt = 0;
+            *q = fq;
+            *flags |= TF_ADOPT_Q;
+            (*adopted)++;
+            return 1;
+        }
+        /* the other solver stopped for another reason: the leaving step decides */
+        return fq < 0 && !*opt && follow_status != OR_OPTIMAL;
+    }
+    if (fq == *q) return 1;
+    int ok = fq < N && pos[fq] < 0;
+    if (ok && bland) {
+        for (int j = 0; j < fq && ok; ++j)
+            if (pos[j] < 0 && d[j] > o->tol_d + eps * dmax(1.0, o->tol_d)) ok = 0;
+        if (d[fq] < o->tol_d - eps * dmax(1.0, o->tol_d)) ok = 0;
+    } else if (ok) {
+        int asp = (*flags & TF_ASPIRATION) != 0;
+        if (!asp && tabu_until[fq] > it) ok = 0;
+        if (o->follow_relaxed) {
+            /* any improving column is a valid simplex pivot */
+            if (!(d[fq] > o->tol_d - eps * dmax(1.0, o->tol_d))) ok = 0;
+        } else if (d[fq] < d[*q] - eps * dmax(1.0, fabs(d[*q]))) {
+            ok = 0;
+        }
+    }
+    if (!ok) return 0;
+    *q = fq;
+    *flags |= TF_ADOPT_Q;
+    (*adopted)++;
+    return 1;
+}
+
+/* The other solver's leaving row fr (fr < 0: unbounded) against the oracle's
+   own r, for the same entering column.  A different row is accepted when it
+   is in the tie set within tie_cmp and tied with r by the ratio rule (or r
+   itself is at the tie set's edge); it is then adopted (*r, theta[fr],
+   *flags |= TF_ADOPT_R).  Returns 0 on a mismatch. */
+static int follow_leaving(const oracle_opts* o, int m, const double* Binv, const double* bbar, const double* alpha,
+                          double* theta, double tmin, double thr, int bland, int fr, int* r, int* flags,
+                          int32_t* adopted) {
+    const double eps = o->tie_cmp;
+    if (fr < 0 || *r < 0) {
+        if (fr < 0 && *r < 0) return 1;
+        double amax = -INFINITY;
+        for (int i = 0; i < m; ++i) amax = dmax(amax, alpha[i]);
+        int border = fabs(amax - o->tol_piv) <= eps * dmax(1.0, o->tol_piv);
+        if (!border) return 0;
+        *r = fr;
+        if (fr >= 0) {
+            theta[fr] = bbar[fr] / alpha[fr];
+            *flags |= TF_ADOPT_R;
+        }
+        (*adopted)++;
+        return 1;
+    }
+    if (fr == *r) return 1;
+    int ok = fr < m && alpha[fr] > o->tol_piv - eps * dmax(1.0, o->tol_piv);
+    if (ok) {
+        double th = bbar[fr] / alpha[fr];
+        double sc = dmax(1.0, fabs(tmin));
+        if (th > thr + eps * sc) ok = 0;
+        /* the oracle's row r must itself be near the tie-set edge, or fr must
+           carry a pivot tied with alpha_r */
+        int r_border = theta[*r] >= thr - eps * sc;
+        int a_tie = alpha[fr] >= alpha[*r] - eps * dmax(1.0, alpha[*r]);
+        if (o->ratio_rule == 1 || bland) a_tie = 1;
+        /* lexicographic: fr may not come after r beyond the follow tolerance */
+        if (o->ratio_rule == 2) a_tie = lex_cmp(Binv, m, alpha, fr, *r, eps) <= 0;
+        if (!(a_tie || r_border)) ok = 0;
+        if (ok) theta[fr] = th;
+    }
+    if (!ok) return 0;
+    *r = fr;
+    *flags |= TF_ADOPT_R;
+    (*adopted)++;
+    return 1;
+}
+
 int oracle_solve(int m, int n, const double* A, const double* b, const double* c,
                  const oracle_opts* o, const int32_t* start_basis,
                  const int32_t* follow_q, const int32_t* follow_r, int32_t follow_len, int32_t follow_status,
@@ -319,7 +447,6 @@ int oracle_solve(int m, int n, const double* A, const double* b, const double* c
         }
     }
     int degen_run = 0, bland = 0;
-    const double eps = o->tie_cmp;
 
     for (;;) {
         if (it >= o->max_iters) { res->status = OR_ITER_LIMIT; break; }
@@ -349,66 +476,17 @@ int oracle_solve(int m, int n, const double* A, const double* b, const double* c
                     for (int j = 0; j < N; ++j)
                         if (pos[j] < 0 && d[j] > o->tol_d && (q < 0 || d[j] > d[q])) q = j;
                 }
-                /* separation of q from the best other candidate of the same rule */
-                double second = -INFINITY;
-                int asp = (flags & TF_ASPIRATION) != 0;
-                for (int j = 0; j < N; ++j)
-                    if (j != q && pos[j] < 0 && (asp || tabu_until[j] <= it) && d[j] > second) second = d[j];
-                margin_q = (d[q] - second) / dmax(1.0, fabs(d[q]));
+                margin_q = entering_margin(N, d, pos, tabu_until, it, (flags & TF_ASPIRATION) != 0, q);
             }
         }
 
-        /* Follow mode: compare with the other solver's entering choice. */
-        if (it < follow_len) {
-            int fq = follow_q[it];
-            if (fq < 0 || opt) {
-                int agree = (fq < 0 && opt && follow_status == OR_OPTIMAL);
-                if (!agree) {
-                    /* borderline optimality: max d within the tie window of tol_d */
-                    int border = fabs(dmax_all - o->tol_d) <= eps * dmax(1.0, fabs(o->tol_d));
-                    if (fq < 0 && follow_status == OR_OPTIMAL && border) {
-                        opt = 1;
-                        res->adopted++;
-                    } else if (fq >= 0 && opt && border && fq < N && pos[fq] < 0) {
-                        opt = 0;
-                        q = fq;
-                        flags |= TF_ADOPT_Q;
-                        res->adopted++;
-                    } else if (fq < 0 && !opt && follow_status != OR_OPTIMAL) {
-                        /* the other solver stopped for another reason; decided below */
-                    } else {
-                        res->status = OR_MISMATCH;
-                        res->mismatch_at = it;
-                        res->mismatch_kind = 1;
-                        break;
-                    }
-                }
-            } else if (fq != q) {
-                int ok = fq < N && pos[fq] < 0;
-                if (ok && bland) {
-                    for (int j = 0; j < fq && ok; ++j)
-                        if (pos[j] < 0 && d[j] > o->tol_d + eps * dmax(1.0, o->tol_d)) ok = 0;
-                    if (d[fq] < o->tol_d - eps * dmax(1.0, o->tol_d)) ok = 0;
-                } else if (ok) {
-                    int asp = (flags & TF_ASPIRATION) != 0;
-                    if (!asp && tabu_until[fq] > it) ok = 0;
-                    if (o->follow_relaxed) {
-                        /* any improving column is a valid simplex pivot */
-                        if (!(d[fq] > o->tol_d - eps * dmax(1.0, o->tol_d))) ok = 0;
-                    } else if (d[fq] < d[q] - eps * dmax(1.0, fabs(d[q]))) {
-                        ok = 0;
-                    }
-                }
-                if (!ok) {
-                    res->status = OR_MISMATCH;
-                    res->mismatch_at = it;
-                    res->mismatch_kind = 1;
-                    break;
-                }
-                q = fq;
-                flags |= TF_ADOPT_Q;
-                res->adopted++;
-            }
+        /* Follow mode: the other solver's entering choice, adopted when tied. */
+        if (it < follow_len && !follow_entering(o, N, d, pos, tabu_until, it, bland, dmax_all, follow_q[it],
+                                                follow_status, &opt, &q, &flags, &res->adopted)) {
+            res->status = OR_MISMATCH;
+            res->mismatch_at = it;
+            res->mismatch_kind = 1;
+            break;
         }
         if (opt) { res->status = OR_OPTIMAL; break; }
         double dq = d[q];
@@ -456,65 +534,16 @@ int oracle_solve(int m, int n, const double* A, const double* b, const double* c
                 }
             }
         }
-        double margin_r = INFINITY;
-        if (r >= 0) {
-            for (int i = 0; i < m; ++i) {
-                if (i == r || !(alpha[i] > o->tol_piv)) continue;
-                double sep;
-                if (theta[i] <= thr && o->ratio_rule == 2) sep = INFINITY;  /* lexicographic: no alpha margin */
-                else if (theta[i] <= thr) sep = (alpha[r] - alpha[i]) / dmax(1.0, alpha[r]);
-                else sep = (theta[i] - thr) / dmax(1.0, fabs(tmin));
-                if (sep < margin_r) margin_r = sep;
-            }
-        }
+        const double margin_r = r >= 0 ? leaving_margin(m, o, alpha, theta, tmin, thr, r) : INFINITY;
 
-        if (it < follow_len && follow_q[it] >= 0) {
-            int fr = follow_r[it];
-            if (fr < 0 || r < 0) {
-                int agree = (fr < 0 && r < 0);
-                if (!agree) {
-                    double amax = -INFINITY;
-                    for (int i = 0; i < m; ++i) amax = dmax(amax, alpha[i]);
-                    int border = fabs(amax - o->tol_piv) <= eps * dmax(1.0, o->tol_piv);
-                    if (!border) {
-                        res->status = OR_MISMATCH;
-                        res->mismatch_at = it;
-                        res->mismatch_kind = 2;
-                        break;
-                    }
-                    r = fr;
-                    if (r >= 0) {
-                        theta[r] = bbar[r] / alpha[r];
-                        flags |= TF_ADOPT_R;
-                    }
-                    res->adopted++;
-                }
-            } else if (fr != r) {
-                int ok = fr < m && alpha[fr] > o->tol_piv - eps * dmax(1.0, o->tol_piv);
-                if (ok) {
-                    double th = bbar[fr] / alpha[fr];
-                    double sc = dmax(1.0, fabs(tmin));
-                    if (th > thr + eps * sc) ok = 0;
-                    /* the oracle's row r must itself be near the tie-set edge,
-                       or fr must carry a pivot tied with alpha_r */
-                    int r_border = theta[r] >= thr - eps * sc;
-                    int a_tie = alpha[fr] >= alpha[r] - eps * dmax(1.0, alpha[r]);
-                    if (o->ratio_rule == 1 || bland) a_tie = 1;
-                    /* lexicographic: fr may not come after r beyond the follow tolerance */
-                    if (o->ratio_rule == 2) a_tie = lex_cmp(Binv, m, alpha, fr, r, eps) <= 0;
-                    if (!(a_tie || r_border)) ok = 0;
-                    if (ok) theta[fr] = th;
-                }
-                if (!ok) {
-                    res->status = OR_MISMATCH;
-                    res->mismatch_at = it;
-                    res->mismatch_kind = 2;
-                    break;
-                }
-                r = fr;
-                flags |= TF_ADOPT_R;
-                res->adopted++;
-            }
+        /* Follow mode: the other solver's leaving row, adopted when tied. */
+        if (it < follow_len && follow_q[it] >= 0 &&
+            !follow_leaving(o, m, Binv, bbar, alpha, theta, tmin, thr, bland, follow_r[it], &r, &flags,
+                            &res->adopted)) {
+            res->status = OR_MISMATCH;
+            res->mismatch_at = it;
+            res->mismatch_kind = 2;
+            break;
         }
         if (r < 0) { res->status = OR_UNBOUNDED; break; }
         if (tcount > 1) flags |= TF_TIE_SET;
