@@ -389,7 +389,35 @@ __device__ __forceinline__ PriceRec to_price_rec(const Cand& c) {
 // CHUZC over the per-CTA partials (result in thread 0): the warps that hold
 // them take one record per lane (four 16-byte loads), reduce it across the
 // warp by redux, and warp 0 reduces the warps' results the same way.
-__device__ Cand reduce_price_parts_s(const PriceRec* part, int nparts) {
+// cand_warp_reduce restricted to the categories a step can use: the smallest
+// improving index only under the Bland safety net, the priority candidate only
+// while a priority list is set (otherwise no candidate carries one).  The
+// categories left out keep their initial values, which are also what a full
+// reduction would give for them.
+__device__ Cand cand_warp_reduce_sel(const Cand& c, bool need_min, bool need_pr) {
+    Cand g;
+    cand_init(g);
+    long long kb;
+    int w = warp_argmax_key(c.d_all, c.j_all, c.j_all >= 0, kb);
+    if (w >= 0) { g.d_all = kb; g.j_all = __shfl_sync(0xffffffffu, c.j_all, w); }
+    w = warp_argmax_key(c.d_nt, c.j_nt, c.j_nt >= 0, kb);
+    if (w >= 0) { g.d_nt = kb; g.j_nt = __shfl_sync(0xffffffffu, c.j_nt, w); }
+    if (need_min) {
+        w = warp_argmin_index(c.j_min, c.j_min >= 0);
+        if (w >= 0) { g.j_min = __shfl_sync(0xffffffffu, c.j_min, w); g.d_min = __shfl_sync(0xffffffffu, c.d_min, w); }
+    }
+    if (need_pr) {
+        w = warp_argmax_key(c.d_pr, c.j_pr, c.j_pr >= 0, kb);
+        if (w >= 0) {
+            g.d_pr = kb;
+            g.j_pr = __shfl_sync(0xffffffffu, c.j_pr, w);
+            g.k_pr = __shfl_sync(0xffffffffu, c.k_pr, w);
+        }
+    }
+    return g;
+}
+
+__device__ Cand reduce_price_parts_s(const PriceRec* part, int nparts, bool need_min, bool need_pr) {
     __shared__ Cand wsh[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwu = (nparts + 31) >> 5;  // warps holding partials
@@ -410,14 +438,14 @@ __device__ Cand reduce_price_parts_s(const PriceRec* part, int nparts) {
             o.k_pr = w3.x;
             cand_merge(g, o);
         }
-        g = cand_warp_reduce(g);
+        g = cand_warp_reduce_sel(g, need_min, need_pr);
         if (lane == 0) wsh[warp] = g;
     }
     __syncthreads();
     if (warp == 0) {
         if (lane < nwu) g = wsh[lane];
         else cand_init(g);
-        g = cand_warp_reduce(g);
+        g = cand_warp_reduce_sel(g, need_min, need_pr);
     }
     return g;
 }
@@ -482,27 +510,36 @@ __device__ __forceinline__ int fkey(float x) {
     return b >= 0 ? b : (b ^ 0x7fffffff);
 }
 
-__device__ __forceinline__ void dot2_f32(const float4* __restrict__ c0, const float4* __restrict__ c1,
-                                         const float4* y4, int n4, int lane, float& s0, float& a0, float& s1,
-                                         float& a1) {
-    s0 = a0 = s1 = a1 = 0.f;
+// kNC columns at once: s[c] = sum y a_c and a[c] = sum |y| |a_c| over the n4
+// float4 groups, lane-strided, then across the warp by butterflies (every lane
+// gets the sums): per lane a chain of 4 fused multiply-adds per float4 in
+// increasing k, then five butterfly levels, as the screen's error bound counts.
+template <int kNC>
+__device__ __forceinline__ void dotn_f32(const float4* const (&col)[kNC], const float4* y4, int n4, int lane,
+                                         float (&sv)[kNC], float (&av)[kNC]) {
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) sv[c] = av[c] = 0.f;
 #pragma unroll 2
     for (int k = lane; k < n4; k += 32) {
         const float4 y = y4[k];
-        const float4 u = __ldcg(c0 + k), v = __ldcg(c1 + k);
-        s0 = fmaf(u.x, y.x, s0); s0 = fmaf(u.y, y.y, s0); s0 = fmaf(u.z, y.z, s0); s0 = fmaf(u.w, y.w, s0);
-        s1 = fmaf(v.x, y.x, s1); s1 = fmaf(v.y, y.y, s1); s1 = fmaf(v.z, y.z, s1); s1 = fmaf(v.w, y.w, s1);
-        a0 = fmaf(fabsf(u.x), fabsf(y.x), a0); a0 = fmaf(fabsf(u.y), fabsf(y.y), a0);
-        a0 = fmaf(fabsf(u.z), fabsf(y.z), a0); a0 = fmaf(fabsf(u.w), fabsf(y.w), a0);
-        a1 = fmaf(fabsf(v.x), fabsf(y.x), a1); a1 = fmaf(fabsf(v.y), fabsf(y.y), a1);
-        a1 = fmaf(fabsf(v.z), fabsf(y.z), a1); a1 = fmaf(fabsf(v.w), fabsf(y.w), a1);
+        float4 u[kNC];
+#pragma unroll
+        for (int c = 0; c < kNC; ++c) u[c] = __ldcg(col[c] + k);
+#pragma unroll
+        for (int c = 0; c < kNC; ++c) {
+            sv[c] = fmaf(u[c].x, y.x, sv[c]); sv[c] = fmaf(u[c].y, y.y, sv[c]);
+            sv[c] = fmaf(u[c].z, y.z, sv[c]); sv[c] = fmaf(u[c].w, y.w, sv[c]);
+            av[c] = fmaf(fabsf(u[c].x), fabsf(y.x), av[c]); av[c] = fmaf(fabsf(u[c].y), fabsf(y.y), av[c]);
+            av[c] = fmaf(fabsf(u[c].z), fabsf(y.z), av[c]); av[c] = fmaf(fabsf(u[c].w), fabsf(y.w), av[c]);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+#pragma unroll
+        for (int c = 0; c < kNC; ++c) {
+            sv[c] += __shfl_xor_sync(0xffffffffu, sv[c], o);
+            av[c] += __shfl_xor_sync(0xffffffffu, av[c], o);
+        }
     }
 }
 
@@ -510,6 +547,7 @@ __device__ __forceinline__ void dot2_f32(const float4* __restrict__ c0, const fl
 // pending rank-1 update to the CTA's rows; the pricing warps synchronise on
 // named barrier 1 (kPT threads), never on the block barrier.
 constexpr int kPriceWarpsS = 20;
+constexpr int kScreenCols = 2;  // columns one warp screens at a time
 constexpr int kPriceGroupS = 32 * kPriceWarpsS;
 
 template <int kPT>
@@ -532,6 +570,14 @@ __device__ int list_patch(const DevState& s, const PricePatch& pp, int* jl, doub
     const bool rm = bj >= 0 && bj < s.p.n && bj % G == (int)blockIdx.x;
     const bool add = fj >= 0 && fj < s.p.n && fj % G == (int)blockIdx.x;
     const int cnt = *cnt_sh;
+    // the joining column's cost, tabu expiry and priority, loaded before the search
+    double fc = 0.0;
+    int ft = 0, fr = kNoRank;
+    if (threadIdx.x == 0 && add) {
+        fc = s.c[fj];
+        ft = patched_tabu(s, pp, fj);
+        fr = s.rank[fj];
+    }
     if (threadIdx.x == 0) rm_sh = -1;
     group_sync<kPT>();
     if (rm)
@@ -546,7 +592,7 @@ __device__ int list_patch(const DevState& s, const PricePatch& pp, int* jl, doub
             jl[e] = jl[c]; jc[e] = jc[c]; jt[e] = jt[c]; jr[e] = jr[c];
         }
         if (add) {
-            jl[c] = fj; jc[c] = s.c[fj]; jt[c] = patched_tabu(s, pp, fj); jr[c] = s.rank[fj];
+            jl[c] = fj; jc[c] = fc; jt[c] = ft; jr[c] = fr;
             ++c;
         }
         *cnt_sh = c;
@@ -596,11 +642,12 @@ __device__ int list_nonbasic_g(const DevState& s, const PricePatch& pp, int lb, 
     return cnt;
 }
 
-// cand_block_reduce over the kPT pricing threads (the result in thread 0)
+// cand_block_reduce over the kPT pricing threads (the result in thread 0);
+// the screened PRICE never runs under the Bland safety net
 template <int kPT>
-__device__ Cand cand_group_reduce(Cand c) {
+__device__ Cand cand_group_reduce(Cand c, bool need_pr) {
     __shared__ Cand csh[32];
-    c = cand_warp_reduce(c);
+    c = cand_warp_reduce_sel(c, false, need_pr);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     group_sync<kPT>();
     if (lane == 0) csh[wid] = c;
@@ -608,7 +655,7 @@ __device__ Cand cand_group_reduce(Cand c) {
     if (wid == 0) {
         if (lane < kPT / 32) c = csh[lane];
         else cand_init(c);
-        c = cand_warp_reduce(c);
+        c = cand_warp_reduce_sel(c, false, need_pr);
     }
     return c;
 }
@@ -660,25 +707,28 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
         const int cnt = (keep && *list_ok) ? list_patch<kPT>(s, pp, jl, jc, jt, jr, &list_cnt)
                                            : list_nonbasic_g<kPT>(s, pp, lb, owned, jl, jc, jt, jr, wcnt);
         if (keep && threadIdx.x == 0) list_cnt = cnt;
-        // (1) FP32 screen, two listed columns per warp
-        for (int e0 = 2 * warp; e0 < cnt; e0 += 2 * nw) {
-            const int e1 = min(e0 + 1, cnt - 1);
-            const int j0 = jl[e0], j1 = jl[e1];
-            const float4* c0 = reinterpret_cast<const float4*>(s.A_p32 + (size_t)j0 * P.ld);
-            const float4* c1 = reinterpret_cast<const float4*>(s.A_p32 + (size_t)j1 * P.ld);
-            float cl0 = 0.f, ch0 = 0.f, cl1 = 0.f, ch1 = 0.f;
-            if (lane == 0) {
-                cl0 = __ldg(s.c32lo + j0); ch0 = __ldg(s.c32hi + j0);
-                cl1 = __ldg(s.c32lo + j1); ch1 = __ldg(s.c32hi + j1);
+        // (1) FP32 screen, kScreenCols listed columns per warp (the last
+        // group repeats its final column; the repeat writes the same keys)
+        for (int e0 = kScreenCols * warp; e0 < cnt; e0 += kScreenCols * nw) {
+            const float4* cp[kScreenCols];
+            float cl[kScreenCols], ch[kScreenCols];
+#pragma unroll
+            for (int c = 0; c < kScreenCols; ++c) {
+                const int j = jl[min(e0 + c, cnt - 1)];
+                cp[c] = reinterpret_cast<const float4*>(s.A_p32 + (size_t)j * P.ld);
+                cl[c] = ch[c] = 0.f;
+                if (lane == 0) { cl[c] = __ldg(s.c32lo + j); ch[c] = __ldg(s.c32hi + j); }
             }
-            float s0, a0, s1, a1;
-            dot2_f32(c0, c1, y4, n4, lane, s0, a0, s1, a1);
+            float sv[kScreenCols], av[kScreenCols];
+            dotn_f32<kScreenCols>(cp, y4, n4, lane, sv, av);
             if (lane == 0) {
-                const float E0 = __fmaf_ru(umul, a0, uabs), E1 = __fmaf_ru(umul, a1, uabs);
-                klo[e0] = fkey(__fsub_rd(cl0, __fadd_ru(s0, E0)));
-                khi[e0] = fkey(__fadd_ru(__fsub_ru(ch0, s0), E0));
-                klo[e1] = fkey(__fsub_rd(cl1, __fadd_ru(s1, E1)));
-                khi[e1] = fkey(__fadd_ru(__fsub_ru(ch1, s1), E1));
+#pragma unroll
+                for (int c = 0; c < kScreenCols; ++c) {
+                    const int e = min(e0 + c, cnt - 1);
+                    const float E = __fmaf_ru(umul, av[c], uabs);
+                    klo[e] = fkey(__fsub_rd(cl[c], __fadd_ru(sv[c], E)));
+                    khi[e] = fkey(__fadd_ru(__fsub_ru(ch[c], sv[c]), E));
+                }
             }
         }
         group_sync<kPT>();
@@ -751,7 +801,7 @@ __device__ Cand price_block_screened(const DevState& s, int it, const double* ys
         const int j = P.n + row;
         cand_offer(cand, -ysh[i], j, patched_tabu(s, pp, j) <= it, ktol, s.rank[j]);
     }
-    return cand_group_reduce<kPT>(cand);
+    return cand_group_reduce<kPT>(cand, P.prio != 0);
 }
 
 __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int iters) {
@@ -948,7 +998,7 @@ __global__ void __launch_bounds__(kUpdateThreads, 1) k_iterate_s(DevState s, int
             }
             if (!grid_barrier(s.gbar, epoch, &fail)) break;
             // ---- (B) CHUZC (every CTA), then UPDATE + FTRAN + ratios
-            const Cand g = reduce_price_parts_s(s.price_rec, G);
+            const Cand g = reduce_price_parts_s(s.price_rec, G, S.bland != 0, P.prio != 0);
             if (threadIdx.x == 0) {
                 const Chuzc d = chuzc_decide(g, S.bland != 0, P.tol_d);
                 if (d.optimal) {

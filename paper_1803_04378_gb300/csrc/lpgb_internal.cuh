@@ -53,6 +53,7 @@ struct Params {
     int32_t price_mode;    // 0: FP64 PRICE; 1: BF16 screen + FP64 re-price of the top k
     int32_t topk;          // candidates re-priced in FP64 (price_mode 1), <= kMaxTopk
     int32_t lex;           // 1: lexicographic leaving rule (no tabu list, no safety net)
+    int32_t prio;          // 1: a priority list is set (lp_set_priority; guided entering rule)
     double nnz;            // price_mode 2: nonzeros of A
     int32_t screen;        // slack-structured engine: PRICE through the exact FP32 screen
     int32_t reinvert_tc;   // slack-row product of the reinversion on the tensor cores

@@ -687,6 +687,7 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     P.price_mode = h->opt.price_mode;
     P.topk = h->opt.topk;
     P.lex = h->opt.anticycling == LP_ANTICYCLING_LEXICOGRAPHIC ? 1 : 0;
+    P.prio = 0;
     P.reinvert_tc = h->opt.reinvert_tc;
     if (P.lex) {
         // the lexicographic rule needs neither the tabu list nor the safety net
@@ -967,6 +968,8 @@ int lp_set_priority(lp_handle* h, const int32_t* vars, int32_t count) {
     }
     CK(cudaMemcpyAsync(h->ds.rank, rank.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    h->p.prio = count > 0 ? 1 : 0;  // the persistent kernels skip the priority reductions without a list
+    h->ds.p.prio = h->p.prio;
     return LP_OK;
 }
 
