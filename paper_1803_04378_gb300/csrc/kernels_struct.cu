@@ -115,6 +115,38 @@ constexpr int kMaxOwnedRows = 256;  // rows of B^-1 per CTA (ratio-test records 
 // kn.  Row l of the CTA leaves alpha', bbar_i and its basic variable in
 // ral/rb/rvar[l] (alpha' and the variable also in global memory for the ratio
 // test of other CTAs); the ratios themselves are formed in row_record.
+// Warp sum of a + b over the 32 lanes (every lane gets it) in 64-bit fixed
+// point.  The values are aligned to the warp's largest binary exponent E
+// (one redux): a value is t 2^(E - 1079) with |t| < 2^57, rounded to nearest;
+// the t are added exactly by integer shuffles, and the sum is rounded to
+// binary64 once (ll_scaled).  Relative to 2^(E - 1022), which bounds every
+// |value|, the error is below 2^-51 plus the final rounding -- no more than
+// the FP64 butterfly's -- and the sum does not depend on the lane order.  It
+// spends no FP64 instruction (each holds the FP64 pipe for ~64 cycles on this
+// chip, and the butterfly needs six per row).  Subnormal, infinite and NaN
+// inputs take the FP64 butterfly.
+__device__ __forceinline__ double warp_sum2_fixed(double a, double b) {
+    const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+    const int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
+    const bool odd = (ea == 0 && (ua << 1) != 0) || (eb == 0 && (ub << 1) != 0) || ea == 0x7ff || eb == 0x7ff;
+    const unsigned emax = __reduce_max_sync(0xffffffffu, (unsigned)max(ea, eb));
+    if (__any_sync(0xffffffffu, odd) || emax == 0) return warp_sum(a + b);
+    auto fix = [emax](unsigned long long u, int e) -> long long {
+        if (e == 0) return 0;  // +-0
+        const long long mant = (long long)((u & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+        const int sh = e - (int)emax + 4;  // at most 4
+        long long t = 0;
+        if (sh >= 0) t = mant << sh;
+        else if (sh > -60) t = (mant + (1ll << (-sh - 1))) >> (-sh);
+        return (u >> 63) ? -t : t;
+    };
+    long long t = fix(ua, ea) + fix(ub, eb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t == 0 ? 0.0 : ll_scaled(t, (int)emax - 1079);
+}
+
 // upd: which rows take the pending rank-1 update here -- kUpdAll, kUpdRowR
 // (only row r: the others were updated by the update warps while the rest of
 // the CTA priced), kUpdButR (every row but r, no FTRAN: the update warps), or
@@ -196,7 +228,7 @@ __device__ void update_block_s(const DevState& s, const SlotMoves& v, int r, int
             }
         }
         if (do_ftran) {
-            const double al = warp_sum(a0 + a1);
+            const double al = warp_sum2_fixed(a0, a1);
             if (lane == 0) {
                 const double alf = al + (us >= 0 ? aqs[us] : 0.0);
                 anxt[i] = alf;

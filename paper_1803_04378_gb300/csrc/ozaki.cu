@@ -143,33 +143,6 @@ __global__ void __launch_bounds__(256) k_oz_slice(Src src, int nout, int K, cons
     }
 }
 
-// t 2^s as the nearest binary64 (ties to even), t != 0, built from the
-// IEEE-754 binary64 format with integer instructions only (on this chip every
-// FP64 instruction holds a scheduler's FP64 pipe for ~64 cycles); results
-// below 2^-1022 flush to zero, above the range become infinite.
-__device__ __forceinline__ double ll_scaled(long long t, int s) {
-    const unsigned long long sign = t < 0 ? (1ull << 63) : 0ull;
-    const unsigned long long u = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
-    const int msb = 63 - __clzll((long long)u);
-    int e = msb + s;  // weight of the leading bit
-    unsigned long long mant;
-    if (msb > 52) {
-        const int sh = msb - 52;
-        const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-        mant = u >> sh;
-        if (rem > half || (rem == half && (mant & 1ull))) {
-            ++mant;
-            if (mant == (1ull << 53)) { mant >>= 1; ++e; }
-        }
-    } else {
-        mant = u << (52 - msb);
-    }
-    const int be = e + 1023;
-    if (be >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
-    if (be <= 0) return __longlong_as_double((long long)sign);
-    return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull)));
-}
-
 // GEMM epilogue: combines the 64 digit pairs of each output (see the file
 // comment) and writes sign * (X Y)[i][c] into out (row stride ldo); integer
 // instructions only.
