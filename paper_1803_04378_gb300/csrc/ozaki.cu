@@ -39,6 +39,8 @@ namespace lpgb {
 namespace {
 
 constexpr int kSlices = 8;   // 7-bit digits per operand (56 bits)
+constexpr int kOzBN = 128;     // GEMM tile columns; two TMEM accumulators of them per CTA
+constexpr int kOzStages = 3;   // shared-memory stages (two persistent CTAs per SM)
 constexpr int kLevels = 8;   // digit pairs with p + q <= kLevels are combined
 constexpr int kFrac = 51;    // fraction bits of the fixed-point combination
 constexpr int kNoDigits = INT_MIN / 4;  // exponent of an all-zero row or column
@@ -218,12 +220,12 @@ cudaError_t oz_product(SX sx, SY sy, int M, int N, int K, double* out, int ldo, 
     k_oz_slice<<<dim3((M + 31) / 32, (K + 31) / 32), 256, 0, st>>>(sx, M, K, ex, xs, ldk, err);
     k_oz_slice<<<dim3((N + 31) / 32, (K + 31) / 32), 256, 0, st>>>(sy, N, K, ey, ys, ldk, err);
     CUtensorMap ma, mb;
-    constexpr int BN = 128;
+    constexpr int BN = kOzBN;
     if (!tc_make_map_16bit(&ma, xs, kSlices * M, K, ldk, tcg::kTM, true) ||
         !tc_make_map_16bit(&mb, ys, kSlices * N, K, ldk, BN, true))
         return cudaErrorInvalidValue;
     const OzEpi epi{out, ldo, M, N, ex, ey, negate};
-    return tcg::launch_tc_gemm<BN, 3, 2, true>(ma, mb, epi, kSlices * M, kSlices * N, K, err, st);
+    return tcg::launch_tc_gemm_p<BN, kOzStages, true>(ma, mb, epi, kSlices * M, kSlices * N, K, err, st);
 }
 
 }  // namespace
