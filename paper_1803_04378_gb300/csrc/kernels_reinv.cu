@@ -859,7 +859,7 @@ int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live
                                    &s.ctrl->err, st) == cudaSuccess) {
         k_refine_finish_residual<<<(k + 7) / 8, 256, 0, st>>>(s, k);
         k_refine_norm<<<1, 1024, 0, st>>>(s, k, 1);
-        return 9;
+        return 7;
     }
     (void)cudaGetLastError();
     const int nt = (k + kRT - 1) / kRT;
@@ -876,7 +876,7 @@ int launch_refine_apply(const DevState& s, int k, cudaStream_t st) {
         int blocks = (int)((kk + 255) / 256);
         if (blocks > 4096) blocks = 4096;
         k_refine_add<<<blocks, 256, 0, st>>>(s, k);
-        return 6;
+        return 4;
     }
     (void)cudaGetLastError();
     const int nt = (k + kRT - 1) / kRT;

@@ -100,11 +100,9 @@ struct SrcColsOf {
 // exp[o] = 1 + max_l E(src(o, l)) over l < K (kNoDigits when all zero);
 // 32 outer indices per block (consecutive, for coalescing) x 8 inner groups.
 template <class Src>
-__global__ void __launch_bounds__(256) k_oz_exp(Src src, int nout, int K, int32_t* exps, const int32_t* err) {
-    if (*err != kErrNone) return;
-    __shared__ int red[8][33];
+__device__ void oz_exp_block(Src src, int nout, int K, int32_t* exps, int bx, int (*red)[33]) {
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int o = blockIdx.x * 32 + tx;
+    const int o = bx * 32 + tx;
     int e = kNoDigits;
     if (o < nout)
         for (int l = ty; l < K; l += 8) e = max(e, dexp(src(o, l)));
@@ -121,11 +119,9 @@ __global__ void __launch_bounds__(256) k_oz_exp(Src src, int nout, int K, int32_
 // out[(8 o + p) * ldk + l] = digit p of src(o, l) / 2^exp[o]; 32 x 32 tiles
 // read along o and written along l through shared memory.
 template <class Src>
-__global__ void __launch_bounds__(256) k_oz_slice(Src src, int nout, int K, const int32_t* exps,
-                                                  __nv_bfloat16* out, int ldk, const int32_t* err) {
-    if (*err != kErrNone) return;
-    __shared__ __nv_bfloat16 t[kSlices][32][34];  // [p][o][l]
-    const int o0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
+__device__ void oz_slice_block(Src src, int nout, int K, const int32_t* exps, __nv_bfloat16* out, int ldk, int bx,
+                               int by, __nv_bfloat16 (*t)[32][34]) {
+    const int o0 = bx * 32, l0 = by * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int o = o0 + tx;
     const int e = o < nout ? exps[o] : kNoDigits;
@@ -143,6 +139,31 @@ __global__ void __launch_bounds__(256) k_oz_slice(Src src, int nout, int K, cons
         const int orow = o0 + oo, l = l0 + tx;
         if (orow < nout && l < K) out[(size_t)(kSlices * orow + p) * ldk + l] = t[p][oo][tx];
     }
+}
+
+// The exponents of both operands in one launch: blocks 0 .. ceil(M/32)-1 take
+// the rows of X, the others the columns of Y.
+template <class SX, class SY>
+__global__ void __launch_bounds__(256) k_oz_exp(SX sx, int M, SY sy, int N, int K, int32_t* ex, int32_t* ey,
+                                                const int32_t* err) {
+    if (*err != kErrNone) return;
+    __shared__ int red[8][33];
+    const int bxm = (M + 31) / 32;
+    if ((int)blockIdx.x < bxm) oz_exp_block(sx, M, K, ex, blockIdx.x, red);
+    else oz_exp_block(sy, N, K, ey, blockIdx.x - bxm, red);
+}
+
+// The slices of both operands in one launch (grid: outer tiles of X then of
+// Y, by 32-element chunks of K).
+template <class SX, class SY>
+__global__ void __launch_bounds__(256) k_oz_slice(SX sx, int M, SY sy, int N, int K, const int32_t* ex,
+                                                  const int32_t* ey, __nv_bfloat16* xs, __nv_bfloat16* ys, int ldk,
+                                                  const int32_t* err) {
+    if (*err != kErrNone) return;
+    __shared__ __nv_bfloat16 t[kSlices][32][34];  // [p][o][l]
+    const int bxm = (M + 31) / 32;
+    if ((int)blockIdx.x < bxm) oz_slice_block(sx, M, K, ex, xs, ldk, blockIdx.x, blockIdx.y, t);
+    else oz_slice_block(sy, N, K, ey, ys, ldk, blockIdx.x - bxm, blockIdx.y, t);
 }
 
 // GEMM epilogue: combines the 64 digit pairs of each output (see the file
@@ -215,10 +236,9 @@ cudaError_t oz_product(SX sx, SY sy, int M, int N, int K, double* out, int ldo, 
                        __nv_bfloat16* ys, int32_t* ex, int32_t* ey, int32_t* err, cudaStream_t st) {
     if (!oz_fits(K) || M < 1 || N < 1) return cudaErrorInvalidValue;
     const int ldk = (K + 7) & ~7;
-    k_oz_exp<<<(M + 31) / 32, 256, 0, st>>>(sx, M, K, ex, err);
-    k_oz_exp<<<(N + 31) / 32, 256, 0, st>>>(sy, N, K, ey, err);
-    k_oz_slice<<<dim3((M + 31) / 32, (K + 31) / 32), 256, 0, st>>>(sx, M, K, ex, xs, ldk, err);
-    k_oz_slice<<<dim3((N + 31) / 32, (K + 31) / 32), 256, 0, st>>>(sy, N, K, ey, ys, ldk, err);
+    const int bx = (M + 31) / 32 + (N + 31) / 32;
+    k_oz_exp<<<bx, 256, 0, st>>>(sx, M, sy, N, K, ex, ey, err);
+    k_oz_slice<<<dim3(bx, (K + 31) / 32), 256, 0, st>>>(sx, M, sy, N, K, ex, ey, xs, ys, ldk, err);
     CUtensorMap ma, mb;
     constexpr int BN = kOzBN;
     if (!tc_make_map_16bit(&ma, xs, kSlices * M, K, ldk, tcg::kTM, true) ||

@@ -397,7 +397,7 @@ int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = fal
     CK(cudaEventRecord(h->era, h->stream));
     if (launch_reinv_assemble(h->ds, k, h->geo, h->stream, refined ? 0 : 1, !compact)) {
         h->reinv_tc++;
-        h->launches += 4;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
+        h->launches += 2;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
     }
     launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible);
     CK(cudaGetLastError());
