@@ -144,11 +144,17 @@ __global__ void __launch_bounds__(kGemmThreads, kMinBlocks)
 //   tfull[a]            MMA -> epilogue: accumulator a holds a finished tile;
 //   tempty[a]           epilogue -> MMA: accumulator a was read (one arrival
 //                       per epilogue warp).
+// Eight epilogue warps (2-9): the two warps of a TMEM lane quarter (w and w + 4)
+// take alternate 32-column chunks, so four warps per scheduler hide the
+// latency of the epilogue's dependent integer chains and shuffles.
 // Every wait is bounded.  On a timeout the kernel records kErrTimeout, the
 // producer waits (bounded) for the loads it issued, the MMA issuer for its
 // MMAs, and the TMEM is freed.
+constexpr int kGemmThreadsP = 320;  // warp 0 TMA, warp 1 MMA, the rest epilogue
+constexpr int kEpiPerQuarterP = (kGemmThreadsP - 64) / 128;  // epilogue warps per TMEM lane quarter
+
 template <int BN, int kStages, bool kBF16, class Epi>
-__global__ void __launch_bounds__(kGemmThreads, 2)
+__global__ void __launch_bounds__(kGemmThreadsP, 2)
     k_tc_gemm_p(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb, Epi epi, int M,
                 int N, int K, int32_t* err) {
     static_assert(2 * 2 * BN <= 512, "two accumulators for each of two co-resident CTAs");
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2)
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(&tfull[a], 1);
-            tc::mbar_init(&tempty[a], 4);
+            tc::mbar_init(&tempty[a], (kGemmThreadsP - 64) / 32);
         }
         tc::mbar_init(mdone, 1);
         tc::fence_barrier_init();
@@ -246,6 +252,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2)
     } else {
         const int lg = warp & 3;  // TMEM lane group of this warp
         const int trow = lg * 32 + lane;
+        const int cfirst = 32 * ((warp - 2) >> 2);  // the quarter's warps take chunks cfirst, + 32 kEpiPerQuarterP, ...
         int i = 0;
         for (int t = blockIdx.x; t < ntiles && !fail; t += gridDim.x, ++i) {
             const int a = i & 1;
@@ -256,7 +263,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2)
             tc::tc_fence_after();
             const int m0 = (t / ntn) * kTM, n0 = (t % ntn) * BN;
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            for (int c0 = cfirst; c0 < BN; c0 += 32 * kEpiPerQuarterP) {
                 float v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(a * BN + c0), v);
                 epi(trow, m0, n0, c0, v);
@@ -293,7 +300,7 @@ cudaError_t launch_tc_gemm_p(const CUtensorMap& ma, const CUtensorMap& mb, const
     }
     const int tiles = ((N + BN - 1) / BN) * ((M + kTM - 1) / kTM);
     const int grid = tiles < 2 * sms ? tiles : 2 * sms;
-    k_tc_gemm_p<BN, kStages, kBF16, Epi><<<grid, kGemmThreads, L::kBytes, st>>>(ma, mb, epi, M, N, K, err);
+    k_tc_gemm_p<BN, kStages, kBF16, Epi><<<grid, kGemmThreadsP, L::kBytes, st>>>(ma, mb, epi, M, N, K, err);
     return cudaGetLastError();
 }
 
