@@ -21,11 +21,12 @@
 //
 // Combination (GEMM epilogue).  X Y = 2^{e_i + f_c} sum_{p,q} S_pq 2^{-7(p+q+2)};
 // the pairs with p + q <= 8 are added as 64-bit integers in fixed point with
-// 51 fraction bits relative to 2^{e_i + f_c} (exact left shifts; the right
-// shifts of the 22 pairs with p + q >= 6 round to nearest), the 8 lanes that
+// 51 fraction bits relative to 2^{e_i + f_c} (each pair's S_pq multiplied by its
+// power of two into one of two exact 64-bit accumulators, levels p + q <= 4 and
+// 5..8, the second rounded once to the 51 bits), the 8 lanes that
 // hold p = 0..7 of one row combine by shuffles, and the sum is converted to
 // FP64 once.  Relative to 2^{e_i + f_c}, the error is below K 2^-55 (the
-// remainders r), K 2^-60 (the pairs left out) and 2^-47 (the fixed-point
+// remainders r), K 2^-60 (the pairs left out) and 2^-49 (the fixed-point
 // roundings), plus the final rounding to FP64: of the order of an FP64
 // product's own rounding (bound K 2^-53 sum_l |X_il||Y_lc|) unless a row or
 // column mixes entries of very different size.
@@ -179,18 +180,28 @@ struct OzEpi {
         const int grow = m0 + trow;
         const int i = grow >> 3, p = grow & 7;
         const int cb = (n0 + c0) >> 3;  // n0 + c0 is a multiple of 32
+        // Pair (p, q) of level L = p + q weighs 2^{-7L - 14} (relative to
+        // 2^{e_i + f_c}).  Two exact accumulators take the levels with 32-bit
+        // multipliers: levels 0..4 in units of 2^-42 (mh = 2^{28 - 7L}), levels
+        // 5..8 in units of 2^-70 (ml = 2^{56 - 7L}); a pair left out gets 0.
+        int mh[kSlices], ml[kSlices];
+#pragma unroll
+        for (int q = 0; q < kSlices; ++q) {
+            const int L = p + q;
+            mh[q] = L <= 4 ? 1 << (28 - 7 * L) : 0;
+            ml[q] = (L >= 5 && L <= kLevels) ? 1 << (56 - 7 * L) : 0;
+        }
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-            long long t = 0;
+            long long th = 0, tl = 0;
 #pragma unroll
             for (int q = 0; q < kSlices; ++q) {
-                const int L = p + q;
-                if (L <= kLevels) {
-                    const long long sv = __float2int_rz(v[cc * 8 + q]);  // an exact integer below 2^24
-                    const int sh = kFrac - 14 - 7 * L;
-                    t += sh >= 0 ? (long long)((unsigned long long)sv << sh) : ((sv + (1ll << (-sh - 1))) >> (-sh));
-                }
+                const int sv = __float2int_rz(v[cc * 8 + q]);  // an exact integer below 2^24
+                th += (long long)sv * mh[q];
+                tl += (long long)sv * ml[q];
             }
+            // into units of 2^-kFrac: th exactly, tl rounded to nearest once
+            long long t = th * (1ll << (kFrac - 42)) + ((tl + (1ll << (69 - kFrac))) >> (70 - kFrac));
             t += __shfl_xor_sync(0xffffffffu, t, 1);
             t += __shfl_xor_sync(0xffffffffu, t, 2);
             t += __shfl_xor_sync(0xffffffffu, t, 4);
