@@ -19,17 +19,17 @@
 // lp_tc_gemm).  One GEMM computes all 64 digit pairs: the A operand stacks
 // the slices of X with row 8 i + p, the B operand those of Y with row 8 c + q.
 //
-// Combination (GEMM epilogue).  X Y = 2^{e_i + f_c} sum_{p,q} S_pq 2^{-7(p+q+2)};
-// the pairs with p + q <= 8 are added as 64-bit integers in fixed point with
-// 51 fraction bits relative to 2^{e_i + f_c} (each pair's S_pq multiplied by its
-// power of two into one of two exact 64-bit accumulators, levels p + q <= 4 and
-// 5..8, the second rounded once to the 51 bits), the 8 lanes that
-// hold p = 0..7 of one row combine by shuffles, and the sum is converted to
-// FP64 once.  Relative to 2^{e_i + f_c}, the error is below K 2^-55 (the
-// remainders r), K 2^-60 (the pairs left out) and 2^-49 (the fixed-point
-// roundings), plus the final rounding to FP64: of the order of an FP64
-// product's own rounding (bound K 2^-53 sum_l |X_il||Y_lc|) unless a row or
-// column mixes entries of very different size.
+// Combination (GEMM epilogue).  X Y = 2^{e_i + f_c} sum_{p,q} S_pq 2^{-7(p+q+2)},
+// all 64 pairs, added as 64-bit integers in fixed point with 51 fraction bits
+// relative to 2^{e_i + f_c}: the lane holding digit p of row i pairs adjacent
+// q exactly in 32 bits, sums them into two exact 64-bit partials, and shifts
+// each once to the common point (rounding to nearest); the 8 lanes that hold
+// p = 0..7 of one row combine by shuffles, and the sum is converted to FP64
+// once.  Relative to 2^{e_i + f_c}, the error is below K 2^-55 (the
+// remainders r) and 2^-48 (the 16 roundings of the shifts), plus the final
+// rounding to FP64: of the order of an FP64 product's own rounding (bound
+// K 2^-53 sum_l |X_il||Y_lc|) unless a row or column mixes entries of very
+// different size.
 #include "tc_gemm.cuh"
 
 #include <cuda_bf16.h>
@@ -42,7 +42,6 @@ namespace {
 constexpr int kSlices = 8;   // 7-bit digits per operand (56 bits)
 constexpr int kOzBN = 128;     // GEMM tile columns; two TMEM accumulators of them per CTA
 constexpr int kOzStages = 3;   // shared-memory stages (two persistent CTAs per SM)
-constexpr int kLevels = 8;   // digit pairs with p + q <= kLevels are combined
 constexpr int kFrac = 51;    // fraction bits of the fixed-point combination
 constexpr int kNoDigits = INT_MIN / 4;  // exponent of an all-zero row or column
 
@@ -180,38 +179,34 @@ struct OzEpi {
         const int grow = m0 + trow;
         const int i = grow >> 3, p = grow & 7;
         const int cb = (n0 + c0) >> 3;  // n0 + c0 is a multiple of 32
-        // Pair (p, q) of level L = p + q weighs 2^{-7L - 14} (relative to
-        // 2^{e_i + f_c}).  Two exact accumulators take the levels with 32-bit
-        // multipliers: levels 0..4 in units of 2^-42 (mh = 2^{28 - 7L}), levels
-        // 5..8 in units of 2^-70 (ml = 2^{56 - 7L}); a pair left out gets 0.
-        int mh[kSlices], ml[kSlices];
-#pragma unroll
-        for (int q = 0; q < kSlices; ++q) {
-            const int L = p + q;
-            mh[q] = L <= 4 ? 1 << (28 - 7 * L) : 0;
-            ml[q] = (L >= 5 && L <= kLevels) ? 1 << (56 - 7 * L) : 0;
-        }
+        // This lane holds S_pq, q = 0..7, of 4 outputs.  In units of 2^-kFrac
+        // its share is 2^{-7p} sum_q S_pq 2^{kFrac - 14 - 7q}; adjacent digits
+        // pair exactly in 32 bits (w = 128 S_pq + S_p,q+1, |w| < 2^31 for
+        // K <= 1024), and two exact 64-bit sums of two pairs each, a1 (q < 4)
+        // and a2 (q >= 4), give the share as a1 2^{16 - 7p} + a2 2^{-12 - 7p}.
+        static_assert(kFrac == 51, "the pair weights below are for 51 fraction bits");
+        const int s1 = 7 * p, s2 = 12 + 7 * p;
+        const long long r1 = p ? 1ll << (s1 - 1) : 0ll, r2 = 1ll << (s2 - 1);  // round to nearest
+        long long mine = 0;  // the sum of output cb + p (lanes p < 4)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-            long long th = 0, tl = 0;
+            int w[4];
 #pragma unroll
-            for (int q = 0; q < kSlices; ++q) {
-                const int sv = __float2int_rz(v[cc * 8 + q]);  // an exact integer below 2^24
-                th += (long long)sv * mh[q];
-                tl += (long long)sv * ml[q];
-            }
-            // into units of 2^-kFrac: th exactly, tl rounded to nearest once
-            long long t = th * (1ll << (kFrac - 42)) + ((tl + (1ll << (69 - kFrac))) >> (70 - kFrac));
+            for (int j = 0; j < 4; ++j)
+                w[j] = __float2int_rz(v[cc * 8 + 2 * j]) * 128 + __float2int_rz(v[cc * 8 + 2 * j + 1]);
+            const long long a1 = (long long)w[0] * 16384 + w[1], a2 = (long long)w[2] * 16384 + w[3];
+            long long t = ((a1 * 65536 + r1) >> s1) + ((a2 + r2) >> s2);
             t += __shfl_xor_sync(0xffffffffu, t, 1);
             t += __shfl_xor_sync(0xffffffffu, t, 2);
             t += __shfl_xor_sync(0xffffffffu, t, 4);
-            const int c = cb + cc;
-            if (p == cc && i < M && c < N) {
-                double val = 0.0;
-                const int ei = ex[i], fc = ey[c];
-                if (t != 0 && ei != kNoDigits && fc != kNoDigits) val = ll_scaled(negate ? -t : t, ei + fc - kFrac);
-                out[(size_t)i * ldo + c] = val;
-            }
+            if (p == cc) mine = t;
+        }
+        const int c = cb + p;
+        if (p < 4 && i < M && c < N) {
+            double val = 0.0;
+            const int ei = ex[i], fc = ey[c];
+            if (mine != 0 && ei != kNoDigits && fc != kNoDigits) val = ll_scaled(negate ? -mine : mine, ei + fc - kFrac);
+            out[(size_t)i * ldo + c] = val;
         }
     }
 };
