@@ -57,7 +57,7 @@ __device__ int block_excl_scan(int flag, int* total) {
     return excl;
 }
 
-__global__ void __launch_bounds__(kClassifyThreads) k_classify(DevState s) {
+__global__ void __launch_bounds__(kClassifyThreads) k_classify(DevState s, int k_expect) {
     const int m = s.p.m, n = s.p.n;
     int ks = 0, kr = 0, kl = 0;
     for (int c0 = 0; c0 < m; c0 += blockDim.x) {
@@ -83,12 +83,14 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(DevState s) {
     }
     if (threadIdx.x == 0) {
         s.ctrl->k_struct = ks;
-        if (ks != kr || ks + kl != m) s.ctrl->err = kErrBadIndex;
+        s.ctrl->refine_rej = 0;
+        if (ks != kr || ks + kl != m || (k_expect >= 0 && ks != k_expect)) s.ctrl->err = kErrBadIndex;
     }
 }
 
 // B11[a][t] = A[R[a], J[t]] stored column-major: M[t*k + a].
 __global__ void k_gather(DevState s, int k) {
+    if (s.ctrl->err != kErrNone) return;
     const size_t total = (size_t)k * k;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
@@ -559,8 +561,9 @@ __global__ void k_refine_add(DevState s, int k) {
 }
 
 // ||R||_inf from the partial row sums (each row summed in tile order) into
-// ctrl->refine_res; a NaN row counts as infinite.
-__global__ void __launch_bounds__(1024) k_refine_norm(DevState s, int k, int ntc) {
+// ctrl->refine_res, and ctrl->refine_rej = 1 above tol; a NaN row counts as
+// infinite.
+__global__ void __launch_bounds__(1024) k_refine_norm(DevState s, int k, int ntc, double tol) {
     __shared__ double wmax[32];
     const double* part = s.rv_W + (size_t)k * k;
     double mx = 0.0;
@@ -577,7 +580,9 @@ __global__ void __launch_bounds__(1024) k_refine_norm(DevState s, int k, int ntc
     if (threadIdx.x == 0) {
         double m = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
-        s.ctrl->refine_res = s.ctrl->err == kErrNone ? m : DBL_MAX;
+        const double res = s.ctrl->err == kErrNone ? m : DBL_MAX;
+        s.ctrl->refine_res = res;
+        s.ctrl->refine_rej = res <= tol ? 0 : 1;
     }
 }
 
@@ -765,19 +770,19 @@ __global__ void __launch_bounds__(1024) k_reinv_close(DevState s, int check_feas
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += sz[w]; b |= sbad[w]; }
         Ctrl* C = s.ctrl;
         C->z = t;
-        C->n_reinv++;
+        if (!C->refine_rej) C->n_reinv++;  // a rejected refinement is redone by elimination
         C->nsb = C->k_struct;
         C->pending = 0;
         C->ticket_price = C->ticket_update = C->ticket_pivot = 0;
-        if (check_feasible && b && C->err == kErrNone) C->err = kErrInfeasibleStart;
+        if (check_feasible && b && C->err == kErrNone && !C->refine_rej) C->err = kErrInfeasibleStart;
         C->status = (C->it >= s.p.max_iters) ? kIterLimit : kRunning;
     }
 }
 
 }  // namespace
 
-void launch_reinv_classify(const DevState& s, cudaStream_t st) {
-    k_classify<<<1, kClassifyThreads, 0, st>>>(s);
+void launch_reinv_classify(const DevState& s, int k_expect, cudaStream_t st) {
+    k_classify<<<1, kClassifyThreads, 0, st>>>(s, k_expect);
 }
 
 int reinv_gj_launches(int k) {
@@ -848,7 +853,8 @@ bool refine_fits(int k, int m) { return k > 0 && 3 * (size_t)k * k <= (size_t)m 
 static bool refine_on_tc(const DevState& s, int k) { return s.p.reinvert_tc && s.oz_xs && oz_fits(k); }
 
 // Returns the number of kernels launched.
-int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st) {
+int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, double tol,
+                          cudaStream_t st) {
     const size_t kk = (size_t)k * k;
     int blocks = (int)((kk + 255) / 256);
     if (blocks > 4096) blocks = 4096;
@@ -858,13 +864,13 @@ int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live
         oz_refine_residual_product(s.rv_M, s.rv_M + kk, k, s.rv_M + 2 * kk, s.oz_xs, s.oz_ys, s.oz_ex, s.oz_ey,
                                    &s.ctrl->err, st) == cudaSuccess) {
         k_refine_finish_residual<<<(k + 7) / 8, 256, 0, st>>>(s, k);
-        k_refine_norm<<<1, 1024, 0, st>>>(s, k, 1);
+        k_refine_norm<<<1, 1024, 0, st>>>(s, k, 1, tol);
         return 7;
     }
     (void)cudaGetLastError();
     const int nt = (k + kRT - 1) / kRT;
     k_refine_gemm<0><<<dim3(nt, nt), kRT * kRT, 0, st>>>(s, k);
-    k_refine_norm<<<1, 1024, 0, st>>>(s, k, nt);
+    k_refine_norm<<<1, 1024, 0, st>>>(s, k, nt, tol);
     return 4;
 }
 

@@ -103,6 +103,8 @@ struct Ctrl {
     int32_t crash;         // warm-start crash: 1 running, 2 done
     int32_t crash_t;       // next position in the crash list
     int32_t crash_n;       // entries of the crash list
+    int32_t refine_rej;    // reinversion by refinement: the residual was above the tolerance (the
+                           // rebuild is discarded and redone by elimination)
 };
 
 // Per-CTA ratio-test record of k_iterate: the CTA's smallest ratio, and its
@@ -302,7 +304,8 @@ void launch_csc_fill(const double* A_cm, int m, int n, int ld, const int64_t* pt
                      cudaStream_t st);
 
 // ---- reinversion (kernels_reinv.cu) -------------------------------------------
-void launch_reinv_classify(const DevState& s, cudaStream_t st);
+// k_expect >= 0: the structural count the host expects (err = kErrBadIndex otherwise)
+void launch_reinv_classify(const DevState& s, int k_expect, cudaStream_t st);
 void launch_reinv_gj(const DevState& s, int k, const Geometry& g, cudaStream_t st);
 int reinv_gj_launches(int k);
 int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStream_t st, int from_gj, bool dense_rows);
@@ -325,7 +328,8 @@ cudaError_t oz_refine_residual_product(const double* B11_cm, const double* Y0, i
                                        int32_t* err, cudaStream_t st);
 cudaError_t oz_refine_update_product(const double* Y0, const double* R, int k, double* P, __nv_bfloat16* xs,
                                      __nv_bfloat16* ys, int32_t* ex, int32_t* ey, int32_t* err, cudaStream_t st);
-int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st);
+int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, double tol,
+                          cudaStream_t st);
 int launch_refine_apply(const DevState& s, int k, cudaStream_t st);
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible);
 int occupancy_price(int ld);

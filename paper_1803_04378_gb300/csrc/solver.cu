@@ -368,37 +368,36 @@ int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = fal
     const bool compact = to_struct && h->structured;
     TRY(ooc_flush(h));  // the rebuild reads and writes B^-1 in host memory
     h->ooc_primed = false;
+    // A refinement is queued without reading the control block in between:
+    // k is the structural count of the last read (the classification checks
+    // it), and the residual test is taken on the device; a residual above the
+    // tolerance is seen at the end, and the rebuild is then redone by
+    // elimination.
+    const int k_host = h->h_ctrl->nsb;
+    const bool try_refine =
+        refine && h->opt.reinvert_refine && h->h_ctrl->pending == 0 && refine_fits(k_host, h->m);
     CK(cudaEventRecord(h->er0, h->stream));
-    launch_reinv_classify(h->ds, h->stream);
-    TRY(read_ctrl(h));
-    if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
-    const int k = h->h_ctrl->k_struct;
-    CK(cudaEventRecord(h->erg, h->stream));
-    bool refined = false;
-    if (refine && h->opt.reinvert_refine && h->h_ctrl->pending == 0 && refine_fits(k, h->m)) {
-        const bool from_struct = h->structured && h->s_ready;
-        h->launches += launch_refine_residual(h->ds, k, from_struct ? 1 : 0, h->h_ctrl->k_live, h->h_ctrl->map_par,
-                                              h->stream);
-        CK(cudaGetLastError());
+    launch_reinv_classify(h->ds, try_refine ? k_host : -1, h->stream);
+    int k = k_host;
+    if (!try_refine) {
         TRY(read_ctrl(h));
         if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
-        h->refine_res_max = std::max(h->refine_res_max, h->h_ctrl->refine_res);
-        if (h->h_ctrl->refine_res <= h->opt.refine_tol) {
-            h->launches += launch_refine_apply(h->ds, k, h->stream);
-            h->reinv_refined++;
-            refined = true;
-        }
+        k = h->h_ctrl->k_struct;
     }
-    if (!refined) {
+    CK(cudaEventRecord(h->erg, h->stream));
+    if (try_refine) {
+        const bool from_struct = h->structured && h->s_ready;
+        h->launches += launch_refine_residual(h->ds, k, from_struct ? 1 : 0, h->h_ctrl->k_live, h->h_ctrl->map_par,
+                                              h->opt.refine_tol, h->stream);
+        h->launches += launch_refine_apply(h->ds, k, h->stream);
+    } else {
         launch_reinv_gj(h->ds, k, h->geo, h->stream);
         h->launches += reinv_gj_launches(k);
     }
     h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 3 - (compact ? 1 : 0);
     CK(cudaEventRecord(h->era, h->stream));
-    if (launch_reinv_assemble(h->ds, k, h->geo, h->stream, refined ? 0 : 1, !compact)) {
-        h->reinv_tc++;
-        h->launches += 2;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
-    }
+    const int tc = launch_reinv_assemble(h->ds, k, h->geo, h->stream, try_refine ? 0 : 1, !compact);
+    if (tc) h->launches += 2;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
     launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible);
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->er1, h->stream));
@@ -412,7 +411,19 @@ int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = fal
     h->reinv_asm_s += ma * 1e-3;
     h->primed = false;
     h->s_ready = false;
+    if (try_refine && h->h_ctrl->err == kErrBadIndex && h->h_ctrl->k_struct != k_host) {
+        // the basis held another structural count than the host's: nothing was
+        // rebuilt (every kernel after the classification stopped); redo by elimination
+        CK(cudaMemsetAsync(&h->ds.ctrl->err, 0, sizeof(int32_t), h->stream));
+        return reinvert(h, check_feasible, false, to_struct);
+    }
     if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
+    if (try_refine) {
+        h->refine_res_max = std::max(h->refine_res_max, h->h_ctrl->refine_res);
+        if (h->h_ctrl->refine_rej) return reinvert(h, check_feasible, false, to_struct);
+        h->reinv_refined++;
+    }
+    if (tc) h->reinv_tc++;
     if (compact) {
         launch_struct_enter(h->ds, h->s_force ? 1 : 0, h->s_relayout, h->stream, true);
         CK(cudaGetLastError());
