@@ -32,59 +32,68 @@ namespace {
 constexpr int kClassifyThreads = 1024;
 constexpr int kStepThreads = 256;
 
-// exclusive prefix sum of a 0/1 flag across a 1024-thread block
-__device__ int block_excl_scan(int flag, int* total) {
-    __shared__ int wsum[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    const unsigned bal = __ballot_sync(0xffffffffu, flag);
-    const int inwarp = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) wsum[w] = __popc(bal);
+// The three lists in increasing position order, each thread taking a run of
+// consecutive positions: counts, one block scan of the three counts, then the
+// writes.
+__global__ void __launch_bounds__(kClassifyThreads) k_classify(DevState s, int k_expect) {
+    __shared__ int wsum[3][32];
+    const int m = s.p.m, n = s.p.n;
+    const int per = (m + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int p0 = min(m, (int)threadIdx.x * per), p1 = min(m, p0 + per);
+    int cs = 0, cl = 0;
+    for (int p = p0; p < p1; ++p) {
+        cs += s.basis[p] < n ? 1 : 0;
+        cl += s.pos[n + p] >= 0 ? 1 : 0;
+    }
+    const int cr = (p1 - p0) - cl;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int is = cs, il = cl, ir = cr;  // inclusive scans within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, is, o), b = __shfl_up_sync(0xffffffffu, il, o),
+                  c = __shfl_up_sync(0xffffffffu, ir, o);
+        if (lane >= o) { is += a; il += b; ir += c; }
+    }
+    if (lane == 31) { wsum[0][w] = is; wsum[1][w] = il; wsum[2][w] = ir; }
     __syncthreads();
     if (w == 0) {
-        int v = lane < nw ? wsum[lane] : 0;
+        int a = lane < nw ? wsum[0][lane] : 0, b = lane < nw ? wsum[1][lane] : 0, c = lane < nw ? wsum[2][lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
+            const int ua = __shfl_up_sync(0xffffffffu, a, o), ub = __shfl_up_sync(0xffffffffu, b, o),
+                      uc = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) { a += ua; b += ub; c += uc; }
         }
-        wsum[lane] = v;
+        if (lane < nw) { wsum[0][lane] = a; wsum[1][lane] = b; wsum[2][lane] = c; }
     }
     __syncthreads();
-    const int excl = (w ? wsum[w - 1] : 0) + inwarp;
-    *total = wsum[nw - 1];
-    __syncthreads();
-    return excl;
-}
-
-__global__ void __launch_bounds__(kClassifyThreads) k_classify(DevState s, int k_expect) {
-    const int m = s.p.m, n = s.p.n;
-    int ks = 0, kr = 0, kl = 0;
-    for (int c0 = 0; c0 < m; c0 += blockDim.x) {
-        const int p = c0 + threadIdx.x;
-        const int var = p < m ? s.basis[p] : 0;
-        const int fs = (p < m && var < n) ? 1 : 0;
-        int tot;
-        const int e1 = block_excl_scan(fs, &tot);
-        if (fs) s.rv_struct_pos[ks + e1] = p;
-        if (p < m) s.rv_b_of_pos[p] = fs ? ks + e1 : -1;
-        ks += tot;
-        // rows (index p used as a row here): slack basic -> S list, else R list
-        const int fl = (p < m && s.pos[n + p] >= 0) ? 1 : 0;
-        const int e2 = block_excl_scan(fl, &tot);
-        if (fl) s.rv_slack_pos[kl + e2] = p;
-        if (p < m) s.rv_g_of_row[p] = fl ? kl + e2 : -1;
-        kl += tot;
-        const int fr = (p < m && s.pos[n + p] < 0) ? 1 : 0;
-        const int e3 = block_excl_scan(fr, &tot);
-        if (p < m) s.rv_row_index[p] = fr ? kr + e3 : -1;
-        if (fr) s.rv_rows[kr + e3] = p;
-        kr += tot;
+    // rows (index p used as a row here): slack basic -> S list, else R list
+    int ks = (w ? wsum[0][w - 1] : 0) + is - cs;
+    int kl = (w ? wsum[1][w - 1] : 0) + il - cl;
+    int kr = (w ? wsum[2][w - 1] : 0) + ir - cr;
+    for (int p = p0; p < p1; ++p) {
+        if (s.basis[p] < n) {
+            s.rv_struct_pos[ks] = p;
+            s.rv_b_of_pos[p] = ks++;
+        } else {
+            s.rv_b_of_pos[p] = -1;
+        }
+        if (s.pos[n + p] >= 0) {
+            s.rv_slack_pos[kl] = p;
+            s.rv_g_of_row[p] = kl++;
+            s.rv_row_index[p] = -1;
+        } else {
+            s.rv_g_of_row[p] = -1;
+            s.rv_row_index[p] = kr;
+            s.rv_rows[kr++] = p;
+        }
     }
     if (threadIdx.x == 0) {
-        s.ctrl->k_struct = ks;
+        const int ts = wsum[0][nw - 1], tl = wsum[1][nw - 1], tr = wsum[2][nw - 1];
+        s.ctrl->k_struct = ts;
         s.ctrl->refine_rej = 0;
-        if (ks != kr || ks + kl != m || (k_expect >= 0 && ks != k_expect)) s.ctrl->err = kErrBadIndex;
+        s.ctrl->refine_res = 0.0;
+        if (ts != tr || ts + tl != m || (k_expect >= 0 && ts != k_expect)) s.ctrl->err = kErrBadIndex;
     }
 }
 
@@ -529,8 +538,10 @@ __global__ void __launch_bounds__(kRT * kRT) k_refine_gemm(DevState s, int k) {
 // Tensor-core form of the two products (reinvert_tc, k <= 1024): the exact
 // 7-bit-sliced products of ozaki.cu give P = -(B11 Y0) into R's place and
 // P = Y0 R into rv_W; these kernels finish them.
-// R = I - B11 Y0 = I + P in place, and each row's sum of |R| (columns in order,
-// one warp per row) as its single partial for k_refine_norm.
+// R = I - B11 Y0 = I + P in place, and ||R||_inf into ctrl->refine_res (reset
+// to 0 by the classification): each row's sum of |R| (columns in order, one
+// warp per row; NaN counts as DBL_MAX) by an atomic max on the bits of the
+// non-negative doubles, which order as unsigned integers.
 __global__ void __launch_bounds__(256) k_refine_finish_residual(DevState s, int k) {
     if (s.ctrl->err != kErrNone) return;
     const size_t kk = (size_t)k * k;
@@ -547,7 +558,9 @@ __global__ void __launch_bounds__(256) k_refine_finish_residual(DevState s, int 
             t += fabs(v);
         }
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) s.rv_W[kk + i] = t;
+        if (lane == 0)
+            atomicMax(reinterpret_cast<unsigned long long*>(&s.ctrl->refine_res),
+                      (unsigned long long)__double_as_longlong(t >= 0.0 ? t : DBL_MAX));
     }
 }
 
@@ -561,9 +574,8 @@ __global__ void k_refine_add(DevState s, int k) {
 }
 
 // ||R||_inf from the partial row sums (each row summed in tile order) into
-// ctrl->refine_res, and ctrl->refine_rej = 1 above tol; a NaN row counts as
-// infinite.
-__global__ void __launch_bounds__(1024) k_refine_norm(DevState s, int k, int ntc, double tol) {
+// ctrl->refine_res; a NaN row counts as infinite.
+__global__ void __launch_bounds__(1024) k_refine_norm(DevState s, int k, int ntc) {
     __shared__ double wmax[32];
     const double* part = s.rv_W + (size_t)k * k;
     double mx = 0.0;
@@ -580,9 +592,7 @@ __global__ void __launch_bounds__(1024) k_refine_norm(DevState s, int k, int ntc
     if (threadIdx.x == 0) {
         double m = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
-        const double res = s.ctrl->err == kErrNone ? m : DBL_MAX;
-        s.ctrl->refine_res = res;
-        s.ctrl->refine_rej = res <= tol ? 0 : 1;
+        s.ctrl->refine_res = s.ctrl->err == kErrNone ? m : DBL_MAX;
     }
 }
 
@@ -694,12 +704,12 @@ __global__ void k_assemble_rows(DevState s, int k) {
 }
 
 // bbar from the structure: structural position of b: sum_a B11^-1[b][a] b[R[a]];
-// slack of row s: b[s] + sum_a C[g][a] b[R[a]] (warp per basis position)
-__global__ void k_bbar_struct(DevState s, int k) {
-    if (s.ctrl->err != kErrNone) return;
+// slack of row s: b[s] + sum_a C[g][a] b[R[a]] (warp per basis position; the
+// part's blocks bid = 0 .. nb-1)
+__device__ void bbar_struct_part(const DevState& s, int k, int bid, int nb) {
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (bid * (int)blockDim.x + (int)threadIdx.x) >> 5;
+    const int nw = (nb * (int)blockDim.x) >> 5;
     const int m = s.p.m, n = s.p.n;
     for (int p = gw; p < m; p += nw) {
         const int v = s.basis[p];
@@ -721,17 +731,16 @@ __global__ void k_bbar_struct(DevState s, int k) {
 // y[R[a]] = sum_b c_J[b] B11^-1[b][a] (one warp per a: lane-strided partial
 // sums in increasing b, combined in a fixed shuffle order); y = 0 on rows with
 // a basic slack
-__global__ void k_duals_struct(DevState s, int k) {
-    if (s.ctrl->err != kErrNone) return;
+__device__ void duals_struct_part(const DevState& s, int k, int bid, int nb) {
     const int m = s.p.m;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.p.ld; i += gridDim.x * blockDim.x) {
+    for (int i = bid * (int)blockDim.x + (int)threadIdx.x; i < s.p.ld; i += nb * (int)blockDim.x) {
         if (i >= m || s.rv_row_index[i] < 0) {
             s.y[i] = 0.0;
             s.y32[i] = 0.f;
         }
     }
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (bid * (int)blockDim.x + (int)threadIdx.x) >> 5, nw = (nb * (int)blockDim.x) >> 5;
     for (int a = gw; a < k; a += nw) {
         double acc = 0.0;
         for (int b = lane; b < k; b += 32) acc = fma(s.rv_cJ[b], s.rv_W[(size_t)b * k + a], acc);
@@ -745,30 +754,57 @@ __global__ void k_duals_struct(DevState s, int k) {
     }
 }
 
-// objective, feasibility of the rebuilt basis, status for the next iteration
-__global__ void __launch_bounds__(1024) k_reinv_close(DevState s, int check_feasible) {
-    __shared__ double sz[32];
-    __shared__ int sbad[32];
+constexpr int kFinishThreads = 256;
+constexpr int kCloseLanes = 1024;  // the objective is summed as by 1024 threads (32 warp totals in order)
+
+// bbar (blocks 0 .. nb_bbar-1) and y (the others) of the rebuilt basis; the
+// last block to finish then takes the objective, the feasibility of the
+// rebuilt basis, the verdict on a refinement (tol >= 0: its residual against
+// tol) and the status for the next iteration.
+__global__ void __launch_bounds__(kFinishThreads) k_reinv_finish(DevState s, int k, int nb_bbar, int check_feasible,
+                                                                 double tol) {
+    __shared__ double sz[kCloseLanes / 32];
+    __shared__ int sbad[kCloseLanes / 32];
+    __shared__ int last;
+    if (s.ctrl->err == kErrNone) {
+        if ((int)blockIdx.x < nb_bbar) bbar_struct_part(s, k, blockIdx.x, nb_bbar);
+        else duals_struct_part(s, k, blockIdx.x - nb_bbar, gridDim.x - nb_bbar);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&s.ctrl->ticket_reinv, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
     const int m = s.p.m, n = s.p.n;
-    double z = 0.0;
-    int bad = 0;
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
-        const int var = s.basis[p];
-        const double v = s.bbar[p];
-        if (var < n) z = fma(s.c[var], v, z);
-        if (v < -1e-9 * s.p.b_scale) bad = 1;
+    constexpr int kVirt = kCloseLanes / kFinishThreads;  // virtual threads t + j kFinishThreads
+    double z[kVirt];
+    int bad[kVirt];
+#pragma unroll
+    for (int j = 0; j < kVirt; ++j) {
+        z[j] = 0.0;
+        bad[j] = 0;
+        for (int p = threadIdx.x + j * kFinishThreads; p < m; p += kCloseLanes) {
+            const int var = s.basis[p];
+            const double v = __ldcg(s.bbar + p);
+            if (var < n) z[j] = fma(s.c[var], v, z[j]);
+            if (v < -1e-9 * s.p.b_scale) bad[j] = 1;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            z[j] += __shfl_xor_sync(0xffffffffu, z[j], o);
+            bad[j] |= __shfl_xor_sync(0xffffffffu, bad[j], o);
+        }
+        const int vw = (threadIdx.x >> 5) + j * (kFinishThreads / 32);
+        if ((threadIdx.x & 31) == 0) { sz[vw] = z[j]; sbad[vw] = bad[j]; }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        z += __shfl_xor_sync(0xffffffffu, z, o);
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    }
-    if ((threadIdx.x & 31) == 0) { sz[threadIdx.x >> 5] = z; sbad[threadIdx.x >> 5] = bad; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         int b = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += sz[w]; b |= sbad[w]; }
+        for (int w = 0; w < kCloseLanes / 32; ++w) { t += sz[w]; b |= sbad[w]; }
         Ctrl* C = s.ctrl;
+        C->ticket_reinv = 0;
+        if (tol >= 0.0) C->refine_rej = (C->err == kErrNone && C->refine_res <= tol) ? 0 : 1;
         C->z = t;
         if (!C->refine_rej) C->n_reinv++;  // a rejected refinement is redone by elimination
         C->nsb = C->k_struct;
@@ -853,8 +889,7 @@ bool refine_fits(int k, int m) { return k > 0 && 3 * (size_t)k * k <= (size_t)m 
 static bool refine_on_tc(const DevState& s, int k) { return s.p.reinvert_tc && s.oz_xs && oz_fits(k); }
 
 // Returns the number of kernels launched.
-int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, double tol,
-                          cudaStream_t st) {
+int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st) {
     const size_t kk = (size_t)k * k;
     int blocks = (int)((kk + 255) / 256);
     if (blocks > 4096) blocks = 4096;
@@ -864,13 +899,12 @@ int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live
         oz_refine_residual_product(s.rv_M, s.rv_M + kk, k, s.rv_M + 2 * kk, s.oz_xs, s.oz_ys, s.oz_ex, s.oz_ey,
                                    &s.ctrl->err, st) == cudaSuccess) {
         k_refine_finish_residual<<<(k + 7) / 8, 256, 0, st>>>(s, k);
-        k_refine_norm<<<1, 1024, 0, st>>>(s, k, 1, tol);
-        return 7;
+        return 6;
     }
     (void)cudaGetLastError();
     const int nt = (k + kRT - 1) / kRT;
     k_refine_gemm<0><<<dim3(nt, nt), kRT * kRT, 0, st>>>(s, k);
-    k_refine_norm<<<1, 1024, 0, st>>>(s, k, nt, tol);
+    k_refine_norm<<<1, 1024, 0, st>>>(s, k, nt);
     return 4;
 }
 
@@ -918,10 +952,9 @@ int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStrea
     return tc;
 }
 
-void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible) {
-    k_bbar_struct<<<g.sms * 2, 256, 0, st>>>(s, k);
-    k_duals_struct<<<g.sms * 2, 256, 0, st>>>(s, k);
-    k_reinv_close<<<1, 1024, 0, st>>>(s, check_feasible);
+void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible,
+                         double refine_tol) {
+    k_reinv_finish<<<g.sms * 4, kFinishThreads, 0, st>>>(s, k, g.sms * 2, check_feasible, refine_tol);
 }
 
 }  // namespace lpgb

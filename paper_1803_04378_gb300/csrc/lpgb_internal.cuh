@@ -105,6 +105,7 @@ struct Ctrl {
     int32_t crash_n;       // entries of the crash list
     int32_t refine_rej;    // reinversion by refinement: the residual was above the tolerance (the
                            // rebuild is discarded and redone by elimination)
+    int32_t ticket_reinv;  // last-block ticket of k_reinv_finish (reset by the last block)
 };
 
 // Per-CTA ratio-test record of k_iterate: the CTA's smallest ratio, and its
@@ -328,10 +329,11 @@ cudaError_t oz_refine_residual_product(const double* B11_cm, const double* Y0, i
                                        int32_t* err, cudaStream_t st);
 cudaError_t oz_refine_update_product(const double* Y0, const double* R, int k, double* P, __nv_bfloat16* xs,
                                      __nv_bfloat16* ys, int32_t* ex, int32_t* ey, int32_t* err, cudaStream_t st);
-int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, double tol,
-                          cudaStream_t st);
+int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live, int par, cudaStream_t st);
 int launch_refine_apply(const DevState& s, int k, cudaStream_t st);
-void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible);
+// refine_tol >= 0: the rebuild came from a refinement, accepted when its residual is <= refine_tol
+void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible,
+                         double refine_tol);
 int occupancy_price(int ld);
 int occupancy_price_lp(int ld);
 int occupancy_update(int ld);

@@ -185,6 +185,10 @@ struct OzEpi {
         // K <= 1024), and two exact 64-bit sums of two pairs each, a1 (q < 4)
         // and a2 (q >= 4), give the share as a1 2^{16 - 7p} + a2 2^{-12 - 7p}.
         static_assert(kFrac == 51, "the pair weights below are for 51 fraction bits");
+        // the exponents of this lane's output, loaded before the arithmetic
+        const int c = cb + p;
+        const bool mine_out = p < 4 && i < M && c < N;
+        const int ei = mine_out ? __ldg(ex + i) : kNoDigits, fc = mine_out ? __ldg(ey + c) : kNoDigits;
         const int s1 = 7 * p, s2 = 12 + 7 * p;
         const long long r1 = p ? 1ll << (s1 - 1) : 0ll, r2 = 1ll << (s2 - 1);  // round to nearest
         long long mine = 0;  // the sum of output cb + p (lanes p < 4)
@@ -201,10 +205,8 @@ struct OzEpi {
             t += __shfl_xor_sync(0xffffffffu, t, 4);
             if (p == cc) mine = t;
         }
-        const int c = cb + p;
-        if (p < 4 && i < M && c < N) {
+        if (mine_out) {
             double val = 0.0;
-            const int ei = ex[i], fc = ey[c];
             if (mine != 0 && ei != kNoDigits && fc != kNoDigits) val = ll_scaled(negate ? -mine : mine, ei + fc - kFrac);
             out[(size_t)i * ldo + c] = val;
         }

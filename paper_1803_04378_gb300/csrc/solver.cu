@@ -370,9 +370,9 @@ int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = fal
     h->ooc_primed = false;
     // A refinement is queued without reading the control block in between:
     // k is the structural count of the last read (the classification checks
-    // it), and the residual test is taken on the device; a residual above the
-    // tolerance is seen at the end, and the rebuild is then redone by
-    // elimination.
+    // it), and the residual test is taken on the device (k_reinv_finish); a
+    // residual above the tolerance is seen at the end, and the rebuild is then
+    // redone by elimination.
     const int k_host = h->h_ctrl->nsb;
     const bool try_refine =
         refine && h->opt.reinvert_refine && h->h_ctrl->pending == 0 && refine_fits(k_host, h->m);
@@ -388,17 +388,17 @@ int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = fal
     if (try_refine) {
         const bool from_struct = h->structured && h->s_ready;
         h->launches += launch_refine_residual(h->ds, k, from_struct ? 1 : 0, h->h_ctrl->k_live, h->h_ctrl->map_par,
-                                              h->opt.refine_tol, h->stream);
+                                              h->stream);
         h->launches += launch_refine_apply(h->ds, k, h->stream);
     } else {
         launch_reinv_gj(h->ds, k, h->geo, h->stream);
         h->launches += reinv_gj_launches(k);
     }
-    h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 3 - (compact ? 1 : 0);
+    h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 1 - (compact ? 1 : 0);
     CK(cudaEventRecord(h->era, h->stream));
     const int tc = launch_reinv_assemble(h->ds, k, h->geo, h->stream, try_refine ? 0 : 1, !compact);
     if (tc) h->launches += 2;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
-    launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible);
+    launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible, try_refine ? h->opt.refine_tol : -1.0);
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->er1, h->stream));
     TRY(read_ctrl(h));
