@@ -24,8 +24,8 @@
 // relative to 2^{e_i + f_c}: the lane holding digit p of row i pairs adjacent
 // q exactly in 32 bits, sums them into two exact 64-bit partials, and shifts
 // each once to the common point (rounding to nearest); the 8 lanes that hold
-// p = 0..7 of one row combine by shuffles, and the sum is converted to FP64
-// once.  Relative to 2^{e_i + f_c}, the error is below K 2^-55 (the
+// p = 0..7 of one row combine by a reduce-scatter of shuffles, and each sum
+// is converted to FP64 once.  Relative to 2^{e_i + f_c}, the error is below K 2^-55 (the
 // remainders r) and 2^-48 (the 16 roundings of the shifts), plus the final
 // rounding to FP64: of the order of an FP64 product's own rounding (bound
 // K 2^-53 sum_l |X_il||Y_lc|) unless a row or column mixes entries of very
@@ -40,8 +40,10 @@ namespace lpgb {
 namespace {
 
 constexpr int kSlices = 8;   // 7-bit digits per operand (56 bits)
-constexpr int kOzBN = 128;     // GEMM tile columns; two TMEM accumulators of them per CTA
-constexpr int kOzStages = 3;   // shared-memory stages (two persistent CTAs per SM)
+constexpr int kOzBN = 256;     // GEMM tile columns; two TMEM accumulators of them per CTA (all 512)
+constexpr int kOzStages = 4;   // shared-memory stages of 48 KB (one persistent CTA per SM)
+constexpr int kOzEpiWarps = 16;
+constexpr int kOzCtas = 1;
 constexpr int kFrac = 51;    // fraction bits of the fixed-point combination
 constexpr int kNoDigits = INT_MIN / 4;  // exponent of an all-zero row or column
 
@@ -185,13 +187,15 @@ struct OzEpi {
         // K <= 1024), and two exact 64-bit sums of two pairs each, a1 (q < 4)
         // and a2 (q >= 4), give the share as a1 2^{16 - 7p} + a2 2^{-12 - 7p}.
         static_assert(kFrac == 51, "the pair weights below are for 51 fraction bits");
-        // the exponents of this lane's output, loaded before the arithmetic
-        const int c = cb + p;
-        const bool mine_out = p < 4 && i < M && c < N;
+        // The 8 lanes of a row reduce-scatter their 4 sums: lanes 2 cc and
+        // 2 cc + 1 end with output cb + cc (exact integer adds, so the order
+        // does not change the result); the even lane converts and stores it.
+        const int c = cb + (p >> 1);
+        const bool mine_out = (p & 1) == 0 && i < M && c < N;
         const int ei = mine_out ? __ldg(ex + i) : kNoDigits, fc = mine_out ? __ldg(ey + c) : kNoDigits;
         const int s1 = 7 * p, s2 = 12 + 7 * p;
         const long long r1 = p ? 1ll << (s1 - 1) : 0ll, r2 = 1ll << (s2 - 1);  // round to nearest
-        long long mine = 0;  // the sum of output cb + p (lanes p < 4)
+        long long t[4];
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
             int w[4];
@@ -199,12 +203,17 @@ struct OzEpi {
             for (int j = 0; j < 4; ++j)
                 w[j] = __float2int_rz(v[cc * 8 + 2 * j]) * 128 + __float2int_rz(v[cc * 8 + 2 * j + 1]);
             const long long a1 = (long long)w[0] * 16384 + w[1], a2 = (long long)w[2] * 16384 + w[3];
-            long long t = ((a1 * 65536 + r1) >> s1) + ((a2 + r2) >> s2);
-            t += __shfl_xor_sync(0xffffffffu, t, 1);
-            t += __shfl_xor_sync(0xffffffffu, t, 2);
-            t += __shfl_xor_sync(0xffffffffu, t, 4);
-            if (p == cc) mine = t;
+            t[cc] = ((a1 * 65536 + r1) >> s1) + ((a2 + r2) >> s2);
         }
+        const bool hi2 = (p & 4) != 0, hi1 = (p & 2) != 0;
+        long long u[2];  // outputs 2 hi2 + j, summed over lanes p and p ^ 4
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const long long give = hi2 ? t[j] : t[2 + j];
+            u[j] = (hi2 ? t[2 + j] : t[j]) + __shfl_xor_sync(0xffffffffu, give, 4);
+        }
+        long long mine = (hi1 ? u[1] : u[0]) + __shfl_xor_sync(0xffffffffu, hi1 ? u[0] : u[1], 2);
+        mine += __shfl_xor_sync(0xffffffffu, mine, 1);
         if (mine_out) {
             double val = 0.0;
             if (mine != 0 && ei != kNoDigits && fc != kNoDigits) val = ll_scaled(negate ? -mine : mine, ei + fc - kFrac);
@@ -253,7 +262,8 @@ cudaError_t oz_product(SX sx, SY sy, int M, int N, int K, double* out, int ldo, 
         !tc_make_map_16bit(&mb, ys, kSlices * N, K, ldk, BN, true))
         return cudaErrorInvalidValue;
     const OzEpi epi{out, ldo, M, N, ex, ey, negate};
-    return tcg::launch_tc_gemm_p<BN, kOzStages, true>(ma, mb, epi, kSlices * M, kSlices * N, K, err, st);
+    return tcg::launch_tc_gemm_p<BN, kOzStages, kOzEpiWarps, kOzCtas, true>(ma, mb, epi, kSlices * M, kSlices * N, K,
+                                                                           err, st);
 }
 
 }  // namespace

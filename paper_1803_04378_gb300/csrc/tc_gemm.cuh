@@ -144,20 +144,24 @@ __global__ void __launch_bounds__(kGemmThreads, kMinBlocks)
 //   tfull[a]            MMA -> epilogue: accumulator a holds a finished tile;
 //   tempty[a]           epilogue -> MMA: accumulator a was read (one arrival
 //                       per epilogue warp).
-// Eight epilogue warps (2-9): the two warps of a TMEM lane quarter (w and w + 4)
-// take alternate 32-column chunks, so four warps per scheduler hide the
-// latency of the epilogue's dependent integer chains and shuffles.
+// kEpiWarps epilogue warps (2 .. kEpiWarps + 1): the kEpiWarps / 4 warps of a
+// TMEM lane quarter take alternate 32-column chunks, so that several warps per
+// scheduler hide the latency of the epilogue's dependent integer chains and
+// shuffles; kCtas CTAs share an SM (their TMEM, 2 BN columns each, must fit
+// the SM's 512).
 // Every wait is bounded.  On a timeout the kernel records kErrTimeout, the
 // producer waits (bounded) for the loads it issued, the MMA issuer for its
 // MMAs, and the TMEM is freed.
-constexpr int kGemmThreadsP = 320;  // warp 0 TMA, warp 1 MMA, the rest epilogue
-constexpr int kEpiPerQuarterP = (kGemmThreadsP - 64) / 128;  // epilogue warps per TMEM lane quarter
+template <int kEpiWarps>
+constexpr int gemm_p_threads() { return 64 + 32 * kEpiWarps; }
 
-template <int BN, int kStages, bool kBF16, class Epi>
-__global__ void __launch_bounds__(kGemmThreadsP, 2)
+template <int BN, int kStages, int kEpiWarps, int kCtas, bool kBF16, class Epi>
+__global__ void __launch_bounds__(gemm_p_threads<kEpiWarps>(), kCtas)
     k_tc_gemm_p(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb, Epi epi, int M,
                 int N, int K, int32_t* err) {
-    static_assert(2 * 2 * BN <= 512, "two accumulators for each of two co-resident CTAs");
+    static_assert(kCtas * 2 * BN <= 512, "two accumulators for each co-resident CTA");
+    static_assert(kEpiWarps % 4 == 0 && kEpiWarps >= 4, "whole TMEM lane quarters");
+    constexpr int kEpiPerQuarter = kEpiWarps / 4;
     using L = GemmSmem<BN, kStages>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(kGemmThreadsP, 2)
         }
         for (int a = 0; a < 2; ++a) {
             tc::mbar_init(&tfull[a], 1);
-            tc::mbar_init(&tempty[a], (kGemmThreadsP - 64) / 32);
+            tc::mbar_init(&tempty[a], kEpiWarps);
         }
         tc::mbar_init(mdone, 1);
         tc::fence_barrier_init();
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(kGemmThreadsP, 2)
     } else {
         const int lg = warp & 3;  // TMEM lane group of this warp
         const int trow = lg * 32 + lane;
-        const int cfirst = 32 * ((warp - 2) >> 2);  // the quarter's warps take chunks cfirst, + 32 kEpiPerQuarterP, ...
+        const int cfirst = 32 * ((warp - 2) >> 2);  // the quarter's warps take chunks cfirst, + 32 kEpiPerQuarter, ...
         int i = 0;
         for (int t = blockIdx.x; t < ntiles && !fail; t += gridDim.x, ++i) {
             const int a = i & 1;
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(kGemmThreadsP, 2)
             tc::tc_fence_after();
             const int m0 = (t / ntn) * kTM, n0 = (t % ntn) * BN;
 #pragma unroll 1
-            for (int c0 = cfirst; c0 < BN; c0 += 32 * kEpiPerQuarterP) {
+            for (int c0 = cfirst; c0 < BN; c0 += 32 * kEpiPerQuarter) {
                 float v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(a * BN + c0), v);
                 epi(trow, m0, n0, c0, v);
@@ -283,12 +287,14 @@ __global__ void __launch_bounds__(kGemmThreadsP, 2)
 }
 
 // Grid of the persistent form: two CTAs per SM, at most one per tile.
-template <int BN, int kStages, bool kBF16, class Epi>
+// Grid of the persistent form: kCtas CTAs per SM, at most one per tile.
+template <int BN, int kStages, int kEpiWarps, int kCtas, bool kBF16, class Epi>
 cudaError_t launch_tc_gemm_p(const CUtensorMap& ma, const CUtensorMap& mb, const Epi& epi, int M, int N, int K,
                              int32_t* err, cudaStream_t st) {
     using L = GemmSmem<BN, kStages>;
     static_assert(L::kBars >= (2 * kStages + 5) * 8 + 4, "barrier area");
-    static cudaError_t attr_rc = cudaFuncSetAttribute(k_tc_gemm_p<BN, kStages, kBF16, Epi>,
+    static_assert(kCtas * (L::kBytes + 1024) <= 232448, "shared memory of the co-resident CTAs");
+    static cudaError_t attr_rc = cudaFuncSetAttribute(k_tc_gemm_p<BN, kStages, kEpiWarps, kCtas, kBF16, Epi>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
     if (attr_rc != cudaSuccess) return attr_rc;
     static int sms = 0;
@@ -299,8 +305,9 @@ cudaError_t launch_tc_gemm_p(const CUtensorMap& ma, const CUtensorMap& mb, const
         if (sms < 1) sms = 1;
     }
     const int tiles = ((N + BN - 1) / BN) * ((M + kTM - 1) / kTM);
-    const int grid = tiles < 2 * sms ? tiles : 2 * sms;
-    k_tc_gemm_p<BN, kStages, kBF16, Epi><<<grid, kGemmThreadsP, L::kBytes, st>>>(ma, mb, epi, M, N, K, err);
+    const int grid = tiles < kCtas * sms ? tiles : kCtas * sms;
+    k_tc_gemm_p<BN, kStages, kEpiWarps, kCtas, kBF16, Epi>
+        <<<grid, gemm_p_threads<kEpiWarps>(), L::kBytes, st>>>(ma, mb, epi, M, N, K, err);
     return cudaGetLastError();
 }
 
