@@ -811,7 +811,8 @@ __global__ void __launch_bounds__(kFinishThreads) k_reinv_finish(DevState s, int
         C->pending = 0;
         C->ticket_price = C->ticket_update = C->ticket_pivot = 0;
         if (check_feasible && b && C->err == kErrNone && !C->refine_rej) C->err = kErrInfeasibleStart;
-        C->status = (C->it >= s.p.max_iters) ? kIterLimit : kRunning;
+        C->status = (C->refine_rej || C->err != kErrNone) ? kRebuildStopped
+                    : (C->it >= s.p.max_iters) ? kIterLimit : kRunning;
     }
 }
 

@@ -30,6 +30,8 @@ constexpr int kOptimal = 1;
 constexpr int kUnbounded = 2;
 constexpr int kIterLimit = 3;
 constexpr int kReinvert = 10;          // host must rebuild B^-1 before continuing
+constexpr int kRebuildStopped = 11;    // a rebuild to be redone by elimination (or one that failed):
+                                       // a launch queued behind it does nothing
 
 // device error codes (Ctrl::err)
 constexpr int kErrNone = 0;

@@ -358,34 +358,43 @@ int ooc_iteration(lp_handle* h) {
 // 2^-52, at the rounding level); above it the basis is eliminated afresh.
 constexpr double kRefineTolMax = 1.0 / 67108864.0;  // 2^-26
 
-// Rebuild B^-1, bbar, y, z from the current basis.  `refine`: the stored
-// inverse is that of the current basis (a periodic reinversion, the last
-// update applied), so B11^-1 may come from one refinement step of it.
-// `to_struct`: the next consumer is the slack-structured engine, which then
-// receives its live columns straight from B11^-1 and the slack rows (the
-// dense B^-1 is not written).
-int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = false) {
-    const bool compact = to_struct && h->structured;
+// What a queued rebuild needs when it is settled.
+struct ReinvQueued {
+    bool try_refine = false;  // B11^-1 by refinement, verdict on the device
+    bool compact = false;     // no dense B^-1: the structured engine follows
+    int tc = 0;               // the slack rows ran on the tensor cores
+    int k_host = 0;           // the structural count the host assumed
+};
+
+// Rebuild B^-1, bbar, y, z from the current basis: queues the kernels (a
+// refinement without reading the control block, elimination after one read of
+// the structural count).  `refine`: the stored inverse is that of the current
+// basis (a periodic reinversion, the last update applied), so B11^-1 may come
+// from one refinement step of it.  `to_struct`: the next consumer is the
+// slack-structured engine, which then receives its live columns straight from
+// B11^-1 and the slack rows (the dense B^-1 is not written).
+//
+// A refinement takes k from the last read (the classification checks it) and
+// its residual test on the device (k_reinv_finish); a residual above the
+// tolerance is seen when the rebuild is settled, and the rebuild is then
+// redone by elimination.  Until then the finishing kernel leaves the status at
+// kRebuildStopped, so that a launch queued behind the rebuild does nothing.
+int reinvert_queue(lp_handle* h, int check_feasible, bool refine, bool to_struct, ReinvQueued* q) {
+    q->compact = to_struct && h->structured;
     TRY(ooc_flush(h));  // the rebuild reads and writes B^-1 in host memory
     h->ooc_primed = false;
-    // A refinement is queued without reading the control block in between:
-    // k is the structural count of the last read (the classification checks
-    // it), and the residual test is taken on the device (k_reinv_finish); a
-    // residual above the tolerance is seen at the end, and the rebuild is then
-    // redone by elimination.
-    const int k_host = h->h_ctrl->nsb;
-    const bool try_refine =
-        refine && h->opt.reinvert_refine && h->h_ctrl->pending == 0 && refine_fits(k_host, h->m);
+    q->k_host = h->h_ctrl->nsb;
+    q->try_refine = refine && h->opt.reinvert_refine && h->h_ctrl->pending == 0 && refine_fits(q->k_host, h->m);
     CK(cudaEventRecord(h->er0, h->stream));
-    launch_reinv_classify(h->ds, try_refine ? k_host : -1, h->stream);
-    int k = k_host;
-    if (!try_refine) {
+    launch_reinv_classify(h->ds, q->try_refine ? q->k_host : -1, h->stream);
+    int k = q->k_host;
+    if (!q->try_refine) {
         TRY(read_ctrl(h));
         if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
         k = h->h_ctrl->k_struct;
     }
     CK(cudaEventRecord(h->erg, h->stream));
-    if (try_refine) {
+    if (q->try_refine) {
         const bool from_struct = h->structured && h->s_ready;
         h->launches += launch_refine_residual(h->ds, k, from_struct ? 1 : 0, h->h_ctrl->k_live, h->h_ctrl->map_par,
                                               h->stream);
@@ -394,14 +403,23 @@ int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = fal
         launch_reinv_gj(h->ds, k, h->geo, h->stream);
         h->launches += reinv_gj_launches(k);
     }
-    h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 1 - (compact ? 1 : 0);
+    h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 1 - (q->compact ? 1 : 0);
     CK(cudaEventRecord(h->era, h->stream));
-    const int tc = launch_reinv_assemble(h->ds, k, h->geo, h->stream, try_refine ? 0 : 1, !compact);
-    if (tc) h->launches += 2;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
-    launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible, try_refine ? h->opt.refine_tol : -1.0);
+    q->tc = launch_reinv_assemble(h->ds, k, h->geo, h->stream, q->try_refine ? 0 : 1, !q->compact);
+    if (q->tc) h->launches += 2;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
+    launch_reinv_finish(h->ds, k, h->geo, h->stream, check_feasible, q->try_refine ? h->opt.refine_tol : -1.0);
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->er1, h->stream));
-    TRY(read_ctrl(h));
+    h->primed = false;
+    return LP_OK;
+}
+
+// After a read of the control block behind a queued rebuild: its time, its
+// counters and the verdict.  *redo: the rebuild must be done again by
+// elimination (the refinement's residual was above the tolerance, or the basis
+// held another structural count than the host's; that error flag is cleared).
+int reinvert_settle(lp_handle* h, const ReinvQueued& q, bool* redo) {
+    *redo = false;
     float ms = 0.f, mg = 0.f, ma = 0.f;
     CK(cudaEventElapsedTime(&ms, h->er0, h->er1));
     CK(cudaEventElapsedTime(&mg, h->erg, h->era));
@@ -409,28 +427,46 @@ int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = fal
     h->reinvert_seconds += ms * 1e-3;
     h->reinv_gj_s += mg * 1e-3;
     h->reinv_asm_s += ma * 1e-3;
-    h->primed = false;
-    h->s_ready = false;
-    if (try_refine && h->h_ctrl->err == kErrBadIndex && h->h_ctrl->k_struct != k_host) {
-        // the basis held another structural count than the host's: nothing was
-        // rebuilt (every kernel after the classification stopped); redo by elimination
+    const Ctrl& C = *h->h_ctrl;
+    if (q.try_refine && C.err == kErrBadIndex && C.k_struct != q.k_host) {
+        // every kernel after the classification stopped: nothing was rebuilt
         CK(cudaMemsetAsync(&h->ds.ctrl->err, 0, sizeof(int32_t), h->stream));
-        return reinvert(h, check_feasible, false, to_struct);
+        *redo = true;
+        return LP_OK;
     }
-    if (h->h_ctrl->err != kErrNone) return device_err_code(h->h_ctrl->err);
-    if (try_refine) {
-        h->refine_res_max = std::max(h->refine_res_max, h->h_ctrl->refine_res);
-        if (h->h_ctrl->refine_rej) return reinvert(h, check_feasible, false, to_struct);
+    if (C.err != kErrNone) return device_err_code(C.err);
+    if (q.try_refine) {
+        h->refine_res_max = std::max(h->refine_res_max, C.refine_res);
+        if (C.refine_rej) {
+            *redo = true;
+            return LP_OK;
+        }
         h->reinv_refined++;
     }
-    if (tc) h->reinv_tc++;
-    if (compact) {
-        launch_struct_enter(h->ds, h->s_force ? 1 : 0, h->s_relayout, h->stream, true);
-        CK(cudaGetLastError());
-        h->launches += 3;
-        h->s_force = false;
-        h->s_ready = true;
-    }
+    if (q.tc) h->reinv_tc++;
+    return LP_OK;
+}
+
+// The structured engine's entry from a compact rebuild.
+int struct_enter_compact(lp_handle* h) {
+    launch_struct_enter(h->ds, h->s_force ? 1 : 0, h->s_relayout, h->stream, true);
+    CK(cudaGetLastError());
+    h->launches += 3;
+    h->s_force = false;
+    h->s_ready = true;
+    return LP_OK;
+}
+
+// The rebuild, read and settled.
+int reinvert(lp_handle* h, int check_feasible, bool refine, bool to_struct = false) {
+    ReinvQueued q;
+    TRY(reinvert_queue(h, check_feasible, refine, to_struct, &q));
+    TRY(read_ctrl(h));
+    h->s_ready = false;
+    bool redo = false;
+    TRY(reinvert_settle(h, q, &redo));
+    if (redo) return reinvert(h, check_feasible, false, to_struct);
+    if (q.compact) TRY(struct_enter_compact(h));
     return LP_OK;
 }
 
@@ -1102,14 +1138,34 @@ int lp_solve(lp_handle* h, lp_result* out) {
         h->primed = false;
     }
     TRY(read_ctrl(h));
+    // A periodic rebuild for the structured engine is queued with its entry and
+    // the next launch behind it, and settled at the read after that launch.
+    ReinvQueued rq;
+    bool queued = false;
     for (;;) {
         const Ctrl& C = *h->h_ctrl;
+        if (queued) {
+            queued = false;
+            bool redo = false;
+            TRY(reinvert_settle(h, rq, &redo));
+            if (redo) {
+                TRY(reinvert(h, 0, false, true));
+                continue;
+            }
+        }
         if (C.err != kErrNone) return device_err_code(C.err);
         if (C.status == kReinvert) {
-            TRY(reinvert(h, 0, true, true));
-            continue;
+            if (h->structured && h->s_ready && !h->ooc) {
+                TRY(reinvert_queue(h, 0, true, true, &rq));
+                TRY(struct_enter_compact(h));
+                queued = true;  // the launch below runs behind the rebuild
+            } else {
+                TRY(reinvert(h, 0, true, true));
+                continue;
+            }
+        } else if (C.status != kRunning) {
+            break;
         }
-        if (C.status != kRunning) break;
         if (h->ooc) {
             TRY(ooc_iteration(h));
             TRY(read_ctrl(h));
@@ -1146,6 +1202,12 @@ int lp_solve(lp_handle* h, lp_result* out) {
             // the cooperative launch was refused: rebuild the dense state and
             // continue on the dense engines
             (void)cudaGetLastError();
+            if (queued) {
+                queued = false;
+                TRY(read_ctrl(h));
+                bool redo = false;
+                TRY(reinvert_settle(h, rq, &redo));
+            }
             h->structured = false;
             TRY(reinvert(h, 0, false));
             continue;
