@@ -32,9 +32,9 @@ namespace {
 constexpr int kClassifyThreads = 1024;
 constexpr int kStepThreads = 256;
 
-// The three lists in increasing position order, each thread taking a run of
-// consecutive positions: counts, one block scan of the three counts, then the
-// writes.
+// The three lists in increasing position order (and J, c_J with the
+// structural positions), each thread taking a run of consecutive positions:
+// counts, one block scan of the three counts, then the writes.
 __global__ void __launch_bounds__(kClassifyThreads) k_classify(DevState s, int k_expect) {
     __shared__ int wsum[3][32];
     const int m = s.p.m, n = s.p.n;
@@ -72,8 +72,11 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(DevState s, int k
     int kl = (w ? wsum[1][w - 1] : 0) + il - cl;
     int kr = (w ? wsum[2][w - 1] : 0) + ir - cr;
     for (int p = p0; p < p1; ++p) {
-        if (s.basis[p] < n) {
+        const int var = s.basis[p];
+        if (var < n) {
             s.rv_struct_pos[ks] = p;
+            s.rv_J[ks] = var;
+            s.rv_cJ[ks] = s.c[var];
             s.rv_b_of_pos[p] = ks++;
         } else {
             s.rv_b_of_pos[p] = -1;
@@ -456,13 +459,14 @@ __global__ void __launch_bounds__(kTrailThreads) k_gj_trail(DevState s, int k, i
 // steps.  The slack rows -A[S, J] B11^-1 then follow from Y1 as after an
 // elimination.  A larger residual (or a NaN) falls back to Gauss-Jordan.
 //
-// Scratch: B11 (column-major, from k_gather), Y0 and R = I - B11 Y0
+// Scratch: B11 (column-major, as k_gather writes it), Y0 and R = I - B11 Y0
 // (row-major) in rv_M, which needs 3 k^2 <= m^2; per-tile partial row sums of
 // |R| after the first k^2 entries of rv_W; Y1 into rv_W, where the
 // elimination leaves B11^-1.
 
-// Y0[b][a] = stored B^-1[P_b][R_a]: the dense inverse, or the live column of
-// row R_a in the slack-structured state (slot map `par`, `k_live` live slots).
+// B11 (as k_gather) and Y0[b][a] = stored B^-1[P_b][R_a]: the dense inverse,
+// or the live column of row R_a in the slack-structured state (slot map
+// `par`, `k_live` live slots).
 __global__ void k_refine_extract(DevState s, int k, int from_struct, int k_live, int par) {
     if (s.ctrl->err != kErrNone) return;
     const size_t total = (size_t)k * k;
@@ -470,6 +474,11 @@ __global__ void k_refine_extract(DevState s, int k, int from_struct, int k_live,
     const int32_t* rs = s.row_slot + (size_t)par * s.p.m;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
+        {
+            // B11 (column-major, as k_gather)
+            const int t = (int)(e / k), a = (int)(e % k);
+            s.rv_M[e] = s.A_cm[(size_t)s.rv_J[t] * s.p.ld + s.rv_rows[a]];
+        }
         const int b = (int)(e / k), a = (int)(e % k);
         const size_t prow = (size_t)s.rv_struct_pos[b] * s.p.ld;
         const int i = s.rv_rows[a];
@@ -605,20 +614,15 @@ __global__ void k_pivinv(DevState s, int k) {
     }
 }
 
-// J[b], c_J[b] and, after an elimination, the dense B11^-1 (row b, column a)
-// = M[pinv[a]*k + pivrow[b]] (a refinement writes it directly)
-__global__ void k_b11i(DevState s, int k, int from_gj) {
+// After an elimination, the dense B11^-1 (row b, column a) = M[pinv[a]*k +
+// pivrow[b]] (a refinement writes it directly)
+__global__ void k_b11i(DevState s, int k) {
     if (s.ctrl->err != kErrNone) return;
-    const size_t total = from_gj ? (size_t)k * k : 0;
+    const size_t total = (size_t)k * k;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(e / k), a = (int)(e % k);
         s.rv_W[e] = s.rv_M[(size_t)s.rv_rowdone[a] * k + s.rv_pivrow[b]];
-    }
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < k; b += gridDim.x * blockDim.x) {
-        const int j = s.basis[s.rv_struct_pos[b]];
-        s.rv_J[b] = j;
-        s.rv_cJ[b] = s.c[j];
     }
 }
 
@@ -894,19 +898,18 @@ int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live
     const size_t kk = (size_t)k * k;
     int blocks = (int)((kk + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_gather<<<blocks, 256, 0, st>>>(s, k);
     k_refine_extract<<<blocks, 256, 0, st>>>(s, k, from_struct, k_live, par);
     if (refine_on_tc(s, k) &&
         oz_refine_residual_product(s.rv_M, s.rv_M + kk, k, s.rv_M + 2 * kk, s.oz_xs, s.oz_ys, s.oz_ex, s.oz_ey,
                                    &s.ctrl->err, st) == cudaSuccess) {
         k_refine_finish_residual<<<(k + 7) / 8, 256, 0, st>>>(s, k);
-        return 6;
+        return 5;
     }
     (void)cudaGetLastError();
     const int nt = (k + kRT - 1) / kRT;
     k_refine_gemm<0><<<dim3(nt, nt), kRT * kRT, 0, st>>>(s, k);
     k_refine_norm<<<1, 1024, 0, st>>>(s, k, nt);
-    return 4;
+    return 3;
 }
 
 int launch_refine_apply(const DevState& s, int k, cudaStream_t st) {
@@ -936,7 +939,7 @@ int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStrea
         const size_t kk = (size_t)k * k;
         int blocks = (int)((kk + 255) / 256);
         if (blocks > 4096) blocks = 4096;
-        k_b11i<<<blocks, 256, 0, st>>>(s, k, from_gj);
+        if (from_gj) k_b11i<<<blocks, 256, 0, st>>>(s, k);
         if (nslack > 0) {
             if (s.p.reinvert_tc && s.oz_xs && oz_fits(k) &&
                 oz_slack_product(s.A_cm, s.p.ld, s.rv_J, s.rv_slack_pos, s.rv_W, k, nslack, s.rv_W + kk, s.oz_xs,

@@ -403,7 +403,8 @@ int reinvert_queue(lp_handle* h, int check_feasible, bool refine, bool to_struct
         launch_reinv_gj(h->ds, k, h->geo, h->stream);
         h->launches += reinv_gj_launches(k);
     }
-    h->launches += 1 + (k > 0 ? 2 + (h->ds.p.m > k ? 1 : 0) : 1) + 1 - (q->compact ? 1 : 0);
+    // classification, B11^-1 of an elimination, the slack rows, the dense rows, the finish
+    h->launches += 1 + (k > 0 && !q->try_refine ? 1 : 0) + (k > 0 && h->ds.p.m > k ? 1 : 0) + (q->compact ? 0 : 1) + 1;
     CK(cudaEventRecord(h->era, h->stream));
     q->tc = launch_reinv_assemble(h->ds, k, h->geo, h->stream, q->try_refine ? 0 : 1, !q->compact);
     if (q->tc) h->launches += 2;  // exponents and slices of both operands (the GEMM replaces k_slack_gemm)
