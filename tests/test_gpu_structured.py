@@ -57,11 +57,14 @@ def test_pivot_sequence_and_objective(kind, m, n, seed):
 @pytest.mark.parametrize("kind,m,n,seed,K,G", [
     ("real", 256, 512, 1, 0, 64), ("int", 200, 200, 0, 0, 64), ("degenerate", 128, 256, 2, 0, 64),
     ("real", 300, 200, 3, 100, 64), ("real", 160, 300, 6, 0, 1), ("degenerate", 96, 160, 7, 0, 5),
-    ("real", 200, 330, 8, 77, 3)])
+    ("real", 200, 330, 8, 77, 3), ("real", 300, 500, 9, 64, 64), ("real", 300, 500, 9, 128, 64),
+    ("int", 200, 200, 0, 129, 64)])
 def test_matches_dense_engine(kind, m, n, seed, K, G):
     """Same pivots, counters and final state as the dense persistent engine
-    (K > 0 stops at an iteration limit; G pivots per launch: the state crosses
-    launch boundaries in every phase of the slot moves)."""
+    (K > 0 stops at an iteration limit, also one that falls on a periodic
+    reinversion, which the structured engine queues with its next launch; G
+    pivots per launch: the state crosses launch boundaries in every phase of
+    the slot moves)."""
     from paper_1803_04378_gb300 import lpgb
     A, b, c = lpgen.make(kind, m, n, seed)
     runs = []
