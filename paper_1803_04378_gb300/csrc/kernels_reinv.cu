@@ -36,6 +36,7 @@ constexpr int kStepThreads = 256;
 // structural positions), each thread taking a run of consecutive positions:
 // counts, one block scan of the three counts, then the writes.
 __global__ void __launch_bounds__(kClassifyThreads) k_classify(DevState s, int k_expect) {
+    pdl_enter();
     __shared__ int wsum[3][32];
     const int m = s.p.m, n = s.p.n;
     const int per = (m + (int)blockDim.x - 1) / (int)blockDim.x;
@@ -468,6 +469,7 @@ __global__ void __launch_bounds__(kTrailThreads) k_gj_trail(DevState s, int k, i
 // or the live column of row R_a in the slack-structured state (slot map
 // `par`, `k_live` live slots).
 __global__ void k_refine_extract(DevState s, int k, int from_struct, int k_live, int par) {
+    pdl_enter();
     if (s.ctrl->err != kErrNone) return;
     const size_t total = (size_t)k * k;
     double* Y = s.rv_M + total;
@@ -552,6 +554,7 @@ __global__ void __launch_bounds__(kRT * kRT) k_refine_gemm(DevState s, int k) {
 // warp per row; NaN counts as DBL_MAX) by an atomic max on the bits of the
 // non-negative doubles, which order as unsigned integers.
 __global__ void __launch_bounds__(256) k_refine_finish_residual(DevState s, int k) {
+    pdl_enter();
     if (s.ctrl->err != kErrNone) return;
     const size_t kk = (size_t)k * k;
     double* R = s.rv_M + 2 * kk;
@@ -575,6 +578,7 @@ __global__ void __launch_bounds__(256) k_refine_finish_residual(DevState s, int 
 
 // Y1 = Y0 + P, P = Y0 R in rv_W
 __global__ void k_refine_add(DevState s, int k) {
+    pdl_enter();
     if (s.ctrl->err != kErrNone) return;
     const size_t kk = (size_t)k * k;
     const double* Y0 = s.rv_M + kk;
@@ -767,6 +771,7 @@ constexpr int kCloseLanes = 1024;  // the objective is summed as by 1024 threads
 // tol) and the status for the next iteration.
 __global__ void __launch_bounds__(kFinishThreads) k_reinv_finish(DevState s, int k, int nb_bbar, int check_feasible,
                                                                  double tol) {
+    pdl_enter();
     __shared__ double sz[kCloseLanes / 32];
     __shared__ int sbad[kCloseLanes / 32];
     __shared__ int last;
@@ -823,7 +828,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_reinv_finish(DevState s, int
 }  // namespace
 
 void launch_reinv_classify(const DevState& s, int k_expect, cudaStream_t st) {
-    k_classify<<<1, kClassifyThreads, 0, st>>>(s, k_expect);
+    launch_k(k_classify, dim3(1), dim3(kClassifyThreads), 0, st, true, s, k_expect);
 }
 
 int reinv_gj_launches(int k) {
@@ -898,11 +903,11 @@ int launch_refine_residual(const DevState& s, int k, int from_struct, int k_live
     const size_t kk = (size_t)k * k;
     int blocks = (int)((kk + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_refine_extract<<<blocks, 256, 0, st>>>(s, k, from_struct, k_live, par);
+    launch_k(k_refine_extract, dim3(blocks), dim3(256), 0, st, true, s, k, from_struct, k_live, par);
     if (refine_on_tc(s, k) &&
         oz_refine_residual_product(s.rv_M, s.rv_M + kk, k, s.rv_M + 2 * kk, s.oz_xs, s.oz_ys, s.oz_ex, s.oz_ey,
                                    &s.ctrl->err, st) == cudaSuccess) {
-        k_refine_finish_residual<<<(k + 7) / 8, 256, 0, st>>>(s, k);
+        launch_k(k_refine_finish_residual, dim3((k + 7) / 8), dim3(256), 0, st, true, s, k);
         return 5;
     }
     (void)cudaGetLastError();
@@ -919,7 +924,7 @@ int launch_refine_apply(const DevState& s, int k, cudaStream_t st) {
                                  &s.ctrl->err, st) == cudaSuccess) {
         int blocks = (int)((kk + 255) / 256);
         if (blocks > 4096) blocks = 4096;
-        k_refine_add<<<blocks, 256, 0, st>>>(s, k);
+        launch_k(k_refine_add, dim3(blocks), dim3(256), 0, st, true, s, k);
         return 4;
     }
     (void)cudaGetLastError();
@@ -958,7 +963,8 @@ int launch_reinv_assemble(const DevState& s, int k, const Geometry& g, cudaStrea
 
 void launch_reinv_finish(const DevState& s, int k, const Geometry& g, cudaStream_t st, int check_feasible,
                          double refine_tol) {
-    k_reinv_finish<<<g.sms * 4, kFinishThreads, 0, st>>>(s, k, g.sms * 2, check_feasible, refine_tol);
+    launch_k(k_reinv_finish, dim3(g.sms * 4), dim3(kFinishThreads), 0, st, true, s, k, g.sms * 2, check_feasible,
+             refine_tol);
 }
 
 }  // namespace lpgb

@@ -148,6 +148,7 @@ __device__ void oz_slice_block(Src src, int nout, int K, const int32_t* exps, __
 template <class SX, class SY>
 __global__ void __launch_bounds__(256) k_oz_exp(SX sx, int M, SY sy, int N, int K, int32_t* ex, int32_t* ey,
                                                 const int32_t* err) {
+    pdl_enter();
     if (*err != kErrNone) return;
     __shared__ int red[8][33];
     const int bxm = (M + 31) / 32;
@@ -161,6 +162,7 @@ template <class SX, class SY>
 __global__ void __launch_bounds__(256) k_oz_slice(SX sx, int M, SY sy, int N, int K, const int32_t* ex,
                                                   const int32_t* ey, __nv_bfloat16* xs, __nv_bfloat16* ys, int ldk,
                                                   const int32_t* err) {
+    pdl_enter();
     if (*err != kErrNone) return;
     __shared__ __nv_bfloat16 t[kSlices][32][34];  // [p][o][l]
     const int bxm = (M + 31) / 32;
@@ -254,8 +256,12 @@ cudaError_t oz_product(SX sx, SY sy, int M, int N, int K, double* out, int ldo, 
     if (!oz_fits(K) || M < 1 || N < 1) return cudaErrorInvalidValue;
     const int ldk = (K + 7) & ~7;
     const int bx = (M + 31) / 32 + (N + 31) / 32;
-    k_oz_exp<<<bx, 256, 0, st>>>(sx, M, sy, N, K, ex, ey, err);
-    k_oz_slice<<<dim3(bx, (K + 31) / 32), 256, 0, st>>>(sx, M, sy, N, K, ex, ey, xs, ys, ldk, err);
+    const int32_t* cerr = err;
+    launch_k(k_oz_exp<SX, SY>, dim3(bx), dim3(256), 0, st, true, sx, M, sy, N, K, ex, ey, cerr);
+    const int32_t* cex = ex;
+    const int32_t* cey = ey;
+    launch_k(k_oz_slice<SX, SY>, dim3(bx, (K + 31) / 32), dim3(256), 0, st, true, sx, M, sy, N, K, cex, cey, xs, ys,
+             ldk, cerr);
     CUtensorMap ma, mb;
     constexpr int BN = kOzBN;
     if (!tc_make_map_16bit(&ma, xs, kSlices * M, K, ldk, tcg::kTM, true) ||

@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(gemm_p_threads<kEpiWarps>(), kCtas)
     static_assert(kCtas * 2 * BN <= 512, "two accumulators for each co-resident CTA");
     static_assert(kEpiWarps % 4 == 0 && kEpiWarps >= 4, "whole TMEM lane quarters");
     constexpr int kEpiPerQuarter = kEpiWarps / 4;
+    pdl_enter();  // the operands' slices come from the previous launch
     using L = GemmSmem<BN, kStages>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -306,9 +307,8 @@ cudaError_t launch_tc_gemm_p(const CUtensorMap& ma, const CUtensorMap& mb, const
     }
     const int tiles = ((N + BN - 1) / BN) * ((M + kTM - 1) / kTM);
     const int grid = tiles < kCtas * sms ? tiles : kCtas * sms;
-    k_tc_gemm_p<BN, kStages, kEpiWarps, kCtas, kBF16, Epi>
-        <<<grid, gemm_p_threads<kEpiWarps>(), L::kBytes, st>>>(ma, mb, epi, M, N, K, err);
-    return cudaGetLastError();
+    return launch_k(k_tc_gemm_p<BN, kStages, kEpiWarps, kCtas, kBF16, Epi>, dim3(grid),
+                    dim3(gemm_p_threads<kEpiWarps>()), L::kBytes, st, true, ma, mb, epi, M, N, K, err);
 }
 
 // Tensor maps of the two operands and the launch (grid = N/BN x M/128 tiles).
