@@ -287,8 +287,8 @@ __global__ void __launch_bounds__(gemm_p_threads<kEpiWarps>(), kCtas)
     if (threadIdx.x == 0 && fail && err) atomicExch(err, kErrTimeout);
 }
 
-// Grid of the persistent form: two CTAs per SM, at most one per tile.
-// Grid of the persistent form: kCtas CTAs per SM, at most one per tile.
+// Grid of the persistent form: kCtas CTAs per SM, at most one per tile; a
+// programmatic dependent launch (the kernel waits before it reads its operands).
 template <int BN, int kStages, int kEpiWarps, int kCtas, bool kBF16, class Epi>
 cudaError_t launch_tc_gemm_p(const CUtensorMap& ma, const CUtensorMap& mb, const Epi& epi, int M, int N, int K,
                              int32_t* err, cudaStream_t st) {
