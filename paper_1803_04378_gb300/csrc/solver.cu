@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 using namespace lpgb;
@@ -484,10 +485,50 @@ int reset_state(lp_handle* h) {
     return LP_OK;
 }
 
+// x[0 .. n) holds no NaN or infinity: a double is finite unless its 11
+// exponent bits are all ones; branch-free over each chunk, and large arrays
+// split over up to 16 host threads.
 bool finite_all(const double* x, size_t n) {
-    for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(x[i])) return false;
+    const auto chunk = [x](size_t i0, size_t i1) {
+        uint64_t bad = 0;
+        for (size_t i = i0; i < i1; ++i) {
+            uint64_t u;
+            std::memcpy(&u, x + i, sizeof(u));
+            bad |= (uint64_t)(((u >> 52) & 0x7ffu) == 0x7ffu);
+        }
+        return bad == 0;
+    };
+    constexpr size_t kPar = size_t(1) << 22;
+    const unsigned nt = std::min(16u, std::thread::hardware_concurrency());
+    if (n < kPar || nt < 2) return chunk(0, n);
+    const size_t per = (n + nt - 1) / nt;
+    std::vector<char> ok(nt, 1);
+    std::vector<std::thread> th;
+    try {
+        for (unsigned t = 0; t < nt; ++t)
+            th.emplace_back([&chunk, &ok, per, n, t] {
+                const size_t i0 = std::min(n, (size_t)t * per), i1 = std::min(n, i0 + per);
+                ok[t] = chunk(i0, i1) ? 1 : 0;
+            });
+    } catch (...) {
+        for (auto& t : th) t.join();
+        return chunk(0, n);  // no threads to be had: one pass
+    }
+    for (auto& t : th) t.join();
+    for (char v : ok)
+        if (!v) return false;
     return true;
+}
+
+// The device address of a host array the device can read directly (pinned
+// or registered host memory), else nullptr.
+const void* host_device_view(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 // Rows p0 .. p0+np-1 of B^-1 (indexed by constraint row) into out[np][m],
@@ -656,7 +697,10 @@ static int upload_problem(lp_handle* h, const double* A, const double* b, const 
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const double* A_src = A;
     double* staging = nullptr;
-    if (!on_device) {
+    const void* view = on_device ? nullptr : host_device_view(A);
+    if (view) {
+        A_src = static_cast<const double*>(view);  // pinned host memory: the transpose reads it in place
+    } else if (!on_device) {
         CK(cudaMalloc(&staging, (size_t)m * n * sizeof(double)));
         cudaError_t e = cudaMemcpyAsync(staging, A, (size_t)m * n * sizeof(double), kind, h->stream);
         if (e != cudaSuccess) { cudaFree(staging); return cuda_fail(e); }
@@ -938,7 +982,9 @@ int lp_create(lp_handle** out, int32_t m, int32_t n, const double* A, const doub
         o.bland_after < 0 || o.price_mode < 0 || o.price_mode > 2 || o.topk < 1 || o.topk > kMaxTopk || !(o.tol_d >= 0) || !(o.tol_piv > 0) || !(o.tol_tie >= 0) || !(o.refine_tol >= 0 && o.refine_tol <= kRefineTolMax))
         return LP_ERR_INVALID_ARG;
     if (!on_device) {
-        if (!finite_all(A, (size_t)m * n) || !finite_all(c, n) || !finite_all(b, m)) return LP_ERR_INVALID_ARG;
+        // (a pinned A is checked on the device after its upload, like device inputs)
+        if ((!host_device_view(A) && !finite_all(A, (size_t)m * n)) || !finite_all(c, n) || !finite_all(b, m))
+            return LP_ERR_INVALID_ARG;
     }
     lp_handle* h = new (std::nothrow) lp_handle();
     if (!h) return LP_ERR_OOM;
@@ -992,7 +1038,8 @@ int lp_set_basis(lp_handle* h, const int32_t* basis) {
 int lp_update_problem(lp_handle* h, const double* A, const double* b, const double* c, int32_t on_device) {
     if (!h || !A || !b || !c) return LP_ERR_INVALID_ARG;
     if (!on_device) {
-        if (!finite_all(A, (size_t)h->m * h->n) || !finite_all(c, h->n) || !finite_all(b, h->m))
+        if ((!host_device_view(A) && !finite_all(A, (size_t)h->m * h->n)) || !finite_all(c, h->n) ||
+            !finite_all(b, h->m))
             return LP_ERR_INVALID_ARG;
     }
     h->warm_pending = false;

@@ -66,6 +66,17 @@ def test_option_defaults_and_validation_on_host():
     h = ctypes.c_void_p()
     assert lpgb.lib().lp_create(ctypes.byref(h), 3, 4, lpgb._ptr(A), lpgb._ptr(b), lpgb._ptr(c), 0,
                                 ctypes.byref(lpgb.default_options())) == lpgb.LP_ERR_INVALID_ARG
+    # a large host A (4.4 M entries) is checked by several threads; the last
+    # entry of the last thread's share, and the first of the first
+    m, n = 1100, 4000
+    Ab, bb, cb = np.ones((m, n)), np.ones(m), np.ones(n)
+    for pos in ((m - 1, n - 1), (0, 0), (m // 2, 7)):
+        Ab[pos] = float("nan") if pos[0] else float("-inf")
+        h = ctypes.c_void_p()
+        assert lpgb.lib().lp_create(ctypes.byref(h), m, n, lpgb._ptr(Ab), lpgb._ptr(bb), lpgb._ptr(cb), 0,
+                                    ctypes.byref(lpgb.default_options())) == lpgb.LP_ERR_INVALID_ARG, pos
+        assert not h.value
+        Ab[pos] = 1.0
 
 
 def test_struct_layout_matches_the_binding(tmp_path):

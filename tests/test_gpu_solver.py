@@ -237,6 +237,39 @@ def test_trivial_and_unbounded():
     lp.close()
 
 
+def test_pinned_host_inputs():
+    """A in pinned host memory is read in place by the upload's transpose
+    and validated on the device: the same solve as from pageable memory, and
+    a NaN or an infinity anywhere in it (also in a large A, past the host's
+    threaded check size) is rejected with LP_ERR_INVALID_ARG."""
+    import torch
+    from paper_1803_04378_gb300 import lpgb
+    A, b, c = lpgen.make("real", 300, 500, 3)
+    Ap = torch.empty(A.shape, dtype=torch.float64, pin_memory=True)
+    Ap.numpy()[:] = A
+    with lpgb.LP(Ap.numpy(), b, c) as lp0, lpgb.LP(A, b, c) as lp1:
+        r0, r1 = lp0.solve(), lp1.solve()
+        assert r0.status == r1.status == 1 and r0.iterations == r1.iterations
+        assert lp0.solution()[2] == lp1.solution()[2]
+    for bad in (float("nan"), float("inf"), -float("inf")):
+        Ap.numpy()[123, 456] = bad
+        with pytest.raises(lpgb.LPError) as e:
+            lpgb.LP(Ap.numpy(), b, c)
+        assert e.value.code == lpgb.LP_ERR_INVALID_ARG
+        Ap.numpy()[123, 456] = A[123, 456]
+    m, n = 1100, 4000  # 4.4 M entries
+    Ab = torch.ones((m, n), dtype=torch.float64, pin_memory=True)
+    Ab.numpy()[m - 1, n - 1] = float("nan")
+    with pytest.raises(lpgb.LPError) as e:
+        lpgb.LP(Ab.numpy(), np.ones(m), np.ones(n))
+    assert e.value.code == lpgb.LP_ERR_INVALID_ARG
+    An = np.ones((m, n))
+    An[m - 1, n - 1] = float("inf")  # pageable: the host's threaded check
+    with pytest.raises(lpgb.LPError) as e:
+        lpgb.LP(An, np.ones(m), np.ones(n))
+    assert e.value.code == lpgb.LP_ERR_INVALID_ARG
+
+
 def test_invalid_arguments():
     from paper_1803_04378_gb300 import lpgb
     A = np.ones((2, 2))
