@@ -232,7 +232,12 @@ void lp_default_options(lp_options* opt);
  *                   are read on the handle's stream (lp_options.cuda_stream,
  *                   else a non-blocking stream of the handle's own), which
  *                   does not wait for other streams: the caller finishes
- *                   (or orders before that stream) the work that writes them
+ *                   (or orders before that stream) the work that writes them.
+ *                   Host inputs are read before lp_create returns.  A host A
+ *                   in pinned or registered memory is read in place by the
+ *                   device and checked for NaN/Inf there, as device inputs
+ *                   are; a pageable one is checked on the host (by several
+ *                   threads when large) before any device work, then copied.
  *  opt              options, or NULL for the defaults
  * Errors: LP_ERR_INVALID_ARG (sizes, NULL, NaN/Inf), LP_ERR_OOM,
  * LP_ERR_CUDA.  The handle is on the current CUDA device.
