@@ -33,6 +33,8 @@ struct lp_handle {
     cudaGraphExec_t rgraph = nullptr;  // kRepairBatch warm-start repair steps (captured on first use)
     cudaGraphExec_t cgraph = nullptr;  // kRepairBatch warm-start crash steps (captured on first use)
     std::vector<void*> allocs;
+    char* pool_base = nullptr;  // the chunk small buffers are carved from (dalloc)
+    size_t pool_used = 0;
     int32_t* flag = nullptr;         // device validation flag
     bool solved = false;
     bool primed = false;             // q and r of the next pivot are on the device
@@ -92,12 +94,32 @@ int cuda_fail(cudaError_t e) {
         if (e_ != cudaSuccess) return cuda_fail(e_); \
     } while (0)
 
+// Device buffers of the handle.  Buffers of at most kPoolMax bytes are carved,
+// 256-byte aligned as cudaMalloc's, from shared chunks of kPoolChunk bytes;
+// larger ones get an allocation of their own.  A handle makes a dozen
+// cudaMalloc calls (and its destruction as many cudaFree calls) instead of
+// dozens.  Everything is freed with the handle (free_all).
+constexpr size_t kPoolMax = size_t(1) << 20, kPoolChunk = size_t(16) << 20, kPoolAlign = 256;
 template <typename T>
 int dalloc(lp_handle* h, T** ptr, size_t count) {
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
-    if (e != cudaSuccess) return cuda_fail(e);
-    h->allocs.push_back(p);
+    if (bytes <= kPoolMax) {
+        const size_t need = (bytes + kPoolAlign - 1) & ~(kPoolAlign - 1);
+        if (!h->pool_base || h->pool_used + need > kPoolChunk) {
+            cudaError_t e = cudaMalloc(&p, kPoolChunk);
+            if (e != cudaSuccess) return cuda_fail(e);
+            h->allocs.push_back(p);
+            h->pool_base = static_cast<char*>(p);
+            h->pool_used = 0;
+        }
+        p = h->pool_base + h->pool_used;
+        h->pool_used += need;
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return cuda_fail(e);
+        h->allocs.push_back(p);
+    }
     *ptr = static_cast<T*>(p);
     return LP_OK;
 }
@@ -130,6 +152,8 @@ void free_all(lp_handle* h) {
     if (h->cgraph) cudaGraphExecDestroy(h->cgraph);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
+    h->pool_base = nullptr;
+    h->pool_used = 0;
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -905,7 +929,6 @@ static int create_impl(lp_handle* h, int32_t m, int32_t n, const double* A, cons
     }
     TRY(upload_problem(h, A, b, c, on_device));
     TRY(reset_state(h));
-    TRY(capture_graph(h));
     // Persistent engines.  The slack-structured one when asked for (the
     // default) and it fits: price_mode 0, a device that runs cooperative
     // launches with one 1024-thread CTA on every SM.  Otherwise the dense one,
@@ -1289,6 +1312,7 @@ int lp_solve(lp_handle* h, lp_result* out) {
             (void)cudaGetLastError();
             h->persist = false;
         }
+        if (!h->graph) TRY(capture_graph(h));  // on the first use of the captured-graph engine
         CK(cudaGraphLaunch(h->graph, h->stream));
         h->launches += 3 * (int64_t)h->opt.graph_iters;
         TRY(read_ctrl(h));
