@@ -153,7 +153,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // Host: a 2-D tensor map over a row-major matrix of 16-bit elements (rows x
 // cols, row stride ld elements, ld*2 a multiple of 16 bytes, base 16-byte
 // aligned), box = box_rows x 64 elements with the 128-byte swizzle; elements
-// outside the matrix read as zero.  Returns false when the driver rejects it.
+// outside the matrix read as zero.  Returns false when cuTensorMapEncodeTiled rejects it.
 bool tc_make_map_16bit(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows, bool bf16);
 
 }  // namespace lpgb
