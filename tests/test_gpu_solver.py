@@ -257,6 +257,20 @@ def test_pinned_host_inputs():
             lpgb.LP(Ap.numpy(), b, c)
         assert e.value.code == lpgb.LP_ERR_INVALID_ARG
         Ap.numpy()[123, 456] = A[123, 456]
+    # lp_update_problem takes the same path: a pinned A' on a handle built from
+    # another problem solves as a fresh handle on A', and a NaN in it is refused
+    A2, b2, c2 = lpgen.make("real", 300, 500, 4)
+    Ap.numpy()[:] = A2
+    with lpgb.LP(A, b, c) as lpu, lpgb.LP(A2, b2, c2) as lpf:
+        lpu.update_problem(Ap.numpy(), b2, c2)
+        ru, rf = lpu.solve(), lpf.solve()
+        assert ru.status == rf.status == 1 and ru.iterations == rf.iterations
+        assert lpu.solution()[2] == lpf.solution()[2]
+        Ap.numpy()[7, 9] = float("nan")
+        with pytest.raises(lpgb.LPError) as e:
+            lpu.update_problem(Ap.numpy(), b2, c2)
+        assert e.value.code == lpgb.LP_ERR_INVALID_ARG
+    Ap.numpy()[:] = A
     m, n = 1100, 4000  # 4.4 M entries
     Ab = torch.ones((m, n), dtype=torch.float64, pin_memory=True)
     Ab.numpy()[m - 1, n - 1] = float("nan")
